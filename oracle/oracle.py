@@ -1,0 +1,335 @@
+"""Python face of the CPU oracle (test infrastructure only).
+
+The arithmetic lives in ``tp_oracle.c``; this module only marshals numpy
+arrays into it and strings the steps together in the paper's order
+(Sec. 2.2.1 RFI thresholding -> Sec. 2.2.2 dedispersion -> Sec. 2.2.3
+normalisation -> Sec. 2.3 detection).  Only the tests, the package smoke
+check and the benchmark's CPU-baseline leg may import it.
+
+Input blocks are numpy arrays of shape (nchan, nsamp) in channel-major order
+(the paper's beam/channel/time organisation, Sec. 2.1): ``uint8``,
+``float16``, ``float32``, or ``uint16`` holding bfloat16 bit patterns
+(pass ``dtype="bf16"``).
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+DTYPE_CODES = {"u8": 0, "f16": 1, "bf16": 2, "f32": 3}
+
+STATS_BLOCK = 0
+STATS_EXTERNAL = 1
+
+_lib = None
+
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+
+
+class Candidate(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int32), ("dm_idx", ctypes.c_int32), ("t_abs", ctypes.c_int64),
+                ("snr", ctypes.c_float), ("value", ctypes.c_float)]
+
+
+def lib():
+    """Load (building first if needed) the oracle shared library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        sig = {
+            "orc_set_threads": (None, [_i]),
+            "orc_get_threads": (_i, []),
+            "orc_has_openmp": (_i, []),
+            "orc_channel_freqs": (None, [_i, _d, _d, _p]),
+            "orc_delay_exact": (None, [_i, _d, _d, _d, _p, _i, _p]),
+            "orc_delay_table": (_i64, [_i, _d, _d, _d, _p, _i, _p]),
+            "orc_bandpass_float": (None, [_p, _i, _i, _i64, _i64, _p, _p]),
+            "orc_bandpass_u8": (None, [_p, _i, _i64, _i64, _p, _p, _p, _p, _p, _p]),
+            "orc_channel_mask_float": (None, [_p, _i, _i, _i64, _i64, _i, _d, _i, _p, _p, _p, _p]),
+            "orc_channel_mask_u8": (None, [_p, _i, _i64, _i64, _i, _d, _i, _p, _p, _p, _p]),
+            "orc_channel_mask_u8_ext": (None, [_p, _i, _i64, _i64, _i, _d, _i, _p, _p, _p, _p]),
+            "orc_spectrum_mask_float": (None, [_p, _i, _i, _i64, _i64, _i, _d, _p, _p, _p, _p]),
+            "orc_spectrum_mask_u8": (None, [_p, _i, _i64, _i64, _i, _d, _p, _p, _p, _p]),
+            "orc_spectrum_mask_u8_ext": (None, [_p, _i, _i64, _i64, _i, _d, _p, _p, _p, _p]),
+            "orc_corrected_float": (None, [_p, _i, _i, _i64, _i64, _p, _p, _p, _i, _p]),
+            "orc_dedisperse_float": (None, [_p, _i, _i, _i64, _i64, _p, _p, _p, _i, _p, _i, _i64, _p]),
+            "orc_dedisperse_u8": (None, [_p, _i, _i64, _i64, _p, _p, _p, _i, _p, _i, _i64, _p]),
+            "orc_dedisperse_points_float": (None, [_p, _i, _i, _i64, _i64, _p, _p, _p, _i, _p, _p, _p, _i64, _p]),
+            "orc_dedisperse_points_u8": (None, [_p, _i, _i64, _i64, _p, _p, _p, _i, _p, _p, _p, _i64, _p]),
+            "orc_abs_mass_points_float": (None, [_p, _i, _i, _i64, _i64, _p, _p, _p, _i, _p, _p, _p, _i64, _p]),
+            "orc_series_stats_float": (None, [_p, _i, _i64, _p, _p]),
+            "orc_series_stats_int": (None, [_p, _i, _i64, _p, _p, _p, _p]),
+            "orc_candidates_float": (_i64, [_p, _i, _i64, _p, _p, _d, _i, _i64, _p, _i64]),
+            "orc_candidates_int": (_i64, [_p, _i, _i64, _p, _p, _d, _i, _i64, _p, _i64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def set_threads(n):
+    """Threads used by the dedispersion loop (1 unless OpenMP is available)."""
+    lib().orc_set_threads(int(n))
+    return lib().orc_get_threads() if lib().orc_has_openmp() else 1
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _input(x, dtype):
+    code = DTYPE_CODES[dtype]
+    want = {"u8": np.uint8, "f16": np.float16, "bf16": np.uint16, "f32": np.float32}[dtype]
+    x = np.ascontiguousarray(x)
+    if x.dtype != want:
+        raise TypeError(f"dtype {dtype} needs a {np.dtype(want)} array, got {x.dtype}")
+    if x.ndim != 2:
+        raise ValueError("input must be (nchan, nsamp)")
+    return x, code
+
+
+@dataclass
+class RfiParams:
+    """Thresholding parameters of Sec. 2.2.1 (readings R5, R6)."""
+    enable_channel: bool = True
+    enable_spectrum: bool = True
+    chunk_width: int = 256          # W_c
+    tau_channel: float = 5.0        # channel threshold, in sigma_c sqrt(n) units
+    tau_spectrum: float = 6.0       # spectrum threshold, in sqrt(sum sigma_c^2) units
+    dilate_channels: bool = False   # also flag the same chunk of adjacent channels
+
+
+# ---- plan ----------------------------------------------------------------------
+
+def channel_freqs(nchan, f_lo, bw):
+    f = np.empty(nchan, np.float64)
+    lib().orc_channel_freqs(nchan, f_lo, bw, _ptr(f))
+    return f
+
+
+def delay_exact(nchan, f_lo, bw, t_samp, dm):
+    dm = _c(dm, np.float64)
+    out = np.empty((len(dm), nchan), np.float64)
+    lib().orc_delay_exact(nchan, f_lo, bw, t_samp, _ptr(dm), len(dm), _ptr(out))
+    return out
+
+
+def delay_table(nchan, f_lo, bw, t_samp, dm):
+    """Integer delay table (ndm, nchan) int32 and its maximum (Eq. 1, R1-R3)."""
+    dm = _c(dm, np.float64)
+    out = np.zeros((max(len(dm), 1), max(nchan, 1)), np.int32)
+    dmax = lib().orc_delay_table(nchan, f_lo, bw, t_samp, _ptr(dm), len(dm), _ptr(out))
+    if dmax < 0:
+        raise ValueError("invalid plan arguments")
+    return out, int(dmax)
+
+
+# ---- A1-A3 ---------------------------------------------------------------------
+
+def bandpass(x, dtype):
+    """Block bandpass statistics (R4).  For 8-bit input also the exact sums."""
+    x, code = _input(x, dtype)
+    nchan, nsamp = x.shape
+    mu = np.empty(nchan, np.float64)
+    sigma = np.empty(nchan, np.float64)
+    if dtype == "u8":
+        S, Q, V, b = (np.empty(nchan, np.int64) for _ in range(4))
+        lib().orc_bandpass_u8(_ptr(x), nchan, nsamp, nsamp, _ptr(S), _ptr(Q), _ptr(V), _ptr(b),
+                              _ptr(mu), _ptr(sigma))
+        return dict(mu=mu, sigma=sigma, S=S, Q=Q, V=V, b=b, external=False)
+    lib().orc_bandpass_float(_ptr(x), code, nchan, nsamp, nsamp, _ptr(mu), _ptr(sigma))
+    return dict(mu=mu, sigma=sigma, external=False)
+
+
+def external_stats(dtype, mu, sigma):
+    """Statistics supplied by the caller instead of measured on the block.
+    For 8-bit input the bandpass value is the integer floor(mu + 1/2)."""
+    mu = _c(mu, np.float64)
+    sigma = _c(sigma, np.float64)
+    st = dict(mu=mu, sigma=sigma, external=True)
+    if dtype == "u8":
+        st["b"] = np.floor(mu + 0.5).astype(np.int64)
+    return st
+
+
+def channel_mask(x, dtype, stats, rfi):
+    x, code = _input(x, dtype)
+    nchan, nsamp = x.shape
+    W = int(rfi.chunk_width)
+    nchunk = (nsamp + W - 1) // W
+    raw = np.zeros((nchan, nchunk), np.uint8)
+    flag = np.zeros((nchan, nchunk), np.uint8)
+    if not rfi.enable_channel:
+        return raw, flag
+    dil = int(bool(rfi.dilate_channels))
+    if dtype == "u8" and not stats["external"]:
+        lib().orc_channel_mask_u8(_ptr(x), nchan, nsamp, nsamp, W, rfi.tau_channel, dil,
+                                  _ptr(stats["S"]), _ptr(stats["V"]), _ptr(raw), _ptr(flag))
+    elif dtype == "u8":
+        lib().orc_channel_mask_u8_ext(_ptr(x), nchan, nsamp, nsamp, W, rfi.tau_channel, dil,
+                                      _ptr(stats["b"]), _ptr(stats["sigma"]), _ptr(raw), _ptr(flag))
+    else:
+        lib().orc_channel_mask_float(_ptr(x), code, nchan, nsamp, nsamp, W, rfi.tau_channel, dil,
+                                     _ptr(stats["mu"]), _ptr(stats["sigma"]), _ptr(raw), _ptr(flag))
+    return raw, flag
+
+
+def spectrum_mask(x, dtype, stats, rfi, chunk_flag):
+    x, code = _input(x, dtype)
+    nchan, nsamp = x.shape
+    W = int(rfi.chunk_width)
+    spec = np.zeros(nsamp, np.uint8)
+    if not rfi.enable_spectrum:
+        return spec
+    cf = _c(chunk_flag, np.uint8)
+    if dtype == "u8" and not stats["external"]:
+        lib().orc_spectrum_mask_u8(_ptr(x), nchan, nsamp, nsamp, W, rfi.tau_spectrum,
+                                   _ptr(stats["S"]), _ptr(stats["V"]), _ptr(cf), _ptr(spec))
+    elif dtype == "u8":
+        lib().orc_spectrum_mask_u8_ext(_ptr(x), nchan, nsamp, nsamp, W, rfi.tau_spectrum,
+                                       _ptr(stats["b"]), _ptr(stats["sigma"]), _ptr(cf), _ptr(spec))
+    else:
+        lib().orc_spectrum_mask_float(_ptr(x), code, nchan, nsamp, nsamp, W, rfi.tau_spectrum,
+                                      _ptr(stats["mu"]), _ptr(stats["sigma"]), _ptr(cf), _ptr(spec))
+    return spec
+
+
+def corrected(x, dtype, stats, chunk_flag, spec_flag, W):
+    """Substituted, bandpass-corrected samples y[c][t] (R7), float64."""
+    x, code = _input(x, dtype)
+    nchan, nsamp = x.shape
+    cf = _c(chunk_flag, np.uint8)
+    sf = _c(spec_flag, np.uint8)
+    if dtype == "u8":
+        b = stats["b"]
+        flag = cf[:, np.arange(nsamp) // W].astype(bool) | sf.astype(bool)[None, :]
+        return np.where(flag, 0, x.astype(np.int64) - b[:, None]).astype(np.float64)
+    y = np.empty((nchan, nsamp), np.float64)
+    lib().orc_corrected_float(_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["mu"]), _ptr(cf),
+                              _ptr(sf), W, _ptr(y))
+    return y
+
+
+# ---- A5 ------------------------------------------------------------------------
+
+def dedisperse(x, dtype, stats, chunk_flag, spec_flag, W, delay, T):
+    """D[d][t] for 0 <= t < T: float64 for float input, int64 for 8-bit input."""
+    x, code = _input(x, dtype)
+    nchan, nsamp = x.shape
+    delay = _c(delay, np.int32)
+    ndm = delay.shape[0]
+    cf = _c(chunk_flag, np.uint8)
+    sf = _c(spec_flag, np.uint8)
+    if T <= 0:
+        raise ValueError("block shorter than the largest delay")
+    if dtype == "u8":
+        D = np.empty((ndm, T), np.int64)
+        lib().orc_dedisperse_u8(_ptr(x), nchan, nsamp, nsamp, _ptr(stats["b"]), _ptr(cf), _ptr(sf),
+                                W, _ptr(delay), ndm, T, _ptr(D))
+    else:
+        D = np.empty((ndm, T), np.float64)
+        lib().orc_dedisperse_float(_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["mu"]), _ptr(cf),
+                                   _ptr(sf), W, _ptr(delay), ndm, T, _ptr(D))
+    return D
+
+
+def dedisperse_points(x, dtype, stats, chunk_flag, spec_flag, W, delay, d_idx, t_idx):
+    """D at selected (d, t) pairs, plus (float input) the sum of |y| there."""
+    x, code = _input(x, dtype)
+    nchan, nsamp = x.shape
+    delay = _c(delay, np.int32)
+    d_idx = _c(d_idx, np.int32)
+    t_idx = _c(t_idx, np.int64)
+    n = len(d_idx)
+    cf = _c(chunk_flag, np.uint8)
+    sf = _c(spec_flag, np.uint8)
+    if dtype == "u8":
+        out = np.empty(n, np.int64)
+        lib().orc_dedisperse_points_u8(_ptr(x), nchan, nsamp, nsamp, _ptr(stats["b"]), _ptr(cf),
+                                       _ptr(sf), W, _ptr(delay), _ptr(d_idx), _ptr(t_idx), n, _ptr(out))
+        return out, None
+    out = np.empty(n, np.float64)
+    mass = np.empty(n, np.float64)
+    args = (_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["mu"]), _ptr(cf), _ptr(sf), W,
+            _ptr(delay), _ptr(d_idx), _ptr(t_idx), n)
+    lib().orc_dedisperse_points_float(*args, _ptr(out))
+    lib().orc_abs_mass_points_float(*args, _ptr(mass))
+    return out, mass
+
+
+# ---- A6-A7 ---------------------------------------------------------------------
+
+def series_stats(D):
+    D = np.ascontiguousarray(D)
+    ndm, T = D.shape
+    mu = np.empty(ndm, np.float64)
+    sigma = np.empty(ndm, np.float64)
+    if D.dtype == np.int64:
+        SD = np.empty(ndm, np.int64)
+        SD2 = np.empty(ndm, np.int64)
+        lib().orc_series_stats_int(_ptr(D), ndm, T, _ptr(SD), _ptr(SD2), _ptr(mu), _ptr(sigma))
+        return dict(mu=mu, sigma=sigma, SD=SD, SD2=SD2)
+    D = _c(D, np.float64)
+    lib().orc_series_stats_float(_ptr(D), ndm, T, _ptr(mu), _ptr(sigma))
+    return dict(mu=mu, sigma=sigma)
+
+
+CAND_DTYPE = np.dtype([("beam", np.int32), ("dm_idx", np.int32), ("t_abs", np.int64),
+                       ("snr", np.float32), ("value", np.float32)])
+
+
+def candidates(D, mu, sigma, nsigma, beam=0, t0=0, cap=None):
+    """Candidates in (d, t) order as a structured array, and the total count."""
+    D = np.ascontiguousarray(D)
+    ndm, T = D.shape
+    if cap is None:
+        cap = ndm * T
+    out = np.zeros(max(int(cap), 1), CAND_DTYPE)
+    mu = _c(mu, np.float64)
+    sigma = _c(sigma, np.float64)
+    if D.dtype == np.int64:
+        n = lib().orc_candidates_int(_ptr(D), ndm, T, _ptr(mu), _ptr(sigma), nsigma, beam, t0,
+                                     _ptr(out), cap)
+    else:
+        D = _c(D, np.float64)
+        n = lib().orc_candidates_float(_ptr(D), ndm, T, _ptr(mu), _ptr(sigma), nsigma, beam, t0,
+                                       _ptr(out), cap)
+    return out[:min(n, cap)], int(n)
+
+
+# ---- the whole block -------------------------------------------------------------
+
+def search_block(x, dtype, delay, max_delay, rfi=None, nsigma=5.0, beam=0, t0=0, stats=None,
+                 cand_cap=None, keep_series=True):
+    """Run A1-A7 on one block window x (nchan, nsamp).  ``stats`` replaces the
+    measured bandpass when given (see ``external_stats``).  Returns every
+    intermediate product."""
+    rfi = rfi or RfiParams()
+    x, _ = _input(x, dtype)
+    nchan, nsamp = x.shape
+    T = nsamp - max_delay
+    st = stats if stats is not None else bandpass(x, dtype)
+    raw, cflag = channel_mask(x, dtype, st, rfi)
+    sflag = spectrum_mask(x, dtype, st, rfi, cflag)
+    D = dedisperse(x, dtype, st, cflag, sflag, rfi.chunk_width, delay, T)
+    ss = series_stats(D)
+    cands, n = candidates(D, ss["mu"], ss["sigma"], nsigma, beam=beam, t0=t0, cap=cand_cap)
+    out = dict(stats=st, chunk_raw=raw, chunk_flag=cflag, spec_flag=sflag, series=ss,
+               candidates=cands, n_candidates=n, T=T)
+    if keep_series:
+        out["D"] = D
+    return out
