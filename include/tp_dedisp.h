@@ -1,0 +1,241 @@
+/*
+ * tp_dedisp.h -- C ABI of the GB300 dedispersion search library.
+ *
+ * The library runs the data-parallel hot path of the multibeam transient
+ * pipeline of Magro, Hickish & Zarb Adami (arXiv:1307.5700) on one GPU:
+ *
+ *   A0  plan: channel frequencies and the integer delay table of Eq. 1
+ *   A1  per-channel bandpass statistics ("Bandpass Correction", Sec. 2.2.1)
+ *   A2  channel thresholding ("Channel Thresholding", Sec. 2.2.1)
+ *   A3  spectrum thresholding ("Spectrum Thresholding", Sec. 2.2.1)
+ *   A4  substitution of flagged samples by the bandpass (Sec. 2.2.1)
+ *   A5  brute-force incoherent dedispersion (Sec. 2.2.2)
+ *   A6  per-DM series mean / standard deviation (Sec. 2.2.3)
+ *   A7  n-sigma thresholding into a candidate list compacted on the device
+ *       (Sec. 2.3, first stage of event detection)
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: TP_OK (0) or a negative TP_E* code.  The text of the last
+ *     error of the calling thread is available from tp_last_error_string().
+ *   - Every GPU operation of an engine is issued on the engine's stream (or on
+ *     the beam's stream, see tp_beam_set_stream) and is asynchronous unless the
+ *     entry point says it blocks.
+ *   - Filterbank blocks are channel-major: sample t of channel c is at element
+ *     c * nsamp + t (the paper's beam / channel / time order, Sec. 2.1).
+ *   - Pointers are plain host or device addresses, as stated per argument;
+ *     the library never keeps a caller pointer after the call returns.
+ */
+#ifndef TP_DEDISP_H
+#define TP_DEDISP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------------- */
+#define TP_OK 0
+#define TP_EINVAL -1     /* an argument is out of range or inconsistent       */
+#define TP_ENOMEM -2     /* a device or host allocation failed                */
+#define TP_EADMIT -3     /* the beam does not fit the engine's HBM budget     */
+#define TP_EBUSY -4      /* the beam's window still holds an unprocessed block */
+#define TP_ENOTREADY -5  /* the step that must come first has not been issued */
+#define TP_ETRUNC -6     /* more candidates than the caller's buffer holds    */
+#define TP_ECUDA -7      /* a CUDA runtime call failed                         */
+#define TP_ETIMEOUT -8   /* a bounded device-side wait gave up                 */
+#define TP_EBOUNDS -9    /* a device-side bounds check failed                  */
+#define TP_EOVERFLOW -10 /* the candidate buffer of the beam overflowed        */
+
+/* ---- sample formats ---------------------------------------------------------- */
+#define TP_U8 0   /* unsigned 8-bit power; exact int32 sums                    */
+#define TP_F16 1  /* IEEE binary16; FP32 accumulation                          */
+#define TP_BF16 2 /* bfloat16; FP32 accumulation                               */
+#define TP_F32 3  /* IEEE binary32; FP32 accumulation                          */
+
+/* ---- bandpass statistics modes ---------------------------------------------- */
+#define TP_STATS_BLOCK 0    /* measured on each block's window (default)       */
+#define TP_STATS_EXTERNAL 1 /* supplied by tp_beam_set_bandpass                */
+
+/* RFI thresholding parameters (Sec. 2.2.1).  The paper gives no numbers; the
+ * defaults are W_c = 256 samples, tau_c = 5, tau_s = 6.
+ *   channel stage : chunk k of channel c (samples [kW, min((k+1)W, N))) exceeds
+ *                   when sum(x - mu_c) > tau_channel * sigma_c * sqrt(n_k); the
+ *                   chunk and its time-adjacent chunks (and, with
+ *                   dilate_channels, the same chunk of channels c-1, c+1) are
+ *                   flagged.
+ *   spectrum stage: spectrum t is flagged when the sum over channels of the
+ *                   bandpass-corrected samples, flagged chunks counting 0,
+ *                   exceeds tau_spectrum * sqrt(sum_c sigma_c^2).
+ *   A flagged sample is replaced by its channel's bandpass value. */
+typedef struct tp_rfi_params {
+  int32_t enable_channel;  /* 1: run the channel stage                         */
+  int32_t enable_spectrum; /* 1: run the spectrum stage                        */
+  int32_t chunk_width;     /* W_c in samples, >= 1                             */
+  int32_t dilate_channels; /* 1: also flag adjacent channels' chunks           */
+  double tau_channel;      /* tau_c                                            */
+  double tau_spectrum;     /* tau_s                                            */
+  int32_t stats_mode;      /* TP_STATS_BLOCK or TP_STATS_EXTERNAL              */
+  int32_t reserved;        /* must be 0                                        */
+} tp_rfi_params;
+
+/* One detection (Sec. 2.3: the (time, DM, intensity) triplet, plus the beam
+ * and the dedispersed value).  24 bytes. */
+typedef struct tp_candidate {
+  int32_t beam;   /* beam id                                                   */
+  int32_t dm_idx; /* index into the plan's DM list                              */
+  int64_t t_abs;  /* stream sample index (arrival time at the top channel)     */
+  float snr;      /* (D - mu_d) / sigma_d                                       */
+  float value;    /* D[dm_idx][t]                                               */
+} tp_candidate;
+
+typedef struct tp_engine tp_engine;
+typedef struct tp_plan tp_plan;
+
+/* Fill *p with the defaults listed above. */
+void tp_rfi_defaults(tp_rfi_params *p);
+
+/* ---- engine ------------------------------------------------------------------- */
+
+/* Create an engine bound to CUDA device `device`.  The engine owns the device
+ * memory of its plans and beams and admits beams only while their footprint
+ * fits `hbm_budget_bytes` (0 = 90 % of the device memory free at creation).
+ * `cuda_stream` is a cudaStream_t borrowed from the caller (NULL = the legacy
+ * default stream); it must outlive the engine.  Errors: TP_EINVAL (bad device),
+ * TP_ECUDA. */
+int tp_engine_create(int device, size_t hbm_budget_bytes, void *cuda_stream, tp_engine **out);
+
+/* Free everything the engine owns (its plans and beams included) after waiting
+ * for its streams.  NULL is accepted. */
+int tp_engine_destroy(tp_engine *e);
+
+/* Wait until all work the engine issued has finished. */
+int tp_sync(tp_engine *e);
+
+/* Device bytes currently held by the engine, and its budget. */
+int tp_engine_memory(const tp_engine *e, size_t *used, size_t *budget);
+
+/* ---- A0: plan (Eq. 1) --------------------------------------------------------
+ * Channel c has centre frequency f_lo_mhz + (c + 1/2) * bw_mhz / nchan (bw < 0:
+ * the band descends with channel index).  The reference frequency is the
+ * highest centre.  delay[d][c] = floor(4148.808 * dm_list[d] * (f_c^-2 -
+ * f_ref^-2) / t_samp_s + 1/2), evaluated in binary64 on the GPU in exactly
+ * that operation order, without fused multiply-adds.
+ * dm_list (host, ndm doubles) is copied; it must be finite, >= 0 and
+ * non-decreasing.  `rfi` may be NULL for the defaults.  `nsigma` is the
+ * detection threshold of A7.  The call blocks until the table is built.
+ * Errors: TP_EINVAL (nchan <= 0, ndm <= 0, t_samp <= 0, bw = 0, a channel
+ * frequency <= 0, a DM negative / not finite / decreasing, bad rfi params,
+ * a delay above 2^31 - 1), TP_ENOMEM, TP_ECUDA. */
+int tp_create_plan(tp_engine *e, int nchan, double f_lo_mhz, double bw_mhz, double t_samp_s,
+                   const double *dm_list, int ndm, int dtype, const tp_rfi_params *rfi,
+                   double nsigma, tp_plan **out);
+
+/* Destroy a plan; fails with TP_EBUSY while an open beam uses it. */
+int tp_plan_destroy(tp_plan *p);
+
+/* Sizes of a plan (any pointer may be NULL). */
+int tp_plan_info(const tp_plan *p, int *nchan, int *ndm, int *max_delay, int *dtype);
+
+/* Copy the delay table (ndm x nchan int32, row = DM) to host memory `out`
+ * holding `count` elements.  Blocks. */
+int tp_get_delay_table(const tp_plan *p, int32_t *out, size_t count);
+
+/* ---- beams -----------------------------------------------------------------------
+ * A beam is one filterbank stream processed with a plan.  It owns a device
+ * window of max_delay + block_nsamp samples per channel (the overlap tail of
+ * the previous block followed by the new block), its statistics, masks,
+ * dedispersed series (ndm x T) and a candidate buffer of `cand_capacity`
+ * records.  Admission is by HBM footprint; on TP_EADMIT nothing is allocated.
+ * block_nsamp must exceed the plan's max_delay. */
+int tp_beam_open(tp_engine *e, const tp_plan *p, int block_nsamp, int cand_capacity, int *beam_id);
+int tp_beam_close(tp_engine *e, int beam);
+
+/* Device bytes beam_open would take for these sizes (no allocation). */
+int tp_beam_footprint(const tp_plan *p, int block_nsamp, int cand_capacity, size_t *bytes);
+
+/* Issue this beam's work on `cuda_stream` instead of the engine's (NULL =
+ * the engine stream).  The stream is borrowed. */
+int tp_beam_set_stream(tp_engine *e, int beam, void *cuda_stream);
+
+/* Statistics for TP_STATS_EXTERNAL plans: mu and sigma (host, nchan doubles
+ * each) replace the measured bandpass from the next block on.  For 8-bit data
+ * the bandpass value is the integer floor(mu + 1/2). */
+int tp_beam_set_bandpass(tp_engine *e, int beam, const double *mu, const double *sigma, int nchan);
+
+/* Append one block of `nsamp` (1..block_nsamp) new samples per channel.
+ * `buf` is channel-major [nchan][nsamp] in the plan's dtype, in device memory
+ * when buf_is_device, else in host memory (pinned for asynchrony).  The data
+ * are copied on the beam's stream: a device buffer may be reused once that
+ * stream reaches this point, a pageable host buffer when the call returns.
+ * The first block of a stream must be longer than max_delay; it yields
+ * nsamp - max_delay outputs, each later block nsamp outputs.
+ * Errors: TP_EINVAL (size), TP_EBUSY (previous block not yet dedispersed). */
+int tp_push_block(tp_engine *e, int beam, const void *buf, int nsamp, int buf_is_device);
+
+/* A1-A5 on the beam's current window (async).  beam = -1 processes every beam
+ * holding a new block in one batched launch per stage.  TP_ENOTREADY if no
+ * block is waiting. */
+int tp_dedisperse(tp_engine *e, int beam);
+
+/* A6-A7 on the beam's dedispersed series (async); beam = -1: every beam that
+ * was dedispersed and not yet detected.  TP_ENOTREADY if not dedispersed. */
+int tp_detect(tp_engine *e, int beam);
+
+/* Wait for the beam's detection and copy min(cap, n_total) candidates, sorted
+ * by (dm_idx, t_abs), to host memory `out`.  *n_total receives the number
+ * found (which can exceed the beam's capacity; only the first
+ * cand_capacity in (dm_idx, t) order are kept).  Returns TP_ETRUNC when
+ * n_total > cap, TP_EOVERFLOW when n_total exceeded the beam capacity. */
+int tp_get_candidates(tp_engine *e, int beam, tp_candidate *out, int cap, int *n_total);
+
+/* ---- inspection (tests, debugging) -------------------------------------------- */
+
+/* Window length, number of outputs, stream index of window sample 0 and the
+ * number of W_c chunks of the beam's current block. */
+int tp_beam_info(tp_engine *e, int beam, int64_t *nsamp_window, int64_t *nout, int64_t *t0_abs,
+                 int *nchunk);
+
+/* Dedispersed series D (ndm x nout, row-major, float32 for float plans, int32
+ * for 8-bit plans) into `out` of `bytes` bytes (device memory when
+ * out_is_device).  Blocks. */
+int tp_get_series(tp_engine *e, int beam, void *out, size_t bytes, int out_is_device);
+
+/* Bandpass statistics of the current block (host, nchan doubles each). */
+int tp_get_bandpass(tp_engine *e, int beam, double *mu, double *sigma, int nchan);
+
+/* Masks of the current block: chunk flags (nchan x nchunk bytes, after
+ * dilation), the undilated exceedances (same shape), and spectrum flags (one
+ * byte per window sample).  Any pointer may be NULL.  Blocks. */
+int tp_get_masks(tp_engine *e, int beam, uint8_t *chunk_flag, uint8_t *chunk_raw, uint8_t *spec_flag);
+
+/* Series statistics mu_d, sigma_d (host, ndm doubles each). */
+int tp_get_series_stats(tp_engine *e, int beam, double *mu, double *sigma, int ndm);
+
+/* ---- tracing -------------------------------------------------------------------- */
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing on every beam of the
+ * engine.  While enabled each block records events around its stages on the
+ * beam's stream. */
+int tp_set_profiling(tp_engine *e, int enable);
+
+/* Accumulated stage times of a beam since profiling was enabled, in ms:
+ * ms[0] push (window assembly copies), ms[1] A1-A3 (statistics and masks),
+ * ms[2] A4-A5 (dedispersion), ms[3] A6-A7 (detection); *count = blocks timed.
+ * Blocks until the beam's last timed stage has finished. */
+int tp_get_stage_times(tp_engine *e, int beam, double *ms, int64_t *count);
+
+/* Kernels launched by the engine since it was created. */
+int tp_engine_launches(const tp_engine *e, uint64_t *n);
+
+/* Text of the calling thread's last error. */
+const char *tp_last_error_string(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int tp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TP_DEDISP_H */

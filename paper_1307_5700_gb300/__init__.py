@@ -1,0 +1,339 @@
+"""GB300 multibeam dedispersion search -- Python binding of ``libtpdd.so``.
+
+A thin ctypes layer over the C ABI declared in ``include/tp_dedisp.h``: every
+function here has the name of the C entry point it calls and only marshals
+arguments (numpy arrays and host buffers as host pointers, torch CUDA tensors
+as device pointers, torch streams as ``cudaStream_t``).  All computation runs
+in the library's CUDA kernels; there is no CPU path.  Importing works without a
+GPU; calling an entry point needs the built library (``build()``), and the
+library needs a CUDA device.
+
+Negative status codes raise ``TpError`` carrying the code and the library's
+error text.  ``TP_ETRUNC`` / ``TP_EOVERFLOW`` from ``tp_get_candidates`` are
+reported in its return value instead, since the records are still valid.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+TP_OK = 0
+TP_EINVAL = -1
+TP_ENOMEM = -2
+TP_EADMIT = -3
+TP_EBUSY = -4
+TP_ENOTREADY = -5
+TP_ETRUNC = -6
+TP_ECUDA = -7
+TP_ETIMEOUT = -8
+TP_EBOUNDS = -9
+TP_EOVERFLOW = -10
+
+TP_U8, TP_F16, TP_BF16, TP_F32 = 0, 1, 2, 3
+DTYPES = {"u8": TP_U8, "f16": TP_F16, "bf16": TP_BF16, "f32": TP_F32}
+TP_STATS_BLOCK, TP_STATS_EXTERNAL = 0, 1
+
+# Every entry point of include/tp_dedisp.h (checked by the tests).
+EXPORTS = (
+    "tp_rfi_defaults", "tp_engine_create", "tp_engine_destroy", "tp_sync", "tp_engine_memory",
+    "tp_create_plan", "tp_plan_destroy", "tp_plan_info", "tp_get_delay_table", "tp_beam_open",
+    "tp_beam_close", "tp_beam_footprint", "tp_beam_set_stream", "tp_beam_set_bandpass",
+    "tp_push_block", "tp_dedisperse", "tp_detect", "tp_get_candidates", "tp_beam_info",
+    "tp_get_series", "tp_get_bandpass", "tp_get_masks", "tp_get_series_stats",
+    "tp_set_profiling", "tp_get_stage_times", "tp_engine_launches", "tp_last_error_string",
+    "tp_version",
+)
+
+
+class TpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class tp_rfi_params(ctypes.Structure):
+    _fields_ = [("enable_channel", ctypes.c_int32), ("enable_spectrum", ctypes.c_int32),
+                ("chunk_width", ctypes.c_int32), ("dilate_channels", ctypes.c_int32),
+                ("tau_channel", ctypes.c_double), ("tau_spectrum", ctypes.c_double),
+                ("stats_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class tp_candidate(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int32), ("dm_idx", ctypes.c_int32), ("t_abs", ctypes.c_int64),
+                ("snr", ctypes.c_float), ("value", ctypes.c_float)]
+
+
+CAND_DTYPE = np.dtype([("beam", np.int32), ("dm_idx", np.int32), ("t_abs", np.int64),
+                       ("snr", np.float32), ("value", np.float32)])
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_sz = ctypes.c_size_t
+_d = ctypes.c_double
+
+_SIGS = {
+    "tp_rfi_defaults": (None, [_vp]),
+    "tp_engine_create": (_i, [_i, _sz, _vp, _vp]),
+    "tp_engine_destroy": (_i, [_vp]),
+    "tp_sync": (_i, [_vp]),
+    "tp_engine_memory": (_i, [_vp, _vp, _vp]),
+    "tp_create_plan": (_i, [_vp, _i, _d, _d, _d, _vp, _i, _i, _vp, _d, _vp]),
+    "tp_plan_destroy": (_i, [_vp]),
+    "tp_plan_info": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "tp_get_delay_table": (_i, [_vp, _vp, _sz]),
+    "tp_beam_open": (_i, [_vp, _vp, _i, _i, _vp]),
+    "tp_beam_close": (_i, [_vp, _i]),
+    "tp_beam_footprint": (_i, [_vp, _i, _i, _vp]),
+    "tp_beam_set_stream": (_i, [_vp, _i, _vp]),
+    "tp_beam_set_bandpass": (_i, [_vp, _i, _vp, _vp, _i]),
+    "tp_push_block": (_i, [_vp, _i, _vp, _i, _i]),
+    "tp_dedisperse": (_i, [_vp, _i]),
+    "tp_detect": (_i, [_vp, _i]),
+    "tp_get_candidates": (_i, [_vp, _i, _vp, _i, _vp]),
+    "tp_beam_info": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "tp_get_series": (_i, [_vp, _i, _vp, _sz, _i]),
+    "tp_get_bandpass": (_i, [_vp, _i, _vp, _vp, _i]),
+    "tp_get_masks": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "tp_get_series_stats": (_i, [_vp, _i, _vp, _vp, _i]),
+    "tp_set_profiling": (_i, [_vp, _i]),
+    "tp_get_stage_times": (_i, [_vp, _i, _vp, _vp]),
+    "tp_engine_launches": (_i, [_vp, _vp]),
+    "tp_last_error_string": (ctypes.c_char_p, []),
+    "tp_version": (_i, []),
+}
+
+
+def build(force=False):
+    """Compile the CUDA library for sm_103a (in-tree) and return its path."""
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded library.  Raises if it has not been built: there is no
+    fallback implementation."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is not built; call "
+                               "paper_1307_5700_gb300.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc < 0:
+        raise TpError(rc, lib().tp_last_error_string().decode(errors="replace"))
+    return rc
+
+
+def _addr(obj):
+    """Address of a buffer: numpy array (host), torch tensor (its device or
+    host address), ctypes object, int, or None."""
+    if obj is None:
+        return None
+    if isinstance(obj, int):
+        return obj
+    if isinstance(obj, np.ndarray):
+        if not obj.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return obj.ctypes.data
+    if hasattr(obj, "data_ptr"):
+        if hasattr(obj, "is_contiguous") and not obj.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return obj.data_ptr()
+    return ctypes.addressof(obj)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+# ---- entry points ------------------------------------------------------------------
+
+def tp_rfi_defaults():
+    p = tp_rfi_params()
+    lib().tp_rfi_defaults(ctypes.byref(p))
+    return p
+
+
+def tp_version():
+    return lib().tp_version()
+
+
+def tp_last_error_string():
+    return lib().tp_last_error_string().decode(errors="replace")
+
+
+def tp_engine_create(device=0, hbm_budget_bytes=0, cuda_stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().tp_engine_create(device, hbm_budget_bytes, _stream(cuda_stream), ctypes.byref(h)))
+    return h
+
+
+def tp_engine_destroy(e):
+    return _check(lib().tp_engine_destroy(e))
+
+
+def tp_sync(e):
+    return _check(lib().tp_sync(e))
+
+
+def tp_engine_memory(e):
+    used, budget = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().tp_engine_memory(e, ctypes.byref(used), ctypes.byref(budget)))
+    return used.value, budget.value
+
+
+def tp_create_plan(e, nchan, f_lo_mhz, bw_mhz, t_samp_s, dm_list, dtype, rfi=None, nsigma=5.0):
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    h = ctypes.c_void_p()
+    _check(lib().tp_create_plan(e, nchan, f_lo_mhz, bw_mhz, t_samp_s, dm.ctypes.data, len(dm), dtype,
+                                ctypes.byref(rfi) if rfi is not None else None, nsigma, ctypes.byref(h)))
+    return h
+
+
+def tp_plan_destroy(p):
+    return _check(lib().tp_plan_destroy(p))
+
+
+def tp_plan_info(p):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().tp_plan_info(p, *[ctypes.byref(x) for x in v]))
+    return dict(nchan=v[0].value, ndm=v[1].value, max_delay=v[2].value, dtype=v[3].value)
+
+
+def tp_get_delay_table(p):
+    info = tp_plan_info(p)
+    out = np.empty((info["ndm"], info["nchan"]), np.int32)
+    _check(lib().tp_get_delay_table(p, out.ctypes.data, out.size))
+    return out
+
+
+def tp_beam_footprint(p, block_nsamp, cand_capacity):
+    n = ctypes.c_size_t()
+    _check(lib().tp_beam_footprint(p, block_nsamp, cand_capacity, ctypes.byref(n)))
+    return n.value
+
+
+def tp_beam_open(e, p, block_nsamp, cand_capacity):
+    b = ctypes.c_int()
+    _check(lib().tp_beam_open(e, p, block_nsamp, cand_capacity, ctypes.byref(b)))
+    return b.value
+
+
+def tp_beam_close(e, beam):
+    return _check(lib().tp_beam_close(e, beam))
+
+
+def tp_beam_set_stream(e, beam, cuda_stream):
+    return _check(lib().tp_beam_set_stream(e, beam, _stream(cuda_stream)))
+
+
+def tp_beam_set_bandpass(e, beam, mu, sigma):
+    mu = np.ascontiguousarray(mu, np.float64)
+    sigma = np.ascontiguousarray(sigma, np.float64)
+    return _check(lib().tp_beam_set_bandpass(e, beam, mu.ctypes.data, sigma.ctypes.data, len(mu)))
+
+
+def tp_push_block(e, beam, buf, nsamp=None, buf_is_device=None):
+    """``buf``: (nchan, nsamp) numpy array (host) or torch tensor (device or
+    host), in the plan's sample format (bfloat16 as uint16 bits on the host)."""
+    if nsamp is None:
+        nsamp = buf.shape[-1]
+    if buf_is_device is None:
+        buf_is_device = bool(getattr(buf, "is_cuda", False))
+    return _check(lib().tp_push_block(e, beam, _addr(buf), int(nsamp), int(bool(buf_is_device))))
+
+
+def tp_dedisperse(e, beam):
+    return _check(lib().tp_dedisperse(e, beam))
+
+
+def tp_detect(e, beam):
+    return _check(lib().tp_detect(e, beam))
+
+
+def tp_get_candidates(e, beam, cap):
+    """Returns (records as a CAND_DTYPE array, n_total, status)."""
+    out = np.zeros(max(int(cap), 1), CAND_DTYPE)
+    n = ctypes.c_int()
+    rc = lib().tp_get_candidates(e, beam, out.ctypes.data, int(cap), ctypes.byref(n))
+    if rc < 0 and rc not in (TP_ETRUNC, TP_EOVERFLOW):
+        _check(rc)
+    return out[:min(n.value, int(cap))], n.value, rc
+
+
+def tp_beam_info(e, beam):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    k = ctypes.c_int()
+    _check(lib().tp_beam_info(e, beam, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(k)))
+    return dict(nsamp_window=a.value, nout=b.value, t0_abs=c.value, nchunk=k.value)
+
+
+def tp_get_series(e, beam, out=None, ndm=None, is_int=False):
+    """D (ndm x nout) into ``out`` (numpy or torch), allocated on the host if
+    None."""
+    info = tp_beam_info(e, beam)
+    if out is None:
+        out = np.empty((ndm, info["nout"]), np.int32 if is_int else np.float32)
+    nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+    is_dev = bool(getattr(out, "is_cuda", False))
+    _check(lib().tp_get_series(e, beam, _addr(out), nbytes, int(is_dev)))
+    return out
+
+
+def tp_get_bandpass(e, beam, nchan):
+    mu = np.empty(nchan, np.float64)
+    sigma = np.empty(nchan, np.float64)
+    _check(lib().tp_get_bandpass(e, beam, mu.ctypes.data, sigma.ctypes.data, nchan))
+    return mu, sigma
+
+
+def tp_get_masks(e, beam, nchan):
+    info = tp_beam_info(e, beam)
+    cf = np.empty((nchan, info["nchunk"]), np.uint8)
+    cr = np.empty((nchan, info["nchunk"]), np.uint8)
+    sf = np.empty(info["nsamp_window"], np.uint8)
+    _check(lib().tp_get_masks(e, beam, cf.ctypes.data, cr.ctypes.data, sf.ctypes.data))
+    return cf, cr, sf
+
+
+def tp_get_series_stats(e, beam, ndm):
+    mu = np.empty(ndm, np.float64)
+    sigma = np.empty(ndm, np.float64)
+    _check(lib().tp_get_series_stats(e, beam, mu.ctypes.data, sigma.ctypes.data, ndm))
+    return mu, sigma
+
+
+def tp_set_profiling(e, enable=True):
+    return _check(lib().tp_set_profiling(e, int(bool(enable))))
+
+
+def tp_get_stage_times(e, beam):
+    """(ms[4]: push, A1-A3, A4-A5, A6-A7 accumulated; number of blocks)."""
+    ms = np.zeros(4, np.float64)
+    n = ctypes.c_int64()
+    _check(lib().tp_get_stage_times(e, beam, ms.ctypes.data, ctypes.byref(n)))
+    return ms, n.value
+
+
+def tp_engine_launches(e):
+    n = ctypes.c_uint64()
+    _check(lib().tp_engine_launches(e, ctypes.byref(n)))
+    return n.value

@@ -1,0 +1,982 @@
+// C ABI: engine, plans, beams and the per-block pipeline (see tp_dedisp.h).
+//
+// Host-side runtime: device memory is allocated once per plan / beam and kept
+// resident (the overlap window, statistics, masks, series and candidate
+// buffers of every beam), admission is by device-memory footprint, and every
+// step of a block is issued asynchronously on the beam's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tp_common.cuh"
+
+namespace tp {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+int cuda_error(cudaError_t err, const char* what) {
+  return set_error(TP_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(err), cudaGetErrorName(err));
+}
+
+size_t dtype_size(int dtype) {
+  switch (dtype) {
+    case TP_U8: return 1;
+    case TP_F16:
+    case TP_BF16: return 2;
+    case TP_F32: return 4;
+    default: return 0;
+  }
+}
+
+// Sum of sigma_c^2 in channel order, binary64, times tau_s: the spectrum
+// threshold under externally supplied statistics.
+double external_spectrum_threshold(const double* sigma, int nchan, double tau_s) {
+  volatile double v = 0.0;  // keep the sequential order and separate roundings
+  for (int c = 0; c < nchan; ++c) {
+    const volatile double sq = sigma[c] * sigma[c];
+    v = v + sq;
+  }
+  return tau_s * std::sqrt((double)v);
+}
+
+}  // namespace tp
+
+using namespace tp;
+
+namespace {
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+enum BeamState { kEmpty = 0, kReady = 1, kDedispersed = 2, kDetected = 3 };
+
+struct Beam {
+  tp_engine* e = nullptr;
+  const tp_plan* plan = nullptr;
+  int id = -1;
+  int B = 0;         // block length
+  int cap = 0;       // candidate capacity
+  int64_t pitch = 0; // window row pitch (elements)
+  int nchunk_max = 0;
+  int ntt_max = 0;
+  int nblk_max = 0;
+  int64_t hit_pitch = 0;
+  int64_t dpitch = 0;
+  cudaStream_t stream = nullptr;
+  bool own_event = false;
+  cudaEvent_t ev_detect = nullptr;
+  // device buffers
+  void* win[2] = {nullptr, nullptr};
+  void* chunk_sums = nullptr;
+  uint8_t* chunk_raw = nullptr;
+  uint8_t* chunk_flag = nullptr;
+  int* chan_nflag = nullptr;
+  double* mu = nullptr;
+  double* sigma = nullptr;
+  long long* S = nullptr;
+  long long* V = nullptr;
+  int* bint = nullptr;
+  float* mu_hi = nullptr;
+  float* mu_lo = nullptr;
+  uint32_t* spec_bits = nullptr;
+  int* spec_nflag = nullptr;
+  double* spec_thr = nullptr;
+  void* D = nullptr;
+  void* row_part = nullptr;
+  double* row_mu = nullptr;
+  double* row_sigma = nullptr;
+  uint32_t* hit_bits = nullptr;
+  uint32_t* blk_count = nullptr;
+  uint32_t* blk_off = nullptr;
+  tp_candidate* cand = nullptr;
+  unsigned long long* n_total = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  // stream state
+  int cur = 0;
+  int64_t nsamp_win = 0;
+  int64_t nout = 0;
+  int64_t t0_abs = 0;
+  int64_t pushed = 0;
+  BeamState state = kEmpty;
+  bool have_ext = false;
+  double ext_thr = 0.0;
+  // stage timing (tp_set_profiling)
+  struct EventSet {
+    cudaEvent_t ev[6];  // push start/end, rfi start, rfi end / dd start, dd end, detect end
+  };
+  std::vector<EventSet*> ev_pool;
+  std::vector<EventSet*> ev_pending;
+  EventSet* ev_cur = nullptr;
+  double stage_ms[4] = {0, 0, 0, 0};
+  int64_t stage_count = 0;
+};
+
+}  // namespace
+
+struct tp_plan {
+  tp_engine* e = nullptr;
+  int nchan = 0, ndm = 0, max_delay = 0, dtype = 0;
+  double f_lo = 0, bw = 0, t_samp = 0;
+  std::vector<double> dm;
+  tp_rfi_params rfi{};
+  double nsigma = 5.0;
+  int32_t* d_delay = nullptr;
+  std::vector<int32_t> h_delay;
+  std::vector<DmTile> h_tiles;
+  DmTile* d_tiles = nullptr;
+  int users = 0;
+  size_t bytes = 0;
+};
+
+struct tp_engine {
+  int device = 0;
+  size_t budget = 0, used = 0;
+  cudaStream_t stream = nullptr;
+  bool profiling = false;
+  uint64_t launches = 0;
+  std::vector<tp_plan*> plans;
+  std::vector<Beam*> beams;
+  std::recursive_mutex mu;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    cudaGetDevice(&now);
+    if (prev >= 0 && now != prev) cudaSetDevice(prev);
+  }
+};
+
+int check_rfi(const tp_rfi_params& r) {
+  if (r.chunk_width < 1) return set_error(TP_EINVAL, "chunk_width must be >= 1");
+  if (!std::isfinite(r.tau_channel) || !std::isfinite(r.tau_spectrum))
+    return set_error(TP_EINVAL, "thresholds must be finite");
+  if (r.stats_mode != TP_STATS_BLOCK && r.stats_mode != TP_STATS_EXTERNAL)
+    return set_error(TP_EINVAL, "unknown stats_mode %d", r.stats_mode);
+  return TP_OK;
+}
+
+// Greedy DM tiling: consecutive DMs while the tile holds < kMaxTileDm trials
+// and the spread of any channel's delay inside the tile stays <= kMaxOverhang.
+std::vector<DmTile> make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan) {
+  std::vector<DmTile> tiles;
+  int d0 = 0;
+  while (d0 < ndm) {
+    int nd = 1;
+    while (nd < kMaxTileDm && d0 + nd < ndm) {
+      int spread = 0;
+      const int32_t* a = &delay[(size_t)d0 * nchan];
+      const int32_t* b = &delay[(size_t)(d0 + nd) * nchan];
+      for (int c = 0; c < nchan; ++c) spread = std::max(spread, b[c] - a[c]);
+      if (spread > kMaxOverhang) break;
+      ++nd;
+    }
+    tiles.push_back(DmTile{d0, nd});
+    d0 += nd;
+  }
+  return tiles;
+}
+
+Beam* get_beam(tp_engine* e, int id) {
+  if (!e || id < 0 || id >= (int)e->beams.size()) return nullptr;
+  return e->beams[id];
+}
+
+struct Sizes {
+  size_t total = 0;
+  std::vector<std::pair<void**, size_t>> items;
+};
+
+// Every device buffer of a beam, in one place (footprint and allocation).
+void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
+  const size_t es = dtype_size(p->dtype);
+  const int64_t nmax = (int64_t)p->max_delay + B;
+  const int64_t pitch = (int64_t)round_up((size_t)nmax * es, 256) / (int64_t)es;
+  const int W = p->rfi.chunk_width;
+  const int nchunk = (int)((nmax + W - 1) / W);
+  const int ntt = (int)((B + kTileT - 1) / kTileT);
+  const int nblk = (int)((B + kDetectT - 1) / kDetectT);
+  const int64_t hit_pitch = (B + 31) / 32;
+  const int64_t dpitch = (int64_t)round_up((size_t)B, 64);
+  b->pitch = pitch;
+  b->nchunk_max = nchunk;
+  b->ntt_max = ntt;
+  b->nblk_max = nblk;
+  b->hit_pitch = hit_pitch;
+  b->dpitch = dpitch;
+  const size_t nc = (size_t)p->nchan, nd = (size_t)p->ndm;
+  auto add = [&](void** ptr, size_t bytes) {
+    bytes = round_up(std::max<size_t>(bytes, 1), 256);
+    out->items.push_back({ptr, bytes});
+    out->total += bytes;
+  };
+  add(&b->win[0], nc * (size_t)pitch * es);
+  add(&b->win[1], nc * (size_t)pitch * es);
+  add(&b->chunk_sums, nc * (size_t)nchunk * 16);
+  add((void**)&b->chunk_raw, nc * (size_t)nchunk);
+  add((void**)&b->chunk_flag, nc * (size_t)nchunk);
+  add((void**)&b->chan_nflag, nc * sizeof(int));
+  add((void**)&b->mu, nc * 8);
+  add((void**)&b->sigma, nc * 8);
+  add((void**)&b->S, nc * 8);
+  add((void**)&b->V, nc * 8);
+  add((void**)&b->bint, nc * 4);
+  add((void**)&b->mu_hi, nc * 4);
+  add((void**)&b->mu_lo, nc * 4);
+  add((void**)&b->spec_bits, (size_t)((nmax + 31) / 32) * 4);
+  add((void**)&b->spec_nflag, 4);
+  add((void**)&b->spec_thr, 8);
+  add(&b->D, nd * (size_t)dpitch * 4);
+  add(&b->row_part, nd * (size_t)ntt * 16);
+  add((void**)&b->row_mu, nd * 8);
+  add((void**)&b->row_sigma, nd * 8);
+  add((void**)&b->hit_bits, nd * (size_t)hit_pitch * 4);
+  add((void**)&b->blk_count, nd * (size_t)nblk * 4);
+  add((void**)&b->blk_off, nd * (size_t)nblk * 4);
+  add((void**)&b->cand, (size_t)cap * sizeof(tp_candidate));
+  add((void**)&b->n_total, 8);
+}
+
+void free_beam(Beam* b) {
+  if (b->ev_cur) b->ev_pending.push_back(b->ev_cur);
+  b->ev_cur = nullptr;
+  for (auto* v : {&b->ev_pool, &b->ev_pending})
+    for (Beam::EventSet* es : *v) {
+      for (cudaEvent_t ev : es->ev) cudaEventDestroy(ev);
+      delete es;
+    }
+  b->ev_pool.clear();
+  b->ev_pending.clear();
+  if (b->ev_detect) cudaEventDestroy(b->ev_detect);
+  for (void* p : b->allocs) cudaFree(p);
+  b->allocs.clear();
+}
+
+cudaStream_t beam_stream(const tp_engine* e, const Beam* b) { return b->stream ? b->stream : e->stream; }
+
+// Stage timing: an event set follows one block from push to detection.
+void prof_harvest(Beam* b, bool wait) {
+  size_t done = 0;
+  for (; done < b->ev_pending.size(); ++done) {
+    Beam::EventSet* es = b->ev_pending[done];
+    if (wait) cudaEventSynchronize(es->ev[5]);
+    else if (cudaEventQuery(es->ev[5]) != cudaSuccess) break;
+    float ms[4] = {0, 0, 0, 0};
+    cudaEventElapsedTime(&ms[0], es->ev[0], es->ev[1]);
+    cudaEventElapsedTime(&ms[1], es->ev[2], es->ev[3]);
+    cudaEventElapsedTime(&ms[2], es->ev[3], es->ev[4]);
+    cudaEventElapsedTime(&ms[3], es->ev[4], es->ev[5]);
+    for (int i = 0; i < 4; ++i) b->stage_ms[i] += ms[i];
+    b->stage_count++;
+    b->ev_pool.push_back(es);
+  }
+  b->ev_pending.erase(b->ev_pending.begin(), b->ev_pending.begin() + done);
+  cudaGetLastError();
+}
+
+void prof_record(tp_engine* e, Beam* b, int which, cudaStream_t s) {
+  if (!e->profiling) return;
+  if (which == 0) {
+    prof_harvest(b, false);
+    if (b->ev_cur) {  // a block that never reached detection
+      b->ev_pool.push_back(b->ev_cur);
+      b->ev_cur = nullptr;
+    }
+    if (b->ev_pool.empty()) {
+      auto* es = new Beam::EventSet();
+      for (cudaEvent_t& ev : es->ev) cudaEventCreate(&ev);
+      b->ev_pool.push_back(es);
+    }
+    b->ev_cur = b->ev_pool.back();
+    b->ev_pool.pop_back();
+  }
+  if (!b->ev_cur) return;
+  cudaEventRecord(b->ev_cur->ev[which], s);
+  if (which == 5) {
+    b->ev_pending.push_back(b->ev_cur);
+    b->ev_cur = nullptr;
+  }
+}
+
+RfiArgs rfi_args(const tp_plan* p, Beam* b) {
+  RfiArgs a{};
+  a.x = b->win[b->cur];
+  a.pitch = b->pitch;
+  a.nchan = p->nchan;
+  a.nsamp = b->nsamp_win;
+  a.W = p->rfi.chunk_width;
+  a.nchunk = (int)((b->nsamp_win + a.W - 1) / a.W);
+  a.dtype = p->dtype;
+  a.stats_mode = p->rfi.stats_mode;
+  a.enable_channel = p->rfi.enable_channel;
+  a.enable_spectrum = p->rfi.enable_spectrum;
+  a.dilate_channels = p->rfi.dilate_channels;
+  a.tau_c = p->rfi.tau_channel;
+  a.tau_s = p->rfi.tau_spectrum;
+  a.mu = b->mu;
+  a.sigma = b->sigma;
+  a.S = b->S;
+  a.V = b->V;
+  a.bint = b->bint;
+  a.mu_hi = b->mu_hi;
+  a.mu_lo = b->mu_lo;
+  a.chunk_raw = b->chunk_raw;
+  a.chunk_flag = b->chunk_flag;
+  a.chan_nflag = b->chan_nflag;
+  a.spec_bits = b->spec_bits;
+  a.spec_nflag = b->spec_nflag;
+  a.spec_thr = b->spec_thr;
+  return a;
+}
+
+int issue_dedisperse(tp_engine* e, Beam* b) {
+  const tp_plan* p = b->plan;
+  if (b->state != kReady) return set_error(TP_ENOTREADY, "beam %d holds no new block", b->id);
+  if (p->rfi.stats_mode == TP_STATS_EXTERNAL && !b->have_ext)
+    return set_error(TP_ENOTREADY, "beam %d: external statistics not set", b->id);
+  cudaStream_t s = beam_stream(e, b);
+  RfiArgs ra = rfi_args(p, b);
+  prof_record(e, b, 2, s);
+  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->ext_thr, s));
+  prof_record(e, b, 3, s);
+  e->launches += 2 + (ra.enable_channel ? 1 : 0) + (ra.enable_spectrum ? 1 : 0);
+  DedispArgs da{};
+  da.x = b->win[b->cur];
+  da.pitch = b->pitch;
+  da.nchan = p->nchan;
+  da.nsamp = b->nsamp_win;
+  da.nout = b->nout;
+  da.dtype = p->dtype;
+  da.W = ra.W;
+  da.nchunk = ra.nchunk;
+  da.delay = p->d_delay;
+  da.ndm = p->ndm;
+  da.tiles = p->d_tiles;
+  da.ntiles = (int)p->h_tiles.size();
+  da.ntt = (int)((b->nout + kTileT - 1) / kTileT);
+  da.mu_hi = b->mu_hi;
+  da.mu_lo = b->mu_lo;
+  da.bint = b->bint;
+  da.chunk_flag = b->chunk_flag;
+  da.chan_nflag = b->chan_nflag;
+  da.spec_bits = b->spec_bits;
+  da.spec_nflag = b->spec_nflag;
+  da.D = b->D;
+  da.dpitch = b->dpitch;
+  da.row_part = b->row_part;
+  TP_CUDA_TRY(launch_dedisperse(da, s));
+  prof_record(e, b, 4, s);
+  e->launches += 1;
+  b->state = kDedispersed;
+  return TP_OK;
+}
+
+int issue_detect(tp_engine* e, Beam* b) {
+  const tp_plan* p = b->plan;
+  if (b->state != kDedispersed) return set_error(TP_ENOTREADY, "beam %d is not dedispersed", b->id);
+  cudaStream_t s = beam_stream(e, b);
+  DetectArgs a{};
+  a.D = b->D;
+  a.dpitch = b->dpitch;
+  a.ndm = p->ndm;
+  a.nout = b->nout;
+  a.is_int = p->dtype == TP_U8;
+  a.row_part = b->row_part;
+  a.ntt = (int)((b->nout + kTileT - 1) / kTileT);
+  a.nsigma = p->nsigma;
+  a.beam = b->id;
+  a.t0_abs = b->t0_abs;
+  a.row_mu = b->row_mu;
+  a.row_sigma = b->row_sigma;
+  a.hit_bits = b->hit_bits;
+  a.hit_pitch = (b->nout + 31) / 32;
+  a.blk_count = b->blk_count;
+  a.blk_off = b->blk_off;
+  a.nblk_t = (int)((b->nout + kDetectT - 1) / kDetectT);
+  a.cand = b->cand;
+  a.cap = b->cap;
+  a.n_total = b->n_total;
+  TP_CUDA_TRY(launch_detect(a, s));
+  e->launches += 3;
+  prof_record(e, b, 5, s);
+  TP_CUDA_TRY(cudaEventRecord(b->ev_detect, s));
+  b->state = kDetected;
+  return TP_OK;
+}
+
+}  // namespace
+
+namespace tp {
+const char* last_error_cstr();
+}
+
+extern "C" {
+
+void tp_rfi_defaults(tp_rfi_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->enable_channel = 1;
+  p->enable_spectrum = 1;
+  p->chunk_width = 256;
+  p->dilate_channels = 0;
+  p->tau_channel = 5.0;
+  p->tau_spectrum = 6.0;
+  p->stats_mode = TP_STATS_BLOCK;
+}
+
+int tp_version(void) { return 100; }
+
+const char* tp_last_error_string(void) { return tp::last_error_cstr(); }
+
+int tp_engine_create(int device, size_t hbm_budget_bytes, void* cuda_stream, tp_engine** out) {
+  if (!out) return set_error(TP_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  TP_CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return set_error(TP_EINVAL, "device %d of %d", device, n);
+  DeviceGuard g(device);
+  size_t free_b = 0, total_b = 0;
+  TP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  tp_engine* e = new (std::nothrow) tp_engine();
+  if (!e) return set_error(TP_ENOMEM, "engine allocation");
+  e->device = device;
+  e->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
+  e->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = e;
+  return TP_OK;
+}
+
+int tp_engine_destroy(tp_engine* e) {
+  if (!e) return TP_OK;
+  {
+    std::lock_guard<std::recursive_mutex> lk(e->mu);
+    DeviceGuard g(e->device);
+    cudaStreamSynchronize(e->stream);
+    for (Beam* b : e->beams)
+      if (b) {
+        cudaStreamSynchronize(beam_stream(e, b));
+        free_beam(b);
+        delete b;
+      }
+    e->beams.clear();
+    for (tp_plan* p : e->plans) {
+      cudaFree(p->d_delay);
+      cudaFree(p->d_tiles);
+      delete p;
+    }
+    e->plans.clear();
+  }
+  delete e;
+  return TP_OK;
+}
+
+int tp_sync(tp_engine* e) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
+  for (Beam* b : e->beams)
+    if (b && b->stream) TP_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return TP_OK;
+}
+
+int tp_engine_memory(const tp_engine* e, size_t* used, size_t* budget) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  if (used) *used = e->used;
+  if (budget) *budget = e->budget;
+  return TP_OK;
+}
+
+int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, double t_samp_s,
+                   const double* dm_list, int ndm, int dtype, const tp_rfi_params* rfi,
+                   double nsigma, tp_plan** out) {
+  if (!e || !out) return set_error(TP_EINVAL, "engine or out is NULL");
+  *out = nullptr;
+  if (nchan <= 0 || ndm <= 0) return set_error(TP_EINVAL, "nchan %d / ndm %d must be > 0", nchan, ndm);
+  if (!(t_samp_s > 0.0) || !std::isfinite(t_samp_s)) return set_error(TP_EINVAL, "t_samp must be > 0");
+  if (!std::isfinite(f_lo_mhz) || !std::isfinite(bw_mhz) || bw_mhz == 0.0)
+    return set_error(TP_EINVAL, "f_lo / bw invalid");
+  if (dtype_size(dtype) == 0) return set_error(TP_EINVAL, "unknown dtype %d", dtype);
+  if (!dm_list) return set_error(TP_EINVAL, "dm_list is NULL");
+  if (!std::isfinite(nsigma)) return set_error(TP_EINVAL, "nsigma must be finite");
+  for (int d = 0; d < ndm; ++d) {
+    if (!std::isfinite(dm_list[d]) || dm_list[d] < 0.0)
+      return set_error(TP_EINVAL, "DM %d is negative or not finite", d);
+    if (d > 0 && dm_list[d] < dm_list[d - 1]) return set_error(TP_EINVAL, "DM list must be non-decreasing");
+  }
+  const double df = bw_mhz / nchan;
+  const double fa = f_lo_mhz + 0.5 * df, fb = f_lo_mhz + ((double)nchan - 0.5) * df;
+  if (!(fa > 0.0) || !(fb > 0.0)) return set_error(TP_EINVAL, "channel frequencies must be > 0");
+  tp_rfi_params r;
+  if (rfi) r = *rfi;
+  else tp_rfi_defaults(&r);
+  int rc = check_rfi(r);
+  if (rc) return rc;
+
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  tp_plan* p = new tp_plan();
+  p->e = e;
+  p->nchan = nchan;
+  p->ndm = ndm;
+  p->dtype = dtype;
+  p->f_lo = f_lo_mhz;
+  p->bw = bw_mhz;
+  p->t_samp = t_samp_s;
+  p->dm.assign(dm_list, dm_list + ndm);
+  p->rfi = r;
+  p->nsigma = nsigma;
+  const size_t n = (size_t)nchan * ndm;
+  double* d_dm = nullptr;
+  int* d_err = nullptr;
+  auto fail = [&](int code) {
+    cudaFree(d_dm);
+    cudaFree(d_err);
+    cudaFree(p->d_delay);
+    cudaFree(p->d_tiles);
+    delete p;
+    return code;
+  };
+  cudaError_t ce;
+  if ((ce = cudaMalloc(&p->d_delay, n * 4)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(delay)"));
+  if ((ce = cudaMalloc(&d_dm, ndm * 8)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(dm)"));
+  if ((ce = cudaMalloc(&d_err, 4)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(err)"));
+  if ((ce = cudaMemcpyAsync(d_dm, dm_list, ndm * 8, cudaMemcpyHostToDevice, e->stream)) != cudaSuccess)
+    return fail(cuda_error(ce, "copy dm"));
+  if ((ce = cudaMemsetAsync(d_err, 0, 4, e->stream)) != cudaSuccess) return fail(cuda_error(ce, "memset"));
+  if ((ce = launch_delay_table(nchan, f_lo_mhz, bw_mhz, t_samp_s, d_dm, ndm, p->d_delay, d_err, e->stream)) !=
+      cudaSuccess)
+    return fail(cuda_error(ce, "delay table kernel"));
+  e->launches += 1;
+  p->h_delay.resize(n);
+  int herr = 0;
+  if ((ce = cudaMemcpyAsync(p->h_delay.data(), p->d_delay, n * 4, cudaMemcpyDeviceToHost, e->stream)) !=
+      cudaSuccess)
+    return fail(cuda_error(ce, "copy delay"));
+  if ((ce = cudaMemcpyAsync(&herr, d_err, 4, cudaMemcpyDeviceToHost, e->stream)) != cudaSuccess)
+    return fail(cuda_error(ce, "copy err"));
+  if ((ce = cudaStreamSynchronize(e->stream)) != cudaSuccess) return fail(cuda_error(ce, "sync"));
+  cudaFree(d_dm);
+  d_dm = nullptr;
+  cudaFree(d_err);
+  d_err = nullptr;
+  if (herr) return fail(set_error(TP_EINVAL, "a delay exceeds 2^31 - 1 samples"));
+  int dmax = 0;
+  for (int32_t v : p->h_delay) dmax = std::max(dmax, (int)v);
+  p->max_delay = dmax;
+  p->h_tiles = make_tiles(p->h_delay, ndm, nchan);
+  const size_t tb = p->h_tiles.size() * sizeof(DmTile);
+  if ((ce = cudaMalloc(&p->d_tiles, tb)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(tiles)"));
+  if ((ce = cudaMemcpy(p->d_tiles, p->h_tiles.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail(cuda_error(ce, "copy tiles"));
+  p->bytes = n * 4 + tb;
+  e->used += p->bytes;
+  e->plans.push_back(p);
+  *out = p;
+  return TP_OK;
+}
+
+int tp_plan_destroy(tp_plan* p) {
+  if (!p) return TP_OK;
+  tp_engine* e = p->e;
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  if (p->users > 0) return set_error(TP_EBUSY, "plan is used by %d open beams", p->users);
+  DeviceGuard g(e->device);
+  cudaStreamSynchronize(e->stream);
+  cudaFree(p->d_delay);
+  cudaFree(p->d_tiles);
+  e->used -= p->bytes;
+  e->plans.erase(std::remove(e->plans.begin(), e->plans.end(), p), e->plans.end());
+  delete p;
+  return TP_OK;
+}
+
+int tp_plan_info(const tp_plan* p, int* nchan, int* ndm, int* max_delay, int* dtype) {
+  if (!p) return set_error(TP_EINVAL, "plan is NULL");
+  if (nchan) *nchan = p->nchan;
+  if (ndm) *ndm = p->ndm;
+  if (max_delay) *max_delay = p->max_delay;
+  if (dtype) *dtype = p->dtype;
+  return TP_OK;
+}
+
+int tp_get_delay_table(const tp_plan* p, int32_t* out, size_t count) {
+  if (!p || !out) return set_error(TP_EINVAL, "plan or out is NULL");
+  if (count < p->h_delay.size()) return set_error(TP_EINVAL, "buffer holds %zu of %zu", count, p->h_delay.size());
+  std::memcpy(out, p->h_delay.data(), p->h_delay.size() * 4);
+  return TP_OK;
+}
+
+int tp_beam_footprint(const tp_plan* p, int block_nsamp, int cand_capacity, size_t* bytes) {
+  if (!p || !bytes) return set_error(TP_EINVAL, "plan or bytes is NULL");
+  if (block_nsamp <= p->max_delay)
+    return set_error(TP_EINVAL, "block_nsamp %d must exceed the largest delay %d", block_nsamp, p->max_delay);
+  if (cand_capacity < 1) return set_error(TP_EINVAL, "cand_capacity must be >= 1");
+  Beam tmp;
+  Sizes sz;
+  beam_layout(p, block_nsamp, cand_capacity, &tmp, &sz);
+  *bytes = sz.total;
+  return TP_OK;
+}
+
+int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capacity, int* beam_id) {
+  if (!e || !p || !beam_id) return set_error(TP_EINVAL, "engine, plan or beam_id is NULL");
+  if (p->e != e) return set_error(TP_EINVAL, "plan belongs to another engine");
+  size_t need = 0;
+  int rc = tp_beam_footprint(p, block_nsamp, cand_capacity, &need);
+  if (rc) return rc;
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  if (e->used + need > e->budget)
+    return set_error(TP_EADMIT, "beam needs %zu bytes, %zu of %zu in use", need, e->used, e->budget);
+  DeviceGuard g(e->device);
+  Beam* b = new Beam();
+  b->e = e;
+  b->plan = p;
+  b->B = block_nsamp;
+  b->cap = cand_capacity;
+  Sizes sz;
+  beam_layout(p, block_nsamp, cand_capacity, b, &sz);
+  for (auto& it : sz.items) {
+    void* ptr = nullptr;
+    cudaError_t ce = cudaMalloc(&ptr, it.second);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      free_beam(b);
+      delete b;
+      return set_error(TP_ENOMEM, "cudaMalloc(%zu): %s", it.second, cudaGetErrorString(ce));
+    }
+    b->allocs.push_back(ptr);
+    *it.first = ptr;
+  }
+  cudaError_t ce = cudaEventCreateWithFlags(&b->ev_detect, cudaEventDisableTiming);
+  if (ce != cudaSuccess) {
+    free_beam(b);
+    delete b;
+    return cuda_error(ce, "cudaEventCreate");
+  }
+  b->bytes = sz.total;
+  int id = -1;
+  for (int i = 0; i < (int)e->beams.size(); ++i)
+    if (!e->beams[i]) {
+      id = i;
+      break;
+    }
+  if (id < 0) {
+    id = (int)e->beams.size();
+    e->beams.push_back(nullptr);
+  }
+  b->id = id;
+  e->beams[id] = b;
+  e->used += b->bytes;
+  const_cast<tp_plan*>(p)->users++;
+  *beam_id = id;
+  return TP_OK;
+}
+
+int tp_beam_close(tp_engine* e, int beam) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  DeviceGuard g(e->device);
+  cudaStreamSynchronize(beam_stream(e, b));
+  const_cast<tp_plan*>(b->plan)->users--;
+  e->used -= b->bytes;
+  free_beam(b);
+  e->beams[beam] = nullptr;
+  delete b;
+  return TP_OK;
+}
+
+int tp_beam_set_stream(tp_engine* e, int beam, void* cuda_stream) {
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  return TP_OK;
+}
+
+int tp_beam_set_bandpass(tp_engine* e, int beam, const double* mu, const double* sigma, int nchan) {
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  const tp_plan* p = b->plan;
+  if (p->rfi.stats_mode != TP_STATS_EXTERNAL)
+    return set_error(TP_EINVAL, "plan does not use external statistics");
+  if (!mu || !sigma || nchan != p->nchan) return set_error(TP_EINVAL, "need %d mu and sigma values", p->nchan);
+  for (int c = 0; c < nchan; ++c)
+    if (!std::isfinite(mu[c]) || !std::isfinite(sigma[c]) || sigma[c] < 0.0)
+      return set_error(TP_EINVAL, "channel %d: mu/sigma invalid", c);
+  std::vector<float> hi(nchan), lo(nchan);
+  std::vector<int> bi(nchan);
+  for (int c = 0; c < nchan; ++c) {
+    hi[c] = (float)mu[c];
+    lo[c] = (float)(mu[c] - (double)hi[c]);
+    bi[c] = (int)std::floor(mu[c] + 0.5);
+  }
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  TP_CUDA_TRY(cudaMemcpyAsync(b->mu, mu, nchan * 8, cudaMemcpyHostToDevice, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(b->sigma, sigma, nchan * 8, cudaMemcpyHostToDevice, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(b->mu_hi, hi.data(), nchan * 4, cudaMemcpyHostToDevice, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(b->mu_lo, lo.data(), nchan * 4, cudaMemcpyHostToDevice, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(b->bint, bi.data(), nchan * 4, cudaMemcpyHostToDevice, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
+  b->ext_thr = external_spectrum_threshold(sigma, nchan, p->rfi.tau_spectrum);
+  b->have_ext = true;
+  return TP_OK;
+}
+
+int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is_device) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  const tp_plan* p = b->plan;
+  if (!buf) return set_error(TP_EINVAL, "buf is NULL");
+  if (nsamp < 1 || nsamp > b->B) return set_error(TP_EINVAL, "nsamp %d not in [1, %d]", nsamp, b->B);
+  if (b->state == kReady) return set_error(TP_EBUSY, "beam %d: previous block not dedispersed", beam);
+  const int64_t dmax = p->max_delay;
+  if (b->pushed == 0 && nsamp <= dmax)
+    return set_error(TP_EINVAL, "first block (%d samples) must exceed the largest delay %lld", nsamp,
+                     (long long)dmax);
+  const size_t es = dtype_size(p->dtype);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  const cudaMemcpyKind kind = buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t dpitch = (size_t)b->pitch * es;
+  prof_record(e, b, 0, s);
+  if (b->pushed == 0) {
+    b->cur = 0;
+    TP_CUDA_TRY(cudaMemcpy2DAsync(b->win[0], dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
+                                  kind, s));
+    b->nsamp_win = nsamp;
+    b->nout = nsamp - dmax;
+    b->t0_abs = 0;
+  } else {
+    const int nxt = b->cur ^ 1;
+    char* dst = static_cast<char*>(b->win[nxt]);
+    if (dmax > 0) {
+      const char* src = static_cast<const char*>(b->win[b->cur]) + (size_t)(b->nsamp_win - dmax) * es;
+      TP_CUDA_TRY(cudaMemcpy2DAsync(dst, dpitch, src, dpitch, (size_t)dmax * es, p->nchan,
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    TP_CUDA_TRY(cudaMemcpy2DAsync(dst + (size_t)dmax * es, dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es,
+                                  p->nchan, kind, s));
+    b->cur = nxt;
+    b->nsamp_win = dmax + nsamp;
+    b->nout = nsamp;
+    b->t0_abs = b->pushed - dmax;
+  }
+  prof_record(e, b, 1, s);
+  b->pushed += nsamp;
+  b->state = kReady;
+  return TP_OK;
+}
+
+int tp_dedisperse(tp_engine* e, int beam) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  if (beam >= 0) {
+    Beam* b = get_beam(e, beam);
+    if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+    return issue_dedisperse(e, b);
+  }
+  int n = 0;
+  for (Beam* b : e->beams)
+    if (b && b->state == kReady) {
+      int rc = issue_dedisperse(e, b);
+      if (rc) return rc;
+      ++n;
+    }
+  return n ? TP_OK : set_error(TP_ENOTREADY, "no beam holds a new block");
+}
+
+int tp_detect(tp_engine* e, int beam) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  if (beam >= 0) {
+    Beam* b = get_beam(e, beam);
+    if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+    return issue_detect(e, b);
+  }
+  int n = 0;
+  for (Beam* b : e->beams)
+    if (b && b->state == kDedispersed) {
+      int rc = issue_detect(e, b);
+      if (rc) return rc;
+      ++n;
+    }
+  return n ? TP_OK : set_error(TP_ENOTREADY, "no beam is dedispersed");
+}
+
+int tp_get_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, int* n_total) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->state != kDetected) return set_error(TP_ENOTREADY, "beam %d: detection not issued", beam);
+  if (cap < 0 || (cap > 0 && !out)) return set_error(TP_EINVAL, "bad output buffer");
+  DeviceGuard g(e->device);
+  TP_CUDA_TRY(cudaEventSynchronize(b->ev_detect));
+  unsigned long long tot = 0;
+  TP_CUDA_TRY(cudaMemcpy(&tot, b->n_total, 8, cudaMemcpyDeviceToHost));
+  const unsigned long long kept = std::min<unsigned long long>(tot, (unsigned long long)b->cap);
+  const int ncopy = (int)std::min<unsigned long long>(kept, (unsigned long long)cap);
+  if (ncopy > 0) TP_CUDA_TRY(cudaMemcpy(out, b->cand, (size_t)ncopy * sizeof(tp_candidate), cudaMemcpyDeviceToHost));
+  if (n_total) *n_total = (int)std::min<unsigned long long>(tot, 0x7fffffffull);
+  if (tot > (unsigned long long)b->cap)
+    return set_error(TP_EOVERFLOW, "beam %d found %llu candidates, capacity %d", beam, tot, b->cap);
+  if (tot > (unsigned long long)cap) return set_error(TP_ETRUNC, "%llu candidates, buffer holds %d", tot, cap);
+  return TP_OK;
+}
+
+int tp_beam_info(tp_engine* e, int beam, int64_t* nsamp_window, int64_t* nout, int64_t* t0_abs, int* nchunk) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  const int W = b->plan->rfi.chunk_width;
+  if (nsamp_window) *nsamp_window = b->nsamp_win;
+  if (nout) *nout = b->nout;
+  if (t0_abs) *t0_abs = b->t0_abs;
+  if (nchunk) *nchunk = (int)((b->nsamp_win + W - 1) / W);
+  return TP_OK;
+}
+
+int tp_get_series(tp_engine* e, int beam, void* out, size_t bytes, int out_is_device) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->state < kDedispersed) return set_error(TP_ENOTREADY, "beam %d is not dedispersed", beam);
+  const size_t row = (size_t)b->nout * 4;
+  if (!out || bytes < row * b->plan->ndm) return set_error(TP_EINVAL, "need %zu bytes", row * b->plan->ndm);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  TP_CUDA_TRY(cudaMemcpy2DAsync(out, row, b->D, (size_t)b->dpitch * 4, row, b->plan->ndm,
+                                out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+}
+
+int tp_get_bandpass(tp_engine* e, int beam, double* mu, double* sigma, int nchan) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (nchan != b->plan->nchan) return set_error(TP_EINVAL, "nchan %d != %d", nchan, b->plan->nchan);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  if (mu) TP_CUDA_TRY(cudaMemcpyAsync(mu, b->mu, nchan * 8, cudaMemcpyDeviceToHost, s));
+  if (sigma) TP_CUDA_TRY(cudaMemcpyAsync(sigma, b->sigma, nchan * 8, cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+}
+
+int tp_get_masks(tp_engine* e, int beam, uint8_t* chunk_flag, uint8_t* chunk_raw, uint8_t* spec_flag) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->state < kDedispersed) return set_error(TP_ENOTREADY, "beam %d is not dedispersed", beam);
+  const tp_plan* p = b->plan;
+  const int W = p->rfi.chunk_width;
+  const size_t nk = (size_t)((b->nsamp_win + W - 1) / W);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  if (chunk_flag) TP_CUDA_TRY(cudaMemcpyAsync(chunk_flag, b->chunk_flag, p->nchan * nk, cudaMemcpyDeviceToHost, s));
+  if (chunk_raw) TP_CUDA_TRY(cudaMemcpyAsync(chunk_raw, b->chunk_raw, p->nchan * nk, cudaMemcpyDeviceToHost, s));
+  std::vector<uint32_t> bits;
+  if (spec_flag) {
+    bits.resize((size_t)((b->nsamp_win + 31) / 32));
+    TP_CUDA_TRY(cudaMemcpyAsync(bits.data(), b->spec_bits, bits.size() * 4, cudaMemcpyDeviceToHost, s));
+  }
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (spec_flag)
+    for (int64_t t = 0; t < b->nsamp_win; ++t) spec_flag[t] = (uint8_t)((bits[t >> 5] >> (t & 31)) & 1u);
+  return TP_OK;
+}
+
+int tp_get_series_stats(tp_engine* e, int beam, double* mu, double* sigma, int ndm) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->state != kDetected) return set_error(TP_ENOTREADY, "beam %d: detection not issued", beam);
+  if (ndm != b->plan->ndm) return set_error(TP_EINVAL, "ndm %d != %d", ndm, b->plan->ndm);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  if (mu) TP_CUDA_TRY(cudaMemcpyAsync(mu, b->row_mu, ndm * 8, cudaMemcpyDeviceToHost, s));
+  if (sigma) TP_CUDA_TRY(cudaMemcpyAsync(sigma, b->row_sigma, ndm * 8, cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int tp_set_profiling(tp_engine* e, int enable) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  e->profiling = enable != 0;
+  if (e->profiling)
+    for (Beam* b : e->beams)
+      if (b) {
+        DeviceGuard g(e->device);
+        prof_harvest(b, true);
+        for (double& v : b->stage_ms) v = 0.0;
+        b->stage_count = 0;
+      }
+  return TP_OK;
+}
+
+int tp_get_stage_times(tp_engine* e, int beam, double* ms, int64_t* count) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  DeviceGuard g(e->device);
+  prof_harvest(b, true);
+  if (ms)
+    for (int i = 0; i < 4; ++i) ms[i] = b->stage_ms[i];
+  if (count) *count = b->stage_count;
+  return TP_OK;
+}
+
+int tp_engine_launches(const tp_engine* e, uint64_t* n) {
+  if (!e || !n) return set_error(TP_EINVAL, "engine or n is NULL");
+  *n = e->launches;
+  return TP_OK;
+}
+
+}  // extern "C"

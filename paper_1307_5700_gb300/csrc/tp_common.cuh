@@ -1,0 +1,122 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "tp_dedisp.h"
+
+namespace tp {
+
+// Sets the thread's last-error text (printf-style) and returns `code`.
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t err, const char* what);
+
+#define TP_CUDA_TRY(expr)                                         \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) return ::tp::cuda_error(_e, #expr);    \
+  } while (0)
+
+// ---- per-block device arguments ------------------------------------------------
+
+// What the RFI kernels need about one beam's current block.
+struct RfiArgs {
+  const void* x;          // window, channel-major, row pitch `pitch` elements
+  int64_t pitch;          // elements per channel row
+  int nchan;
+  int64_t nsamp;          // window length N_s
+  int W;                  // chunk width W_c
+  int nchunk;             // ceil(N_s / W)
+  int dtype;              // TP_U8 / TP_F16 / TP_BF16 / TP_F32
+  int stats_mode;         // TP_STATS_BLOCK / TP_STATS_EXTERNAL
+  int enable_channel, enable_spectrum, dilate_channels;
+  double tau_c, tau_s;
+  // per-channel statistics (outputs in block mode, inputs in external mode)
+  double* mu;             // [nchan]
+  double* sigma;          // [nchan]
+  long long* S;           // [nchan] exact sum (8-bit, block mode)
+  long long* V;           // [nchan] N*Q - S^2 (8-bit, block mode)
+  int* bint;              // [nchan] integer bandpass value (8-bit)
+  float* mu_hi;           // [nchan] mu split into two floats (float data)
+  float* mu_lo;
+  // masks
+  uint8_t* chunk_raw;     // [nchan][nchunk] exceedances
+  uint8_t* chunk_flag;    // [nchan][nchunk] after dilation
+  int* chan_nflag;        // [nchan] flagged chunks per channel
+  uint32_t* spec_bits;    // [ceil(N_s/32)] spectrum flags
+  int* spec_nflag;        // [1] flagged spectra
+  double* spec_thr;       // [1] spectrum threshold (per-block constant)
+};
+
+// A tile of consecutive DM trials processed by one dedispersion CTA.
+struct DmTile {
+  int d0;     // first DM index
+  int nd;     // number of DMs (<= kMaxTileDm)
+};
+
+struct DedispArgs {
+  const void* x;
+  int64_t pitch;
+  int nchan;
+  int64_t nsamp;          // window length
+  int64_t nout;           // T
+  int dtype;
+  int W, nchunk;
+  const int32_t* delay;   // [ndm][nchan]
+  int ndm;
+  const DmTile* tiles;    // [ntiles]
+  int ntiles;
+  int ntt;                // number of time tiles
+  const float* mu_hi;
+  const float* mu_lo;
+  const int* bint;
+  const uint8_t* chunk_flag;
+  const int* chan_nflag;
+  const uint32_t* spec_bits;
+  const int* spec_nflag;
+  void* D;                // [ndm][dpitch] float or int32
+  int64_t dpitch;
+  void* row_part;         // [ndm][ntt] (float: double2 {sum, sumsq}; int: longlong2)
+};
+
+struct DetectArgs {
+  const void* D;
+  int64_t dpitch;
+  int ndm;
+  int64_t nout;
+  int is_int;
+  const void* row_part;   // as in DedispArgs
+  int ntt;
+  double nsigma;
+  int beam;
+  int64_t t0_abs;
+  double* row_mu;         // [ndm]
+  double* row_sigma;      // [ndm]
+  uint32_t* hit_bits;     // [ndm][ceil(nout/32)]
+  int64_t hit_pitch;      // words per row
+  uint32_t* blk_count;    // [nblk]
+  uint32_t* blk_off;      // [nblk]
+  int nblk_t;             // CTAs per row
+  tp_candidate* cand;
+  int cap;
+  unsigned long long* n_total;  // [1]
+};
+
+// Dedispersion tiling constants (shared by the planner and the kernel).
+constexpr int kMaxTileDm = 32;      // DM trials per CTA tile
+constexpr int kTileT = 512;         // output samples per CTA tile
+constexpr int kMaxOverhang = 512;   // max delay spread inside a DM tile
+constexpr int kDetectT = 4096;      // samples per detection CTA
+
+// ---- launchers (each returns a cudaError_t of the launch) -----------------------
+cudaError_t launch_delay_table(int nchan, double f_lo, double bw, double t_samp, const double* dm,
+                               int ndm, int32_t* delay, int* err_flag, cudaStream_t s);
+cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, cudaStream_t s);
+double external_spectrum_threshold(const double* sigma, int nchan, double tau_s);
+cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s);
+cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s);
+
+size_t dtype_size(int dtype);
+
+}  // namespace tp

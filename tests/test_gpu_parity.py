@@ -1,0 +1,327 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: bit-exact delay tables, masks, 8-bit int32 series and candidate sets;
+FP32 series within |D_gpu - D_oracle| <= 1e-5 * sum_c |y| (the magnitude of the
+terms summed at that point); binary16 / bfloat16 storage judged against the
+binary64 oracle run on the same quantised input, with the same bound.  Float
+candidate sets must match except entries whose oracle statistic lies within
+that bound of the threshold (reported; the seeded inputs keep them rare)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import paper_1307_5700_gb300 as tp
+import synth
+from oracle import oracle as O
+from tests.gpu_run import GpuBeam
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    tp.build()
+    O.set_threads(os.cpu_count() or 1)
+
+
+def _mass_all(x, dtype, st, cf, sf, W, delay, T):
+    ndm = delay.shape[0]
+    dd = np.repeat(np.arange(ndm, dtype=np.int32), T)
+    tt = np.tile(np.arange(T, dtype=np.int64), ndm)
+    _, mass = O.dedisperse_points(x, dtype, st, cf, sf, W, delay, dd, tt)
+    return mass.reshape(ndm, T)
+
+
+def _cand_set(c):
+    return {(int(r["dm_idx"]), int(r["t_abs"])) for r in c}
+
+
+def check_block(g, o, x, dtype, delay, rfi, nsigma, t0=0):
+    """Compare one block's GPU products with the oracle's."""
+    T = o["T"]
+    assert g["info"]["nout"] == T
+    assert np.array_equal(g["chunk_raw"], o["chunk_raw"]), "channel exceedances differ"
+    assert np.array_equal(g["chunk_flag"], o["chunk_flag"]), "chunk flags differ"
+    assert np.array_equal(g["spec_flag"], o["spec_flag"]), "spectrum flags differ"
+    np.testing.assert_allclose(g["mu"], o["stats"]["mu"], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(g["sigma"], o["stats"]["sigma"], rtol=1e-7, atol=1e-9)
+    Dg, Do = g["D"], o["D"]
+    if dtype == "u8":
+        assert Dg.dtype == np.int32
+        assert np.array_equal(Dg.astype(np.int64), Do), "int32 series differ"
+        assert np.array_equal(g["row_mu"], o["series"]["mu"])
+        assert np.array_equal(g["row_sigma"], o["series"]["sigma"])
+        got = g["candidates"]
+        want = o["candidates"]
+        assert g["n_candidates"] == o["n_candidates"]
+        assert np.array_equal(got["dm_idx"], want["dm_idx"]) and np.array_equal(got["t_abs"], want["t_abs"])
+        assert np.array_equal(got["snr"], want["snr"]) and np.array_equal(got["value"], want["value"])
+        return
+    mass = _mass_all(x, dtype, o["stats"], o["chunk_flag"], o["spec_flag"], rfi.chunk_width, delay, T)
+    err = np.abs(Dg.astype(np.float64) - Do)
+    bound = TOL * mass + 1e-30
+    worst = float((err / np.maximum(mass, 1e-300)).max())
+    assert np.all(err <= bound), f"max |dD|/mass = {worst:.3e}"
+    np.testing.assert_allclose(g["row_mu"], o["series"]["mu"], rtol=0,
+                               atol=1e-5 * float(np.abs(Do).mean()) + 1e-9)
+    np.testing.assert_allclose(g["row_sigma"], o["series"]["sigma"], rtol=1e-5)
+    # candidates, except entries within the D bound of the threshold
+    stat = Do - o["series"]["mu"][:, None] - nsigma * o["series"]["sigma"][:, None]
+    border = np.abs(stat) <= TOL * mass + 1e-6 * nsigma * o["series"]["sigma"][:, None]
+    bset = {(int(d), int(t) + t0) for d, t in zip(*np.nonzero(border))}
+    gs, os_ = _cand_set(g["candidates"]), _cand_set(o["candidates"])
+    assert gs - bset == os_ - bset, f"candidate sets differ: {sorted((gs ^ os_) - bset)[:10]}"
+    assert len(bset) <= max(5, 1e-4 * Do.size)
+    # records: (dm, t) order, values and snr consistent with the oracle
+    keys = [(int(r["dm_idx"]), int(r["t_abs"])) for r in g["candidates"]]
+    assert keys == sorted(keys)
+    for r in g["candidates"][:2000]:
+        d, t = int(r["dm_idx"]), int(r["t_abs"]) - t0
+        assert abs(r["value"] - Do[d, t]) <= TOL * mass[d, t] + 1e-6 * abs(Do[d, t])
+        snr = (Do[d, t] - o["series"]["mu"][d]) / o["series"]["sigma"][d]
+        assert abs(r["snr"] - snr) <= 1e-4 * max(1.0, abs(snr))
+
+
+def run_both(x, dtype, nchan, f_lo, bw, t_samp, dms, rfi, nsigma=5.0, ox=None):
+    g = GpuBeam(nchan, f_lo, bw, t_samp, dms, dtype, rfi=rfi, nsigma=nsigma)
+    try:
+        delay = g.delays()
+        od, dmax = O.delay_table(nchan, f_lo, bw, t_samp, dms)
+        assert np.array_equal(delay, od), "delay tables differ"
+        res = g.run(x)
+    finally:
+        g.close()
+    o = O.search_block(ox if ox is not None else x, dtype, od, dmax, rfi=rfi, nsigma=nsigma)
+    return res, o, od
+
+
+# ---- A0 -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nchan,f_lo,bw,ts,dms", [
+    (1024, 398.0, 20.0, 51.2e-6, np.arange(64, dtype=np.float64)),
+    (1024, 398.0, 20.0, 51.2e-6, np.arange(640) * 0.2),
+    (4096, 1200.0, 300.0, 64e-6, np.arange(2048, dtype=np.float64)),
+    (1024, 418.0, -20.0, 51.2e-6, np.arange(320) * 0.2),
+    (37, 100.0, 3.3, 1e-3, np.array([0.0, 1.0, 2.5, 10.0, 10.0, 77.7])),
+    (256, 1400.0, 0.5, 1e-4, np.array([0.0, 1e4])),
+])
+def test_delay_table_bit_exact(nchan, f_lo, bw, ts, dms):
+    e = tp.tp_engine_create(0)
+    try:
+        p = tp.tp_create_plan(e, nchan, f_lo, bw, ts, dms, "f32")
+        got = tp.tp_get_delay_table(p)
+        info = tp.tp_plan_info(p)
+        want, dmax = O.delay_table(nchan, f_lo, bw, ts, dms)
+        assert np.array_equal(got, want)
+        assert info["max_delay"] == dmax
+        tp.tp_plan_destroy(p)
+    finally:
+        tp.tp_engine_destroy(e)
+
+
+def test_plan_rejects_invalid():
+    e = tp.tp_engine_create(0)
+    try:
+        for args in [(0, 398.0, 20.0, 51.2e-6, [1.0]), (16, 398.0, 20.0, 0.0, [1.0]),
+                     (16, 398.0, 20.0, 51.2e-6, [-1.0]), (16, 398.0, 20.0, 51.2e-6, [2.0, 1.0]),
+                     (16, -30.0, 20.0, 51.2e-6, [1.0]), (16, 398.0, 0.0, 51.2e-6, [1.0])]:
+            with pytest.raises(tp.TpError) as ei:
+                tp.tp_create_plan(e, *args[:4], np.array(args[4]), "f32")
+            assert ei.value.code == tp.TP_EINVAL
+    finally:
+        tp.tp_engine_destroy(e)
+
+
+# ---- whole blocks ------------------------------------------------------------------------
+
+def test_config1_single_block_f32():
+    """1024 channels over 398-418 MHz, 32768 FP32 samples, DM 0..63: pulse at
+    DM 30 / t 12000 (SNR 20), narrowband and broadband RFI."""
+    dms = np.arange(64, dtype=np.float64)
+    od, dmax = O.delay_table(1024, 398.0, 20.0, 51.2e-6, dms)
+    x = synth.single_block_workload(lambda: od[30].astype(np.float64), seed=1000)
+    rfi = O.RfiParams()
+    g, o, _ = run_both(x, "f32", 1024, 398.0, 20.0, 51.2e-6, dms, rfi)
+    assert o["chunk_flag"][[300, 301, 700, 701]].any(axis=1).all()
+    assert o["spec_flag"][[5000, 20000, 26000]].all()
+    check_block(g, o, x, "f32", od, rfi, 5.0)
+    D = g["D"]
+    d, t = np.unravel_index(np.argmax(D), D.shape)
+    assert abs(d - 30) <= 1 and abs(t - 12000) <= 10
+
+
+def test_u8_block_exact():
+    nchan, nsamp = 256, 40000
+    dms = np.arange(96) * 0.5
+    od, dmax = O.delay_table(nchan, 398.0, 20.0, 51.2e-6, dms)
+    xf = synth.noise(nchan, nsamp, 5001, mean=128.0, std=16.0)
+    synth.add_pulse(xf, od[40].astype(np.float64) + 20000, 19.5, 16 * 25 / math.sqrt(nchan))
+    synth.add_narrowband(xf, [17, 18, 19], 3000, 7000, 160.0)
+    synth.add_broadband(xf, [15000, 31000], 100.0)
+    x = synth.to_u8(xf)
+    rfi = O.RfiParams(chunk_width=128)
+    g, o, _ = run_both(x, "u8", nchan, 398.0, 20.0, 51.2e-6, dms, rfi, nsigma=4.0)
+    assert o["chunk_flag"].any() and o["spec_flag"].any() and o["n_candidates"] > 0
+    check_block(g, o, x, "u8", od, rfi, 4.0)
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_half_precision_storage(dtype):
+    nchan, nsamp = 512, 20000
+    dms = np.arange(80) * 0.4
+    od, dmax = O.delay_table(nchan, 398.0, 20.0, 51.2e-6, dms)
+    xf = synth.noise(nchan, nsamp, 6001)
+    synth.add_pulse(xf, od[50].astype(np.float64) + 9000, 19.5, 20 / math.sqrt(nchan))
+    synth.add_narrowband(xf, [100, 101], 2000, 4000, 8.0)
+    x = synth.to_f16(xf) if dtype == "f16" else synth.to_bf16_bits(xf)
+    rfi = O.RfiParams()
+    g, o, _ = run_both(x, dtype, nchan, 398.0, 20.0, 51.2e-6, dms, rfi)
+    check_block(g, o, x, dtype, od, rfi, 5.0)
+    # error against the FP32 original, in sigma_D units (quantisation dominated)
+    o32 = O.search_block(xf, "f32", od, dmax, rfi=rfi)
+    sd = float(np.median(o32["series"]["sigma"]))
+    q = float(np.abs(g["D"].astype(np.float64) - o32["D"]).max()) / sd
+    assert q < (0.05 if dtype == "f16" else 0.4), q
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_ragged_shapes(dtype):
+    """37 channels, 33 DMs with a wide step (the planner splits DM tiles by
+    delay spread), window not a multiple of 512 or of W = 100."""
+    nchan, nsamp = 37, 9999
+    dms = np.concatenate([np.arange(20) * 3.0, 60 + np.arange(13) * 40.0])
+    f_lo, bw, ts = 398.0, 20.0, 51.2e-6
+    od, dmax = O.delay_table(nchan, f_lo, bw, ts, dms)
+    assert dmax < nsamp
+    xf = synth.noise(nchan, nsamp, 7001, mean=128.0 if dtype == "u8" else 0.0, std=16.0 if dtype == "u8" else 1.0)
+    xf[5, 1000:1700] += 200.0 if dtype == "u8" else 12.0
+    x = synth.to_u8(xf) if dtype == "u8" else xf
+    rfi = O.RfiParams(chunk_width=100, dilate_channels=True)
+    g, o, _ = run_both(x, dtype, nchan, f_lo, bw, ts, dms, rfi, nsigma=3.5)
+    assert o["chunk_flag"].any()
+    check_block(g, o, x, dtype, od, rfi, 3.5)
+
+
+def test_degenerate_dm0_single_channel():
+    for nchan, dms in [(1, np.array([0.0])), (64, np.array([0.0])), (3, np.array([0.0, 0.0, 1.0]))]:
+        x = synth.noise(nchan, 1500, 8001 + nchan)
+        rfi = O.RfiParams(enable_channel=False, enable_spectrum=False)
+        g, o, od = run_both(x, "f32", nchan, 398.0, 20.0, 51.2e-6, dms, rfi, nsigma=2.5)
+        check_block(g, o, x, "f32", od, rfi, 2.5)
+        if dms.max() == 0:
+            y = x.astype(np.float64) - x.astype(np.float64).mean(axis=1, keepdims=True)
+            np.testing.assert_allclose(g["D"][0], y.sum(axis=0), rtol=0, atol=1e-4 * nchan)
+
+
+def test_streaming_equals_long_block():
+    """Blocks pushed one after another (overlap tail carried on the device)
+    give the same series as one long block, with a fixed bandpass."""
+    nchan, B, nblk = 128, 3000, 4
+    dms = np.arange(40) * 1.0
+    f_lo, bw, ts = 398.0, 20.0, 51.2e-6
+    od, dmax = O.delay_table(nchan, f_lo, bw, ts, dms)
+    for dtype in ("f32", "u8"):
+        xf = synth.noise(nchan, B * nblk, 9001, mean=128.0 if dtype == "u8" else 0.5,
+                         std=16.0 if dtype == "u8" else 1.0)
+        x = synth.to_u8(xf) if dtype == "u8" else xf
+        mu = x.astype(np.float64).mean(axis=1)
+        sig = x.astype(np.float64).std(axis=1)
+        rfi = O.RfiParams(enable_channel=False, enable_spectrum=False)
+        g = GpuBeam(nchan, f_lo, bw, ts, dms, dtype, rfi=rfi, external=True, nsigma=3.0)
+        try:
+            g.open(B)
+            tp.tp_beam_set_bandpass(g.e, g.beam, mu, sig)
+            outs, t0s = [], []
+            for k in range(nblk):
+                r = g.run(x[:, k * B:(k + 1) * B].copy())
+                outs.append(r["D"])
+                t0s.append(r["info"]["t0_abs"])
+                assert r["info"]["nout"] == (B - dmax if k == 0 else B)
+        finally:
+            g.close()
+        assert t0s == [0] + [k * B - dmax for k in range(1, nblk)]
+        Dcat = np.concatenate(outs, axis=1)
+        st = O.external_stats(dtype, mu, sig)
+        T = B * nblk - dmax
+        Do = O.dedisperse(x, dtype, st, np.zeros((nchan, 1 + (B * nblk) // 256), np.uint8),
+                          np.zeros(B * nblk, np.uint8), 256, od, T)
+        assert Dcat.shape == Do.shape
+        if dtype == "u8":
+            assert np.array_equal(Dcat.astype(np.int64), Do)
+        else:
+            mass = _mass_all(x, dtype, st, np.zeros((nchan, 1 + (B * nblk) // 256), np.uint8),
+                             np.zeros(B * nblk, np.uint8), 256, od, T)
+            assert np.all(np.abs(Dcat - Do) <= TOL * mass)
+
+
+def test_candidate_capacity_and_truncation():
+    nchan = 64
+    dms = np.arange(16) * 2.0
+    x = synth.noise(nchan, 6000, 9101)
+    rfi = O.RfiParams(enable_channel=False, enable_spectrum=False)
+    g = GpuBeam(nchan, 398.0, 20.0, 51.2e-6, dms, "f32", rfi=rfi, nsigma=2.0, cap=10)
+    try:
+        r = g.run(x)
+        assert r["rc"] == tp.TP_EOVERFLOW and r["n_candidates"] > 10
+        assert len(r["candidates"]) == 10
+        c2, n2, rc2 = tp.tp_get_candidates(g.e, g.beam, 3)
+        assert len(c2) == 3 and n2 == r["n_candidates"]
+        assert np.array_equal(c2, r["candidates"][:3])
+    finally:
+        g.close()
+    od, dmax = O.delay_table(nchan, 398.0, 20.0, 51.2e-6, dms)
+    o = O.search_block(x, "f32", od, dmax, rfi=rfi, nsigma=2.0)
+    first = [(int(c["dm_idx"]), int(c["t_abs"])) for c in o["candidates"][:10]]
+    assert [(int(c["dm_idx"]), int(c["t_abs"])) for c in r["candidates"]] == first
+
+
+def test_device_buffer_push_and_errors():
+    import torch
+    nchan = 32
+    dms = np.arange(8) * 4.0
+    x = synth.noise(nchan, 4000, 9201)
+    rfi = O.RfiParams()
+    g = GpuBeam(nchan, 398.0, 20.0, 51.2e-6, dms, "f32", rfi=rfi)
+    try:
+        g.open(4000)
+        with pytest.raises(tp.TpError) as ei:
+            tp.tp_dedisperse(g.e, g.beam)
+        assert ei.value.code == tp.TP_ENOTREADY
+        with pytest.raises(tp.TpError) as ei:
+            tp.tp_push_block(g.e, g.beam, x[:, :10].copy())
+        assert ei.value.code == tp.TP_EINVAL
+        xt = torch.from_numpy(x).cuda()
+        tp.tp_push_block(g.e, g.beam, xt)
+        with pytest.raises(tp.TpError) as ei:
+            tp.tp_push_block(g.e, g.beam, xt)
+        assert ei.value.code == tp.TP_EBUSY
+        tp.tp_dedisperse(g.e, g.beam)
+        tp.tp_detect(g.e, g.beam)
+        c, n, rc = tp.tp_get_candidates(g.e, g.beam, 100)
+        D = tp.tp_get_series(g.e, g.beam, ndm=8)
+    finally:
+        g.close()
+    r2, o, od = run_both(x, "f32", nchan, 398.0, 20.0, 51.2e-6, dms, rfi)
+    assert np.array_equal(D, r2["D"])
+
+
+def test_admission_by_footprint():
+    e = tp.tp_engine_create(0, hbm_budget_bytes=64 << 20)
+    try:
+        p = tp.tp_create_plan(e, 1024, 398.0, 20.0, 51.2e-6, np.arange(64) * 1.0, "f32")
+        need = tp.tp_beam_footprint(p, 32768, 1000)
+        assert need > 64 << 20
+        with pytest.raises(tp.TpError) as ei:
+            tp.tp_beam_open(e, p, 32768, 1000)
+        assert ei.value.code == tp.TP_EADMIT
+        used, budget = tp.tp_engine_memory(e)
+        assert used < budget == 64 << 20
+        b = tp.tp_beam_open(e, p, 4000, 10)
+        tp.tp_beam_close(e, b)
+        tp.tp_plan_destroy(p)
+    finally:
+        tp.tp_engine_destroy(e)
