@@ -1,23 +1,27 @@
-// A4-A5: substitution of flagged samples and brute-force incoherent
-// dedispersion (Sec. 2.2.2, delays of Eq. 1):
+// A5: brute-force incoherent dedispersion (Sec. 2.2.2, delays of Eq. 1)
 //
 //   D[d][t] = sum_{c=0}^{nchan-1} y[c][t + delay[d][c]],   0 <= t < T,
-//   y[c][u] = 0 where (c, u) is flagged, else x[c][u] - b_c.
 //
-// One CTA owns a tile of up to 32 consecutive DM trials x 512 output samples.
-// It walks the channels in order, 8 at a time: the samples a channel
-// contributes to the tile, [t0 + delay[d_first][c], t0 + 512 + delay[d_last][c]),
-// are staged once into shared memory with the bandpass subtracted and the
-// flags applied (y is never written to HBM), and then every DM of the tile reads
-// its shifted 512-sample window from that copy.  Each (d, t) accumulates its
-// channels in index order: in FP32 for float data (binary16 / bfloat16 are
-// widened exactly), in int32 for 8-bit data (exact).
+// over the substituted, bandpass-corrected series y written by the A3/A4
+// kernel (FP32; exact small integers for 8-bit data).
 //
-// Warp w holds DMs w, w + 8, w + 16, w + 24 of the tile; lane l holds samples
-// t0 + l + 32 s, s < 16, so every shared-memory read of a warp is 32
-// consecutive words (conflict-free) and every store of D is a coalesced
-// 128-byte line.  The epilogue writes D and per-(DM, time-tile) sums of D and
-// D^2 for the series statistics of A6.
+// Work decomposition.  A CTA owns a tile of consecutive DM trials (up to 8
+// groups of K) x TT = 32 S output samples; warp w owns group w, lane l owns
+// the S consecutive outputs t0 + l S .. t0 + l S + S - 1 of each of the K DMs.
+// The CTA walks the channels in order, NC per pipeline stage: for every
+// channel one elected thread copies the samples the tile needs,
+// [t0 + delay[d_first][c], t0 + TT + delay[d_last][c]) rounded out to 16 B,
+// from global into shared memory with cp.async.bulk, completing on an
+// mbarrier (NSTAGE stages in flight).  The consumer warps then load, per lane,
+// a register window of S + spread + 4 consecutive samples with 128-bit shared
+// loads and add it into the K x S accumulators at each DM's offset inside the
+// window.  The offsets are warp-uniform run-time values, so each DM selects an
+// unrolled add sequence through a switch over 0..OMAX: every sample loaded
+// from shared memory feeds up to K adds from registers.  Each (d, t) adds its
+// channels in index order in FP32.
+//
+// The epilogue writes D (FP32, or int32 for 8-bit data, exact) and per
+// (DM, time tile) sums of D and D^2 for the series statistics of A6.
 #include <cstdint>
 
 #include "tp_common.cuh"
@@ -27,203 +31,298 @@ namespace tp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCB = 8;                          // channels per stage
-constexpr int kSlot = kTileT + kMaxOverhang;    // staged samples per channel
-constexpr int kPerLane = kTileT / 32;           // outputs per lane per DM
-constexpr int kDmPerWarp = kMaxTileDm / 8;
+constexpr int kWarps = 8;
+constexpr int kNC = 4;                 // channels per pipeline stage
+constexpr int kStages = 4;             // pipeline depth
+constexpr long long kSpinLimit = 1LL << 24;  // bounded mbarrier waits
 
-template <int DT>
-__device__ __forceinline__ float load_f(const void* x, int64_t i);
-template <>
-__device__ __forceinline__ float load_f<TP_F32>(const void* x, int64_t i) {
-  return __ldg(static_cast<const float*>(x) + i);
-}
-template <>
-__device__ __forceinline__ float load_f<TP_F16>(const void* x, int64_t i) {
-  unsigned short h = __ldg(static_cast<const unsigned short*>(x) + i);
-  float f;
-  asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
-  return f;
-}
-template <>
-__device__ __forceinline__ float load_f<TP_BF16>(const void* x, int64_t i) {
-  unsigned short h = __ldg(static_cast<const unsigned short*>(x) + i);
-  return __uint_as_float((unsigned)h << 16);
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-template <int DT>
-struct Acc {
-  using T = float;
-};
-template <>
-struct Acc<TP_U8> {
-  using T = int;
-};
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
 
-template <int DT>
-__device__ __forceinline__ typename Acc<DT>::T corrected(const DedispArgs& a, int c, int64_t g,
-                                                         bool check, float mh, float ml, int b) {
-  bool f = false;
-  if (check) {
-    const bool chunk = a.chan_nflag[c] != 0 && a.chunk_flag[(int64_t)c * a.nchunk + g / a.W];
-    const bool spec = (a.spec_bits[g >> 5] >> (g & 31)) & 1u;
-    f = chunk || spec;
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int S, int L, int O>
+__device__ __forceinline__ void add_at(float (&acc)[S], const float (&w)[L]) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) acc[s] += w[O + s];
+}
+
+#define TP_CASE(o)                                       \
+  case (o):                                              \
+    if constexpr ((o) <= OMAX) add_at<S, L, (o)>(acc, w); \
+    break;
+#define TP_CASE8(b) \
+  TP_CASE(b + 0) TP_CASE(b + 1) TP_CASE(b + 2) TP_CASE(b + 3) TP_CASE(b + 4) TP_CASE(b + 5) TP_CASE(b + 6) TP_CASE(b + 7)
+
+// acc[s] += w[o + s] for a warp-uniform o in [0, OMAX] (OMAX <= 63).
+template <int S, int L, int OMAX>
+__device__ __forceinline__ void add_shifted(int o, float (&acc)[S], const float (&w)[L]) {
+  static_assert(OMAX < 64, "offset range");
+  switch (o) {
+    TP_CASE8(0) TP_CASE8(8) TP_CASE8(16) TP_CASE8(24) TP_CASE8(32) TP_CASE8(40) TP_CASE8(48) TP_CASE8(56)
+    default: break;
   }
-  if constexpr (DT == TP_U8) {
-    const int v = __ldg(static_cast<const unsigned char*>(a.x) + (int64_t)c * a.pitch + g);
-    return f ? 0 : v - b;
-  } else {
-    const float v = load_f<DT>(a.x, (int64_t)c * a.pitch + g);
-    return f ? 0.f : (v - mh) - ml;
-  }
 }
+#undef TP_CASE8
+#undef TP_CASE
 
-template <int DT>
-__global__ void __launch_bounds__(kThreads, 2) dedisperse_kernel(DedispArgs a) {
-  using AT = typename Acc<DT>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  AT* sy = reinterpret_cast<AT*>(smem_raw);                   // [2][kCB][kSlot]
-  int* soff = reinterpret_cast<int*>(sy + 2 * kCB * kSlot);   // [2][kCB][kMaxTileDm]
+template <int K, int S, int OMAX>
+struct Shape {
+  static constexpr int TT = 32 * S;                        // output samples per tile
+  static constexpr int L = ((S + OMAX + 1) + 3) / 4 * 4;   // register window
+  static constexpr int ROW = (TT + kMaxOverhang + OMAX + 8 + 31) / 32 * 32;  // staged floats per channel
+  static constexpr size_t smem = sizeof(float) * kStages * kNC * ROW + 16 * kStages;
+};
+
+template <int K, int S, int OMAX, bool kInt>
+__global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
+  using Sh = Shape<K, S, OMAX>;
+  constexpr int TT = Sh::TT, L = Sh::L, ROW = Sh::ROW;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* srow = reinterpret_cast<float*>(smem_raw);                                    // [kStages][kNC][ROW]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(float) * kStages * kNC * ROW);
 
   const int tile = blockIdx.x % a.ntiles;
   const int tt = blockIdx.x / a.ntiles;
   const DmTile dt = a.tiles[tile];
-  const int64_t t0 = (int64_t)tt * kTileT;
+  const int64_t t0 = (int64_t)tt * TT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool any_spec = *a.spec_nflag != 0;
+  const int nchan = a.nchan;
+  const int32_t* __restrict__ delay = a.delay;
+  const int d_last = dt.d0 + dt.nd - 1;
+  const int dw0 = dt.d0 + warp * K;             // first DM of this warp's group
+  const bool warp_live = warp * K < dt.nd;
+  const int nstage = (nchan + kNC - 1) / kNC;
 
-  AT acc[kDmPerWarp][kPerLane];
-#pragma unroll
-  for (int i = 0; i < kDmPerWarp; ++i)
-#pragma unroll
-    for (int s = 0; s < kPerLane; ++s) acc[i][s] = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 
-  auto stage = [&](int cbase, int buf) {
-    AT* dst = sy + buf * kCB * kSlot;
-    int* off = soff + buf * kCB * kMaxTileDm;
-    for (int i = threadIdx.x; i < kCB * kMaxTileDm; i += kThreads) {
-      const int ci = i / kMaxTileDm, j = i % kMaxTileDm;
-      const int c = cbase + ci;
-      int v = 0;
-      if (c < a.nchan && j < dt.nd)
-        v = a.delay[(int64_t)(dt.d0 + j) * a.nchan + c] - a.delay[(int64_t)dt.d0 * a.nchan + c];
-      off[i] = v;
-    }
-    for (int ci = 0; ci < kCB; ++ci) {
-      const int c = cbase + ci;
-      if (c >= a.nchan) break;
-      const int lo = a.delay[(int64_t)dt.d0 * a.nchan + c];
-      const int hi = a.delay[(int64_t)(dt.d0 + dt.nd - 1) * a.nchan + c];
-      const int span = kTileT + hi - lo;
-      const int64_t base = t0 + lo;
-      const bool check = any_spec || a.chan_nflag[c] != 0;
-      float mh = 0.f, ml = 0.f;
-      int b = 0;
-      if constexpr (DT == TP_U8) {
-        b = a.bint[c];
-      } else {
-        mh = a.mu_hi[c];
-        ml = a.mu_lo[c];
-      }
-      AT* row = dst + ci * kSlot;
-      for (int u = threadIdx.x; u < span; u += kThreads) {
-        const int64_t g = base + u;
-        row[u] = g < a.nsamp ? corrected<DT>(a, c, g, check, mh, ml, b) : AT(0);
+  // Producer: stage i copies channels [i kNC, i kNC + kNC) into buffer i % kStages.
+  auto produce = [&](int i) {
+    const int buf = i % kStages;
+    const int cb = i * kNC;
+    unsigned total = 0;
+    unsigned bytes[kNC];
+    const float* src[kNC];
+#pragma unroll
+    for (int ci = 0; ci < kNC; ++ci) {
+      const int c = cb + ci;
+      bytes[ci] = 0;
+      src[ci] = nullptr;
+      if (c < nchan) {
+        const int lo = delay[(int64_t)dt.d0 * nchan + c];
+        const int hi = delay[(int64_t)d_last * nchan + c];
+        const int64_t base = (t0 + lo) & ~int64_t(3);
+        const int64_t end = t0 + TT + hi + 4;
+        const int64_t n = ((end - base) + 3) & ~int64_t(3);
+        bytes[ci] = (unsigned)(n * 4);
+        src[ci] = a.y + (int64_t)c * a.ypitch + base;
+        total += bytes[ci];
       }
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(&bars[buf], total);
+#pragma unroll
+    for (int ci = 0; ci < kNC; ++ci)
+      if (bytes[ci]) bulk_g2s(srow + (buf * kNC + ci) * ROW, src[ci], bytes[ci], &bars[buf]);
   };
 
-  stage(0, 0);
-  __syncthreads();
-  int buf = 0;
-  for (int cb = 0; cb < a.nchan; cb += kCB, buf ^= 1) {
-    if (cb + kCB < a.nchan) stage(cb + kCB, buf ^ 1);
-    const AT* src = sy + buf * kCB * kSlot;
-    const int* off = soff + buf * kCB * kMaxTileDm;
-    const int nc = a.nchan - cb < kCB ? a.nchan - cb : kCB;
-    for (int ci = 0; ci < nc; ++ci) {
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kStages && i < nstage; ++i) produce(i);
+
+  float acc[K][S];
 #pragma unroll
-      for (int i = 0; i < kDmPerWarp; ++i) {
-        const int slot = warp + 8 * i;
-        if (slot < dt.nd) {
-          const AT* r = src + ci * kSlot + off[ci * kMaxTileDm + slot] + lane;
+  for (int j = 0; j < K; ++j)
 #pragma unroll
-          for (int s = 0; s < kPerLane; ++s) acc[i][s] += r[32 * s];
-        }
+    for (int s = 0; s < S; ++s) acc[j][s] = 0.f;
+
+  bool failed = false;
+  for (int i = 0; i < nstage; ++i) {
+    const int buf = i % kStages;
+    const int cb = i * kNC;
+    // delays of this stage's channels for the warp's DMs (issued before the wait)
+    int dv = 0;
+    {
+      const int ci = lane / (K + 1), j = lane % (K + 1);
+      const int c = cb + ci;
+      if (ci < kNC && c < nchan) {
+        const int d = j < K ? (dw0 + j <= d_last ? dw0 + j : d_last) : dt.d0;
+        dv = delay[(int64_t)d * nchan + c];
       }
     }
-    __syncthreads();
+    bool ready = false;
+    for (long long spin = 0; spin < kSpinLimit; ++spin)
+      if (mbar_try_wait(&bars[buf], (unsigned)((i / kStages) & 1))) {
+        ready = true;
+        break;
+      }
+    const int nc = nchan - cb < kNC ? nchan - cb : kNC;
+    if (ready && warp_live) {
+      for (int ci = 0; ci < nc; ++ci) {
+        const int lo = __shfl_sync(0xffffffffu, dv, ci * (K + 1) + K);
+        const int dw = __shfl_sync(0xffffffffu, dv, ci * (K + 1));
+        const int64_t base = (t0 + lo) & ~int64_t(3);
+        const int aw = (int)(t0 + dw - base);
+        int o[K];
+        int omax = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          o[j] = (aw & 3) + __shfl_sync(0xffffffffu, dv, ci * (K + 1) + j) - dw;
+          omax = o[j] > omax ? o[j] : omax;
+        }
+        const float* r = srow + (buf * kNC + ci) * ROW + lane * S + (aw & ~3);
+        const int nq = (S + omax + 3) >> 2;
+        float w[L];
+#pragma unroll
+        for (int q = 0; q < L / 4; ++q) {
+          if (q < nq) {
+            const float4 v = *reinterpret_cast<const float4*>(r + 4 * q);
+            w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
+          } else {
+            w[4 * q] = w[4 * q + 1] = w[4 * q + 2] = w[4 * q + 3] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) add_shifted<S, L, OMAX>(o[j], acc[j], w);
+      }
+    }
+    failed = __syncthreads_or(!ready) != 0;
+    if (failed) {
+      // let the copies already issued land (bounded) before the CTA exits
+      if (threadIdx.x == 0) {
+        for (int k = i + 1; k < nstage && k < i + kStages; ++k)
+          for (long long spin = 0; spin < kSpinLimit; ++spin)
+            if (mbar_try_wait(&bars[k % kStages], (unsigned)((k / kStages) & 1))) break;
+        atomicExch(a.status, TP_ETIMEOUT);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && i + kStages < nstage) produce(i + kStages);
   }
 
-  // epilogue: D and per-tile row sums
+  // epilogue
+  if (!warp_live) return;
 #pragma unroll
-  for (int i = 0; i < kDmPerWarp; ++i) {
-    const int slot = warp + 8 * i;
-    if (slot >= dt.nd) continue;
-    const int d = dt.d0 + slot;
-    AT* Drow = static_cast<AT*>(a.D) + (int64_t)d * a.dpitch;
-    if constexpr (DT == TP_U8) {
+  for (int j = 0; j < K; ++j) {
+    const int d = dw0 + j;
+    if (d > d_last) break;
+    const int64_t tl = t0 + (int64_t)lane * S;
+    if constexpr (kInt) {
+      int* Drow = static_cast<int*>(a.D) + (int64_t)d * a.dpitch;
       long long s1 = 0, s2 = 0;
 #pragma unroll
-      for (int s = 0; s < kPerLane; ++s) {
-        const int64_t t = t0 + lane + 32 * s;
-        if (t < a.nout) {
-          Drow[t] = acc[i][s];
-          s1 += acc[i][s];
-          s2 += (long long)acc[i][s] * acc[i][s];
+      for (int s = 0; s < S; ++s) {
+        const int v = __float2int_rn(acc[j][s]);
+        if (tl + s < a.nout) {
+          Drow[tl + s] = v;
+          s1 += v;
+          s2 += (long long)v * v;
         }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
       }
-      if (lane == 0)
-        static_cast<longlong2*>(a.row_part)[(int64_t)d * a.ntt + tt] = make_longlong2(s1, s2);
+      if (lane == 0) static_cast<longlong2*>(a.row_part)[(int64_t)d * a.ntt + tt] = make_longlong2(s1, s2);
     } else {
+      float* Drow = static_cast<float*>(a.D) + (int64_t)d * a.dpitch;
       float s1 = 0.f, s2 = 0.f;
+      if (tl + S <= a.nout) {
 #pragma unroll
-      for (int s = 0; s < kPerLane; ++s) {
-        const int64_t t = t0 + lane + 32 * s;
-        if (t < a.nout) {
-          Drow[t] = acc[i][s];
-          s1 += acc[i][s];
-          s2 += acc[i][s] * acc[i][s];
+        for (int s = 0; s < S; s += 4)
+          *reinterpret_cast<float4*>(Drow + tl + s) =
+              make_float4(acc[j][s], acc[j][s + 1], acc[j][s + 2], acc[j][s + 3]);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          s1 += acc[j][s];
+          s2 += acc[j][s] * acc[j][s];
         }
+      } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+          if (tl + s < a.nout) {
+            Drow[tl + s] = acc[j][s];
+            s1 += acc[j][s];
+            s2 += acc[j][s] * acc[j][s];
+          }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
       }
       if (lane == 0)
-        static_cast<double2*>(a.row_part)[(int64_t)d * a.ntt + tt] =
-            make_double2((double)s1, (double)s2);
+        static_cast<double2*>(a.row_part)[(int64_t)d * a.ntt + tt] = make_double2((double)s1, (double)s2);
     }
   }
 }
 
-template <int DT>
-cudaError_t launch_t(const DedispArgs& a, cudaStream_t s) {
-  using AT = typename Acc<DT>::T;
-  const size_t smem = sizeof(AT) * 2 * kCB * kSlot + sizeof(int) * 2 * kCB * kMaxTileDm;
-  cudaError_t e = cudaFuncSetAttribute(dedisperse_kernel<DT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+template <int K, int S, int OMAX>
+cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
+  using Sh = Shape<K, S, OMAX>;
   const long long grid = (long long)a.ntiles * a.ntt;
   if (grid <= 0 || grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-  dedisperse_kernel<DT><<<(unsigned)grid, kThreads, smem, s>>>(a);
+  cudaError_t e;
+  if (a.dtype == TP_U8) {
+    e = cudaFuncSetAttribute(dedisperse_kernel<K, S, OMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Sh::smem);
+    if (e != cudaSuccess) return e;
+    dedisperse_kernel<K, S, OMAX, true><<<(unsigned)grid, kThreads, Sh::smem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(dedisperse_kernel<K, S, OMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Sh::smem);
+    if (e != cudaSuccess) return e;
+    dedisperse_kernel<K, S, OMAX, false><<<(unsigned)grid, kThreads, Sh::smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
+// Kernel shapes: (DMs per warp K, outputs per lane S, max in-window offset).
+const KernelShape kShapes[kNumShapes] = {
+    {4, 20, 36},  // adjacent DMs within 33 samples of each other
+    {2, 28, 36},
+    {1, 28, 4},
+};
+
+int shape_tile_t(int shape) { return 32 * kShapes[shape].S; }
+
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
-  switch (a.dtype) {
-    case TP_U8: return launch_t<TP_U8>(a, s);
-    case TP_F16: return launch_t<TP_F16>(a, s);
-    case TP_BF16: return launch_t<TP_BF16>(a, s);
-    default: return launch_t<TP_F32>(a, s);
+  switch (a.shape) {
+    case 0: return launch_shape<4, 20, 36>(a, s);
+    case 1: return launch_shape<2, 28, 36>(a, s);
+    default: return launch_shape<1, 28, 4>(a, s);
   }
 }
 

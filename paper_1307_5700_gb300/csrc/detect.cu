@@ -4,14 +4,19 @@
 //   mu_d = sum_t D / T,  sigma_d^2 = sum_t D^2 / T - mu_d^2   (population)
 //   candidate (d, t)  <=>  sigma_d > 0  and  D[d][t] - mu_d >= nsigma * sigma_d
 //
-// The sums come from the per-(DM, time-tile) partials written by the
-// dedispersion epilogue (exact int64 for 8-bit data).  Compaction is
-// deterministic and ordered by (d, t) without a sort:
-//   count : one CTA per (d, 4096 samples) evaluates the predicate, writes one
-//           hit bit per sample and the CTA's hit count;
-//   scan  : one CTA turns the counts into offsets (row-major in (d, t-block));
+// row_stats (one CTA per DM) folds the per-(DM, time-tile) partial sums of the
+// dedispersion epilogue (exact int64 for 8-bit data) into mu_d, sigma_d and
+// turns the binary64 predicate into an equivalent threshold on the stored
+// value: the predicate is monotone in D, so "D >= smallest passing value" is
+// the same test, made once per row instead of once per sample.
+// Compaction is deterministic and ordered by (d, t) without a sort:
+//   count : one CTA per (d, 4096 samples) writes one hit bit per sample and
+//           its hit count;
+//   scan  : one CTA turns the counts into offsets (row-major in (d, block));
 //   write : each CTA ranks its hits in t order (ballots + a 128-entry scan) and
 //           writes records at offset + rank, keeping those below the capacity.
+#include <cfloat>
+#include <climits>
 #include <cstdint>
 
 #include "tp_common.cuh"
@@ -24,9 +29,10 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPer = kDetectT / kThreads;  // 16 samples per thread
 
-// Row statistics from the partials; every CTA of the row computes the same
-// values in the same order.
-__device__ void row_stats(const DetectArgs& a, int d, double* mu, double* sigma) {
+__device__ __forceinline__ bool passes(double v, double mu, double thr) { return __dsub_rn(v, mu) >= thr; }
+
+__global__ void __launch_bounds__(kThreads) row_stats_kernel(DetectArgs a) {
+  const int d = blockIdx.x;
   __shared__ double s_a[kThreads], s_b[kThreads];
   __shared__ long long s_ia[kThreads], s_ib[kThreads];
   if (a.is_int) {
@@ -63,6 +69,7 @@ __device__ void row_stats(const DetectArgs& a, int d, double* mu, double* sigma)
     }
     __syncthreads();
   }
+  if (threadIdx.x != 0) return;
   const double T = (double)a.nout;
   double m, var;
   if (a.is_int) {
@@ -72,39 +79,77 @@ __device__ void row_stats(const DetectArgs& a, int d, double* mu, double* sigma)
     m = __ddiv_rn(s_a[0], T);
     var = __dsub_rn(__ddiv_rn(s_b[0], T), __dmul_rn(m, m));
   }
-  *mu = m;
-  *sigma = __dsqrt_rn(var > 0.0 ? var : 0.0);
-  __syncthreads();
-}
-
-__device__ __forceinline__ double value_at(const DetectArgs& a, int d, int64_t t) {
-  if (a.is_int) return (double)static_cast<const int*>(a.D)[(int64_t)d * a.dpitch + t];
-  return (double)static_cast<const float*>(a.D)[(int64_t)d * a.dpitch + t];
+  const double sig = __dsqrt_rn(var > 0.0 ? var : 0.0);
+  a.row_mu[d] = m;
+  a.row_sigma[d] = sig;
+  const double thr = __dmul_rn(a.nsigma, sig);
+  if (!(sig > 0.0)) {  // nothing passes
+    a.row_thr_f[d] = __int_as_float(0x7f800000);  // +inf: no finite D reaches it
+    a.row_thr_i[d] = INT_MAX;
+    return;
+  }
+  // smallest float f with passes(f); the predicate is monotone in f
+  float f = (float)__dadd_rn(m, thr);
+  if (passes((double)f, m, thr)) {
+    for (int it = 0; it < 64; ++it) {
+      const float g = nextafterf(f, -FLT_MAX);
+      if (g == f || !passes((double)g, m, thr)) break;
+      f = g;
+    }
+  } else {
+    for (int it = 0; it < 64 && !passes((double)f, m, thr); ++it) f = nextafterf(f, FLT_MAX);
+  }
+  a.row_thr_f[d] = f;
+  // smallest int i with passes(i)
+  const double c = ceil(__dadd_rn(m, thr));
+  long long i = c > 2147483647.0 ? 2147483647LL : (c < -2147483648.0 ? -2147483648LL : (long long)c);
+  while (i > INT_MIN && passes((double)(i - 1), m, thr)) --i;
+  while (i < INT_MAX && !passes((double)i, m, thr)) ++i;
+  a.row_thr_i[d] = (int)i;
 }
 
 __global__ void __launch_bounds__(kThreads) detect_count(DetectArgs a) {
   const int d = blockIdx.y;
   const int64_t t0 = (int64_t)blockIdx.x * kDetectT;
-  double mu, sigma;
-  row_stats(a, d, &mu, &sigma);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.row_mu[d] = mu;
-    a.row_sigma[d] = sigma;
-  }
-  const double thr = __dmul_rn(a.nsigma, sigma);
-  const bool live = sigma > 0.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float tf = a.row_thr_f[d];
+  const int ti = a.row_thr_i[d];
   int cnt = 0;
-#pragma unroll 4
-  for (int j = 0; j < kPer; ++j) {
-    const int64_t t = t0 + (int64_t)j * kThreads + threadIdx.x;
-    bool hit = false;
-    if (live && t < a.nout) hit = __dsub_rn(value_at(a, d, t), mu) >= thr;
-    const unsigned bits = __ballot_sync(0xffffffffu, hit);
-    const int64_t word = (t0 >> 5) + j * kWarps + warp;
-    if (lane == 0 && word < a.hit_pitch) a.hit_bits[(int64_t)d * a.hit_pitch + word] = bits;
-    cnt += __popc(bits);
+  // thread handles 4 runs of 4 consecutive samples: t = t0 + 1024 r + 4 tid + e
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t tb = t0 + 1024 * r + 4 * threadIdx.x;
+    bool hit[4] = {false, false, false, false};
+    if (a.is_int) {
+      const int* row = static_cast<const int*>(a.D) + (int64_t)d * a.dpitch;
+      if (tb + 3 < a.nout) {
+        const int4 v = *reinterpret_cast<const int4*>(row + tb);
+        hit[0] = v.x >= ti, hit[1] = v.y >= ti, hit[2] = v.z >= ti, hit[3] = v.w >= ti;
+      } else {
+        for (int e = 0; e < 4; ++e) hit[e] = tb + e < a.nout && row[tb + e] >= ti;
+      }
+    } else {
+      const float* row = static_cast<const float*>(a.D) + (int64_t)d * a.dpitch;
+      if (tb + 3 < a.nout) {
+        const float4 v = *reinterpret_cast<const float4*>(row + tb);
+        hit[0] = v.x >= tf, hit[1] = v.y >= tf, hit[2] = v.z >= tf, hit[3] = v.w >= tf;
+      } else {
+        for (int e = 0; e < 4; ++e) hit[e] = tb + e < a.nout && row[tb + e] >= tf;
+      }
+    }
+    // bit (t - t0) of the CTA's 128 words; 4 consecutive samples per lane
+    const unsigned nib = (unsigned)hit[0] | ((unsigned)hit[1] << 1) | ((unsigned)hit[2] << 2) |
+                         ((unsigned)hit[3] << 3);
+    // lanes 8k..8k+7 fill one 32-bit word
+    unsigned wv = nib << (4 * (lane & 7));
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) wv |= __shfl_xor_sync(0xffffffffu, wv, o);
+    const int64_t word = (t0 + 1024 * r + 4 * (threadIdx.x & ~7)) >> 5;
+    if ((lane & 7) == 0 && word < a.hit_pitch) a.hit_bits[(int64_t)d * a.hit_pitch + word] = wv;
+    cnt += __popc(nib);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   __shared__ int s_cnt[kWarps];
   if (lane == 0) s_cnt[warp] = cnt;
   __syncthreads();
@@ -139,6 +184,7 @@ __global__ void __launch_bounds__(1024) detect_scan(DetectArgs a, int nblk) {
   if (threadIdx.x == 1023) *a.n_total = s[1023];
 }
 
+// Thread (warp w, lane l) owns hit word j*8 + w of the CTA (words in t order).
 __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
   const int d = blockIdx.y;
   const int64_t t0 = (int64_t)blockIdx.x * kDetectT;
@@ -183,8 +229,9 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
       const uint32_t rank = s_pre[j * kWarps + warp] + __popc(w & ((1u << lane) - 1u));
       const uint64_t pos = base + rank;
       if (pos < (uint64_t)a.cap) {
-        const int64_t t = t0 + (int64_t)j * kThreads + threadIdx.x;
-        const double v = value_at(a, d, t);
+        const int64_t t = t0 + 32 * ((int64_t)j * kWarps + warp) + lane;
+        const double v = a.is_int ? (double)static_cast<const int*>(a.D)[(int64_t)d * a.dpitch + t]
+                                  : (double)static_cast<const float*>(a.D)[(int64_t)d * a.dpitch + t];
         tp_candidate r;
         r.beam = a.beam;
         r.dm_idx = d;
@@ -200,9 +247,12 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
 }  // namespace
 
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s) {
+  row_stats_kernel<<<a.ndm, kThreads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)a.nblk_t, (unsigned)a.ndm);
   detect_count<<<grid, kThreads, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   detect_scan<<<1, 1024, 0, s>>>(a, a.nblk_t * a.ndm);
   e = cudaGetLastError();

@@ -99,10 +99,15 @@ struct Beam {
   uint32_t* spec_bits = nullptr;
   int* spec_nflag = nullptr;
   double* spec_thr = nullptr;
+  float* y = nullptr;
+  int64_t ypitch = 0;
+  int* status = nullptr;
   void* D = nullptr;
   void* row_part = nullptr;
   double* row_mu = nullptr;
   double* row_sigma = nullptr;
+  float* row_thr_f = nullptr;
+  int* row_thr_i = nullptr;
   uint32_t* hit_bits = nullptr;
   uint32_t* blk_count = nullptr;
   uint32_t* blk_off = nullptr;
@@ -117,6 +122,7 @@ struct Beam {
   int64_t t0_abs = 0;
   int64_t pushed = 0;
   BeamState state = kEmpty;
+  int ntt = 0;
   bool have_ext = false;
   double ext_thr = 0.0;
   // stage timing (tp_set_profiling)
@@ -143,6 +149,7 @@ struct tp_plan {
   std::vector<int32_t> h_delay;
   std::vector<DmTile> h_tiles;
   DmTile* d_tiles = nullptr;
+  int shape = 0;
   int users = 0;
   size_t bytes = 0;
 };
@@ -182,25 +189,52 @@ int check_rfi(const tp_rfi_params& r) {
   return TP_OK;
 }
 
-// Greedy DM tiling: consecutive DMs while the tile holds < kMaxTileDm trials
-// and the spread of any channel's delay inside the tile stays <= kMaxOverhang.
-std::vector<DmTile> make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan) {
-  std::vector<DmTile> tiles;
+// Largest delay spread over channels between DM trials d0 and d1 (d0 <= d1;
+// delays grow with DM for every channel).
+int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
+  int s = 0;
+  const int32_t* a = &delay[(size_t)d0 * nchan];
+  const int32_t* b = &delay[(size_t)d1 * nchan];
+  for (int c = 0; c < nchan; ++c) s = std::max(s, b[c] - a[c]);
+  return s;
+}
+
+// Tiling for the dedispersion kernel: pick the first register shape whose DM
+// groups (K consecutive trials) all fit its in-window offset range, then pack
+// up to kMaxGroups consecutive groups into a CTA tile while the tile's delay
+// spread stays within kMaxOverhang.
+int make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int forced_shape,
+               std::vector<DmTile>* tiles) {
+  int shape = -1;
+  for (int sh = 0; sh < kNumShapes; ++sh) {
+    if (forced_shape >= 0 && sh != forced_shape) continue;
+    const int K = kShapes[sh].K;
+    bool ok = true;
+    for (int d0 = 0; d0 < ndm && ok; d0 += K) {
+      const int d1 = std::min(d0 + K, ndm) - 1;
+      ok = spread(delay, nchan, d0, d1) + 3 <= kShapes[sh].OMAX;
+    }
+    if (ok) {
+      shape = sh;
+      break;
+    }
+  }
+  if (shape < 0) return -1;
+  const int K = kShapes[shape].K;
+  tiles->clear();
   int d0 = 0;
   while (d0 < ndm) {
-    int nd = 1;
-    while (nd < kMaxTileDm && d0 + nd < ndm) {
-      int spread = 0;
-      const int32_t* a = &delay[(size_t)d0 * nchan];
-      const int32_t* b = &delay[(size_t)(d0 + nd) * nchan];
-      for (int c = 0; c < nchan; ++c) spread = std::max(spread, b[c] - a[c]);
-      if (spread > kMaxOverhang) break;
-      ++nd;
+    int ng = 1;
+    while (ng < kMaxGroups && d0 + ng * K < ndm) {
+      const int d1 = std::min(d0 + (ng + 1) * K, ndm) - 1;
+      if (spread(delay, nchan, d0, d1) > kMaxOverhang) break;
+      ++ng;
     }
-    tiles.push_back(DmTile{d0, nd});
+    const int nd = std::min(ng * K, ndm - d0);
+    tiles->push_back(DmTile{d0, nd});
     d0 += nd;
   }
-  return tiles;
+  return shape;
 }
 
 Beam* get_beam(tp_engine* e, int id) {
@@ -220,7 +254,8 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   const int64_t pitch = (int64_t)round_up((size_t)nmax * es, 256) / (int64_t)es;
   const int W = p->rfi.chunk_width;
   const int nchunk = (int)((nmax + W - 1) / W);
-  const int ntt = (int)((B + kTileT - 1) / kTileT);
+  const int ntt = (int)((B + kMinTileT - 1) / kMinTileT);
+  const int64_t ypitch = (int64_t)round_up((size_t)nmax + kMaxTileT + 64, 64);
   const int nblk = (int)((B + kDetectT - 1) / kDetectT);
   const int64_t hit_pitch = (B + 31) / 32;
   const int64_t dpitch = (int64_t)round_up((size_t)B, 64);
@@ -230,6 +265,7 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   b->nblk_max = nblk;
   b->hit_pitch = hit_pitch;
   b->dpitch = dpitch;
+  b->ypitch = ypitch;
   const size_t nc = (size_t)p->nchan, nd = (size_t)p->ndm;
   auto add = [&](void** ptr, size_t bytes) {
     bytes = round_up(std::max<size_t>(bytes, 1), 256);
@@ -252,10 +288,14 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->spec_bits, (size_t)((nmax + 31) / 32) * 4);
   add((void**)&b->spec_nflag, 4);
   add((void**)&b->spec_thr, 8);
+  add((void**)&b->y, nc * (size_t)ypitch * 4);
+  add((void**)&b->status, 4);
   add(&b->D, nd * (size_t)dpitch * 4);
   add(&b->row_part, nd * (size_t)ntt * 16);
   add((void**)&b->row_mu, nd * 8);
   add((void**)&b->row_sigma, nd * 8);
+  add((void**)&b->row_thr_f, nd * 4);
+  add((void**)&b->row_thr_i, nd * 4);
   add((void**)&b->hit_bits, nd * (size_t)hit_pitch * 4);
   add((void**)&b->blk_count, nd * (size_t)nblk * 4);
   add((void**)&b->blk_off, nd * (size_t)nblk * 4);
@@ -363,33 +403,26 @@ int issue_dedisperse(tp_engine* e, Beam* b) {
   cudaStream_t s = beam_stream(e, b);
   RfiArgs ra = rfi_args(p, b);
   prof_record(e, b, 2, s);
-  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->ext_thr, s));
+  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->ext_thr, b->y, b->ypitch, s));
   prof_record(e, b, 3, s);
-  e->launches += 2 + (ra.enable_channel ? 1 : 0) + (ra.enable_spectrum ? 1 : 0);
+  e->launches += 4;
   DedispArgs da{};
-  da.x = b->win[b->cur];
-  da.pitch = b->pitch;
+  da.y = b->y;
+  da.ypitch = b->ypitch;
   da.nchan = p->nchan;
-  da.nsamp = b->nsamp_win;
   da.nout = b->nout;
   da.dtype = p->dtype;
-  da.W = ra.W;
-  da.nchunk = ra.nchunk;
   da.delay = p->d_delay;
   da.ndm = p->ndm;
   da.tiles = p->d_tiles;
   da.ntiles = (int)p->h_tiles.size();
-  da.ntt = (int)((b->nout + kTileT - 1) / kTileT);
-  da.mu_hi = b->mu_hi;
-  da.mu_lo = b->mu_lo;
-  da.bint = b->bint;
-  da.chunk_flag = b->chunk_flag;
-  da.chan_nflag = b->chan_nflag;
-  da.spec_bits = b->spec_bits;
-  da.spec_nflag = b->spec_nflag;
+  da.shape = p->shape;
+  da.ntt = (int)((b->nout + shape_tile_t(p->shape) - 1) / shape_tile_t(p->shape));
   da.D = b->D;
   da.dpitch = b->dpitch;
   da.row_part = b->row_part;
+  da.status = b->status;
+  b->ntt = da.ntt;
   TP_CUDA_TRY(launch_dedisperse(da, s));
   prof_record(e, b, 4, s);
   e->launches += 1;
@@ -408,12 +441,14 @@ int issue_detect(tp_engine* e, Beam* b) {
   a.nout = b->nout;
   a.is_int = p->dtype == TP_U8;
   a.row_part = b->row_part;
-  a.ntt = (int)((b->nout + kTileT - 1) / kTileT);
+  a.ntt = b->ntt;
   a.nsigma = p->nsigma;
   a.beam = b->id;
   a.t0_abs = b->t0_abs;
   a.row_mu = b->row_mu;
   a.row_sigma = b->row_sigma;
+  a.row_thr_f = b->row_thr_f;
+  a.row_thr_i = b->row_thr_i;
   a.hit_bits = b->hit_bits;
   a.hit_pitch = (b->nout + 31) / 32;
   a.blk_count = b->blk_count;
@@ -423,7 +458,7 @@ int issue_detect(tp_engine* e, Beam* b) {
   a.cap = b->cap;
   a.n_total = b->n_total;
   TP_CUDA_TRY(launch_detect(a, s));
-  e->launches += 3;
+  e->launches += 4;
   prof_record(e, b, 5, s);
   TP_CUDA_TRY(cudaEventRecord(b->ev_detect, s));
   b->state = kDetected;
@@ -590,7 +625,8 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
   int dmax = 0;
   for (int32_t v : p->h_delay) dmax = std::max(dmax, (int)v);
   p->max_delay = dmax;
-  p->h_tiles = make_tiles(p->h_delay, ndm, nchan);
+  p->shape = make_tiles(p->h_delay, ndm, nchan, -1, &p->h_tiles);
+  if (p->shape < 0) return fail(set_error(TP_EINVAL, "no kernel shape fits this DM list"));
   const size_t tb = p->h_tiles.size() * sizeof(DmTile);
   if ((ce = cudaMalloc(&p->d_tiles, tb)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(tiles)"));
   if ((ce = cudaMemcpy(p->d_tiles, p->h_tiles.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -674,7 +710,14 @@ int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capac
     b->allocs.push_back(ptr);
     *it.first = ptr;
   }
-  cudaError_t ce = cudaEventCreateWithFlags(&b->ev_detect, cudaEventDisableTiming);
+  cudaError_t ce = cudaMemset(b->y, 0, (size_t)p->nchan * b->ypitch * 4);
+  if (ce == cudaSuccess) ce = cudaMemset(b->status, 0, 4);
+  if (ce != cudaSuccess) {
+    free_beam(b);
+    delete b;
+    return cuda_error(ce, "cudaMemset");
+  }
+  ce = cudaEventCreateWithFlags(&b->ev_detect, cudaEventDisableTiming);
   if (ce != cudaSuccess) {
     free_beam(b);
     delete b;
@@ -847,6 +890,12 @@ int tp_get_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, int* n
   if (cap < 0 || (cap > 0 && !out)) return set_error(TP_EINVAL, "bad output buffer");
   DeviceGuard g(e->device);
   TP_CUDA_TRY(cudaEventSynchronize(b->ev_detect));
+  int status = 0;
+  TP_CUDA_TRY(cudaMemcpy(&status, b->status, 4, cudaMemcpyDeviceToHost));
+  if (status != 0) {
+    TP_CUDA_TRY(cudaMemset(b->status, 0, 4));
+    return set_error(status, "beam %d: a device-side wait gave up (status %d)", beam, status);
+  }
   unsigned long long tot = 0;
   TP_CUDA_TRY(cudaMemcpy(&tot, b->n_total, 8, cudaMemcpyDeviceToHost));
   const unsigned long long kept = std::min<unsigned long long>(tot, (unsigned long long)b->cap);

@@ -59,7 +59,40 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 }
 
 // Chunk sums (float data).  Writes chunk_sums[c][k] = {sum(x - p), sum((x - p)^2)}
-// and the channel statistics.
+// and the channel statistics.  When W is a multiple of 128 every lane reads
+// float-aligned quads (two per 256-sample sub-chunk, issued together).
+template <int DT>
+__device__ __forceinline__ void load4(const void* x, int64_t i, int64_t lim, float p, float (&e)[4],
+                                      bool (&ok)[4]) {
+  if (i + 3 < lim) {
+    if constexpr (DT == TP_F32) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(x) + i));
+      e[0] = v.x - p, e[1] = v.y - p, e[2] = v.z - p, e[3] = v.w - p;
+    } else {
+      const uint2 v = __ldg(reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(x) + i));
+      const unsigned short h[4] = {(unsigned short)(v.x & 0xffff), (unsigned short)(v.x >> 16),
+                                   (unsigned short)(v.y & 0xffff), (unsigned short)(v.y >> 16)};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float f;
+        if constexpr (DT == TP_F16)
+          asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h[r]));
+        else
+          f = __uint_as_float((unsigned)h[r] << 16);
+        e[r] = f - p;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) ok[r] = true;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      ok[r] = i + r < lim;
+      e[r] = ok[r] ? load_as_float<DT>(x, i + r) - p : 0.f;
+    }
+  }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2* chunk_sums) {
   const int c = blockIdx.x;
@@ -82,6 +115,7 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
   }
   __syncthreads();
   const float p = s_pivot;
+  const bool vec = (a.W % 128) == 0;
 
   double tot_s = 0.0, tot_q = 0.0;  // lane-0 accumulators of this warp
   for (int k = warp; k < a.nchunk; k += kWarps) {
@@ -91,10 +125,27 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
     for (int64_t sub = lo; sub < hi; sub += 256) {
       const int64_t sh = sub + 256 < hi ? sub + 256 : hi;
       float fs = 0.f, fq = 0.f;
-      for (int64_t t = sub + lane; t < sh; t += 32) {
-        const float e = load_as_float<DT>(a.x, row + t) - p;
-        fs += e;
-        fq += e * e;
+      if (vec) {
+        float e0[4], e1[4];
+        bool k0[4], k1[4];
+        load4<DT>(a.x, row + sub + 4 * lane, row + sh, p, e0, k0);
+        load4<DT>(a.x, row + sub + 128 + 4 * lane, row + sh, p, e1, k1);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          fs += e0[r];
+          fq += e0[r] * e0[r];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          fs += e1[r];
+          fq += e1[r] * e1[r];
+        }
+      } else {
+        for (int64_t t = sub + lane; t < sh; t += 32) {
+          const float e = load_as_float<DT>(a.x, row + t) - p;
+          fs += e;
+          fq += e * e;
+        }
       }
       fs = warp_sum_f(fs);
       fq = warp_sum_f(fq);
@@ -299,101 +350,174 @@ __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a,
   }
 }
 
-// Spectrum flags.  CTA = 256 consecutive samples; warp w sums channels
-// w, w + 8, ...; lane handles samples t0 + lane + 32 j, j < 8.
+// A3 + A4: spectrum flags and the substituted, bandpass-corrected series
+//   y[c][t] = 0 if chunk (c, t / W) or spectrum t is flagged, else x - b_c
+// (float data: (x - mu_hi) - mu_lo in FP32; 8-bit data: the exact integer
+// x - b_c, stored as FP32).  CTA = 32 consecutive samples (one flag word) x
+// every channel; thread (g = tid / 8, q = tid % 8) handles samples
+// t0 + 4q .. t0 + 4q + 3 of channels g, g + 32, ...  Pass 1 sums the corrected
+// samples of unflagged chunks over channels (FP32 runs of 8 channels folded
+// into FP64; exact integers for 8-bit data); pass 2 re-reads the tile (an L2
+// hit) and writes y.
 template <int DT>
-__global__ void __launch_bounds__(kThreads) spectrum_flags_kernel(RfiArgs a) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t t0 = (int64_t)blockIdx.x * 256;
-  constexpr bool kU8 = DT == TP_U8;
-  int kj[8];
-  bool vj[8];
+__device__ __forceinline__ void load_quad(const void* x, int64_t i, int64_t valid, float (&v)[4]) {
+  if (valid >= 4) {
+    if constexpr (DT == TP_F32) {
+      const float4 f = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(x) + i));
+      v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
+    } else if constexpr (DT == TP_U8) {
+      const unsigned w = __ldg(reinterpret_cast<const unsigned*>(static_cast<const unsigned char*>(x) + i));
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int64_t t = t0 + lane + 32 * j;
-    vj[j] = t < a.nsamp;
-    kj[j] = vj[j] ? (int)(t / a.W) : 0;
-  }
-  __shared__ double s_f[kWarps][256];
-  __shared__ long long s_i[kWarps][256];
-  if constexpr (!kU8) {
-    double acc[8];
-    float part[8];
+      for (int r = 0; r < 4; ++r) v[r] = (float)((w >> (8 * r)) & 0xffu);
+    } else {
+      const uint2 u = __ldg(reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(x) + i));
+      const unsigned short h[4] = {(unsigned short)(u.x & 0xffff), (unsigned short)(u.x >> 16),
+                                   (unsigned short)(u.y & 0xffff), (unsigned short)(u.y >> 16)};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.0, part[j] = 0.f;
-    int n = 0;
-    for (int c = warp; c < a.nchan; c += kWarps) {
-      const float mh = a.mu_hi[c], ml = a.mu_lo[c];
-      const int64_t row = (int64_t)c * a.pitch;
-      const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
-      const bool any = a.chan_nflag[c] != 0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (vj[j] && !(any && cf[kj[j]])) {
-          const float v = load_as_float<DT>(a.x, row + t0 + lane + 32 * j);
-          part[j] += (v - mh) - ml;
-        }
-      }
-      if (++n == 8) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] += (double)part[j], part[j] = 0.f;
-        n = 0;
+      for (int r = 0; r < 4; ++r) {
+        if constexpr (DT == TP_F16)
+          asm("cvt.f32.f16 %0, %1;" : "=f"(v[r]) : "h"(h[r]));
+        else
+          v[r] = __uint_as_float((unsigned)h[r] << 16);
       }
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) s_f[warp][lane + 32 * j] = acc[j] + (double)part[j];
   } else {
-    const bool ext = a.stats_mode == TP_STATS_EXTERNAL;
-    const long long N = a.nsamp;
-    int sx[8];
-    long long sS[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) sx[j] = 0, sS[j] = 0;
-    for (int c = warp; c < a.nchan; c += kWarps) {
-      const long long off = ext ? (long long)a.bint[c] : a.S[c];
-      const int64_t row = (int64_t)c * a.pitch;
-      const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
-      const bool any = a.chan_nflag[c] != 0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (vj[j] && !(any && cf[kj[j]])) {
-          sx[j] += (int)load_u8(a.x, row + t0 + lane + 32 * j);
-          sS[j] += off;
-        }
+    for (int r = 0; r < 4; ++r) {
+      if (r < valid) {
+        if constexpr (DT == TP_U8)
+          v[r] = (float)load_u8(x, i + r);
+        else
+          v[r] = load_as_float<DT>(x, i + r);
+      } else {
+        v[r] = 0.f;
       }
     }
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a, float* __restrict__ y,
+                                                                       int64_t ypitch) {
+  constexpr bool kU8 = DT == TP_U8;
+  const int tid = threadIdx.x;
+  const int g = tid >> 3, q = tid & 7;
+  const int64_t t0 = (int64_t)blockIdx.x * 32;
+  const int64_t tq = t0 + 4 * q;
+  const int64_t left = a.nsamp - tq;
+  const int valid = left >= 4 ? 4 : (left > 0 ? (int)left : 0);
+  int kk[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      s_i[warp][lane + 32 * j] = ext ? (long long)sx[j] - sS[j] : N * (long long)sx[j] - sS[j];
+  for (int r = 0; r < 4; ++r) kk[r] = r < valid ? (int)((tq + r) / a.W) : 0;
+  __shared__ double s_f[32][33];
+  __shared__ long long s_i[32][33];
+  __shared__ unsigned s_word;
+
+  if (a.enable_spectrum) {
+    if constexpr (!kU8) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      float part[4] = {0.f, 0.f, 0.f, 0.f};
+      int n = 0;
+      for (int c = g; c < a.nchan; c += 32) {
+        float v[4];
+        load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
+        const float mh = a.mu_hi[c], ml = a.mu_lo[c];
+        const bool any = a.chan_nflag[c] != 0;
+        const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (r < valid && !(any && cf[kk[r]])) part[r] += (v[r] - mh) - ml;
+        if (++n == 8) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[r] += (double)part[r], part[r] = 0.f;
+          n = 0;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) s_f[g][4 * q + r] = acc[r] + (double)part[r];
+    } else {
+      const bool ext = a.stats_mode == TP_STATS_EXTERNAL;
+      int sx[4] = {0, 0, 0, 0};
+      long long sS[4] = {0, 0, 0, 0};
+      for (int c = g; c < a.nchan; c += 32) {
+        float v[4];
+        load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
+        const long long off = ext ? (long long)a.bint[c] : a.S[c];
+        const bool any = a.chan_nflag[c] != 0;
+        const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (r < valid && !(any && cf[kk[r]])) {
+            sx[r] += (int)v[r];
+            sS[r] += off;
+          }
+      }
+      const long long N = a.nsamp;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) s_i[g][4 * q + r] = ext ? (long long)sx[r] - sS[r] : N * (long long)sx[r] - sS[r];
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const double thr = *a.spec_thr;
+      bool flag = false;
+      if (t0 + tid < a.nsamp) {
+        if constexpr (!kU8) {
+          double m = 0.0;
+          for (int w = 0; w < 32; ++w) m += s_f[w][tid];
+          flag = m > thr;
+        } else {
+          long long m = 0;
+          for (int w = 0; w < 32; ++w) m += s_i[w][tid];
+          flag = (double)m > thr;
+        }
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, flag);
+      if (tid == 0) {
+        s_word = bits;
+        if (t0 < a.nsamp) a.spec_bits[t0 >> 5] = bits;
+        if (bits) atomicAdd(a.spec_nflag, __popc(bits));
+      }
+    }
+  } else if (tid == 0) {
+    s_word = 0u;
+    if (t0 < a.nsamp) a.spec_bits[t0 >> 5] = 0u;
   }
   __syncthreads();
-  const int64_t t = t0 + threadIdx.x;
-  const double thr = *a.spec_thr;
-  bool flag = false;
-  if (t < a.nsamp) {
-    if (!kU8) {
-      double m = 0.0;
+  const unsigned word = s_word;
+  bool sflag[4];
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) m += s_f[w][threadIdx.x];
-      flag = m > thr;
+  for (int r = 0; r < 4; ++r) sflag[r] = (word >> (4 * q + r)) & 1u;
+
+  // pass 2: y
+  if (valid == 0) return;
+  for (int c = g; c < a.nchan; c += 32) {
+    float v[4];
+    load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
+    const bool any = a.chan_nflag[c] != 0;
+    const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
+    float o[4];
+    if constexpr (kU8) {
+      const float b = (float)a.bint[c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) o[r] = (sflag[r] || (any && cf[kk[r]])) ? 0.f : v[r] - b;
     } else {
-      long long m = 0;
+      const float mh = a.mu_hi[c], ml = a.mu_lo[c];
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) m += s_i[w][threadIdx.x];
-      flag = (double)m > thr;
+      for (int r = 0; r < 4; ++r) o[r] = (sflag[r] || (any && cf[kk[r]])) ? 0.f : (v[r] - mh) - ml;
     }
-  }
-  const unsigned bits = __ballot_sync(0xffffffffu, flag);
-  if (lane == 0) {
-    const int64_t word = (t0 >> 5) + warp;
-    if (word * 32 < a.nsamp) a.spec_bits[word] = bits;
-    if (bits) atomicAdd(a.spec_nflag, __popc(bits));
+    float* dst = y + (int64_t)c * ypitch + tq;
+    if (valid == 4) {
+      *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+      for (int r = 0; r < valid; ++r) dst[r] = o[r];
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, cudaStream_t s) {
+cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, float* y, int64_t ypitch,
+                       cudaStream_t s) {
   if (a.dtype == TP_U8)
     chunk_stats_u8<<<a.nchan, kThreads, 0, s>>>(a, static_cast<longlong2*>(chunk_sums));
   else if (a.dtype == TP_F16)
@@ -415,21 +539,15 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, cudaS
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   spectrum_threshold_kernel<<<1, kThreads, 0, s>>>(a, ext_thr);
-  const int64_t words = (a.nsamp + 31) / 32;
-  if (a.enable_spectrum) {
-    const unsigned blocks = (unsigned)((a.nsamp + 255) / 256);
-    if (a.dtype == TP_U8)
-      spectrum_flags_kernel<TP_U8><<<blocks, kThreads, 0, s>>>(a);
-    else if (a.dtype == TP_F16)
-      spectrum_flags_kernel<TP_F16><<<blocks, kThreads, 0, s>>>(a);
-    else if (a.dtype == TP_BF16)
-      spectrum_flags_kernel<TP_BF16><<<blocks, kThreads, 0, s>>>(a);
-    else
-      spectrum_flags_kernel<TP_F32><<<blocks, kThreads, 0, s>>>(a);
-  } else {
-    e = cudaMemsetAsync(a.spec_bits, 0, sizeof(uint32_t) * words, s);
-    if (e != cudaSuccess) return e;
-  }
+  const unsigned blocks = (unsigned)((a.nsamp + 31) / 32);
+  if (a.dtype == TP_U8)
+    spectrum_substitute_kernel<TP_U8><<<blocks, kThreads, 0, s>>>(a, y, ypitch);
+  else if (a.dtype == TP_F16)
+    spectrum_substitute_kernel<TP_F16><<<blocks, kThreads, 0, s>>>(a, y, ypitch);
+  else if (a.dtype == TP_BF16)
+    spectrum_substitute_kernel<TP_BF16><<<blocks, kThreads, 0, s>>>(a, y, ypitch);
+  else
+    spectrum_substitute_kernel<TP_F32><<<blocks, kThreads, 0, s>>>(a, y, ypitch);
   return cudaGetLastError();
 }
 

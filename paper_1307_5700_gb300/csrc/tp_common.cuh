@@ -56,29 +56,32 @@ struct DmTile {
 };
 
 struct DedispArgs {
-  const void* x;
-  int64_t pitch;
+  const float* y;         // substituted, corrected series [nchan][ypitch]
+  int64_t ypitch;         // floats per channel row (>= window + tile + 16)
   int nchan;
-  int64_t nsamp;          // window length
   int64_t nout;           // T
   int dtype;
-  int W, nchunk;
   const int32_t* delay;   // [ndm][nchan]
   int ndm;
   const DmTile* tiles;    // [ntiles]
   int ntiles;
   int ntt;                // number of time tiles
-  const float* mu_hi;
-  const float* mu_lo;
-  const int* bint;
-  const uint8_t* chunk_flag;
-  const int* chan_nflag;
-  const uint32_t* spec_bits;
-  const int* spec_nflag;
+  int shape;              // index into kShapes
   void* D;                // [ndm][dpitch] float or int32
   int64_t dpitch;
   void* row_part;         // [ndm][ntt] (float: double2 {sum, sumsq}; int: longlong2)
+  int* status;            // device status word (TP_ETIMEOUT on a wait that gave up)
 };
+
+// Register-tile shapes of the dedispersion kernel.
+struct KernelShape {
+  int K;      // DM trials per warp
+  int S;      // consecutive outputs per lane (tile = 32 S samples)
+  int OMAX;   // largest in-window offset the kernel handles
+};
+constexpr int kNumShapes = 3;
+extern const KernelShape kShapes[kNumShapes];
+int shape_tile_t(int shape);
 
 struct DetectArgs {
   const void* D;
@@ -93,6 +96,8 @@ struct DetectArgs {
   int64_t t0_abs;
   double* row_mu;         // [ndm]
   double* row_sigma;      // [ndm]
+  float* row_thr_f;       // [ndm] smallest float D that is a detection
+  int* row_thr_i;         // [ndm] smallest int D that is a detection
   uint32_t* hit_bits;     // [ndm][ceil(nout/32)]
   int64_t hit_pitch;      // words per row
   uint32_t* blk_count;    // [nblk]
@@ -104,15 +109,17 @@ struct DetectArgs {
 };
 
 // Dedispersion tiling constants (shared by the planner and the kernel).
-constexpr int kMaxTileDm = 32;      // DM trials per CTA tile
-constexpr int kTileT = 512;         // output samples per CTA tile
-constexpr int kMaxOverhang = 512;   // max delay spread inside a DM tile
+constexpr int kMaxGroups = 8;       // DM groups (warps) per CTA tile
+constexpr int kMinTileT = 640;      // smallest output tile of any shape
+constexpr int kMaxTileT = 896;      // largest output tile of any shape
+constexpr int kMaxOverhang = 512;   // max delay spread inside a CTA tile
 constexpr int kDetectT = 4096;      // samples per detection CTA
 
 // ---- launchers (each returns a cudaError_t of the launch) -----------------------
 cudaError_t launch_delay_table(int nchan, double f_lo, double bw, double t_samp, const double* dm,
                                int ndm, int32_t* delay, int* err_flag, cudaStream_t s);
-cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, cudaStream_t s);
+cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, float* y, int64_t ypitch,
+                       cudaStream_t s);
 double external_spectrum_threshold(const double* sigma, int nchan, double tau_s);
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s);
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s);
