@@ -319,18 +319,22 @@ def test_device_buffer_push_and_errors():
 
 
 def test_admission_by_footprint():
-    e = tp.tp_engine_create(0, hbm_budget_bytes=64 << 20)
+    budget = 256 << 20
+    e = tp.tp_engine_create(0, hbm_budget_bytes=budget)
     try:
         p = tp.tp_create_plan(e, 1024, 398.0, 20.0, 51.2e-6, np.arange(64) * 1.0, "f32")
         need = tp.tp_beam_footprint(p, 32768, 1000)
-        assert need > 64 << 20
+        small = tp.tp_beam_footprint(p, 4000, 10)
+        assert small < budget < need
         with pytest.raises(tp.TpError) as ei:
             tp.tp_beam_open(e, p, 32768, 1000)
         assert ei.value.code == tp.TP_EADMIT
-        used, budget = tp.tp_engine_memory(e)
-        assert used < budget == 64 << 20
+        used, b_ = tp.tp_engine_memory(e)
+        assert used < b_ == budget
         b = tp.tp_beam_open(e, p, 4000, 10)
+        assert tp.tp_engine_memory(e)[0] == used + small
         tp.tp_beam_close(e, b)
+        assert tp.tp_engine_memory(e)[0] == used
         tp.tp_plan_destroy(p)
     finally:
         tp.tp_engine_destroy(e)
