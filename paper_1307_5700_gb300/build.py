@@ -43,7 +43,7 @@ def sources():
 
 def _inputs():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [
-        os.path.abspath(__file__)]
+        os.path.abspath(__file__), os.path.join(CSRC, "gen_dispatch.py")]
 
 
 def stale():
@@ -53,9 +53,18 @@ def stale():
     return any(os.path.getmtime(p) > t for p in _inputs())
 
 
+def generate():
+    """Regenerate csrc/dispatch_gen.cuh if its generator is newer."""
+    gen = os.path.join(CSRC, "gen_dispatch.py")
+    out = os.path.join(CSRC, "dispatch_gen.cuh")
+    if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(gen):
+        subprocess.run([sys.executable, gen], check=True)
+
+
 def build(force=False, verbose=False, extra_flags=()):
     """Compile and link the library if it is missing or older than its
     sources; returns the library path."""
+    generate()
     if not force and not stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)

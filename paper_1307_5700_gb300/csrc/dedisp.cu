@@ -6,35 +6,43 @@
 // kernel (FP32; exact small integers for 8-bit data).
 //
 // Work decomposition.  A CTA owns a tile of consecutive DM trials (up to 8
-// groups of K) x TT = 32 S output samples; warp w owns group w, lane l owns
-// the S consecutive outputs t0 + l S .. t0 + l S + S - 1 of each of the K DMs.
-// The CTA walks the channels in order, NC per pipeline stage: for every
-// channel one elected thread copies the samples the tile needs,
+// groups of K) x TT = 32 S output samples.  Warps 0-7 are consumers: warp w
+// owns group w, lane l owns the S consecutive outputs t0 + l S .. + S - 1 of
+// each of the K DMs.  Warp 8 is the producer: for each pipeline stage (kNC
+// channels) it stages the stage's delays for the tile's DMs into shared memory
+// and copies, per channel, the samples the tile needs,
 // [t0 + delay[d_first][c], t0 + TT + delay[d_last][c]) rounded out to 16 B,
-// from global into shared memory with cp.async.bulk, completing on an
-// mbarrier (NSTAGE stages in flight).  The consumer warps then load, per lane,
-// a register window of S + spread + 4 consecutive samples with 128-bit shared
-// loads and add it into the K x S accumulators at each DM's offset inside the
-// window.  The offsets are warp-uniform run-time values, so each DM selects an
-// unrolled add sequence through a switch over 0..OMAX: every sample loaded
-// from shared memory feeds up to K adds from registers.  Each (d, t) adds its
-// channels in index order in FP32.
+// with cp.async.bulk onto a "full" mbarrier; consumers release a stage on an
+// "empty" mbarrier (kStages stages in flight, no CTA-wide barrier).
+// A consumer lane loads a register window of S + spread + 4 samples with
+// 128-bit shared loads (only as many quads as this channel's spread needs) and
+// adds it into the K x S accumulators at each DM's offset inside the window:
+// the offsets are warp-uniform run-time values, so each DM jumps through a
+// table (brx.idx) into one of OMAX + 1 unrolled add sequences
+// (dispatch_gen.cuh).  Every sample loaded from shared memory thus feeds up to
+// K adds from registers.  Each (d, t) adds its channels in index order (FP32).
+// Every mbarrier wait is bounded; a wait that gives up records TP_ETIMEOUT in
+// the beam's status word and the CTA leaves after letting its copies land.
 //
 // The epilogue writes D (FP32, or int32 for 8-bit data, exact) and per
 // (DM, time tile) sums of D and D^2 for the series statistics of A6.
 #include <cstdint>
 
+#include "dispatch_gen.cuh"
 #include "tp_common.cuh"
 
 namespace tp {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = 8;
-constexpr int kNC = 4;                 // channels per pipeline stage
-constexpr int kStages = 4;             // pipeline depth
-constexpr long long kSpinLimit = 1LL << 24;  // bounded mbarrier waits
+// 8 consumer warps + 1 producer warp: two consumers per SM sub-partition, so
+// the register budget is 168 per thread (three warps on one sub-partition).
+constexpr int kConsumers = 8;                       // consumer warps
+constexpr int kThreads = (kConsumers + 1) * 32;     // + one producer warp
+constexpr int kNC = 4;                              // channels per pipeline stage
+constexpr int kStages = 4;                          // pipeline depth
+constexpr int kTileDm = 32;                         // max DM trials per CTA tile
+constexpr long long kSpinLimit = 1LL << 24;         // bounded mbarrier waits
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -42,6 +50,10 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
@@ -59,6 +71,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (long long spin = 0; spin < kSpinLimit; ++spin)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -67,46 +85,26 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
-template <int S, int L, int O>
-__device__ __forceinline__ void add_at(float (&acc)[S], const float (&w)[L]) {
-#pragma unroll
-  for (int s = 0; s < S; ++s) acc[s] += w[O + s];
-}
-
-#define TP_CASE(o)                                       \
-  case (o):                                              \
-    if constexpr ((o) <= OMAX) add_at<S, L, (o)>(acc, w); \
-    break;
-#define TP_CASE8(b) \
-  TP_CASE(b + 0) TP_CASE(b + 1) TP_CASE(b + 2) TP_CASE(b + 3) TP_CASE(b + 4) TP_CASE(b + 5) TP_CASE(b + 6) TP_CASE(b + 7)
-
-// acc[s] += w[o + s] for a warp-uniform o in [0, OMAX] (OMAX <= 63).
-template <int S, int L, int OMAX>
-__device__ __forceinline__ void add_shifted(int o, float (&acc)[S], const float (&w)[L]) {
-  static_assert(OMAX < 64, "offset range");
-  switch (o) {
-    TP_CASE8(0) TP_CASE8(8) TP_CASE8(16) TP_CASE8(24) TP_CASE8(32) TP_CASE8(40) TP_CASE8(48) TP_CASE8(56)
-    default: break;
-  }
-}
-#undef TP_CASE8
-#undef TP_CASE
-
 template <int K, int S, int OMAX>
 struct Shape {
-  static constexpr int TT = 32 * S;                        // output samples per tile
-  static constexpr int L = ((S + OMAX + 1) + 3) / 4 * 4;   // register window
+  static constexpr int TT = 32 * S;                                          // outputs per tile
+  static constexpr int L = (S + OMAX + 1 + 3) / 4 * 4;                       // register window
   static constexpr int ROW = (TT + kMaxOverhang + OMAX + 8 + 31) / 32 * 32;  // staged floats per channel
-  static constexpr size_t smem = sizeof(float) * kStages * kNC * ROW + 16 * kStages;
+  static constexpr size_t data_bytes = sizeof(float) * kStages * kNC * ROW;
+  static constexpr size_t del_bytes = sizeof(int) * kStages * kNC * kTileDm;
+  static constexpr size_t smem = data_bytes + del_bytes + 16 * kStages;
 };
 
 template <int K, int S, int OMAX, bool kInt>
 __global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
   using Sh = Shape<K, S, OMAX>;
   constexpr int TT = Sh::TT, L = Sh::L, ROW = Sh::ROW;
+  static_assert(kConsumers * K <= kTileDm, "tile DMs");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* srow = reinterpret_cast<float*>(smem_raw);                                    // [kStages][kNC][ROW]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(float) * kStages * kNC * ROW);
+  float* srow = reinterpret_cast<float*>(smem_raw);                        // [kStages][kNC][ROW]
+  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);            // [kStages][kNC][kTileDm]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes);
+  uint64_t* empty = full + kStages;
 
   const int tile = blockIdx.x % a.ntiles;
   const int tt = blockIdx.x / a.ntiles;
@@ -114,127 +112,149 @@ __global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
   const int64_t t0 = (int64_t)tt * TT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchan = a.nchan;
-  const int32_t* __restrict__ delay = a.delay;
-  const int d_last = dt.d0 + dt.nd - 1;
-  const int dw0 = dt.d0 + warp * K;             // first DM of this warp's group
-  const bool warp_live = warp * K < dt.nd;
   const int nstage = (nchan + kNC - 1) / kNC;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kConsumers);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  // Producer: stage i copies channels [i kNC, i kNC + kNC) into buffer i % kStages.
-  auto produce = [&](int i) {
-    const int buf = i % kStages;
-    const int cb = i * kNC;
-    unsigned total = 0;
-    unsigned bytes[kNC];
-    const float* src[kNC];
+  if (warp == kConsumers) {
+    // ---------------------------------------------------------------- producer
+    // lane j < nd holds delayT[c][d0 + j] for the kNC channels of a stage
+    const int32_t* __restrict__ dT = a.delayT;
+    auto fetch = [&](int i, int (&v)[kNC]) {
 #pragma unroll
-    for (int ci = 0; ci < kNC; ++ci) {
-      const int c = cb + ci;
-      bytes[ci] = 0;
-      src[ci] = nullptr;
-      if (c < nchan) {
-        const int lo = delay[(int64_t)dt.d0 * nchan + c];
-        const int hi = delay[(int64_t)d_last * nchan + c];
-        const int64_t base = (t0 + lo) & ~int64_t(3);
-        const int64_t end = t0 + TT + hi + 4;
-        const int64_t n = ((end - base) + 3) & ~int64_t(3);
-        bytes[ci] = (unsigned)(n * 4);
-        src[ci] = a.y + (int64_t)c * a.ypitch + base;
-        total += bytes[ci];
+      for (int ci = 0; ci < kNC; ++ci) {
+        const int c = i * kNC + ci;
+        v[ci] = (c < nchan && lane < dt.nd) ? __ldg(dT + (int64_t)c * a.dtpitch + dt.d0 + lane) : 0;
       }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&bars[buf], total);
+    };
+    int cur[kNC], nxt[kNC];
+    if (nstage > 0) fetch(0, cur);
+    bool ok = true;
+    int issued = 0;
+    for (int i = 0; i < nstage; ++i) {
+      if (i + 1 < nstage) fetch(i + 1, nxt);
+      const int buf = i % kStages;
+      if (i >= kStages) {
+        bool got = false;
+        if (lane == 0) got = mbar_wait_bounded(&empty[buf], (unsigned)(((i / kStages) - 1) & 1));
+        if (!__shfl_sync(0xffffffffu, got, 0)) {
+          ok = false;
+          break;
+        }
+      }
+      int* del = sdel + buf * kNC * kTileDm;
 #pragma unroll
-    for (int ci = 0; ci < kNC; ++ci)
-      if (bytes[ci]) bulk_g2s(srow + (buf * kNC + ci) * ROW, src[ci], bytes[ci], &bars[buf]);
-  };
+      for (int ci = 0; ci < kNC; ++ci) del[ci * kTileDm + lane] = cur[ci];
+      unsigned bytes[kNC];
+      unsigned total = 0;
+#pragma unroll
+      for (int ci = 0; ci < kNC; ++ci) {
+        const int lo = __shfl_sync(0xffffffffu, cur[ci], 0);
+        const int hi = __shfl_sync(0xffffffffu, cur[ci], dt.nd - 1);
+        const int c = i * kNC + ci;
+        bytes[ci] = 0;
+        if (c < nchan) {
+          const int64_t base = (t0 + lo) & ~int64_t(3);
+          const int64_t end = t0 + TT + hi + 4;
+          bytes[ci] = (unsigned)((((end - base) + 3) & ~int64_t(3)) * 4);
+          total += bytes[ci];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&full[buf], total);
+#pragma unroll
+        for (int ci = 0; ci < kNC; ++ci) {
+          if (!bytes[ci]) continue;
+          const int c = i * kNC + ci;
+          const int lo = del[ci * kTileDm];
+          const int64_t base = (t0 + lo) & ~int64_t(3);
+          bulk_g2s(srow + (buf * kNC + ci) * ROW, a.y + (int64_t)c * a.ypitch + base, bytes[ci], &full[buf]);
+        }
+      }
+      ++issued;
+#pragma unroll
+      for (int ci = 0; ci < kNC; ++ci) cur[ci] = nxt[ci];
+    }
+    // let every issued copy land before the CTA can exit
+    if (lane == 0) {
+      for (int k = issued - 1; k >= 0 && k >= issued - kStages; --k)
+        if (!mbar_wait_bounded(&full[k % kStages], (unsigned)((k / kStages) & 1))) ok = false;
+      if (!ok) atomicExch(a.status, TP_ETIMEOUT);
+    }
+    return;
+  }
 
-  if (threadIdx.x == 0)
-    for (int i = 0; i < kStages && i < nstage; ++i) produce(i);
+  // ------------------------------------------------------------------ consumers
+  const int g0 = warp * K;                 // first tile-local DM of this warp
+  const bool live = g0 < dt.nd;
+  const int last = dt.nd - 1;
 
   float acc[K][S];
 #pragma unroll
   for (int j = 0; j < K; ++j)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[j][s] = 0.f;
+  float w[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) w[q] = 0.f;
 
-  bool failed = false;
   for (int i = 0; i < nstage; ++i) {
     const int buf = i % kStages;
-    const int cb = i * kNC;
-    // delays of this stage's channels for the warp's DMs (issued before the wait)
-    int dv = 0;
-    {
-      const int ci = lane / (K + 1), j = lane % (K + 1);
-      const int c = cb + ci;
-      if (ci < kNC && c < nchan) {
-        const int d = j < K ? (dw0 + j <= d_last ? dw0 + j : d_last) : dt.d0;
-        dv = delay[(int64_t)d * nchan + c];
-      }
+    if (!mbar_wait_bounded(&full[buf], (unsigned)((i / kStages) & 1))) {
+      if (lane == 0) atomicExch(a.status, TP_ETIMEOUT);
+      return;
     }
-    bool ready = false;
-    for (long long spin = 0; spin < kSpinLimit; ++spin)
-      if (mbar_try_wait(&bars[buf], (unsigned)((i / kStages) & 1))) {
-        ready = true;
-        break;
-      }
-    const int nc = nchan - cb < kNC ? nchan - cb : kNC;
-    if (ready && warp_live) {
+    const int nc = nchan - i * kNC < kNC ? nchan - i * kNC : kNC;
+    if (live) {
+      const int* del = sdel + buf * kNC * kTileDm;
       for (int ci = 0; ci < nc; ++ci) {
-        const int lo = __shfl_sync(0xffffffffu, dv, ci * (K + 1) + K);
-        const int dw = __shfl_sync(0xffffffffu, dv, ci * (K + 1));
+        const int lo = del[ci * kTileDm];
+        const int dw = del[ci * kTileDm + g0];
         const int64_t base = (t0 + lo) & ~int64_t(3);
         const int aw = (int)(t0 + dw - base);
         int o[K];
         int omax = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          o[j] = (aw & 3) + __shfl_sync(0xffffffffu, dv, ci * (K + 1) + j) - dw;
+          const int jj = g0 + j <= last ? g0 + j : last;
+          o[j] = (aw & 3) + del[ci * kTileDm + jj] - dw;
+          // the planner bounds o[j] by OMAX; the clamp keeps the indexed
+          // branch inside its table whatever the delays hold
+          o[j] = o[j] < 0 ? 0 : (o[j] > OMAX ? OMAX : o[j]);
           omax = o[j] > omax ? o[j] : omax;
         }
         const float* r = srow + (buf * kNC + ci) * ROW + lane * S + (aw & ~3);
         const int nq = (S + omax + 3) >> 2;
-        float w[L];
 #pragma unroll
         for (int q = 0; q < L / 4; ++q) {
           if (q < nq) {
             const float4 v = *reinterpret_cast<const float4*>(r + 4 * q);
             w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
-          } else {
-            w[4 * q] = w[4 * q + 1] = w[4 * q + 2] = w[4 * q + 3] = 0.f;
           }
         }
 #pragma unroll
         for (int j = 0; j < K; ++j) add_shifted<S, L, OMAX>(o[j], acc[j], w);
       }
     }
-    failed = __syncthreads_or(!ready) != 0;
-    if (failed) {
-      // let the copies already issued land (bounded) before the CTA exits
-      if (threadIdx.x == 0) {
-        for (int k = i + 1; k < nstage && k < i + kStages; ++k)
-          for (long long spin = 0; spin < kSpinLimit; ++spin)
-            if (mbar_try_wait(&bars[k % kStages], (unsigned)((k / kStages) & 1))) break;
-        atomicExch(a.status, TP_ETIMEOUT);
-      }
-      return;
-    }
-    if (threadIdx.x == 0 && i + kStages < nstage) produce(i + kStages);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[buf]);
   }
 
   // epilogue
-  if (!warp_live) return;
+  if (!live) return;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    const int d = dw0 + j;
-    if (d > d_last) break;
+    if (g0 + j > last) break;
+    const int d = dt.d0 + g0 + j;
     const int64_t tl = t0 + (int64_t)lane * S;
     if constexpr (kInt) {
       int* Drow = static_cast<int*>(a.D) + (int64_t)d * a.dpitch;
@@ -309,11 +329,14 @@ cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-// Kernel shapes: (DMs per warp K, outputs per lane S, max in-window offset).
+// Kernel shapes, in the planner's order of preference: (DMs per warp K,
+// outputs per lane S, largest in-window offset OMAX).  A plan uses the first
+// shape whose K-trial groups all spread by at most OMAX - 3 samples.
 const KernelShape kShapes[kNumShapes] = {
-    {4, 20, 36},  // adjacent DMs within 33 samples of each other
+    {4, 20, 36},  // e.g. 1024 ch at 398-418 MHz, DM step 0.2
+    {4, 12, 52},  // e.g. 4096 ch at 1200-1500 MHz, DM step 1
     {2, 28, 36},
-    {1, 28, 4},
+    {1, 28, 4},   // any DM list
 };
 
 int shape_tile_t(int shape) { return 32 * kShapes[shape].S; }
@@ -321,7 +344,8 @@ int shape_tile_t(int shape) { return 32 * kShapes[shape].S; }
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
   switch (a.shape) {
     case 0: return launch_shape<4, 20, 36>(a, s);
-    case 1: return launch_shape<2, 28, 36>(a, s);
+    case 1: return launch_shape<4, 12, 52>(a, s);
+    case 2: return launch_shape<2, 28, 36>(a, s);
     default: return launch_shape<1, 28, 4>(a, s);
   }
 }

@@ -146,6 +146,7 @@ struct tp_plan {
   tp_rfi_params rfi{};
   double nsigma = 5.0;
   int32_t* d_delay = nullptr;
+  int32_t* d_delayT = nullptr;  // [nchan][ndm]
   std::vector<int32_t> h_delay;
   std::vector<DmTile> h_tiles;
   DmTile* d_tiles = nullptr;
@@ -413,6 +414,8 @@ int issue_dedisperse(tp_engine* e, Beam* b) {
   da.nout = b->nout;
   da.dtype = p->dtype;
   da.delay = p->d_delay;
+  da.delayT = p->d_delayT;
+  da.dtpitch = p->ndm;
   da.ndm = p->ndm;
   da.tiles = p->d_tiles;
   da.ntiles = (int)p->h_tiles.size();
@@ -522,6 +525,7 @@ int tp_engine_destroy(tp_engine* e) {
     e->beams.clear();
     for (tp_plan* p : e->plans) {
       cudaFree(p->d_delay);
+      cudaFree(p->d_delayT);
       cudaFree(p->d_tiles);
       delete p;
     }
@@ -594,6 +598,7 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
     cudaFree(d_dm);
     cudaFree(d_err);
     cudaFree(p->d_delay);
+    cudaFree(p->d_delayT);
     cudaFree(p->d_tiles);
     delete p;
     return code;
@@ -627,11 +632,19 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
   p->max_delay = dmax;
   p->shape = make_tiles(p->h_delay, ndm, nchan, -1, &p->h_tiles);
   if (p->shape < 0) return fail(set_error(TP_EINVAL, "no kernel shape fits this DM list"));
+  {
+    std::vector<int32_t> tr(n);
+    for (int d = 0; d < ndm; ++d)
+      for (int c = 0; c < nchan; ++c) tr[(size_t)c * ndm + d] = p->h_delay[(size_t)d * nchan + c];
+    if ((ce = cudaMalloc(&p->d_delayT, n * 4)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(delayT)"));
+    if ((ce = cudaMemcpy(p->d_delayT, tr.data(), n * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(cuda_error(ce, "copy delayT"));
+  }
   const size_t tb = p->h_tiles.size() * sizeof(DmTile);
   if ((ce = cudaMalloc(&p->d_tiles, tb)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(tiles)"));
   if ((ce = cudaMemcpy(p->d_tiles, p->h_tiles.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
     return fail(cuda_error(ce, "copy tiles"));
-  p->bytes = n * 4 + tb;
+  p->bytes = 2 * n * 4 + tb;
   e->used += p->bytes;
   e->plans.push_back(p);
   *out = p;
@@ -646,6 +659,7 @@ int tp_plan_destroy(tp_plan* p) {
   DeviceGuard g(e->device);
   cudaStreamSynchronize(e->stream);
   cudaFree(p->d_delay);
+  cudaFree(p->d_delayT);
   cudaFree(p->d_tiles);
   e->used -= p->bytes;
   e->plans.erase(std::remove(e->plans.begin(), e->plans.end(), p), e->plans.end());

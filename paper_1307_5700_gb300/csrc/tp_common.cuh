@@ -62,6 +62,8 @@ struct DedispArgs {
   int64_t nout;           // T
   int dtype;
   const int32_t* delay;   // [ndm][nchan]
+  const int32_t* delayT;  // [nchan][dtpitch] (transposed copy)
+  int64_t dtpitch;
   int ndm;
   const DmTile* tiles;    // [ntiles]
   int ntiles;
@@ -79,7 +81,7 @@ struct KernelShape {
   int S;      // consecutive outputs per lane (tile = 32 S samples)
   int OMAX;   // largest in-window offset the kernel handles
 };
-constexpr int kNumShapes = 3;
+constexpr int kNumShapes = 4;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
@@ -110,7 +112,7 @@ struct DetectArgs {
 
 // Dedispersion tiling constants (shared by the planner and the kernel).
 constexpr int kMaxGroups = 8;       // DM groups (warps) per CTA tile
-constexpr int kMinTileT = 640;      // smallest output tile of any shape
+constexpr int kMinTileT = 384;      // smallest output tile of any shape
 constexpr int kMaxTileT = 896;      // largest output tile of any shape
 constexpr int kMaxOverhang = 512;   // max delay spread inside a CTA tile
 constexpr int kDetectT = 4096;      // samples per detection CTA
