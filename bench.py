@@ -229,6 +229,10 @@ def main():
     # first block of the stream fills the overlap tail; not timed
     tp.tp_push_block(e, beam, dev_blocks[0])
     tp.tp_dedisperse(e, beam)
+    # autotune the dedispersion kernel shape on this plan's geometry
+    best, shape_ms = tp.tp_autotune(e, beam, reps=2)
+    tune = {str(i): round(float(v), 3) for i, v in enumerate(shape_ms[:7]) if v >= 0}
+    tp.tp_dedisperse(e, beam)
     tp.tp_detect(e, beam)
     tp.tp_get_candidates(e, beam, 0)
 
@@ -333,7 +337,8 @@ def main():
             "config": {"workload": WORKLOAD, "nchan": NCHAN, "ndm": len(DMS), "block": BLOCK,
                        "overlap": int(max_delay), "beams_per_gpu": 1,
                        "l2": "inputs larger than L2 (562 MB window per block, 3 distinct blocks cycled)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "kernel_shape": int(best),
+                       "autotune_ms": tune},
             "realtime_beams": value / (len(DMS) / TSAMP),
             "p50_block_latency_ms": float(np.percentile(per_block, 50)),
             "p99_block_latency_ms": float(np.percentile(per_block, 99)),

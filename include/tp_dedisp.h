@@ -213,6 +213,27 @@ int tp_get_masks(tp_engine *e, int beam, uint8_t *chunk_flag, uint8_t *chunk_raw
 /* Series statistics mu_d, sigma_d (host, ndm doubles each). */
 int tp_get_series_stats(tp_engine *e, int beam, double *mu, double *sigma, int ndm);
 
+/* ---- kernel shapes and autotuning -------------------------------------------------
+ * The dedispersion kernel is compiled for several register tilings ("shapes":
+ * DM trials per warp, outputs per lane, largest in-window delay offset,
+ * warps per CTA).  A plan keeps the shapes its DM list fits; the first one is
+ * selected at creation. */
+
+/* Number of shapes (return value); the plan's current shape; and, for
+ * i < n, feasible[i] = 1 if shape i fits the plan's DM list. */
+int tp_plan_shapes(const tp_plan *p, int *shape, int *feasible, int n);
+
+/* Select a feasible shape for every beam of the plan (TP_EINVAL otherwise). */
+int tp_plan_set_shape(tp_plan *p, int shape);
+
+/* Time the dedispersion kernel of every feasible shape `reps` times on the
+ * beam's current window, select the fastest for the beam's plan, and return
+ * it in *best and the mean milliseconds per launch in ms[shape] (-1 for
+ * infeasible shapes; n entries).  Blocks.  The beam's series is overwritten:
+ * call tp_dedisperse again before tp_detect.  TP_ENOTREADY if the beam never
+ * received a block. */
+int tp_autotune(tp_engine *e, int beam, int reps, int *best, float *ms, int n);
+
 /* ---- tracing -------------------------------------------------------------------- */
 
 /* Enable (1) or disable (0) per-stage CUDA-event timing on every beam of the

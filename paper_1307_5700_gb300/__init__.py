@@ -45,7 +45,7 @@ EXPORTS = (
     "tp_push_block", "tp_dedisperse", "tp_detect", "tp_get_candidates", "tp_beam_info",
     "tp_get_series", "tp_get_bandpass", "tp_get_masks", "tp_get_series_stats",
     "tp_set_profiling", "tp_get_stage_times", "tp_engine_launches", "tp_last_error_string",
-    "tp_version",
+    "tp_version", "tp_plan_shapes", "tp_plan_set_shape", "tp_autotune",
 )
 
 
@@ -103,6 +103,9 @@ _SIGS = {
     "tp_set_profiling": (_i, [_vp, _i]),
     "tp_get_stage_times": (_i, [_vp, _i, _vp, _vp]),
     "tp_engine_launches": (_i, [_vp, _vp]),
+    "tp_plan_shapes": (_i, [_vp, _vp, _vp, _i]),
+    "tp_plan_set_shape": (_i, [_vp, _i]),
+    "tp_autotune": (_i, [_vp, _i, _i, _vp, _vp, _i]),
     "tp_last_error_string": (ctypes.c_char_p, []),
     "tp_version": (_i, []),
 }
@@ -337,3 +340,23 @@ def tp_engine_launches(e):
     n = ctypes.c_uint64()
     _check(lib().tp_engine_launches(e, ctypes.byref(n)))
     return n.value
+
+
+def tp_plan_shapes(p):
+    """(current shape, feasible flags per shape)."""
+    sh = ctypes.c_int()
+    feas = np.zeros(32, np.int32)
+    n = _check(lib().tp_plan_shapes(p, ctypes.byref(sh), feas.ctypes.data, len(feas)))
+    return sh.value, feas[:n].astype(bool)
+
+
+def tp_plan_set_shape(p, shape):
+    return _check(lib().tp_plan_set_shape(p, int(shape)))
+
+
+def tp_autotune(e, beam, reps=3):
+    """(best shape, ms per launch for every shape; -1 where infeasible)."""
+    best = ctypes.c_int()
+    ms = np.zeros(32, np.float32)
+    _check(lib().tp_autotune(e, beam, int(reps), ctypes.byref(best), ms.ctypes.data, len(ms)))
+    return best.value, ms

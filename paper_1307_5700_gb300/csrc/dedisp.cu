@@ -35,13 +35,8 @@ namespace tp {
 
 namespace {
 
-// 8 consumer warps + 1 producer warp: two consumers per SM sub-partition, so
-// the register budget is 168 per thread (three warps on one sub-partition).
-constexpr int kConsumers = 8;                       // consumer warps
-constexpr int kThreads = (kConsumers + 1) * 32;     // + one producer warp
 constexpr int kNC = 4;                              // channels per pipeline stage
 constexpr int kStages = 4;                          // pipeline depth
-constexpr int kTileDm = 32;                         // max DM trials per CTA tile
 constexpr long long kSpinLimit = 1LL << 24;         // bounded mbarrier waits
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -85,25 +80,39 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
-template <int K, int S, int OMAX>
+template <int K, int S, int OMAX, int NCONS>
 struct Shape {
   static constexpr int TT = 32 * S;                                          // outputs per tile
   static constexpr int L = (S + OMAX + 1 + 3) / 4 * 4;                       // register window
   static constexpr int ROW = (TT + kMaxOverhang + OMAX + 8 + 31) / 32 * 32;  // staged floats per channel
+  static constexpr int THREADS = (NCONS + 1) * 32;                           // + one producer warp
   static constexpr size_t data_bytes = sizeof(float) * kStages * kNC * ROW;
-  static constexpr size_t del_bytes = sizeof(int) * kStages * kNC * kTileDm;
-  static constexpr size_t smem = data_bytes + del_bytes + 16 * kStages;
+  static constexpr size_t del_bytes = sizeof(int) * kStages * kNC * 32;
+  static constexpr size_t info_bytes = sizeof(int4) * kStages * kNC * NCONS;
+  static constexpr size_t smem = data_bytes + del_bytes + info_bytes + 16 * kStages;
 };
 
-template <int K, int S, int OMAX, bool kInt>
-__global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
-  using Sh = Shape<K, S, OMAX>;
+// Per (stage, channel, consumer warp): where the warp's window starts in
+// shared memory, the K in-window offsets (one byte each) and how many quads
+// of the window the channel needs.  Written by the producer.
+struct WarpChan {
+  int roff;    // float offset of lane 0's window
+  int offs;    // byte j = offset of DM j of the warp's group
+  int nq;      // window quads to load
+  int pad;
+};
+
+template <int K, int S, int OMAX, int NCONS, bool kInt>
+__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisperse_kernel(DedispArgs a) {
+  using Sh = Shape<K, S, OMAX, NCONS>;
   constexpr int TT = Sh::TT, L = Sh::L, ROW = Sh::ROW;
-  static_assert(kConsumers * K <= kTileDm, "tile DMs");
+  static_assert(NCONS * K <= 32, "a producer lane holds one DM of the tile");
+  static_assert(OMAX < 256, "offsets are packed in bytes");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* srow = reinterpret_cast<float*>(smem_raw);                        // [kStages][kNC][ROW]
-  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);            // [kStages][kNC][kTileDm]
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes);
+  float* srow = reinterpret_cast<float*>(smem_raw);                               // [kStages][kNC][ROW]
+  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);                   // [kStages][kNC][32]
+  int4* sinfo = reinterpret_cast<int4*>(smem_raw + Sh::data_bytes + Sh::del_bytes);  // [kStages][kNC][NCONS]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes);
   uint64_t* empty = full + kStages;
 
   const int tile = blockIdx.x % a.ntiles;
@@ -113,17 +122,18 @@ __global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchan = a.nchan;
   const int nstage = (nchan + kNC - 1) / kNC;
+  const int last = dt.nd - 1;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kConsumers);
+      mbar_init(&empty[i], NCONS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  if (warp == kConsumers) {
+  if (warp == NCONS) {
     // ---------------------------------------------------------------- producer
     // lane j < nd holds delayT[c][d0 + j] for the kNC channels of a stage
     const int32_t* __restrict__ dT = a.delayT;
@@ -149,15 +159,38 @@ __global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
           break;
         }
       }
-      int* del = sdel + buf * kNC * kTileDm;
+      int* del = sdel + buf * kNC * 32;
 #pragma unroll
-      for (int ci = 0; ci < kNC; ++ci) del[ci * kTileDm + lane] = cur[ci];
+      for (int ci = 0; ci < kNC; ++ci) del[ci * 32 + lane] = cur[ci];
+      __syncwarp();
+      // window geometry of every (channel, consumer warp) pair of the stage
+      for (int p = lane; p < kNC * NCONS; p += 32) {
+        const int ci = p / NCONS, w = p % NCONS;
+        const int g0 = w * K < last ? w * K : last;
+        const int lo = del[ci * 32];
+        const int dw = del[ci * 32 + g0];
+        const int64_t base = (t0 + lo) & ~int64_t(3);
+        const int aw = (int)(t0 + dw - base);
+        int offs = 0, omax = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const int jj = g0 + j <= last ? g0 + j : last;
+          int o = (aw & 3) + del[ci * 32 + jj] - dw;
+          // the planner bounds o by OMAX; the clamp keeps the indexed branch
+          // inside its table whatever the delays hold
+          o = o < 0 ? 0 : (o > OMAX ? OMAX : o);
+          offs |= o << (8 * j);
+          omax = o > omax ? o : omax;
+        }
+        sinfo[(buf * kNC + ci) * NCONS + w] =
+            make_int4((buf * kNC + ci) * ROW + (aw & ~3), offs, (S + omax + 3) >> 2, 0);
+      }
       unsigned bytes[kNC];
       unsigned total = 0;
 #pragma unroll
       for (int ci = 0; ci < kNC; ++ci) {
         const int lo = __shfl_sync(0xffffffffu, cur[ci], 0);
-        const int hi = __shfl_sync(0xffffffffu, cur[ci], dt.nd - 1);
+        const int hi = __shfl_sync(0xffffffffu, cur[ci], last);
         const int c = i * kNC + ci;
         bytes[ci] = 0;
         if (c < nchan) {
@@ -175,8 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
         for (int ci = 0; ci < kNC; ++ci) {
           if (!bytes[ci]) continue;
           const int c = i * kNC + ci;
-          const int lo = del[ci * kTileDm];
-          const int64_t base = (t0 + lo) & ~int64_t(3);
+          const int64_t base = (t0 + cur[ci]) & ~int64_t(3);
           bulk_g2s(srow + (buf * kNC + ci) * ROW, a.y + (int64_t)c * a.ypitch + base, bytes[ci], &full[buf]);
         }
       }
@@ -196,7 +228,6 @@ __global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
   // ------------------------------------------------------------------ consumers
   const int g0 = warp * K;                 // first tile-local DM of this warp
   const bool live = g0 < dt.nd;
-  const int last = dt.nd - 1;
 
   float acc[K][S];
 #pragma unroll
@@ -215,34 +246,18 @@ __global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
     }
     const int nc = nchan - i * kNC < kNC ? nchan - i * kNC : kNC;
     if (live) {
-      const int* del = sdel + buf * kNC * kTileDm;
       for (int ci = 0; ci < nc; ++ci) {
-        const int lo = del[ci * kTileDm];
-        const int dw = del[ci * kTileDm + g0];
-        const int64_t base = (t0 + lo) & ~int64_t(3);
-        const int aw = (int)(t0 + dw - base);
-        int o[K];
-        int omax = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-          const int jj = g0 + j <= last ? g0 + j : last;
-          o[j] = (aw & 3) + del[ci * kTileDm + jj] - dw;
-          // the planner bounds o[j] by OMAX; the clamp keeps the indexed
-          // branch inside its table whatever the delays hold
-          o[j] = o[j] < 0 ? 0 : (o[j] > OMAX ? OMAX : o[j]);
-          omax = o[j] > omax ? o[j] : omax;
-        }
-        const float* r = srow + (buf * kNC + ci) * ROW + lane * S + (aw & ~3);
-        const int nq = (S + omax + 3) >> 2;
+        const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
+        const float* r = srow + inf.x + lane * S;
 #pragma unroll
         for (int q = 0; q < L / 4; ++q) {
-          if (q < nq) {
+          if (q < inf.z) {
             const float4 v = *reinterpret_cast<const float4*>(r + 4 * q);
             w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
           }
         }
 #pragma unroll
-        for (int j = 0; j < K; ++j) add_shifted<S, L, OMAX>(o[j], acc[j], w);
+        for (int j = 0; j < K; ++j) add_shifted<S, L, OMAX>((inf.y >> (8 * j)) & 0xff, acc[j], w);
       }
     }
     __syncwarp();
@@ -307,46 +322,54 @@ __global__ void __launch_bounds__(kThreads, 1) dedisperse_kernel(DedispArgs a) {
   }
 }
 
-template <int K, int S, int OMAX>
+template <int K, int S, int OMAX, int NCONS>
 cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
-  using Sh = Shape<K, S, OMAX>;
+  using Sh = Shape<K, S, OMAX, NCONS>;
   const long long grid = (long long)a.ntiles * a.ntt;
   if (grid <= 0 || grid > 0x7fffffffLL) return cudaErrorInvalidValue;
   cudaError_t e;
   if (a.dtype == TP_U8) {
-    e = cudaFuncSetAttribute(dedisperse_kernel<K, S, OMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Sh::smem);
+    auto k = dedisperse_kernel<K, S, OMAX, NCONS, true>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
     if (e != cudaSuccess) return e;
-    dedisperse_kernel<K, S, OMAX, true><<<(unsigned)grid, kThreads, Sh::smem, s>>>(a);
+    k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(a);
   } else {
-    e = cudaFuncSetAttribute(dedisperse_kernel<K, S, OMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Sh::smem);
+    auto k = dedisperse_kernel<K, S, OMAX, NCONS, false>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
     if (e != cudaSuccess) return e;
-    dedisperse_kernel<K, S, OMAX, false><<<(unsigned)grid, kThreads, Sh::smem, s>>>(a);
+    k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Kernel shapes, in the planner's order of preference: (DMs per warp K,
-// outputs per lane S, largest in-window offset OMAX).  A plan uses the first
-// shape whose K-trial groups all spread by at most OMAX - 3 samples.
-const KernelShape kShapes[kNumShapes] = {
-    {4, 20, 36},  // e.g. 1024 ch at 398-418 MHz, DM step 0.2
-    {4, 12, 52},  // e.g. 4096 ch at 1200-1500 MHz, DM step 1
-    {2, 28, 36},
-    {1, 28, 4},   // any DM list
-};
+// Kernel shapes: (DMs per warp K, outputs per lane S, largest in-window offset
+// OMAX, consumer warps).  The planner keeps the shapes whose K-trial groups
+// all spread by at most OMAX - 3 samples; the autotuner (or the first
+// feasible shape) picks among them.
+#define TP_SHAPES(X)      \
+  X(0, 4, 20, 36, 8)      \
+  X(1, 2, 20, 16, 12)     \
+  X(2, 2, 28, 16, 8)      \
+  X(3, 3, 20, 24, 8)      \
+  X(4, 4, 12, 52, 8)      \
+  X(5, 2, 20, 24, 12)     \
+  X(6, 1, 28, 4, 16)
+
+#define TP_SHAPE_ENTRY(i, K, S, O, N) {K, S, O, N},
+const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};
+#undef TP_SHAPE_ENTRY
 
 int shape_tile_t(int shape) { return 32 * kShapes[shape].S; }
 
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
   switch (a.shape) {
-    case 0: return launch_shape<4, 20, 36>(a, s);
-    case 1: return launch_shape<4, 12, 52>(a, s);
-    case 2: return launch_shape<2, 28, 36>(a, s);
-    default: return launch_shape<1, 28, 4>(a, s);
+#define TP_SHAPE_CASE(i, K, S, O, N) \
+  case i: return launch_shape<K, S, O, N>(a, s);
+    TP_SHAPES(TP_SHAPE_CASE)
+#undef TP_SHAPE_CASE
+    default: return cudaErrorInvalidValue;
   }
 }
 

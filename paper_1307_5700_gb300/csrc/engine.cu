@@ -148,9 +148,12 @@ struct tp_plan {
   int32_t* d_delay = nullptr;
   int32_t* d_delayT = nullptr;  // [nchan][ndm]
   std::vector<int32_t> h_delay;
-  std::vector<DmTile> h_tiles;
+  std::vector<DmTile> h_tiles;  // tiles of the selected shape
   DmTile* d_tiles = nullptr;
   int shape = 0;
+  bool feasible[kNumShapes] = {};
+  std::vector<DmTile> shape_tiles[kNumShapes];
+  DmTile* d_shape_tiles[kNumShapes] = {};
   int users = 0;
   size_t bytes = 0;
 };
@@ -200,33 +203,21 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
   return s;
 }
 
-// Tiling for the dedispersion kernel: pick the first register shape whose DM
-// groups (K consecutive trials) all fit its in-window offset range, then pack
-// up to kMaxGroups consecutive groups into a CTA tile while the tile's delay
-// spread stays within kMaxOverhang.
-int make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int forced_shape,
-               std::vector<DmTile>* tiles) {
-  int shape = -1;
-  for (int sh = 0; sh < kNumShapes; ++sh) {
-    if (forced_shape >= 0 && sh != forced_shape) continue;
-    const int K = kShapes[sh].K;
-    bool ok = true;
-    for (int d0 = 0; d0 < ndm && ok; d0 += K) {
-      const int d1 = std::min(d0 + K, ndm) - 1;
-      ok = spread(delay, nchan, d0, d1) + 3 <= kShapes[sh].OMAX;
-    }
-    if (ok) {
-      shape = sh;
-      break;
-    }
+// Tiling for the dedispersion kernel with register shape `sh`: the shape is
+// feasible when every group of K consecutive trials spreads by at most
+// OMAX - 3 samples in every channel; tiles pack up to NCONS consecutive groups
+// while the tile's delay spread stays within kMaxOverhang.
+bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int sh, std::vector<DmTile>* tiles) {
+  const int K = kShapes[sh].K;
+  for (int d0 = 0; d0 < ndm; d0 += K) {
+    const int d1 = std::min(d0 + K, ndm) - 1;
+    if (spread(delay, nchan, d0, d1) + 3 > kShapes[sh].OMAX) return false;
   }
-  if (shape < 0) return -1;
-  const int K = kShapes[shape].K;
   tiles->clear();
   int d0 = 0;
   while (d0 < ndm) {
     int ng = 1;
-    while (ng < kMaxGroups && d0 + ng * K < ndm) {
+    while (ng < kShapes[sh].NCONS && d0 + ng * K < ndm) {
       const int d1 = std::min(d0 + (ng + 1) * K, ndm) - 1;
       if (spread(delay, nchan, d0, d1) > kMaxOverhang) break;
       ++ng;
@@ -235,7 +226,7 @@ int make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int forced
     tiles->push_back(DmTile{d0, nd});
     d0 += nd;
   }
-  return shape;
+  return true;
 }
 
 Beam* get_beam(tp_engine* e, int id) {
@@ -396,17 +387,7 @@ RfiArgs rfi_args(const tp_plan* p, Beam* b) {
   return a;
 }
 
-int issue_dedisperse(tp_engine* e, Beam* b) {
-  const tp_plan* p = b->plan;
-  if (b->state != kReady) return set_error(TP_ENOTREADY, "beam %d holds no new block", b->id);
-  if (p->rfi.stats_mode == TP_STATS_EXTERNAL && !b->have_ext)
-    return set_error(TP_ENOTREADY, "beam %d: external statistics not set", b->id);
-  cudaStream_t s = beam_stream(e, b);
-  RfiArgs ra = rfi_args(p, b);
-  prof_record(e, b, 2, s);
-  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->ext_thr, b->y, b->ypitch, s));
-  prof_record(e, b, 3, s);
-  e->launches += 4;
+DedispArgs dedisp_args(const tp_plan* p, Beam* b) {
   DedispArgs da{};
   da.y = b->y;
   da.ypitch = b->ypitch;
@@ -425,6 +406,21 @@ int issue_dedisperse(tp_engine* e, Beam* b) {
   da.dpitch = b->dpitch;
   da.row_part = b->row_part;
   da.status = b->status;
+  return da;
+}
+
+int issue_dedisperse(tp_engine* e, Beam* b) {
+  const tp_plan* p = b->plan;
+  if (b->state != kReady) return set_error(TP_ENOTREADY, "beam %d holds no new block", b->id);
+  if (p->rfi.stats_mode == TP_STATS_EXTERNAL && !b->have_ext)
+    return set_error(TP_ENOTREADY, "beam %d: external statistics not set", b->id);
+  cudaStream_t s = beam_stream(e, b);
+  RfiArgs ra = rfi_args(p, b);
+  prof_record(e, b, 2, s);
+  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->ext_thr, b->y, b->ypitch, s));
+  prof_record(e, b, 3, s);
+  e->launches += 4;
+  DedispArgs da = dedisp_args(p, b);
   b->ntt = da.ntt;
   TP_CUDA_TRY(launch_dedisperse(da, s));
   prof_record(e, b, 4, s);
@@ -526,7 +522,7 @@ int tp_engine_destroy(tp_engine* e) {
     for (tp_plan* p : e->plans) {
       cudaFree(p->d_delay);
       cudaFree(p->d_delayT);
-      cudaFree(p->d_tiles);
+      for (DmTile* t : p->d_shape_tiles) cudaFree(t);
       delete p;
     }
     e->plans.clear();
@@ -599,7 +595,7 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
     cudaFree(d_err);
     cudaFree(p->d_delay);
     cudaFree(p->d_delayT);
-    cudaFree(p->d_tiles);
+    for (DmTile* t : p->d_shape_tiles) cudaFree(t);
     delete p;
     return code;
   };
@@ -630,8 +626,22 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
   int dmax = 0;
   for (int32_t v : p->h_delay) dmax = std::max(dmax, (int)v);
   p->max_delay = dmax;
-  p->shape = make_tiles(p->h_delay, ndm, nchan, -1, &p->h_tiles);
+  p->shape = -1;
+  size_t tb = 0;
+  for (int sh = 0; sh < kNumShapes; ++sh) {
+    p->feasible[sh] = make_tiles(p->h_delay, ndm, nchan, sh, &p->shape_tiles[sh]);
+    if (!p->feasible[sh]) continue;
+    if (p->shape < 0) p->shape = sh;
+    const size_t bts = p->shape_tiles[sh].size() * sizeof(DmTile);
+    if ((ce = cudaMalloc(&p->d_shape_tiles[sh], bts)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(tiles)"));
+    if ((ce = cudaMemcpy(p->d_shape_tiles[sh], p->shape_tiles[sh].data(), bts, cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return fail(cuda_error(ce, "copy tiles"));
+    tb += bts;
+  }
   if (p->shape < 0) return fail(set_error(TP_EINVAL, "no kernel shape fits this DM list"));
+  p->h_tiles = p->shape_tiles[p->shape];
+  p->d_tiles = p->d_shape_tiles[p->shape];
   {
     std::vector<int32_t> tr(n);
     for (int d = 0; d < ndm; ++d)
@@ -640,10 +650,6 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
     if ((ce = cudaMemcpy(p->d_delayT, tr.data(), n * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_error(ce, "copy delayT"));
   }
-  const size_t tb = p->h_tiles.size() * sizeof(DmTile);
-  if ((ce = cudaMalloc(&p->d_tiles, tb)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(tiles)"));
-  if ((ce = cudaMemcpy(p->d_tiles, p->h_tiles.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
-    return fail(cuda_error(ce, "copy tiles"));
   p->bytes = 2 * n * 4 + tb;
   e->used += p->bytes;
   e->plans.push_back(p);
@@ -660,7 +666,7 @@ int tp_plan_destroy(tp_plan* p) {
   cudaStreamSynchronize(e->stream);
   cudaFree(p->d_delay);
   cudaFree(p->d_delayT);
-  cudaFree(p->d_tiles);
+  for (DmTile* t : p->d_shape_tiles) cudaFree(t);
   e->used -= p->bytes;
   e->plans.erase(std::remove(e->plans.begin(), e->plans.end(), p), e->plans.end());
   delete p;
@@ -1039,6 +1045,73 @@ int tp_get_stage_times(tp_engine* e, int beam, double* ms, int64_t* count) {
 int tp_engine_launches(const tp_engine* e, uint64_t* n) {
   if (!e || !n) return set_error(TP_EINVAL, "engine or n is NULL");
   *n = e->launches;
+  return TP_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int tp_plan_shapes(const tp_plan* p, int* shape, int* feasible, int n) {
+  if (!p) return set_error(TP_EINVAL, "plan is NULL");
+  if (shape) *shape = p->shape;
+  if (feasible)
+    for (int i = 0; i < n && i < kNumShapes; ++i) feasible[i] = p->feasible[i] ? 1 : 0;
+  return kNumShapes;
+}
+
+int tp_plan_set_shape(tp_plan* p, int shape) {
+  if (!p) return set_error(TP_EINVAL, "plan is NULL");
+  if (shape < 0 || shape >= kNumShapes || !p->feasible[shape])
+    return set_error(TP_EINVAL, "shape %d is not feasible for this plan", shape);
+  std::lock_guard<std::recursive_mutex> lk(p->e->mu);
+  p->shape = shape;
+  p->h_tiles = p->shape_tiles[shape];
+  p->d_tiles = p->d_shape_tiles[shape];
+  return TP_OK;
+}
+
+int tp_autotune(tp_engine* e, int beam, int reps, int* best, float* ms, int n) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->nsamp_win == 0) return set_error(TP_ENOTREADY, "beam %d has no block yet", beam);
+  tp_plan* p = const_cast<tp_plan*>(b->plan);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  cudaEvent_t e0, e1;
+  TP_CUDA_TRY(cudaEventCreate(&e0));
+  TP_CUDA_TRY(cudaEventCreate(&e1));
+  reps = reps < 1 ? 1 : reps;
+  int bestsh = -1;
+  float bestms = 0.f;
+  for (int sh = 0; sh < kNumShapes; ++sh) {
+    if (ms && sh < n) ms[sh] = -1.f;
+    if (!p->feasible[sh]) continue;
+    DedispArgs da = dedisp_args(p, b);
+    da.shape = sh;
+    da.tiles = p->d_shape_tiles[sh];
+    da.ntiles = (int)p->shape_tiles[sh].size();
+    da.ntt = (int)((b->nout + shape_tile_t(sh) - 1) / shape_tile_t(sh));
+    TP_CUDA_TRY(launch_dedisperse(da, s));  // warm-up
+    TP_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) TP_CUDA_TRY(launch_dedisperse(da, s));
+    TP_CUDA_TRY(cudaEventRecord(e1, s));
+    TP_CUDA_TRY(cudaEventSynchronize(e1));
+    e->launches += reps + 1;
+    float t = 0.f;
+    TP_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+    t /= reps;
+    if (ms && sh < n) ms[sh] = t;
+    if (bestsh < 0 || t < bestms) bestsh = sh, bestms = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the timing runs overwrote the series: the beam must be dedispersed again
+  if (b->state >= kDedispersed) b->state = kReady;
+  tp_plan_set_shape(p, bestsh);
+  if (best) *best = bestsh;
   return TP_OK;
 }
 

@@ -15,7 +15,7 @@ it when the header is older than this script).
 import os
 
 # (S, OMAX) pairs used by the kernel shapes; L = S + OMAX + 1 rounded up to 4.
-SHAPES = [(20, 36), (12, 52), (28, 36), (28, 4)]
+SHAPES = [(20, 36), (20, 16), (28, 16), (20, 24), (12, 52), (28, 4)]
 
 
 def window(S, OMAX):

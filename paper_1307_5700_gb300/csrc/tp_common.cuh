@@ -80,8 +80,9 @@ struct KernelShape {
   int K;      // DM trials per warp
   int S;      // consecutive outputs per lane (tile = 32 S samples)
   int OMAX;   // largest in-window offset the kernel handles
+  int NCONS;  // consumer warps per CTA (DM groups per tile)
 };
-constexpr int kNumShapes = 4;
+constexpr int kNumShapes = 7;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
@@ -111,7 +112,6 @@ struct DetectArgs {
 };
 
 // Dedispersion tiling constants (shared by the planner and the kernel).
-constexpr int kMaxGroups = 8;       // DM groups (warps) per CTA tile
 constexpr int kMinTileT = 384;      // smallest output tile of any shape
 constexpr int kMaxTileT = 896;      // largest output tile of any shape
 constexpr int kMaxOverhang = 512;   // max delay spread inside a CTA tile
