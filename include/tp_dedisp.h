@@ -250,6 +250,38 @@ int tp_get_stage_times(tp_engine *e, int beam, double *ms, int64_t *count);
 /* Kernels launched by the engine since it was created. */
 int tp_engine_launches(const tp_engine *e, uint64_t *n);
 
+/* ---- the same statistics without any allocation ---------------------------------
+ * tp_channel_stats_noalloc: A1-A2 (bandpass mean and standard deviation per
+ * channel, channel-threshold exceedances and the dilated chunk flags) of one
+ * channel-major block, for callers that cannot allocate device memory while
+ * they run (pre-partitioned device memory under a real-time scheduler, work
+ * recorded into a stream capture that must hold no allocation, runtimes that
+ * forbid the CUDA allocator after start-up).  The paper has no counterpart to
+ * this entry point: it is a deployment variant of the statistics step that
+ * tp_dedisperse runs with beam-owned scratch.
+ *
+ * x          device, [nchan][pitch] samples of `dtype`, 16-byte aligned, pitch
+ *            * element size a multiple of 16 bytes; nsamp samples per row used
+ * rfi        NULL for the defaults; stats_mode must be TP_STATS_BLOCK (enable_
+ *            spectrum and tau_spectrum are ignored)
+ * mu, sigma  device, nchan doubles each (outputs)
+ * chunk_flag, chunk_raw  device, nchan x ceil(nsamp / W) bytes each (outputs)
+ * cuda_stream  cudaStream_t (NULL = legacy default stream); the call is
+ *            asynchronous on it
+ *
+ * Scratch: a 32 MiB array inside the library, held by every device that loads
+ * the library until the process exits; TP_EINVAL when nchan * ceil(nsamp / W)
+ * * 16 bytes (+ 48 bytes per channel) does not fit.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and must
+ * therefore come before any stream capture on that device.  No call allocates
+ * or frees memory.  All calls share the array and it keeps the contents of the
+ * last call: calls that can overlap on the GPU (different streams, or
+ * different host threads) race on it and must be ordered by the caller.
+ * Results equal those tp_dedisperse computes for the same window. */
+int tp_channel_stats_noalloc(const void *x, int dtype, int nchan, int64_t nsamp, int64_t pitch,
+                             const tp_rfi_params *rfi, double *mu, double *sigma, uint8_t *chunk_flag,
+                             uint8_t *chunk_raw, void *cuda_stream);
+
 /* Text of the calling thread's last error. */
 const char *tp_last_error_string(void);
 

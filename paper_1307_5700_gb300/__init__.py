@@ -45,7 +45,7 @@ EXPORTS = (
     "tp_push_block", "tp_dedisperse", "tp_detect", "tp_get_candidates", "tp_beam_info",
     "tp_get_series", "tp_get_bandpass", "tp_get_masks", "tp_get_series_stats",
     "tp_set_profiling", "tp_get_stage_times", "tp_engine_launches", "tp_last_error_string",
-    "tp_version", "tp_plan_shapes", "tp_plan_set_shape", "tp_autotune",
+    "tp_version", "tp_plan_shapes", "tp_plan_set_shape", "tp_autotune", "tp_channel_stats_noalloc",
 )
 
 
@@ -106,6 +106,8 @@ _SIGS = {
     "tp_plan_shapes": (_i, [_vp, _vp, _vp, _i]),
     "tp_plan_set_shape": (_i, [_vp, _i]),
     "tp_autotune": (_i, [_vp, _i, _i, _vp, _vp, _i]),
+    "tp_channel_stats_noalloc": (_i, [_vp, _i, _i, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
+                                     _vp]),
     "tp_last_error_string": (ctypes.c_char_p, []),
     "tp_version": (_i, []),
 }
@@ -360,3 +362,15 @@ def tp_autotune(e, beam, reps=3):
     ms = np.zeros(32, np.float32)
     _check(lib().tp_autotune(e, beam, int(reps), ctypes.byref(best), ms.ctypes.data, len(ms)))
     return best.value, ms
+
+
+def tp_channel_stats_noalloc(x, dtype, mu, sigma, chunk_flag, chunk_raw, rfi=None, nsamp=None, stream=None):
+    """A1-A2 of a device block ``x`` (nchan, pitch) into caller-provided device
+    outputs, with no allocation by the library (see tp_dedisp.h)."""
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    nchan, pitch = x.shape
+    nsamp = pitch if nsamp is None else nsamp
+    return _check(lib().tp_channel_stats_noalloc(
+        _addr(x), dtype, nchan, nsamp, pitch, ctypes.byref(rfi) if rfi is not None else None, _addr(mu),
+        _addr(sigma), _addr(chunk_flag), _addr(chunk_raw), _stream(stream)))

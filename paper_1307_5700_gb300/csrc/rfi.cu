@@ -551,4 +551,29 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, float
   return cudaGetLastError();
 }
 
+// A1-A2 alone (bandpass statistics, channel exceedances and their dilation)
+// with the chunk sums in caller-chosen scratch; used by the entry point that
+// allocates nothing.
+cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s) {
+  if (a.dtype == TP_U8)
+    chunk_stats_u8<<<a.nchan, kThreads, 0, s>>>(a, static_cast<longlong2*>(chunk_sums));
+  else if (a.dtype == TP_F16)
+    chunk_stats_float<TP_F16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
+  else if (a.dtype == TP_BF16)
+    chunk_stats_float<TP_BF16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
+  else
+    chunk_stats_float<TP_F32><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t nflag_bytes = (int64_t)a.nchan * a.nchunk;
+  if (a.enable_channel) {
+    dilate_kernel<<<(a.nchan + kWarps - 1) / kWarps, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  e = cudaMemsetAsync(a.chunk_raw, 0, nflag_bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.chunk_flag, 0, nflag_bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.chan_nflag, 0, sizeof(int) * a.nchan, s);
+  return e;
+}
+
 }  // namespace tp

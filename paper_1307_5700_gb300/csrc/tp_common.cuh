@@ -123,6 +123,7 @@ cudaError_t launch_delay_table(int nchan, double f_lo, double bw, double t_samp,
 cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, float* y, int64_t ypitch,
                        cudaStream_t s);
 double external_spectrum_threshold(const double* sigma, int nchan, double tau_s);
+cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s);
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s);
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s);
 
