@@ -44,8 +44,10 @@ METRIC = "DM-trial*samples/s per GB300 (real-time beams sustained, p99 block lat
 WORKLOAD = "stream: 1 beam, 1024 ch 398-418 MHz, 51.2 us, 640 DMs 0-127.8 step 0.2, FP32, 2^17-sample blocks"
 
 
-def make_block(seed, delay, max_delay):
-    """One synthetic FP32 block: noise, 16 pulses on random trials, RFI bursts."""
+def make_block(seed, delay, max_delay, dtype="f32"):
+    """One synthetic block: noise, 16 pulses on random trials, RFI bursts;
+    FP32 N(0,1) by default, stored as binary16 / bfloat16, or as 8-bit
+    round(N(128, 16))."""
     g = synth.rng(seed)
     x = synth.noise(NCHAN, BLOCK, seed)
     for _ in range(16):
@@ -55,6 +57,12 @@ def make_block(seed, delay, max_delay):
         fwhm = float(g.uniform(0.5, 4.0)) * 1e-3 / TSAMP
         synth.add_pulse(x, delay[d].astype(np.float64) + t, fwhm, snr / math.sqrt(NCHAN))
     synth.apply_bursts(x, synth.poisson_bursts(NCHAN, BLOCK, seed + 7))
+    if dtype == "f16":
+        return synth.to_f16(x)
+    if dtype == "bf16":
+        return synth.to_bf16_bits(x)
+    if dtype == "u8":
+        return synth.to_u8(x * 16.0 + 128.0)
     return x
 
 
@@ -205,6 +213,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "u8"],
+                    help="sample storage format (the metric's workload is f32)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -219,13 +229,13 @@ def main():
     stream = torch.cuda.current_stream(dev)
     e = tp.tp_engine_create(local, 0, stream)
     rfi = tp.tp_rfi_defaults()
-    plan = tp.tp_create_plan(e, NCHAN, F_LO, BW, TSAMP, DMS, "f32", rfi, 5.0)
+    plan = tp.tp_create_plan(e, NCHAN, F_LO, BW, TSAMP, DMS, args.dtype, rfi, 5.0)
     delays = tp.tp_get_delay_table(plan)
     max_delay = tp.tp_plan_info(plan)["max_delay"]
     beam = tp.tp_beam_open(e, plan, BLOCK, 1 << 20)
 
-    host = [make_block(2000 + 17 * rank + i, delays, max_delay) for i in range(NBUF)]
-    dev_blocks = [torch.from_numpy(h).to(dev) for h in host]
+    host = [make_block(2000 + 17 * rank + i, delays, max_delay, args.dtype) for i in range(NBUF)]
+    dev_blocks = [torch.from_numpy(h.view(np.int16) if h.dtype == np.uint16 else h).to(dev) for h in host]
     # first block of the stream fills the overlap tail; not timed
     tp.tp_push_block(e, beam, dev_blocks[0])
     tp.tp_dedisperse(e, beam)
@@ -292,9 +302,10 @@ def main():
     e2e = None
     if not args.no_e2e:
         pinned = []
+        tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.int16, "u8": torch.uint8}[args.dtype]
         for h in host:
-            t = torch.empty(h.shape, dtype=torch.float32, pin_memory=True)
-            t.numpy()[...] = h
+            t = torch.empty(h.shape, dtype=tdt, pin_memory=True)
+            t.numpy()[...] = h.view(t.numpy().dtype)
             pinned.append(t)
         cand_buf_cap = 1 << 20
         ncand = []
@@ -316,7 +327,7 @@ def main():
         torch.cuda.synchronize(dev)
         w = max_over_ranks(time.perf_counter() - w0, world, dev)
         e2e = {"value": len(DMS) * BLOCK * ne2e * world / w, "unit": "DM-trial*samples/s",
-               "h2d_bytes_per_step": NCHAN * BLOCK * 4,
+               "h2d_bytes_per_step": int(host[0].nbytes),
                "d2h_bytes_per_step": int(8 + 24 * float(np.mean(ncand))), "steps": ne2e,
                "candidates_per_block": float(np.mean(ncand))}
 
@@ -327,13 +338,13 @@ def main():
     if rank != 0:
         return
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.dtype == "f32":
         cpu = cpu_baseline(delays, max_delay)
         cpu.pop("seconds", None)
     line = {"metric": METRIC, "value": value, "unit": "DM-trial*samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_DERIVED,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "nchan": NCHAN, "ndm": len(DMS), "block": BLOCK,
                        "overlap": int(max_delay), "beams_per_gpu": 1,
                        "l2": "inputs larger than L2 (562 MB window per block, 3 distinct blocks cycled)",

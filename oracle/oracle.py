@@ -64,6 +64,8 @@ def lib():
             "orc_dedisperse_points_float": (None, [_p, _i, _i, _i64, _i64, _p, _p, _p, _i, _p, _p, _p, _i64, _p]),
             "orc_dedisperse_points_u8": (None, [_p, _i, _i64, _i64, _p, _p, _p, _i, _p, _p, _p, _i64, _p]),
             "orc_abs_mass_points_float": (None, [_p, _i, _i, _i64, _i64, _p, _p, _p, _i, _p, _p, _p, _i64, _p]),
+            "orc_storage_bandpass": (None, [_i, _p, _i, _p]),
+            "orc_stored_mass_points": (None, [_p, _i, _i, _i64, _i64, _p, _p, _p, _i, _p, _p, _p, _i64, _p]),
             "orc_series_stats_float": (None, [_p, _i, _i64, _p, _p]),
             "orc_series_stats_int": (None, [_p, _i, _i64, _p, _p, _p, _p]),
             "orc_candidates_float": (_i64, [_p, _i, _i64, _p, _p, _d, _i, _i64, _p, _i64]),
@@ -152,7 +154,16 @@ def bandpass(x, dtype):
                               _ptr(mu), _ptr(sigma))
         return dict(mu=mu, sigma=sigma, S=S, Q=Q, V=V, b=b, external=False)
     lib().orc_bandpass_float(_ptr(x), code, nchan, nsamp, nsamp, _ptr(mu), _ptr(sigma))
-    return dict(mu=mu, sigma=sigma, external=False)
+    return dict(mu=mu, sigma=sigma, b=storage_bandpass(dtype, mu), external=False)
+
+
+def storage_bandpass(dtype, mu):
+    """Bandpass value in the data's storage format (R7): binary16 / bfloat16
+    round mu to nearest even, binary32 keeps mu (8-bit: see bandpass())."""
+    mu = _c(mu, np.float64)
+    b = np.empty_like(mu)
+    lib().orc_storage_bandpass(DTYPE_CODES[dtype], _ptr(mu), len(mu), _ptr(b))
+    return b
 
 
 def external_stats(dtype, mu, sigma):
@@ -163,6 +174,8 @@ def external_stats(dtype, mu, sigma):
     st = dict(mu=mu, sigma=sigma, external=True)
     if dtype == "u8":
         st["b"] = np.floor(mu + 0.5).astype(np.int64)
+    else:
+        st["b"] = storage_bandpass(dtype, mu)
     return st
 
 
@@ -209,7 +222,8 @@ def spectrum_mask(x, dtype, stats, rfi, chunk_flag):
 
 
 def corrected(x, dtype, stats, chunk_flag, spec_flag, W):
-    """Substituted, bandpass-corrected samples y[c][t] (R7), float64."""
+    """Substituted, bandpass-corrected samples y[c][t] = x~ - b_c (R7),
+    float64; b_c is the bandpass value in the storage format."""
     x, code = _input(x, dtype)
     nchan, nsamp = x.shape
     cf = _c(chunk_flag, np.uint8)
@@ -219,7 +233,7 @@ def corrected(x, dtype, stats, chunk_flag, spec_flag, W):
         flag = cf[:, np.arange(nsamp) // W].astype(bool) | sf.astype(bool)[None, :]
         return np.where(flag, 0, x.astype(np.int64) - b[:, None]).astype(np.float64)
     y = np.empty((nchan, nsamp), np.float64)
-    lib().orc_corrected_float(_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["mu"]), _ptr(cf),
+    lib().orc_corrected_float(_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["b"]), _ptr(cf),
                               _ptr(sf), W, _ptr(y))
     return y
 
@@ -242,7 +256,7 @@ def dedisperse(x, dtype, stats, chunk_flag, spec_flag, W, delay, T):
                                 W, _ptr(delay), ndm, T, _ptr(D))
     else:
         D = np.empty((ndm, T), np.float64)
-        lib().orc_dedisperse_float(_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["mu"]), _ptr(cf),
+        lib().orc_dedisperse_float(_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["b"]), _ptr(cf),
                                    _ptr(sf), W, _ptr(delay), ndm, T, _ptr(D))
     return D
 
@@ -264,10 +278,13 @@ def dedisperse_points(x, dtype, stats, chunk_flag, spec_flag, W, delay, d_idx, t
         return out, None
     out = np.empty(n, np.float64)
     mass = np.empty(n, np.float64)
-    args = (_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["mu"]), _ptr(cf), _ptr(sf), W,
+    args = (_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["b"]), _ptr(cf), _ptr(sf), W,
             _ptr(delay), _ptr(d_idx), _ptr(t_idx), n)
     lib().orc_dedisperse_points_float(*args, _ptr(out))
-    lib().orc_abs_mass_points_float(*args, _ptr(mass))
+    if dtype == "f32":
+        lib().orc_abs_mass_points_float(*args, _ptr(mass))
+    else:  # FP32 accumulation of the stored 16-bit samples: bounded by sum |x~|
+        lib().orc_stored_mass_points(*args, _ptr(mass))
     return out, mass
 
 

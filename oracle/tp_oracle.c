@@ -35,9 +35,11 @@
  *       over channels of (x - mu_c), flagged chunks contributing 0, is compared
  *       with tau_s sqrt(sum_c sigma_c^2), i.e. the full-band mean against tau_s
  *       times the standard deviation of that mean.
- *   R7  a flagged sample is replaced by the channel's bandpass value; after the
- *       bandpass is subtracted it contributes exactly 0.  For 8-bit data the
- *       bandpass value is the integer floor(mu_c + 1/2).
+ *   R7  a flagged sample is replaced by the channel's bandpass value b_c and b_c
+ *       is subtracted from every sample, so a flagged sample contributes
+ *       exactly 0.  b_c is mu_c expressed in the data's storage format: the
+ *       integer floor(mu_c + 1/2) for 8-bit data, mu_c rounded to nearest even
+ *       for binary16 / bfloat16 data, mu_c itself for binary32 data.
  *   R8  the detection threshold of Sec. 2.3 is (D - mu_d) >= nsigma * sigma_d
  *       on each dedispersed series, with sigma_d the population standard
  *       deviation of the series; a series with sigma_d = 0 yields nothing.
@@ -211,6 +213,35 @@ void orc_bandpass_u8(const uint8_t *x, int nchan, int64_t nsamp, int64_t pitch, 
     b[c] = (2 * s + nsamp) / (2 * nsamp);
     mu[c] = (double)s / (double)nsamp;
     sigma[c] = sqrt((double)V[c]) / (double)nsamp;
+  }
+}
+
+/* Nearest value of a 16-bit storage format (ties to even), from the format's
+ * definition: `sig` significant bits, smallest normal exponent `emin`, largest
+ * finite value `maxv`.  Used for the bandpass value of 16-bit data (R7). */
+static double round_to_format(double v, int sig, int emin, double maxv) {
+  if (v == 0.0 || !isfinite(v)) return v;
+  double a = fabs(v);
+  int e;
+  frexp(a, &e); /* a = m 2^e, m in [1/2, 1) */
+  int qexp = e - sig;
+  if (qexp < emin - sig + 1) qexp = emin - sig + 1; /* subnormal quantum */
+  double q = ldexp(1.0, qexp);
+  double r = nearbyint(a / q) * q; /* a / q is exact; default rounding is to nearest even */
+  if (r > maxv) r = INFINITY;
+  return copysign(r, v);
+}
+
+/* Bandpass value of each channel in the storage format of the data (R7):
+ * binary16 / bfloat16 round to nearest even, binary32 keeps mu. */
+void orc_storage_bandpass(int dtype, const double *mu, int n, double *b) {
+  for (int c = 0; c < n; ++c) {
+    if (dtype == ORC_F16)
+      b[c] = round_to_format(mu[c], 11, -14, 65504.0);
+    else if (dtype == ORC_BF16)
+      b[c] = round_to_format(mu[c], 8, -126, 3.3895313892515355e38);
+    else
+      b[c] = mu[c];
   }
 }
 
@@ -452,6 +483,25 @@ void orc_abs_mass_points_float(const void *x, int dtype, int nchan, int64_t nsam
     for (int c = 0; c < nchan; ++c)
       acc += fabs(corrected_float(x, dtype, pitch, mu, chunk_flag, spec_flag, nchunk, W, c,
                                   t_idx[i] + delay[(int64_t)d_idx[i] * nchan + c]));
+    out[i] = acc;
+  }
+}
+
+/* Sum over channels of |x~| (the stored, substituted samples) at the delayed
+ * positions: the magnitude against which FP32 accumulation of stored 16-bit
+ * samples is bounded. */
+void orc_stored_mass_points(const void *x, int dtype, int nchan, int64_t nsamp, int64_t pitch,
+                            const double *b, const uint8_t *chunk_flag, const uint8_t *spec_flag, int W,
+                            const int32_t *delay, const int32_t *d_idx, const int64_t *t_idx,
+                            int64_t npts, double *out) {
+  const int nchunk = W > 0 ? (int)((nsamp + W - 1) / W) : 0;
+  for (int64_t i = 0; i < npts; ++i) {
+    double acc = 0.0;
+    for (int c = 0; c < nchan; ++c) {
+      const int64_t t = t_idx[i] + delay[(int64_t)d_idx[i] * nchan + c];
+      acc += flagged(chunk_flag, spec_flag, nchunk, W, c, t) ? fabs(b[c])
+                                                              : fabs(sample(x, dtype, (int64_t)c * pitch + t));
+    }
     out[i] = acc;
   }
 }

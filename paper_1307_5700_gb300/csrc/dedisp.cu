@@ -27,6 +27,7 @@
 // The epilogue writes D (FP32, or int32 for 8-bit data, exact) and per
 // (DM, time tile) sums of D and D^2 for the series statistics of A6.
 #include <cstdint>
+#include <type_traits>
 
 #include "dispatch_gen.cuh"
 #include "tp_common.cuh"
@@ -80,38 +81,43 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
-template <int K, int S, int OMAX, int NCONS>
+// Staged sample formats.
+constexpr int kModeF32 = 0;   // FP32 y (float data)
+constexpr int kModeF16 = 1;   // binary16 x~ (binary16 data, and 8-bit data widened exactly)
+constexpr int kModeBF16 = 2;  // bfloat16 x~
+
+template <int K, int S, int OMAX, int NCONS, int MODE>
 struct Shape {
-  static constexpr int TT = 32 * S;                                          // outputs per tile
-  static constexpr int L = (S + OMAX + 1 + 3) / 4 * 4;                       // register window
-  static constexpr int ROW = (TT + kMaxOverhang + OMAX + 8 + 31) / 32 * 32;  // staged floats per channel
-  static constexpr int THREADS = (NCONS + 1) * 32;                           // + one producer warp
-  static constexpr size_t data_bytes = sizeof(float) * kStages * kNC * ROW;
+  static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
+  static constexpr int QS = 16 / EB;                                          // samples per 16 B
+  static constexpr int TT = 32 * S;                                           // outputs per tile
+  static constexpr int L = (S + OMAX + 1 + QS - 1) / QS * QS;                 // window samples
+  static constexpr int LR = L * EB / 4;                                       // window registers
+  static constexpr int ROW = (TT + kMaxOverhang + OMAX + 2 * QS + 63) / 64 * 64;  // staged samples
+  static constexpr int ROWB = ROW * EB;
+  static constexpr int THREADS = (NCONS + 1) * 32;                            // + one producer warp
+  static constexpr size_t data_bytes = (size_t)kStages * kNC * ROWB;
   static constexpr size_t del_bytes = sizeof(int) * kStages * kNC * 32;
   static constexpr size_t info_bytes = sizeof(int4) * kStages * kNC * NCONS;
   static constexpr size_t smem = data_bytes + del_bytes + info_bytes + 16 * kStages;
+  static_assert((S * EB / 16) % 2 == 1, "lane windows at an odd number of 16-byte units: no bank conflicts");
 };
 
-// Per (stage, channel, consumer warp): where the warp's window starts in
-// shared memory, the K in-window offsets (one byte each) and how many quads
-// of the window the channel needs.  Written by the producer.
-struct WarpChan {
-  int roff;    // float offset of lane 0's window
-  int offs;    // byte j = offset of DM j of the warp's group
-  int nq;      // window quads to load
-  int pad;
-};
+// Per (stage, channel, consumer warp) the producer writes an int4:
+//   x = byte offset of lane 0's window in shared memory,
+//   y = byte j: in-window offset of DM j of the warp's group,
+//   z = number of 16-byte units of the window the channel needs.
 
-template <int K, int S, int OMAX, int NCONS, bool kInt>
-__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisperse_kernel(DedispArgs a) {
-  using Sh = Shape<K, S, OMAX, NCONS>;
-  constexpr int TT = Sh::TT, L = Sh::L, ROW = Sh::ROW;
+template <int K, int S, int OMAX, int NCONS, int MODE>
+__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE>::THREADS, 1) dedisperse_kernel(DedispArgs a) {
+  using Sh = Shape<K, S, OMAX, NCONS, MODE>;
+  constexpr int TT = Sh::TT, LR = Sh::LR, ROWB = Sh::ROWB, EB = Sh::EB, QS = Sh::QS;
   static_assert(NCONS * K <= 32, "a producer lane holds one DM of the tile");
   static_assert(OMAX < 256, "offsets are packed in bytes");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* srow = reinterpret_cast<float*>(smem_raw);                               // [kStages][kNC][ROW]
-  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);                   // [kStages][kNC][32]
-  int4* sinfo = reinterpret_cast<int4*>(smem_raw + Sh::data_bytes + Sh::del_bytes);  // [kStages][kNC][NCONS]
+  unsigned char* srow = smem_raw;                                                     // [kStages][kNC][ROWB]
+  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);                       // [kStages][kNC][32]
+  int4* sinfo = reinterpret_cast<int4*>(smem_raw + Sh::data_bytes + Sh::del_bytes);      // [kStages][kNC][NCONS]
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes);
   uint64_t* empty = full + kStages;
 
@@ -123,6 +129,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
   const int nchan = a.nchan;
   const int nstage = (nchan + kNC - 1) / kNC;
   const int last = dt.nd - 1;
+  const unsigned char* ybytes = static_cast<const unsigned char*>(a.y);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
@@ -169,13 +176,13 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
         const int g0 = w * K < last ? w * K : last;
         const int lo = del[ci * 32];
         const int dw = del[ci * 32 + g0];
-        const int64_t base = (t0 + lo) & ~int64_t(3);
+        const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
         const int aw = (int)(t0 + dw - base);
         int offs = 0, omax = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
           const int jj = g0 + j <= last ? g0 + j : last;
-          int o = (aw & 3) + del[ci * 32 + jj] - dw;
+          int o = (aw & (QS - 1)) + del[ci * 32 + jj] - dw;
           // the planner bounds o by OMAX; the clamp keeps the indexed branch
           // inside its table whatever the delays hold
           o = o < 0 ? 0 : (o > OMAX ? OMAX : o);
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
           omax = o > omax ? o : omax;
         }
         sinfo[(buf * kNC + ci) * NCONS + w] =
-            make_int4((buf * kNC + ci) * ROW + (aw & ~3), offs, (S + omax + 3) >> 2, 0);
+            make_int4((buf * kNC + ci) * ROWB + (aw & ~(QS - 1)) * EB, offs, (S + omax + QS - 1) / QS, 0);
       }
       unsigned bytes[kNC];
       unsigned total = 0;
@@ -194,9 +201,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
         const int c = i * kNC + ci;
         bytes[ci] = 0;
         if (c < nchan) {
-          const int64_t base = (t0 + lo) & ~int64_t(3);
-          const int64_t end = t0 + TT + hi + 4;
-          bytes[ci] = (unsigned)((((end - base) + 3) & ~int64_t(3)) * 4);
+          const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
+          const int64_t end = t0 + TT + hi + QS;
+          bytes[ci] = (unsigned)((((end - base) * EB) + 15) & ~int64_t(15));
           total += bytes[ci];
         }
       }
@@ -208,8 +215,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
         for (int ci = 0; ci < kNC; ++ci) {
           if (!bytes[ci]) continue;
           const int c = i * kNC + ci;
-          const int64_t base = (t0 + cur[ci]) & ~int64_t(3);
-          bulk_g2s(srow + (buf * kNC + ci) * ROW, a.y + (int64_t)c * a.ypitch + base, bytes[ci], &full[buf]);
+          const int64_t base = (t0 + cur[ci]) & ~int64_t(QS - 1);
+          bulk_g2s(srow + (buf * kNC + ci) * ROWB, ybytes + ((int64_t)c * a.ypitch + base) * EB, bytes[ci],
+                   &full[buf]);
         }
       }
       ++issued;
@@ -234,9 +242,10 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
   for (int j = 0; j < K; ++j)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[j][s] = 0.f;
-  float w[L];
+  using WT = typename std::conditional<MODE == kModeF32, float, unsigned>::type;
+  WT w[LR];
 #pragma unroll
-  for (int q = 0; q < L; ++q) w[q] = 0.f;
+  for (int q = 0; q < LR; ++q) w[q] = 0;
 
   for (int i = 0; i < nstage; ++i) {
     const int buf = i % kStages;
@@ -248,35 +257,56 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
     if (live) {
       for (int ci = 0; ci < nc; ++ci) {
         const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
-        const float* r = srow + inf.x + lane * S;
+        const unsigned char* r = srow + inf.x + lane * S * EB;
 #pragma unroll
-        for (int q = 0; q < L / 4; ++q) {
+        for (int q = 0; q < LR / 4; ++q) {
           if (q < inf.z) {
-            const float4 v = *reinterpret_cast<const float4*>(r + 4 * q);
-            w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
+            if constexpr (MODE == kModeF32) {
+              const float4 v = *reinterpret_cast<const float4*>(r + 16 * q);
+              w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
+            } else {
+              const uint4 v = *reinterpret_cast<const uint4*>(r + 16 * q);
+              w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
+            }
           }
         }
 #pragma unroll
-        for (int j = 0; j < K; ++j) add_shifted<S, L, OMAX>((inf.y >> (8 * j)) & 0xff, acc[j], w);
+        for (int j = 0; j < K; ++j) {
+          const int o = (inf.y >> (8 * j)) & 0xff;
+          if constexpr (MODE == kModeF32)
+            add_shifted<S, LR, OMAX>(o, acc[j], w);
+          else
+            add_shifted_h<S, LR, OMAX, MODE == kModeBF16 ? 1 : 0>(o, acc[j], w);
+        }
       }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[buf]);
   }
 
-  // epilogue
+  // epilogue: 16-bit modes accumulated the stored samples x~; subtract the
+  // block's sum of bandpass values (exact integers for 8-bit data)
   if (!live) return;
+  const bool is_int = a.dtype == TP_U8;
+  float bhi = 0.f, blo = 0.f;
+  int bint = 0;
+  if constexpr (MODE != kModeF32) {
+    const double bs = *a.bsum;
+    bhi = (float)bs;
+    blo = (float)(bs - (double)bhi);
+    bint = (int)bs;
+  }
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     if (g0 + j > last) break;
     const int d = dt.d0 + g0 + j;
     const int64_t tl = t0 + (int64_t)lane * S;
-    if constexpr (kInt) {
+    if (is_int) {
       int* Drow = static_cast<int*>(a.D) + (int64_t)d * a.dpitch;
       long long s1 = 0, s2 = 0;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const int v = __float2int_rn(acc[j][s]);
+        const int v = __float2int_rn(acc[j][s]) - bint;
         if (tl + s < a.nout) {
           Drow[tl + s] = v;
           s1 += v;
@@ -290,6 +320,10 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
       }
       if (lane == 0) static_cast<longlong2*>(a.row_part)[(int64_t)d * a.ntt + tt] = make_longlong2(s1, s2);
     } else {
+      if constexpr (MODE != kModeF32) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) acc[j][s] = (acc[j][s] - bhi) - blo;
+      }
       float* Drow = static_cast<float*>(a.D) + (int64_t)d * a.dpitch;
       float s1 = 0.f, s2 = 0.f;
       if (tl + S <= a.nout) {
@@ -322,24 +356,26 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS>::THREADS, 1) dedisper
   }
 }
 
-template <int K, int S, int OMAX, int NCONS>
-cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
-  using Sh = Shape<K, S, OMAX, NCONS>;
+template <int K, int S, int OMAX, int NCONS, int MODE>
+cudaError_t launch_mode(const DedispArgs& a, cudaStream_t s) {
+  using Sh = Shape<K, S, OMAX, NCONS, MODE>;
   const long long grid = (long long)a.ntiles * a.ntt;
   if (grid <= 0 || grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (a.dtype == TP_U8) {
-    auto k = dedisperse_kernel<K, S, OMAX, NCONS, true>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
-    if (e != cudaSuccess) return e;
-    k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(a);
-  } else {
-    auto k = dedisperse_kernel<K, S, OMAX, NCONS, false>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
-    if (e != cudaSuccess) return e;
-    k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(a);
-  }
+  auto k = dedisperse_kernel<K, S, OMAX, NCONS, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int K, int S, int OMAX, int NCONS, int EB>
+cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
+  if constexpr (EB == 4) {
+    return launch_mode<K, S, OMAX, NCONS, kModeF32>(a, s);
+  } else {
+    if (a.dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16>(a, s);
+    return launch_mode<K, S, OMAX, NCONS, kModeF16>(a, s);
+  }
 }
 
 }  // namespace
@@ -348,16 +384,22 @@ cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
 // OMAX, consumer warps).  The planner keeps the shapes whose K-trial groups
 // all spread by at most OMAX - 3 samples; the autotuner (or the first
 // feasible shape) picks among them.
-#define TP_SHAPES(X)      \
-  X(0, 4, 20, 36, 8)      \
-  X(1, 2, 20, 16, 12)     \
-  X(2, 2, 28, 16, 8)      \
-  X(3, 3, 20, 24, 8)      \
-  X(4, 4, 12, 52, 8)      \
-  X(5, 2, 20, 24, 12)     \
-  X(6, 1, 28, 4, 16)
+// EB = bytes per staged sample: 4 for FP32 data, 2 for 16-bit and 8-bit data.
+#define TP_SHAPES(X)          \
+  X(0, 4, 20, 36, 8, 4)       \
+  X(1, 2, 20, 16, 12, 4)      \
+  X(2, 2, 28, 16, 8, 4)       \
+  X(3, 3, 20, 24, 8, 4)       \
+  X(4, 4, 12, 52, 8, 4)       \
+  X(5, 2, 20, 24, 12, 4)      \
+  X(6, 1, 28, 4, 16, 4)       \
+  X(7, 4, 24, 40, 8, 2)       \
+  X(8, 2, 24, 24, 12, 2)      \
+  X(9, 4, 8, 60, 8, 2)        \
+  X(10, 2, 24, 32, 12, 2)     \
+  X(11, 1, 24, 8, 16, 2)
 
-#define TP_SHAPE_ENTRY(i, K, S, O, N) {K, S, O, N},
+#define TP_SHAPE_ENTRY(i, K, S, O, N, EB) {K, S, O, N, EB},
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};
 #undef TP_SHAPE_ENTRY
 
@@ -365,8 +407,8 @@ int shape_tile_t(int shape) { return 32 * kShapes[shape].S; }
 
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
   switch (a.shape) {
-#define TP_SHAPE_CASE(i, K, S, O, N) \
-  case i: return launch_shape<K, S, O, N>(a, s);
+#define TP_SHAPE_CASE(i, K, S, O, N, EB) \
+  case i: return launch_shape<K, S, O, N, EB>(a, s);
     TP_SHAPES(TP_SHAPE_CASE)
 #undef TP_SHAPE_CASE
     default: return cudaErrorInvalidValue;

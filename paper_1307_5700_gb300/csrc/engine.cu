@@ -47,6 +47,42 @@ size_t dtype_size(int dtype) {
   }
 }
 
+// Nearest value of a 16-bit storage format (ties to even), from the format's
+// definition; the same rule the statistics kernel applies on the device.
+static double round_to_format(double v, int sig, int emin, double maxv) {
+  if (v == 0.0 || !std::isfinite(v)) return v;
+  const double a = std::fabs(v);
+  int e;
+  std::frexp(a, &e);
+  int qexp = e - sig;
+  if (qexp < emin - sig + 1) qexp = emin - sig + 1;
+  const double q = std::ldexp(1.0, qexp);
+  double r = std::nearbyint(a / q) * q;
+  if (r > maxv) r = INFINITY;
+  return std::copysign(r, v);
+}
+
+// Bit pattern of a value already representable in the 16-bit format.
+unsigned short storage_bits_host(int dtype, double mu) {
+  if (dtype == TP_BF16) {
+    const float f = (float)round_to_format(mu, 8, -126, 3.3895313892515355e38);
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (unsigned short)(u >> 16);
+  }
+  const double r = round_to_format(mu, 11, -14, 65504.0);
+  const unsigned short sign = std::signbit(r) ? 0x8000 : 0;
+  const double a = std::fabs(r);
+  if (a == 0.0) return sign;
+  if (std::isinf(a)) return sign | 0x7c00;
+  int e;
+  std::frexp(a, &e);                       // a = m 2^e, m in [1/2, 1)
+  if (e - 1 >= -14)                        // normal: a = (1 + f) 2^(e - 1)
+    return sign | (unsigned short)((e - 1 + 15) << 10) |
+           (unsigned short)(std::ldexp(a, 11 - e) - 1024.0);
+  return sign | (unsigned short)std::ldexp(a, 24);  // subnormal: a = m 2^-24
+}
+
 // Sum of sigma_c^2 in channel order, binary64, times tau_s: the spectrum
 // threshold under externally supplied statistics.
 double external_spectrum_threshold(const double* sigma, int nchan, double tau_s) {
@@ -99,8 +135,10 @@ struct Beam {
   uint32_t* spec_bits = nullptr;
   int* spec_nflag = nullptr;
   double* spec_thr = nullptr;
-  float* y = nullptr;
+  void* y = nullptr;          // staged series: FP32 for float data, 16-bit otherwise
   int64_t ypitch = 0;
+  unsigned short* b16 = nullptr;
+  double* bsum = nullptr;
   int* status = nullptr;
   void* D = nullptr;
   void* row_part = nullptr;
@@ -204,14 +242,19 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
 }
 
 // Tiling for the dedispersion kernel with register shape `sh`: the shape is
-// feasible when every group of K consecutive trials spreads by at most
-// OMAX - 3 samples in every channel; tiles pack up to NCONS consecutive groups
+// feasible when it stages the plan's sample size and every group of K
+// consecutive trials spreads by at most OMAX - (16 / bytes per sample - 1)
+// samples in every channel; tiles pack up to NCONS consecutive groups
 // while the tile's delay spread stays within kMaxOverhang.
-bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int sh, std::vector<DmTile>* tiles) {
+bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype, int sh,
+                std::vector<DmTile>* tiles) {
+  const int EB = dtype == TP_F32 ? 4 : 2;
+  if (kShapes[sh].EB != EB) return false;
   const int K = kShapes[sh].K;
+  const int residue = 16 / EB - 1;  // in-window offset of a 16-byte aligned copy
   for (int d0 = 0; d0 < ndm; d0 += K) {
     const int d1 = std::min(d0 + K, ndm) - 1;
-    if (spread(delay, nchan, d0, d1) + 3 > kShapes[sh].OMAX) return false;
+    if (spread(delay, nchan, d0, d1) + residue > kShapes[sh].OMAX) return false;
   }
   tiles->clear();
   int d0 = 0;
@@ -280,7 +323,10 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->spec_bits, (size_t)((nmax + 31) / 32) * 4);
   add((void**)&b->spec_nflag, 4);
   add((void**)&b->spec_thr, 8);
-  add((void**)&b->y, nc * (size_t)ypitch * 4);
+  const size_t yb = p->dtype == TP_F32 ? 4 : 2;
+  add((void**)&b->y, nc * (size_t)ypitch * yb);
+  add((void**)&b->b16, nc * 2);
+  add((void**)&b->bsum, 8);
   add((void**)&b->status, 4);
   add(&b->D, nd * (size_t)dpitch * 4);
   add(&b->row_part, nd * (size_t)ntt * 16);
@@ -378,6 +424,8 @@ RfiArgs rfi_args(const tp_plan* p, Beam* b) {
   a.bint = b->bint;
   a.mu_hi = b->mu_hi;
   a.mu_lo = b->mu_lo;
+  a.b16 = b->b16;
+  a.bsum = b->bsum;
   a.chunk_raw = b->chunk_raw;
   a.chunk_flag = b->chunk_flag;
   a.chan_nflag = b->chan_nflag;
@@ -391,6 +439,7 @@ DedispArgs dedisp_args(const tp_plan* p, Beam* b) {
   DedispArgs da{};
   da.y = b->y;
   da.ypitch = b->ypitch;
+  da.bsum = b->bsum;
   da.nchan = p->nchan;
   da.nout = b->nout;
   da.dtype = p->dtype;
@@ -629,7 +678,7 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
   p->shape = -1;
   size_t tb = 0;
   for (int sh = 0; sh < kNumShapes; ++sh) {
-    p->feasible[sh] = make_tiles(p->h_delay, ndm, nchan, sh, &p->shape_tiles[sh]);
+    p->feasible[sh] = make_tiles(p->h_delay, ndm, nchan, dtype, sh, &p->shape_tiles[sh]);
     if (!p->feasible[sh]) continue;
     if (p->shape < 0) p->shape = sh;
     const size_t bts = p->shape_tiles[sh].size() * sizeof(DmTile);
@@ -730,7 +779,7 @@ int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capac
     b->allocs.push_back(ptr);
     *it.first = ptr;
   }
-  cudaError_t ce = cudaMemset(b->y, 0, (size_t)p->nchan * b->ypitch * 4);
+  cudaError_t ce = cudaMemset(b->y, 0, (size_t)p->nchan * b->ypitch * (p->dtype == TP_F32 ? 4 : 2));
   if (ce == cudaSuccess) ce = cudaMemset(b->status, 0, 4);
   if (ce != cudaSuccess) {
     free_beam(b);
@@ -798,10 +847,12 @@ int tp_beam_set_bandpass(tp_engine* e, int beam, const double* mu, const double*
       return set_error(TP_EINVAL, "channel %d: mu/sigma invalid", c);
   std::vector<float> hi(nchan), lo(nchan);
   std::vector<int> bi(nchan);
+  std::vector<unsigned short> bh(nchan);
   for (int c = 0; c < nchan; ++c) {
     hi[c] = (float)mu[c];
     lo[c] = (float)(mu[c] - (double)hi[c]);
     bi[c] = (int)std::floor(mu[c] + 0.5);
+    bh[c] = p->dtype == TP_F16 || p->dtype == TP_BF16 ? storage_bits_host(p->dtype, mu[c]) : 0;
   }
   DeviceGuard g(e->device);
   cudaStream_t s = beam_stream(e, b);
@@ -810,6 +861,7 @@ int tp_beam_set_bandpass(tp_engine* e, int beam, const double* mu, const double*
   TP_CUDA_TRY(cudaMemcpyAsync(b->mu_hi, hi.data(), nchan * 4, cudaMemcpyHostToDevice, s));
   TP_CUDA_TRY(cudaMemcpyAsync(b->mu_lo, lo.data(), nchan * 4, cudaMemcpyHostToDevice, s));
   TP_CUDA_TRY(cudaMemcpyAsync(b->bint, bi.data(), nchan * 4, cudaMemcpyHostToDevice, s));
+  TP_CUDA_TRY(cudaMemcpyAsync(b->b16, bh.data(), nchan * 2, cudaMemcpyHostToDevice, s));
   TP_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
   b->ext_thr = external_spectrum_threshold(sigma, nchan, p->rfi.tau_spectrum);
   b->have_ext = true;

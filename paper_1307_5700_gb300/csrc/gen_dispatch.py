@@ -14,12 +14,16 @@ it when the header is older than this script).
 """
 import os
 
-# (S, OMAX) pairs used by the kernel shapes; L = S + OMAX + 1 rounded up to 4.
+# (S, OMAX) pairs used by the FP32 kernel shapes; L = S + OMAX + 1 rounded up
+# to 4 samples.
 SHAPES = [(20, 36), (20, 16), (28, 16), (20, 24), (12, 52), (28, 4)]
+# (S, OMAX) pairs of the 16-bit kernel shapes; L = S + OMAX + 1 rounded up to
+# 8 samples, held two per 32-bit register.
+SHAPES16 = [(24, 40), (24, 24), (8, 60), (24, 32), (24, 8)]
 
 
-def window(S, OMAX):
-    return (S + OMAX + 1 + 3) // 4 * 4
+def window(S, OMAX, q=4):
+    return (S + OMAX + 1 + q - 1) // q * q
 
 
 def emit(S, OMAX):
@@ -47,6 +51,41 @@ def emit(S, OMAX):
     return "\n".join(lines)
 
 
+def emit16(S, OMAX, kind):
+    """acc[s] += sample o + s of the packed window w (two samples per b32,
+    low half first), with the mixed-precision add of the sample format."""
+    L = window(S, OMAX, 8)
+    LR = L // 2
+    idx = S
+    w0 = S + 1
+    op = "add.rn.f32.f16" if kind == 0 else "add.rn.f32.bf16"
+    lines = []
+    lines.append(f"template <>\n__device__ __forceinline__ void add_shifted_h<{S}, {LR}, {OMAX}, {kind}>(int o, float (&acc)[{S}], const unsigned (&w)[{LR}]) {{")
+    body = ["{"]
+    body.append(".reg .b16 lo<" + str(LR) + ">, hi<" + str(LR) + ">;")
+    body.append("tbl: .branchtargets " + ", ".join(f"C{o}" for o in range(OMAX + 1)) + ";")
+    body.append(f"brx.idx.uni %{idx}, tbl;")
+    for o in range(OMAX + 1):
+        body.append(f"C{o}:")
+        regs = sorted({(o + s) >> 1 for s in range(S)})
+        for r in regs:
+            body.append(f"mov.b32 {{lo{r}, hi{r}}}, %{w0 + r};")
+        for s in range(S):
+            i = o + s
+            h = f"lo{i >> 1}" if i % 2 == 0 else f"hi{i >> 1}"
+            body.append(f"{op} %{s}, {h}, %{s};")
+        if o != OMAX:
+            body.append("bra.uni CEND;")
+    body.append("CEND:")
+    body.append("}")
+    asm = "\\n\"\n      \"".join(body)
+    outs = ", ".join(f'"+f"(acc[{s}])' for s in range(S))
+    ins = ", ".join([f'"r"(o)'] + [f'"r"(w[{i}])' for i in range(LR)])
+    lines.append(f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins});')
+    lines.append("}\n")
+    return "\n".join(lines)
+
+
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
     out = [
@@ -60,9 +99,16 @@ def main():
         "template <int S, int L, int OMAX>",
         "__device__ __forceinline__ void add_shifted(int o, float (&acc)[S], const float (&w)[L]);",
         "",
+        "// 16-bit samples, two per register; kind 0 = binary16, 1 = bfloat16.",
+        "template <int S, int LR, int OMAX, int KIND>",
+        "__device__ __forceinline__ void add_shifted_h(int o, float (&acc)[S], const unsigned (&w)[LR]);",
+        "",
     ]
     for S, OMAX in SHAPES:
         out.append(emit(S, OMAX))
+    for S, OMAX in SHAPES16:
+        for kind in (0, 1):
+            out.append(emit16(S, OMAX, kind))
     out.append("}  // namespace tp")
     with open(os.path.join(here, "dispatch_gen.cuh"), "w") as f:
         f.write("\n".join(out) + "\n")

@@ -13,6 +13,9 @@
 // neighbours); per-channel flagged-chunk counts.  Kernel spectrum_threshold
 // (one CTA per 256 samples): the sum over channels of the corrected samples of
 // unflagged chunks, compared with tau_s sqrt(sum_c sigma_c^2).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "tp_common.cuh"
@@ -45,6 +48,32 @@ __device__ __forceinline__ float load_as_float<TP_BF16>(const void* x, int64_t i
 
 __device__ __forceinline__ unsigned load_u8(const void* x, int64_t i) {
   return __ldg(static_cast<const unsigned char*>(x) + i);
+}
+
+// Nearest value of a 16-bit storage format (ties to even), from the format's
+// definition: `sig` significant bits, smallest normal exponent `emin`.
+__device__ double round_to_format(double v, int sig, int emin, double maxv) {
+  if (v == 0.0 || !isfinite(v)) return v;
+  const double a = fabs(v);
+  int e;
+  frexp(a, &e);
+  int qexp = e - sig;
+  if (qexp < emin - sig + 1) qexp = emin - sig + 1;
+  const double q = ldexp(1.0, qexp);
+  double r = rint(a / q) * q;
+  if (r > maxv) r = __longlong_as_double(0x7ff0000000000000LL);
+  return copysign(r, v);
+}
+
+// Bandpass value of a 16-bit format as its bit pattern.
+__device__ unsigned short storage_bits(int dtype, double mu) {
+  if (dtype == TP_F16) return __half_as_ushort(__double2half(round_to_format(mu, 11, -14, 65504.0)));
+  return __bfloat16_as_ushort(__double2bfloat16(round_to_format(mu, 8, -126, 3.3895313892515355e38)));
+}
+
+__device__ __forceinline__ double storage_value(int dtype, unsigned short bits) {
+  if (dtype == TP_F16) return (double)__half2float(__ushort_as_half(bits));
+  return (double)__uint_as_float((unsigned)bits << 16);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -187,6 +216,7 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
       const float hi = (float)mu;
       a.mu_hi[c] = hi;
       a.mu_lo[c] = (float)(mu - (double)hi);
+      if (DT != TP_F32) a.b16[c] = storage_bits(DT, mu);
       m = mu - (double)p;
     }
     s_m = m;
@@ -312,7 +342,20 @@ __global__ void __launch_bounds__(kThreads) dilate_kernel(RfiArgs a) {
 __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a, double ext_thr) {
   __shared__ double s_d[kThreads];
   __shared__ unsigned long long s_hi[kThreads], s_lo[kThreads];
+  __shared__ double s_b[kThreads];
   if (threadIdx.x == 0) *a.spec_nflag = 0;
+  // sum of the bandpass values (16-bit and 8-bit staging subtract it once)
+  double bs = 0.0;
+  if (a.dtype != TP_F32)
+    for (int c = threadIdx.x; c < a.nchan; c += kThreads)
+      bs += a.dtype == TP_U8 ? (double)a.bint[c] : storage_value(a.dtype, a.b16[c]);
+  s_b[threadIdx.x] = bs;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s_b[threadIdx.x] += s_b[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.bsum = s_b[0];
   if (a.stats_mode == TP_STATS_EXTERNAL) {
     if (threadIdx.x == 0) *a.spec_thr = ext_thr;
     return;
@@ -397,7 +440,7 @@ __device__ __forceinline__ void load_quad(const void* x, int64_t i, int64_t vali
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a, float* __restrict__ y,
+__global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a, void* __restrict__ yv,
                                                                        int64_t ypitch) {
   constexpr bool kU8 = DT == TP_U8;
   const int tid = threadIdx.x;
@@ -488,35 +531,64 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
 #pragma unroll
   for (int r = 0; r < 4; ++r) sflag[r] = (word >> (4 * q + r)) & 1u;
 
-  // pass 2: y
+  // pass 2: y (FP32 data: x - mu, flagged -> 0) or the stored samples x~
+  // (16-bit data: flagged -> b16; 8-bit data: widened to binary16, exact,
+  // flagged -> b)
   if (valid == 0) return;
   for (int c = g; c < a.nchan; c += 32) {
-    float v[4];
-    load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
     const bool any = a.chan_nflag[c] != 0;
     const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
-    float o[4];
-    if constexpr (kU8) {
-      const float b = (float)a.bint[c];
+    bool fl[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) o[r] = (sflag[r] || (any && cf[kk[r]])) ? 0.f : v[r] - b;
-    } else {
+    for (int r = 0; r < 4; ++r) fl[r] = sflag[r] || (any && cf[kk[r]]);
+    if constexpr (DT == TP_F32) {
+      float v[4];
+      load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
       const float mh = a.mu_hi[c], ml = a.mu_lo[c];
+      float o[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) o[r] = (sflag[r] || (any && cf[kk[r]])) ? 0.f : (v[r] - mh) - ml;
-    }
-    float* dst = y + (int64_t)c * ypitch + tq;
-    if (valid == 4) {
-      *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+      for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - mh) - ml;
+      float* dst = static_cast<float*>(yv) + (int64_t)c * ypitch + tq;
+      if (valid == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+      } else {
+        for (int r = 0; r < valid; ++r) dst[r] = o[r];
+      }
     } else {
-      for (int r = 0; r < valid; ++r) dst[r] = o[r];
+      unsigned short h[4];
+      if constexpr (DT == TP_U8) {
+        float v[4];
+        load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
+        const float b = (float)a.bint[c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) h[r] = __half_as_ushort(__float2half_rn(fl[r] ? b : v[r]));
+      } else {
+        const unsigned short* src = static_cast<const unsigned short*>(a.x) + (int64_t)c * a.pitch + tq;
+        const unsigned short b = a.b16[c];
+        if (valid == 4) {
+          const uint2 u = __ldg(reinterpret_cast<const uint2*>(src));
+          h[0] = u.x & 0xffff, h[1] = u.x >> 16, h[2] = u.y & 0xffff, h[3] = u.y >> 16;
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) h[r] = r < valid ? __ldg(src + r) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) h[r] = fl[r] ? b : h[r];
+      }
+      unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
+      if (valid == 4) {
+        *reinterpret_cast<uint2*>(dst) = make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16),
+                                                    (unsigned)h[2] | ((unsigned)h[3] << 16));
+      } else {
+        for (int r = 0; r < valid; ++r) dst[r] = h[r];
+      }
     }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, float* y, int64_t ypitch,
+cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void* y, int64_t ypitch,
                        cudaStream_t s) {
   if (a.dtype == TP_U8)
     chunk_stats_u8<<<a.nchan, kThreads, 0, s>>>(a, static_cast<longlong2*>(chunk_sums));

@@ -40,6 +40,8 @@ struct RfiArgs {
   int* bint;              // [nchan] integer bandpass value (8-bit)
   float* mu_hi;           // [nchan] mu split into two floats (float data)
   float* mu_lo;
+  unsigned short* b16;    // [nchan] bandpass value in the 16-bit storage format
+  double* bsum;           // [1] sum over channels of the bandpass values
   // masks
   uint8_t* chunk_raw;     // [nchan][nchunk] exceedances
   uint8_t* chunk_flag;    // [nchan][nchunk] after dilation
@@ -56,8 +58,9 @@ struct DmTile {
 };
 
 struct DedispArgs {
-  const float* y;         // substituted, corrected series [nchan][ypitch]
-  int64_t ypitch;         // floats per channel row (>= window + tile + 16)
+  const void* y;          // staged series [nchan][ypitch]: FP32 y, or 16-bit x~
+  int64_t ypitch;         // samples per channel row (>= window + tile + 16)
+  const double* bsum;     // 16-bit modes: sum over channels of the bandpass values
   int nchan;
   int64_t nout;           // T
   int dtype;
@@ -81,8 +84,9 @@ struct KernelShape {
   int S;      // consecutive outputs per lane (tile = 32 S samples)
   int OMAX;   // largest in-window offset the kernel handles
   int NCONS;  // consumer warps per CTA (DM groups per tile)
+  int EB;     // bytes per staged sample (4: FP32 y; 2: 16-bit x~)
 };
-constexpr int kNumShapes = 7;
+constexpr int kNumShapes = 12;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
@@ -120,7 +124,7 @@ constexpr int kDetectT = 4096;      // samples per detection CTA
 // ---- launchers (each returns a cudaError_t of the launch) -----------------------
 cudaError_t launch_delay_table(int nchan, double f_lo, double bw, double t_samp, const double* dm,
                                int ndm, int32_t* delay, int* err_flag, cudaStream_t s);
-cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, float* y, int64_t ypitch,
+cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void* y, int64_t ypitch,
                        cudaStream_t s);
 double external_spectrum_threshold(const double* sigma, int nchan, double tau_s);
 cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s);

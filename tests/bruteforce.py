@@ -40,12 +40,24 @@ def delays_float(nchan, f_lo, bw, t_samp, dms):
     return out
 
 
+def storage_round(v, kind):
+    """mu in the storage format, nearest with ties to even (R7)."""
+    if kind == "f32" or v == 0:
+        return v
+    sig, emin = (11, -14) if kind == "f16" else (8, -126)
+    m, e = math.frexp(abs(v))
+    q = max(e - sig, emin - sig + 1)
+    r = round(abs(v) / 2.0 ** q) * 2.0 ** q     # round() ties to even
+    return math.copysign(r, v)
+
+
 def _chunks(n, W):
     return [(lo, min(lo + W, n)) for lo in range(0, n, W)]
 
 
-def search(x, is_u8, W, tau_c, tau_s, chan_on, spec_on, delays, nsigma, dilate_channels=False):
-    """x: list of channel lists.  Returns (flags, spec, D, mu_d, sigma_d, cands)."""
+def search(x, is_u8, W, tau_c, tau_s, chan_on, spec_on, delays, nsigma, dilate_channels=False, kind="f32"):
+    """x: list of channel lists.  Returns (flags, spec, D, mu_d, sigma_d, cands).
+    kind: storage format of float data ("f32", "f16", "bf16")."""
     nchan, n = len(x), len(x[0])
     # bandpass
     if is_u8:
@@ -92,10 +104,13 @@ def search(x, is_u8, W, tau_c, tau_s, chan_on, spec_on, delays, nsigma, dilate_c
                 m = math.fsum(x[c][t] - mu[c] for c in range(nchan) if not flags[c][t // W])
                 spec[t] = m > thr
 
+    if not is_u8:
+        b = [storage_round(m, kind) for m in mu]
+
     def y(c, t):
         if flags[c][t // W] or spec[t]:
             return 0
-        return x[c][t] - (b[c] if is_u8 else mu[c])
+        return x[c][t] - b[c]
 
     dmax = max(max(r) for r in delays)
     T = n - dmax

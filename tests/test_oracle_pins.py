@@ -132,7 +132,7 @@ def test_bruteforce_agrees(dtype, seed, nchan, nsamp, W, dil):
     rfi = O.RfiParams(chunk_width=W, tau_channel=3.0, tau_spectrum=3.0, dilate_channels=dil)
     r = O.search_block(x, dtype, tab, dmax, rfi=rfi, nsigma=2.0)
     bf = BF.search(_as_lists(x, dtype), dtype == "u8", W, 3.0, 3.0, True, True, tab.tolist(), 2.0,
-                   dilate_channels=dil)
+                   dilate_channels=dil, kind=dtype if dtype != "u8" else "f32")
     assert np.array_equal(r["chunk_raw"].astype(bool), np.array(bf["raw"]))
     assert np.array_equal(r["chunk_flag"].astype(bool), np.array(bf["flags"]))
     assert np.array_equal(r["spec_flag"].astype(bool), np.array(bf["spec"]))
@@ -323,3 +323,18 @@ def test_all_zero_gap_spectra_are_not_flagged():
     sf = O.spectrum_mask(x, "u8", st, rfi, cf)
     assert not sf[300:340].any()
     assert not raw[:, 300 // 32: 340 // 32 + 1].any()
+
+
+def test_storage_bandpass_matches_library_conversions():
+    """The 16-bit bandpass value (R7) is mu rounded to nearest even in the
+    storage format: numpy's binary16 and torch's bfloat16 conversions agree."""
+    import torch
+    g = synth.rng(11)
+    mu = np.concatenate([g.standard_normal(2000) * 10 ** g.uniform(-8, 4, 2000),
+                         [0.0, -0.0, 65504.0, 6.1e-5, 5.96e-8, 1 + 2 ** -11, 1 + 3 * 2 ** -11, 128.3]])
+    b16 = O.storage_bandpass("f16", mu)
+    assert np.array_equal(b16, mu.astype(np.float16).astype(np.float64))
+    bbf = O.storage_bandpass("bf16", mu)
+    ref = torch.tensor(mu, dtype=torch.float64).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(bbf, ref)
+    assert np.array_equal(O.storage_bandpass("f32", mu), mu)
