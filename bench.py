@@ -345,7 +345,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_DERIVED,
             "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nchan": NCHAN, "ndm": len(DMS), "block": BLOCK,
+            "config": {"workload": WORKLOAD.replace("FP32", {"f32": "FP32", "f16": "binary16", "bf16": "bfloat16",
+                                                               "u8": "8-bit"}[args.dtype]),
+                       "nchan": NCHAN, "ndm": len(DMS), "block": BLOCK,
                        "overlap": int(max_delay), "beams_per_gpu": 1,
                        "l2": "inputs larger than L2 (562 MB window per block, 3 distinct blocks cycled)",
                        "parallelism": f"replicas x{world}", "kernel_shape": int(best),
