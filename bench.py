@@ -241,7 +241,7 @@ def main():
     tp.tp_dedisperse(e, beam)
     # autotune the dedispersion kernel shape on this plan's geometry
     best, shape_ms = tp.tp_autotune(e, beam, reps=2)
-    tune = {str(i): round(float(v), 3) for i, v in enumerate(shape_ms[:7]) if v >= 0}
+    tune = {str(i): round(float(v), 3) for i, v in enumerate(shape_ms) if v >= 0}
     tp.tp_dedisperse(e, beam)
     tp.tp_detect(e, beam)
     tp.tp_get_candidates(e, beam, 0)

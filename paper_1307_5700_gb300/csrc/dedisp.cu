@@ -81,12 +81,26 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// acc0 += low half, acc1 += high half of a packed pair of 16-bit samples
+// (kind 0: binary16, 1: bfloat16), FP32 accumulation.
+template <int KIND>
+__device__ __forceinline__ void add_pair_h(float& acc0, float& acc1, unsigned pr) {
+  if constexpr (KIND == 0)
+    asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n add.rn.f32.f16 %0, l, %0;\n add.rn.f32.f16 %1, h, %1;\n}"
+        : "+f"(acc0), "+f"(acc1)
+        : "r"(pr));
+  else
+    asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n add.rn.f32.bf16 %0, l, %0;\n add.rn.f32.bf16 %1, h, %1;\n}"
+        : "+f"(acc0), "+f"(acc1)
+        : "r"(pr));
+}
+
 // Staged sample formats.
 constexpr int kModeF32 = 0;   // FP32 y (float data)
 constexpr int kModeF16 = 1;   // binary16 x~ (binary16 data, and 8-bit data widened exactly)
 constexpr int kModeBF16 = 2;  // bfloat16 x~
 
-template <int K, int S, int OMAX, int NCONS, int MODE>
+template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO>
 struct Shape {
   static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
   static constexpr int QS = 16 / EB;                                          // samples per 16 B
@@ -100,7 +114,10 @@ struct Shape {
   static constexpr size_t del_bytes = sizeof(int) * kStages * kNC * 32;
   static constexpr size_t info_bytes = sizeof(int4) * kStages * kNC * NCONS;
   static constexpr size_t smem = data_bytes + del_bytes + info_bytes + 16 * kStages;
-  static_assert((S * EB / 16) % 2 == 1, "lane windows at an odd number of 16-byte units: no bank conflicts");
+  // no bank conflicts: register windows (ALGO 0) start an odd number of 16-byte
+  // units apart, direct 32-bit loads (ALGO 1) an odd number of words apart
+  static_assert(ALGO == 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
+  static_assert(ALGO == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
 };
 
 // Per (stage, channel, consumer warp) the producer writes an int4:
@@ -108,9 +125,10 @@ struct Shape {
 //   y = byte j: in-window offset of DM j of the warp's group,
 //   z = number of 16-byte units of the window the channel needs.
 
-template <int K, int S, int OMAX, int NCONS, int MODE>
-__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE>::THREADS, 1) dedisperse_kernel(DedispArgs a) {
-  using Sh = Shape<K, S, OMAX, NCONS, MODE>;
+template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
+__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS, MINB)
+    dedisperse_kernel(DedispArgs a) {
+  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO>;
   constexpr int TT = Sh::TT, LR = Sh::LR, ROWB = Sh::ROWB, EB = Sh::EB, QS = Sh::QS;
   static_assert(NCONS * K <= 32, "a producer lane holds one DM of the tile");
   static_assert(OMAX < 256, "offsets are packed in bytes");
@@ -178,6 +196,18 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE>::THREADS, 1) de
         const int dw = del[ci * 32 + g0];
         const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
         const int aw = (int)(t0 + dw - base);
+        if constexpr (ALGO == 1) {
+          // sample offset, in the staged row, of each DM's first output of lane 0
+          int o[4] = {0, 0, 0, 0};
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            const int jj = g0 + j <= last ? g0 + j : last;
+            o[j] = (int)(t0 + del[ci * 32 + jj] - base);
+          }
+          sinfo[(buf * kNC + ci) * NCONS + w] =
+              make_int4((buf * kNC + ci) * ROWB, o[0] | (o[1] << 16), o[2] | (o[3] << 16), 0);
+          continue;
+        }
         int offs = 0, omax = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -243,9 +273,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE>::THREADS, 1) de
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[j][s] = 0.f;
   using WT = typename std::conditional<MODE == kModeF32, float, unsigned>::type;
-  WT w[LR];
+  WT w[ALGO == 0 ? LR : 4];
 #pragma unroll
-  for (int q = 0; q < LR; ++q) w[q] = 0;
+  for (int q = 0; q < (ALGO == 0 ? LR : 4); ++q) w[q] = 0;
 
   for (int i = 0; i < nstage; ++i) {
     const int buf = i % kStages;
@@ -254,7 +284,35 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE>::THREADS, 1) de
       return;
     }
     const int nc = nchan - i * kNC < kNC ? nchan - i * kNC : kNC;
-    if (live) {
+    if (live && ALGO == 1) {
+      // direct loads: each DM reads its own S samples at its own offset
+      for (int ci = 0; ci < nc; ++ci) {
+        const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const int oj = ((j < 2 ? inf.y : inf.z) >> (16 * (j & 1))) & 0xffff;
+          const int p = oj + lane * S;
+          if constexpr (MODE == kModeF32) {
+            const float* r = reinterpret_cast<const float*>(srow + inf.x) + p;
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2) acc[j][s2] += r[s2];
+          } else {
+            // words holding samples p .. p + S (two per word); an odd start
+            // shifts every pair by one half-word
+            const unsigned* r = reinterpret_cast<const unsigned*>(srow + inf.x) + (p >> 1);
+            const unsigned sel = (p & 1) ? 0x5432u : 0x3210u;
+            unsigned wv[S / 2 + 1];
+#pragma unroll
+            for (int k = 0; k <= S / 2; ++k) wv[k] = r[k];
+#pragma unroll
+            for (int k = 0; k < S / 2; ++k) {
+              const unsigned pr = __byte_perm(wv[k], wv[k + 1], sel);
+              add_pair_h<MODE == kModeBF16 ? 1 : 0>(acc[j][2 * k], acc[j][2 * k + 1], pr);
+            }
+          }
+        }
+      }
+    } else if (live) {
       for (int ci = 0; ci < nc; ++ci) {
         const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
         const unsigned char* r = srow + inf.x + lane * S * EB;
@@ -273,10 +331,12 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE>::THREADS, 1) de
 #pragma unroll
         for (int j = 0; j < K; ++j) {
           const int o = (inf.y >> (8 * j)) & 0xff;
-          if constexpr (MODE == kModeF32)
-            add_shifted<S, LR, OMAX>(o, acc[j], w);
-          else
-            add_shifted_h<S, LR, OMAX, MODE == kModeBF16 ? 1 : 0>(o, acc[j], w);
+          if constexpr (ALGO == 0) {
+            if constexpr (MODE == kModeF32)
+              add_shifted<S, LR, OMAX>(o, acc[j], w);
+            else
+              add_shifted_h<S, LR, OMAX, MODE == kModeBF16 ? 1 : 0>(o, acc[j], w);
+          }
         }
       }
     }
@@ -326,9 +386,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE>::THREADS, 1) de
       }
       float* Drow = static_cast<float*>(a.D) + (int64_t)d * a.dpitch;
       float s1 = 0.f, s2 = 0.f;
-      if (tl + S <= a.nout) {
+      if (S % 4 == 0 && tl + S <= a.nout) {
 #pragma unroll
-        for (int s = 0; s < S; s += 4)
+        for (int s = 0; s < (S / 4) * 4; s += 4)
           *reinterpret_cast<float4*>(Drow + tl + s) =
               make_float4(acc[j][s], acc[j][s + 1], acc[j][s + 2], acc[j][s + 3]);
 #pragma unroll
@@ -356,25 +416,25 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE>::THREADS, 1) de
   }
 }
 
-template <int K, int S, int OMAX, int NCONS, int MODE>
+template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
 cudaError_t launch_mode(const DedispArgs& a, cudaStream_t s) {
-  using Sh = Shape<K, S, OMAX, NCONS, MODE>;
+  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO>;
   const long long grid = (long long)a.ntiles * a.ntt;
   if (grid <= 0 || grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-  auto k = dedisperse_kernel<K, S, OMAX, NCONS, MODE>;
+  auto k = dedisperse_kernel<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int K, int S, int OMAX, int NCONS, int EB>
+template <int K, int S, int OMAX, int NCONS, int EB, int ALGO, int MINB>
 cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
   if constexpr (EB == 4) {
-    return launch_mode<K, S, OMAX, NCONS, kModeF32>(a, s);
+    return launch_mode<K, S, OMAX, NCONS, kModeF32, ALGO, MINB>(a, s);
   } else {
-    if (a.dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16>(a, s);
-    return launch_mode<K, S, OMAX, NCONS, kModeF16>(a, s);
+    if (a.dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16, ALGO, MINB>(a, s);
+    return launch_mode<K, S, OMAX, NCONS, kModeF16, ALGO, MINB>(a, s);
   }
 }
 
@@ -385,21 +445,29 @@ cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
 // all spread by at most OMAX - 3 samples; the autotuner (or the first
 // feasible shape) picks among them.
 // EB = bytes per staged sample: 4 for FP32 data, 2 for 16-bit and 8-bit data.
-#define TP_SHAPES(X)          \
-  X(0, 4, 20, 36, 8, 4)       \
-  X(1, 2, 20, 16, 12, 4)      \
-  X(2, 2, 28, 16, 8, 4)       \
-  X(3, 3, 20, 24, 8, 4)       \
-  X(4, 4, 12, 52, 8, 4)       \
-  X(5, 2, 20, 24, 12, 4)      \
-  X(6, 1, 28, 4, 16, 4)       \
-  X(7, 4, 24, 40, 8, 2)       \
-  X(8, 2, 24, 24, 12, 2)      \
-  X(9, 4, 8, 60, 8, 2)        \
-  X(10, 2, 24, 32, 12, 2)     \
-  X(11, 1, 24, 8, 16, 2)
+// ALGO 0: register window + jump-table shifted adds (reuse across the K DMs);
+// ALGO 1: direct shared loads per DM (no offset bound, OMAX unused).
+// MINB: CTAs per SM the register allocation is sized for.
+#define TP_SHAPES(X)                 \
+  X(0, 4, 20, 36, 8, 4, 0, 1)        \
+  X(1, 2, 20, 16, 12, 4, 0, 1)       \
+  X(2, 2, 28, 16, 8, 4, 0, 1)        \
+  X(3, 3, 20, 24, 8, 4, 0, 1)        \
+  X(4, 4, 12, 52, 8, 4, 0, 1)        \
+  X(5, 2, 20, 24, 12, 4, 0, 1)       \
+  X(6, 1, 28, 4, 16, 4, 0, 1)        \
+  X(7, 4, 24, 40, 8, 2, 0, 1)        \
+  X(8, 2, 24, 24, 12, 2, 0, 1)       \
+  X(9, 4, 8, 60, 8, 2, 0, 1)         \
+  X(10, 2, 24, 32, 12, 2, 0, 1)      \
+  X(11, 1, 24, 8, 16, 2, 0, 1)       \
+  X(12, 2, 27, 0, 8, 4, 1, 2)        \
+  X(13, 4, 15, 0, 8, 4, 1, 2)        \
+  X(14, 2, 26, 0, 8, 2, 1, 2)        \
+  X(15, 4, 22, 0, 8, 2, 1, 1)        \
+  X(16, 2, 22, 0, 16, 2, 1, 1)
 
-#define TP_SHAPE_ENTRY(i, K, S, O, N, EB) {K, S, O, N, EB},
+#define TP_SHAPE_ENTRY(i, K, S, O, N, EB, A, M) {K, S, O, N, EB, A},
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};
 #undef TP_SHAPE_ENTRY
 
@@ -407,8 +475,8 @@ int shape_tile_t(int shape) { return 32 * kShapes[shape].S; }
 
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
   switch (a.shape) {
-#define TP_SHAPE_CASE(i, K, S, O, N, EB) \
-  case i: return launch_shape<K, S, O, N, EB>(a, s);
+#define TP_SHAPE_CASE(i, K, S, O, N, EB, A, M) \
+  case i: return launch_shape<K, S, O, N, EB, A, M>(a, s);
     TP_SHAPES(TP_SHAPE_CASE)
 #undef TP_SHAPE_CASE
     default: return cudaErrorInvalidValue;

@@ -252,10 +252,11 @@ bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype
   if (kShapes[sh].EB != EB) return false;
   const int K = kShapes[sh].K;
   const int residue = 16 / EB - 1;  // in-window offset of a 16-byte aligned copy
-  for (int d0 = 0; d0 < ndm; d0 += K) {
-    const int d1 = std::min(d0 + K, ndm) - 1;
-    if (spread(delay, nchan, d0, d1) + residue > kShapes[sh].OMAX) return false;
-  }
+  if (kShapes[sh].ALGO == 0)
+    for (int d0 = 0; d0 < ndm; d0 += K) {
+      const int d1 = std::min(d0 + K, ndm) - 1;
+      if (spread(delay, nchan, d0, d1) + residue > kShapes[sh].OMAX) return false;
+    }
   tiles->clear();
   int d0 = 0;
   while (d0 < ndm) {

@@ -85,8 +85,9 @@ struct KernelShape {
   int OMAX;   // largest in-window offset the kernel handles
   int NCONS;  // consumer warps per CTA (DM groups per tile)
   int EB;     // bytes per staged sample (4: FP32 y; 2: 16-bit x~)
+  int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads
 };
-constexpr int kNumShapes = 12;
+constexpr int kNumShapes = 17;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
