@@ -183,6 +183,19 @@ int tp_dedisperse(tp_engine *e, int beam);
  * was dedispersed and not yet detected.  TP_ENOTREADY if not dedispersed. */
 int tp_detect(tp_engine *e, int beam);
 
+/* A1-A7 for every beam holding a new block, as one batch on the engine stream:
+ * per-beam statistics / masks / substitution kernels, then ONE dedispersion
+ * launch per (kernel shape, sample format) group covering all the group's
+ * beams (uneven DM ranges and block lengths included), then per-beam
+ * detection.  With use_graph = 1 the whole batch is recorded once into a CUDA
+ * graph, cached per batch layout (beams, window parity, block length, kernel
+ * shape) and replayed on later calls; this needs a non-default engine
+ * stream.  *nbeams (may be NULL) receives the number of beams processed.
+ * Beams given their own stream with tp_beam_set_stream are refused
+ * (TP_EINVAL); TP_ENOTREADY if no beam holds a new block.  Results equal the
+ * per-beam tp_dedisperse / tp_detect calls. */
+int tp_run_ready(tp_engine *e, int use_graph, int *nbeams);
+
 /* Wait for the beam's detection and copy min(cap, n_total) candidates, sorted
  * by (dm_idx, t_abs), to host memory `out`.  *n_total receives the number
  * found (which can exceed the beam's capacity; only the first

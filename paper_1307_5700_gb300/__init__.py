@@ -46,6 +46,7 @@ EXPORTS = (
     "tp_get_series", "tp_get_bandpass", "tp_get_masks", "tp_get_series_stats",
     "tp_set_profiling", "tp_get_stage_times", "tp_engine_launches", "tp_last_error_string",
     "tp_version", "tp_plan_shapes", "tp_plan_set_shape", "tp_autotune", "tp_channel_stats_noalloc",
+    "tp_run_ready",
 )
 
 
@@ -108,6 +109,7 @@ _SIGS = {
     "tp_autotune": (_i, [_vp, _i, _i, _vp, _vp, _i]),
     "tp_channel_stats_noalloc": (_i, [_vp, _i, _i, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                      _vp]),
+    "tp_run_ready": (_i, [_vp, _i, _vp]),
     "tp_last_error_string": (ctypes.c_char_p, []),
     "tp_version": (_i, []),
 }
@@ -374,3 +376,11 @@ def tp_channel_stats_noalloc(x, dtype, mu, sigma, chunk_flag, chunk_raw, rfi=Non
     return _check(lib().tp_channel_stats_noalloc(
         _addr(x), dtype, nchan, nsamp, pitch, ctypes.byref(rfi) if rfi is not None else None, _addr(mu),
         _addr(sigma), _addr(chunk_flag), _addr(chunk_raw), _stream(stream)))
+
+
+def tp_run_ready(e, use_graph=False):
+    """A1-A7 for every beam holding a new block, batched (see tp_dedisp.h);
+    returns the number of beams processed."""
+    n = ctypes.c_int()
+    _check(lib().tp_run_ready(e, int(bool(use_graph)), ctypes.byref(n)))
+    return n.value

@@ -127,8 +127,21 @@ struct Shape {
 
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
 __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS, MINB)
-    dedisperse_kernel(DedispArgs a) {
+    dedisperse_kernel(BatchArgs ba) {
   using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO>;
+  // the CTA's beam: last b with cta_start[b] <= blockIdx.x
+  int bi = 0;
+  {
+    int lo = 0, hi = ba.nbeams - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ba.cta_start[mid] <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    bi = lo;
+  }
+  const DedispArgs& a = ba.beams[bi];
+  const int local = (int)blockIdx.x - ba.cta_start[bi];
   constexpr int TT = Sh::TT, LR = Sh::LR, ROWB = Sh::ROWB, EB = Sh::EB, QS = Sh::QS;
   static_assert(NCONS * K <= 32, "a producer lane holds one DM of the tile");
   static_assert(OMAX < 256, "offsets are packed in bytes");
@@ -139,8 +152,8 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes);
   uint64_t* empty = full + kStages;
 
-  const int tile = blockIdx.x % a.ntiles;
-  const int tt = blockIdx.x / a.ntiles;
+  const int tile = local % a.ntiles;
+  const int tt = local / a.ntiles;
   const DmTile dt = a.tiles[tile];
   const int64_t t0 = (int64_t)tt * TT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -417,24 +430,23 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 }
 
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
-cudaError_t launch_mode(const DedispArgs& a, cudaStream_t s) {
+cudaError_t launch_mode(const BatchArgs& ba, int ctas, cudaStream_t s) {
   using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO>;
-  const long long grid = (long long)a.ntiles * a.ntt;
-  if (grid <= 0 || grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (ctas <= 0) return cudaErrorInvalidValue;
   auto k = dedisperse_kernel<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(a);
+  k<<<(unsigned)ctas, Sh::THREADS, Sh::smem, s>>>(ba);
   return cudaGetLastError();
 }
 
 template <int K, int S, int OMAX, int NCONS, int EB, int ALGO, int MINB>
-cudaError_t launch_shape(const DedispArgs& a, cudaStream_t s) {
+cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t s) {
   if constexpr (EB == 4) {
-    return launch_mode<K, S, OMAX, NCONS, kModeF32, ALGO, MINB>(a, s);
+    return launch_mode<K, S, OMAX, NCONS, kModeF32, ALGO, MINB>(ba, ctas, s);
   } else {
-    if (a.dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16, ALGO, MINB>(a, s);
-    return launch_mode<K, S, OMAX, NCONS, kModeF16, ALGO, MINB>(a, s);
+    if (dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16, ALGO, MINB>(ba, ctas, s);
+    return launch_mode<K, S, OMAX, NCONS, kModeF16, ALGO, MINB>(ba, ctas, s);
   }
 }
 
@@ -473,10 +485,10 @@ const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};
 
 int shape_tile_t(int shape) { return 32 * kShapes[shape].S; }
 
-cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
-  switch (a.shape) {
+cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s) {
+  switch (shape) {
 #define TP_SHAPE_CASE(i, K, S, O, N, EB, A, M) \
-  case i: return launch_shape<K, S, O, N, EB, A, M>(a, s);
+  case i: return launch_shape<K, S, O, N, EB, A, M>(ba, dtype, ctas, s);
     TP_SHAPES(TP_SHAPE_CASE)
 #undef TP_SHAPE_CASE
     default: return cudaErrorInvalidValue;

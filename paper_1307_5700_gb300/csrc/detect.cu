@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
         tp_candidate r;
         r.beam = a.beam;
         r.dm_idx = d;
-        r.t_abs = a.t0_abs + t;
+        r.t_abs = *a.t0_abs + t;
         r.snr = (float)__ddiv_rn(__dsub_rn(v, mu), sigma);
         r.value = (float)v;
         a.cand[pos] = r;

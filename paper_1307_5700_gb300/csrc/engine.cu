@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -102,6 +103,8 @@ namespace {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+constexpr size_t kBatchBytes = 512 * 1024;  // batch arguments of up to ~2000 beams
+
 enum BeamState { kEmpty = 0, kReady = 1, kDedispersed = 2, kDetected = 3 };
 
 struct Beam {
@@ -135,6 +138,8 @@ struct Beam {
   uint32_t* spec_bits = nullptr;
   int* spec_nflag = nullptr;
   double* spec_thr = nullptr;
+  void* d_args = nullptr;     // device copy of this beam's dedispersion arguments
+  long long* d_t0 = nullptr;  // device copy of t0_abs (read by the detection kernels)
   void* y = nullptr;          // staged series: FP32 for float data, 16-bit otherwise
   int64_t ypitch = 0;
   unsigned short* b16 = nullptr;
@@ -163,6 +168,10 @@ struct Beam {
   int ntt = 0;
   bool have_ext = false;
   double ext_thr = 0.0;
+  // last arguments uploaded to d_args
+  DedispArgs h_args{};
+  int h_cta[2] = {0, 0};
+  bool h_args_valid = false;
   // stage timing (tp_set_profiling)
   struct EventSet {
     cudaEvent_t ev[6];  // push start/end, rfi start, rfi end / dd start, dd end, detect end
@@ -196,12 +205,20 @@ struct tp_plan {
   size_t bytes = 0;
 };
 
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  void* d_args = nullptr;  // the batch arguments the graph's launches read
+};
+
 struct tp_engine {
   int device = 0;
   size_t budget = 0, used = 0;
   cudaStream_t stream = nullptr;
   bool profiling = false;
   uint64_t launches = 0;
+  void* d_batch = nullptr;  // batch arguments for launches outside graphs
+  std::vector<unsigned char> h_batch;
+  std::map<std::string, GraphEntry> graphs;
   std::vector<tp_plan*> plans;
   std::vector<Beam*> beams;
   std::recursive_mutex mu;
@@ -329,6 +346,8 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->b16, nc * 2);
   add((void**)&b->bsum, 8);
   add((void**)&b->status, 4);
+  add(&b->d_args, sizeof(DedispArgs) + 16);
+  add((void**)&b->d_t0, 8);
   add(&b->D, nd * (size_t)dpitch * 4);
   add(&b->row_part, nd * (size_t)ntt * 16);
   add((void**)&b->row_mu, nd * 8);
@@ -459,30 +478,57 @@ DedispArgs dedisp_args(const tp_plan* p, Beam* b) {
   return da;
 }
 
-int issue_dedisperse(tp_engine* e, Beam* b) {
+// Launch the dedispersion kernel for one beam with shape `shape` (its args
+// are re-uploaded only when they changed).
+int launch_single(tp_engine* e, Beam* b, const DedispArgs& da, int shape, cudaStream_t s) {
+  const int ctas = da.ntiles * da.ntt;
+  if (!b->h_args_valid || std::memcmp(&b->h_args, &da, sizeof da) != 0 || b->h_cta[1] != ctas) {
+    unsigned char buf[sizeof(DedispArgs) + 16];
+    std::memcpy(buf, &da, sizeof da);
+    const int cta[2] = {0, ctas};
+    std::memcpy(buf + sizeof da, cta, sizeof cta);
+    TP_CUDA_TRY(cudaMemcpyAsync(b->d_args, buf, sizeof buf, cudaMemcpyHostToDevice, s));
+    b->h_args = da;
+    b->h_cta[1] = ctas;
+    b->h_args_valid = true;
+  }
+  BatchArgs ba{static_cast<const DedispArgs*>(b->d_args),
+               reinterpret_cast<const int*>(static_cast<unsigned char*>(b->d_args) + sizeof(DedispArgs)), 1};
+  TP_CUDA_TRY(launch_dedisperse(shape, da.dtype, ba, ctas, s));
+  e->launches += 1;
+  return TP_OK;
+}
+
+int issue_rfi(tp_engine* e, Beam* b, cudaStream_t s) {
   const tp_plan* p = b->plan;
   if (b->state != kReady) return set_error(TP_ENOTREADY, "beam %d holds no new block", b->id);
   if (p->rfi.stats_mode == TP_STATS_EXTERNAL && !b->have_ext)
     return set_error(TP_ENOTREADY, "beam %d: external statistics not set", b->id);
-  cudaStream_t s = beam_stream(e, b);
   RfiArgs ra = rfi_args(p, b);
-  prof_record(e, b, 2, s);
   TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->ext_thr, b->y, b->ypitch, s));
-  prof_record(e, b, 3, s);
   e->launches += 4;
+  return TP_OK;
+}
+
+int issue_dedisperse(tp_engine* e, Beam* b) {
+  const tp_plan* p = b->plan;
+  cudaStream_t s = beam_stream(e, b);
+  if (b->state == kReady) prof_record(e, b, 2, s);
+  int rc = issue_rfi(e, b, s);
+  if (rc) return rc;
+  prof_record(e, b, 3, s);
   DedispArgs da = dedisp_args(p, b);
   b->ntt = da.ntt;
-  TP_CUDA_TRY(launch_dedisperse(da, s));
+  rc = launch_single(e, b, da, p->shape, s);
+  if (rc) return rc;
   prof_record(e, b, 4, s);
-  e->launches += 1;
   b->state = kDedispersed;
   return TP_OK;
 }
 
-int issue_detect(tp_engine* e, Beam* b) {
+int issue_detect(tp_engine* e, Beam* b, cudaStream_t s) {
   const tp_plan* p = b->plan;
   if (b->state != kDedispersed) return set_error(TP_ENOTREADY, "beam %d is not dedispersed", b->id);
-  cudaStream_t s = beam_stream(e, b);
   DetectArgs a{};
   a.D = b->D;
   a.dpitch = b->dpitch;
@@ -493,7 +539,7 @@ int issue_detect(tp_engine* e, Beam* b) {
   a.ntt = b->ntt;
   a.nsigma = p->nsigma;
   a.beam = b->id;
-  a.t0_abs = b->t0_abs;
+  a.t0_abs = b->d_t0;
   a.row_mu = b->row_mu;
   a.row_sigma = b->row_sigma;
   a.row_thr_f = b->row_thr_f;
@@ -512,6 +558,91 @@ int issue_detect(tp_engine* e, Beam* b) {
   TP_CUDA_TRY(cudaEventRecord(b->ev_detect, s));
   b->state = kDetected;
   return TP_OK;
+}
+
+// ---- batches: every beam holding a new block, one dedispersion launch per
+// (kernel shape, sample format) group, all on the engine stream.
+struct BatchPlan {
+  std::vector<Beam*> beams;                         // in launch order
+  std::vector<std::pair<int, int>> groups;          // (first index, count)
+  std::vector<DedispArgs> args;                     // per beam
+  std::vector<int> cta;                             // per group: count + 1 starts, concatenated
+  std::string key;
+};
+
+BatchPlan plan_batch(tp_engine* e) {
+  BatchPlan bp;
+  std::vector<Beam*> ready;
+  for (Beam* b : e->beams)
+    if (b && b->state == kReady) ready.push_back(b);
+  std::stable_sort(ready.begin(), ready.end(), [](const Beam* x, const Beam* y) {
+    const int mx = x->plan->dtype == TP_BF16, my = y->plan->dtype == TP_BF16;
+    return x->plan->shape != y->plan->shape ? x->plan->shape < y->plan->shape : mx < my;
+  });
+  char tmp[96];
+  for (size_t i = 0; i < ready.size(); ++i) {
+    Beam* b = ready[i];
+    const bool start = i == 0 || ready[i - 1]->plan->shape != b->plan->shape ||
+                       (ready[i - 1]->plan->dtype == TP_BF16) != (b->plan->dtype == TP_BF16);
+    if (start) bp.groups.push_back({(int)i, 0});
+    bp.groups.back().second++;
+    bp.beams.push_back(b);
+    DedispArgs da = dedisp_args(b->plan, b);
+    bp.args.push_back(da);
+    snprintf(tmp, sizeof tmp, "%d:%d:%lld:%d:%d;", b->id, b->cur, (long long)b->nout, b->plan->shape,
+             (int)b->plan->h_tiles.size());
+    bp.key += tmp;
+  }
+  for (auto& g : bp.groups) {
+    int acc = 0;
+    for (int k = 0; k < g.second; ++k) {
+      bp.cta.push_back(acc);
+      const DedispArgs& a = bp.args[g.first + k];
+      acc += a.ntiles * a.ntt;
+    }
+    bp.cta.push_back(acc);
+  }
+  return bp;
+}
+
+size_t batch_bytes(const BatchPlan& bp) { return bp.args.size() * sizeof(DedispArgs) + bp.cta.size() * 4 + 16; }
+
+// Issue RFI + batched dedispersion + detection for a planned batch; batch
+// arguments at `d_args` (device) must already hold the plan's arguments.
+int issue_batch(tp_engine* e, BatchPlan& bp, void* d_args, bool detect) {
+  cudaStream_t s = e->stream;
+  for (Beam* b : bp.beams) {
+    int rc = issue_rfi(e, b, s);
+    if (rc) return rc;
+  }
+  const DedispArgs* dargs = static_cast<const DedispArgs*>(d_args);
+  const int* dcta = reinterpret_cast<const int*>(static_cast<unsigned char*>(d_args) +
+                                                 bp.args.size() * sizeof(DedispArgs));
+  int coff = 0;
+  for (auto& g : bp.groups) {
+    BatchArgs ba{dargs + g.first, dcta + coff, g.second};
+    const int ctas = bp.cta[coff + g.second];
+    const Beam* b0 = bp.beams[g.first];
+    TP_CUDA_TRY(launch_dedisperse(b0->plan->shape, b0->plan->dtype, ba, ctas, s));
+    e->launches += 1;
+    coff += g.second + 1;
+  }
+  for (size_t i = 0; i < bp.beams.size(); ++i) {
+    bp.beams[i]->ntt = bp.args[i].ntt;
+    bp.beams[i]->state = kDedispersed;
+  }
+  if (detect)
+    for (Beam* b : bp.beams) {
+      int rc = issue_detect(e, b, s);
+      if (rc) return rc;
+    }
+  return TP_OK;
+}
+
+void pack_batch(const BatchPlan& bp, std::vector<unsigned char>* out) {
+  out->resize(batch_bytes(bp));
+  std::memcpy(out->data(), bp.args.data(), bp.args.size() * sizeof(DedispArgs));
+  std::memcpy(out->data() + bp.args.size() * sizeof(DedispArgs), bp.cta.data(), bp.cta.size() * 4);
 }
 
 }  // namespace
@@ -549,6 +680,10 @@ int tp_engine_create(int device, size_t hbm_budget_bytes, void* cuda_stream, tp_
   TP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   tp_engine* e = new (std::nothrow) tp_engine();
   if (!e) return set_error(TP_ENOMEM, "engine allocation");
+  if (cudaMalloc(&e->d_batch, kBatchBytes) != cudaSuccess) {
+    delete e;
+    return set_error(TP_ENOMEM, "engine batch arguments");
+  }
   e->device = device;
   e->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
   e->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -576,6 +711,12 @@ int tp_engine_destroy(tp_engine* e) {
       delete p;
     }
     e->plans.clear();
+    for (auto& kv : e->graphs) {
+      cudaGraphExecDestroy(kv.second.exec);
+      cudaFree(kv.second.d_args);
+    }
+    e->graphs.clear();
+    cudaFree(e->d_batch);
   }
   delete e;
   return TP_OK;
@@ -910,6 +1051,7 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
     b->nout = nsamp;
     b->t0_abs = b->pushed - dmax;
   }
+  TP_CUDA_TRY(cudaMemcpyAsync(b->d_t0, &b->t0_abs, 8, cudaMemcpyHostToDevice, s));
   prof_record(e, b, 1, s);
   b->pushed += nsamp;
   b->state = kReady;
@@ -925,14 +1067,13 @@ int tp_dedisperse(tp_engine* e, int beam) {
     if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
     return issue_dedisperse(e, b);
   }
-  int n = 0;
-  for (Beam* b : e->beams)
-    if (b && b->state == kReady) {
-      int rc = issue_dedisperse(e, b);
-      if (rc) return rc;
-      ++n;
-    }
-  return n ? TP_OK : set_error(TP_ENOTREADY, "no beam holds a new block");
+  BatchPlan bp = plan_batch(e);
+  if (bp.beams.empty()) return set_error(TP_ENOTREADY, "no beam holds a new block");
+  const size_t need = batch_bytes(bp);
+  if (need > kBatchBytes) return set_error(TP_EINVAL, "batch of %zu beams too large", bp.beams.size());
+  pack_batch(bp, &e->h_batch);
+  TP_CUDA_TRY(cudaMemcpyAsync(e->d_batch, e->h_batch.data(), need, cudaMemcpyHostToDevice, e->stream));
+  return issue_batch(e, bp, e->d_batch, false);
 }
 
 int tp_detect(tp_engine* e, int beam) {
@@ -942,16 +1083,85 @@ int tp_detect(tp_engine* e, int beam) {
   if (beam >= 0) {
     Beam* b = get_beam(e, beam);
     if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
-    return issue_detect(e, b);
+    return issue_detect(e, b, beam_stream(e, b));
   }
   int n = 0;
   for (Beam* b : e->beams)
     if (b && b->state == kDedispersed) {
-      int rc = issue_detect(e, b);
+      int rc = issue_detect(e, b, e->stream);
       if (rc) return rc;
       ++n;
     }
   return n ? TP_OK : set_error(TP_ENOTREADY, "no beam is dedispersed");
+}
+
+int tp_run_ready(tp_engine* e, int use_graph, int* nbeams) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  BatchPlan bp = plan_batch(e);
+  if (nbeams) *nbeams = (int)bp.beams.size();
+  if (bp.beams.empty()) return set_error(TP_ENOTREADY, "no beam holds a new block");
+  const size_t need = batch_bytes(bp);
+  if (need > kBatchBytes) return set_error(TP_EINVAL, "batch of %zu beams too large", bp.beams.size());
+  for (Beam* b : bp.beams)
+    if (b->stream && b->stream != e->stream)
+      return set_error(TP_EINVAL, "batched beams run on the engine stream (beam %d has its own)", b->id);
+  if (!use_graph) {
+    pack_batch(bp, &e->h_batch);
+    TP_CUDA_TRY(cudaMemcpyAsync(e->d_batch, e->h_batch.data(), need, cudaMemcpyHostToDevice, e->stream));
+    return issue_batch(e, bp, e->d_batch, true);
+  }
+  if (!e->stream) return set_error(TP_EINVAL, "graphs need a non-default engine stream");
+  auto it = e->graphs.find(bp.key);
+  if (it == e->graphs.end()) {
+    GraphEntry ge;
+    TP_CUDA_TRY(cudaMalloc(&ge.d_args, need));
+    pack_batch(bp, &e->h_batch);
+    TP_CUDA_TRY(cudaMemcpy(ge.d_args, e->h_batch.data(), need, cudaMemcpyHostToDevice));
+    // capture a copy of the states: issuing advances them
+    std::vector<BeamState> st;
+    for (Beam* b : bp.beams) st.push_back(b->state);
+    const bool prof = e->profiling;
+    e->profiling = false;
+    TP_CUDA_TRY(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    const uint64_t l0 = e->launches;
+    int rc = issue_batch(e, bp, ge.d_args, true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e->stream, &graph);
+    e->profiling = prof;
+    e->launches = l0;
+    for (size_t i = 0; i < bp.beams.size(); ++i) bp.beams[i]->state = st[i];
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaFree(ge.d_args);
+      return rc;
+    }
+    if (ce != cudaSuccess) {
+      cudaFree(ge.d_args);
+      return cuda_error(ce, "cudaStreamEndCapture");
+    }
+    ce = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      cudaFree(ge.d_args);
+      return cuda_error(ce, "cudaGraphInstantiate");
+    }
+    it = e->graphs.emplace(bp.key, ge).first;
+  }
+  TP_CUDA_TRY(cudaGraphLaunch(it->second.exec, e->stream));
+  // the graph ran every stage of every beam of the batch
+  uint64_t nl = 0;
+  for (Beam* b : bp.beams) nl += 4 + 4;
+  nl += bp.groups.size();
+  e->launches += nl;
+  for (size_t i = 0; i < bp.beams.size(); ++i) {
+    Beam* b = bp.beams[i];
+    b->ntt = bp.args[i].ntt;
+    b->state = kDetected;
+    TP_CUDA_TRY(cudaEventRecord(b->ev_detect, e->stream));
+  }
+  return TP_OK;
 }
 
 int tp_get_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, int* n_total) {
@@ -1147,12 +1357,15 @@ int tp_autotune(tp_engine* e, int beam, int reps, int* best, float* ms, int n) {
     da.tiles = p->d_shape_tiles[sh];
     da.ntiles = (int)p->shape_tiles[sh].size();
     da.ntt = (int)((b->nout + shape_tile_t(sh) - 1) / shape_tile_t(sh));
-    TP_CUDA_TRY(launch_dedisperse(da, s));  // warm-up
+    int rc = launch_single(e, b, da, sh, s);  // warm-up
+    if (rc) return rc;
     TP_CUDA_TRY(cudaEventRecord(e0, s));
-    for (int r = 0; r < reps; ++r) TP_CUDA_TRY(launch_dedisperse(da, s));
+    for (int r = 0; r < reps; ++r) {
+      rc = launch_single(e, b, da, sh, s);
+      if (rc) return rc;
+    }
     TP_CUDA_TRY(cudaEventRecord(e1, s));
     TP_CUDA_TRY(cudaEventSynchronize(e1));
-    e->launches += reps + 1;
     float t = 0.f;
     TP_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
     t /= reps;

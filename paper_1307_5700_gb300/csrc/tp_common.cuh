@@ -78,6 +78,16 @@ struct DedispArgs {
   int* status;            // device status word (TP_ETIMEOUT on a wait that gave up)
 };
 
+// One launch of the dedispersion kernel covers several beams (same kernel
+// shape and sample format): CTA i works for the beam b with
+// cta_start[b] <= i < cta_start[b + 1], on its (i - cta_start[b])-th
+// (DM tile, time tile) pair.
+struct BatchArgs {
+  const DedispArgs* beams;  // device, nbeams entries
+  const int* cta_start;     // device, nbeams + 1 entries
+  int nbeams;
+};
+
 // Register-tile shapes of the dedispersion kernel.
 struct KernelShape {
   int K;      // DM trials per warp
@@ -101,7 +111,7 @@ struct DetectArgs {
   int ntt;
   double nsigma;
   int beam;
-  int64_t t0_abs;
+  const long long* t0_abs;  // [1] stream index of window sample 0 (device)
   double* row_mu;         // [ndm]
   double* row_sigma;      // [ndm]
   float* row_thr_f;       // [ndm] smallest float D that is a detection
@@ -129,7 +139,7 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void*
                        cudaStream_t s);
 double external_spectrum_threshold(const double* sigma, int nchan, double tau_s);
 cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s);
-cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s);
+cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s);
 
 size_t dtype_size(int dtype);
