@@ -267,6 +267,9 @@ bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype
                 std::vector<DmTile>* tiles) {
   const int EB = dtype == TP_F32 ? 4 : 2;
   if (kShapes[sh].EB != EB) return false;
+  // per-beam buffers (partial sums, staging padding) are sized for tiles of
+  // kMinTileT..kMaxTileT outputs
+  if (shape_tile_t(sh) < kMinTileT || shape_tile_t(sh) > kMaxTileT) return false;
   const int K = kShapes[sh].K;
   const int residue = 16 / EB - 1;  // in-window offset of a 16-byte aligned copy
   if (kShapes[sh].ALGO == 0)
@@ -482,6 +485,7 @@ DedispArgs dedisp_args(const tp_plan* p, Beam* b) {
 // are re-uploaded only when they changed).
 int launch_single(tp_engine* e, Beam* b, const DedispArgs& da, int shape, cudaStream_t s) {
   const int ctas = da.ntiles * da.ntt;
+  if (da.ntt > b->ntt_max) return set_error(TP_EINVAL, "beam %d: %d time tiles exceed %d", b->id, da.ntt, b->ntt_max);
   if (!b->h_args_valid || std::memcmp(&b->h_args, &da, sizeof da) != 0 || b->h_cta[1] != ctas) {
     unsigned char buf[sizeof(DedispArgs) + 16];
     std::memcpy(buf, &da, sizeof da);
@@ -588,6 +592,11 @@ BatchPlan plan_batch(tp_engine* e) {
     bp.groups.back().second++;
     bp.beams.push_back(b);
     DedispArgs da = dedisp_args(b->plan, b);
+    if (da.ntt > b->ntt_max) {
+      bp.beams.clear();
+      bp.key = "error";
+      return bp;
+    }
     bp.args.push_back(da);
     snprintf(tmp, sizeof tmp, "%d:%d:%lld:%d:%d;", b->id, b->cur, (long long)b->nout, b->plan->shape,
              (int)b->plan->h_tiles.size());

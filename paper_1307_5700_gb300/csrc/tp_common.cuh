@@ -127,7 +127,7 @@ struct DetectArgs {
 };
 
 // Dedispersion tiling constants (shared by the planner and the kernel).
-constexpr int kMinTileT = 384;      // smallest output tile of any shape
+constexpr int kMinTileT = 256;      // smallest output tile any shape may use (sizes buffers)
 constexpr int kMaxTileT = 896;      // largest output tile of any shape
 constexpr int kMaxOverhang = 512;   // max delay spread inside a CTA tile
 constexpr int kDetectT = 4096;      // samples per detection CTA
