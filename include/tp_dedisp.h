@@ -171,7 +171,9 @@ int tp_beam_set_bandpass(tp_engine *e, int beam, const double *mu, const double 
  * stream reaches this point, a pageable host buffer when the call returns.
  * The first block of a stream must be longer than max_delay; it yields
  * nsamp - max_delay outputs, each later block nsamp outputs.
- * Errors: TP_EINVAL (size), TP_EBUSY (previous block not yet dedispersed). */
+ * Errors: TP_EINVAL (size), TP_EBUSY (the previous block has not been through
+ * tp_detect yet).  On a beam stream of its own the copies first wait for the
+ * beam's previous detection (which may run on the engine stream). */
 int tp_push_block(tp_engine *e, int beam, const void *buf, int nsamp, int buf_is_device);
 
 /* A1-A5 on the beam's current window (async).  beam = -1 processes every beam
@@ -191,9 +193,10 @@ int tp_detect(tp_engine *e, int beam);
  * graph, cached per batch layout (beams, window parity, block length, kernel
  * shape) and replayed on later calls; this needs a non-default engine
  * stream.  *nbeams (may be NULL) receives the number of beams processed.
- * Beams given their own stream with tp_beam_set_stream are refused
- * (TP_EINVAL); TP_ENOTREADY if no beam holds a new block.  Results equal the
- * per-beam tp_dedisperse / tp_detect calls. */
+ * The batch runs on the engine stream, which first waits for the pushes of
+ * beams that have their own stream (tp_beam_set_stream).  TP_ENOTREADY if no
+ * beam holds a new block.  Results equal the per-beam tp_dedisperse /
+ * tp_detect calls. */
 int tp_run_ready(tp_engine *e, int use_graph, int *nbeams);
 
 /* Wait for the beam's detection and copy min(cap, n_total) candidates, sorted
@@ -262,6 +265,79 @@ int tp_get_stage_times(tp_engine *e, int beam, double *ms, int64_t *count);
 
 /* Kernels launched by the engine since it was created. */
 int tp_engine_launches(const tp_engine *e, uint64_t *n);
+
+/* The engine's stream (as given to tp_engine_create) into *stream. */
+int tp_engine_stream(const tp_engine *e, void **stream);
+
+/* ---- serving loop ------------------------------------------------------------------
+ * Many beam streams (any mix of channel counts, bands, DM lists, sample
+ * formats and block lengths) share the engine with continuous batching; the
+ * paper runs one processing thread per beam (Sec. 2.2) and drops work when
+ * late (Sec. 3); here blocks are queued per stream and batched across
+ * streams instead.  A stream's beam is opened when its first block has
+ * arrived and its footprint fits the engine's HBM budget (otherwise the
+ * stream waits for memory), and closed after its last block once the stream
+ * is ended.  Every loop iteration pushes each stream's next arrived block as
+ * soon as the stream's previous block is done -- on the stream's own CUDA
+ * stream, so copies overlap the batches already running -- and launches one
+ * batch (tp_run_ready) for all blocks pushed in that iteration. */
+typedef struct tp_server tp_server;
+
+typedef struct tp_stream_desc {
+  int32_t nchan;
+  int32_t ndm;
+  double f_lo_mhz;
+  double bw_mhz;
+  double t_samp_s;
+  const double *dm_list; /* host, ndm values (copied) */
+  int32_t dtype;
+  int32_t block_nsamp;   /* largest block of the stream */
+  int32_t cand_capacity; /* candidate buffer per block */
+  int32_t reserved;
+} tp_stream_desc;
+
+typedef struct tp_serve_result {
+  int32_t stream;
+  int32_t seq;          /* block index within its stream */
+  double arrival_s;     /* server clock */
+  double start_s;       /* block pushed to the GPU */
+  double done_s;        /* candidates on the host */
+  int64_t n_candidates;
+  int32_t status;       /* TP_OK, TP_ETRUNC or TP_EOVERFLOW */
+  int32_t reserved;
+} tp_serve_result;
+
+/* Create a server on engine `e`; rfi / nsigma apply to every stream (rfi NULL
+ * = defaults).  keep_candidates = 1 keeps every block's candidate records on
+ * the host for tp_server_candidates. */
+int tp_server_create(tp_engine *e, const tp_rfi_params *rfi, double nsigma, int keep_candidates,
+                     tp_server **out);
+
+/* Register a stream (no device memory yet); plans are shared between streams
+ * with identical band, sampling, DM list and format. */
+int tp_server_add_stream(tp_server *s, const tp_stream_desc *d, int *stream_id);
+
+/* Queue one block (host, channel-major [nchan][nsamp]) of a stream, arriving
+ * at `arrival_s` on the server clock (seconds since the first tp_server_run).
+ * The buffer is read when the block is pushed and must stay valid until the
+ * block is done.  Returns the request id (>= 0) or an error. */
+int tp_server_submit(tp_server *s, int stream_id, const void *host_block, int nsamp, double arrival_s);
+
+/* No more blocks for this stream: its beam is closed after its last block. */
+int tp_server_end_stream(tp_server *s, int stream_id);
+
+/* Run the loop on the calling thread until every block submitted so far is
+ * done (TP_OK) or the server clock passes time_limit_s (TP_ETIMEOUT). */
+int tp_server_run(tp_server *s, double time_limit_s);
+
+/* Per-request timings and candidate counts, in request order. */
+int tp_server_results(tp_server *s, tp_serve_result *out, int cap, int *n);
+
+/* Candidate records of a request (keep_candidates servers only). */
+int tp_server_candidates(tp_server *s, int request, tp_candidate *out, int cap, int *n);
+
+/* Wait for the engine, close every stream and free the server's plans. */
+int tp_server_destroy(tp_server *s);
 
 /* ---- the same statistics without any allocation ---------------------------------
  * tp_channel_stats_noalloc: A1-A2 (bandpass mean and standard deviation per

@@ -46,7 +46,8 @@ EXPORTS = (
     "tp_get_series", "tp_get_bandpass", "tp_get_masks", "tp_get_series_stats",
     "tp_set_profiling", "tp_get_stage_times", "tp_engine_launches", "tp_last_error_string",
     "tp_version", "tp_plan_shapes", "tp_plan_set_shape", "tp_autotune", "tp_channel_stats_noalloc",
-    "tp_run_ready",
+    "tp_run_ready", "tp_engine_stream", "tp_server_create", "tp_server_add_stream", "tp_server_submit",
+    "tp_server_end_stream", "tp_server_run", "tp_server_results", "tp_server_candidates", "tp_server_destroy",
 )
 
 
@@ -110,6 +111,15 @@ _SIGS = {
     "tp_channel_stats_noalloc": (_i, [_vp, _i, _i, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                      _vp]),
     "tp_run_ready": (_i, [_vp, _i, _vp]),
+    "tp_engine_stream": (_i, [_vp, _vp]),
+    "tp_server_create": (_i, [_vp, _vp, _d, _i, _vp]),
+    "tp_server_add_stream": (_i, [_vp, _vp, _vp]),
+    "tp_server_submit": (_i, [_vp, _i, _vp, _i, _d]),
+    "tp_server_end_stream": (_i, [_vp, _i]),
+    "tp_server_run": (_i, [_vp, _d]),
+    "tp_server_results": (_i, [_vp, _vp, _i, _vp]),
+    "tp_server_candidates": (_i, [_vp, _i, _vp, _i, _vp]),
+    "tp_server_destroy": (_i, [_vp]),
     "tp_last_error_string": (ctypes.c_char_p, []),
     "tp_version": (_i, []),
 }
@@ -384,3 +394,80 @@ def tp_run_ready(e, use_graph=False):
     n = ctypes.c_int()
     _check(lib().tp_run_ready(e, int(bool(use_graph)), ctypes.byref(n)))
     return n.value
+
+
+class tp_stream_desc(ctypes.Structure):
+    _fields_ = [("nchan", ctypes.c_int32), ("ndm", ctypes.c_int32), ("f_lo_mhz", ctypes.c_double),
+                ("bw_mhz", ctypes.c_double), ("t_samp_s", ctypes.c_double), ("dm_list", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32), ("block_nsamp", ctypes.c_int32), ("cand_capacity", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+SERVE_RESULT_DTYPE = np.dtype([("stream", np.int32), ("seq", np.int32), ("arrival_s", np.float64),
+                               ("start_s", np.float64), ("done_s", np.float64), ("n_candidates", np.int64),
+                               ("status", np.int32), ("reserved", np.int32)])
+
+
+def tp_engine_stream(e):
+    v = ctypes.c_void_p()
+    _check(lib().tp_engine_stream(e, ctypes.byref(v)))
+    return v.value
+
+
+def tp_server_create(e, rfi=None, nsigma=5.0, keep_candidates=False):
+    h = ctypes.c_void_p()
+    _check(lib().tp_server_create(e, ctypes.byref(rfi) if rfi is not None else None, nsigma,
+                                  int(bool(keep_candidates)), ctypes.byref(h)))
+    return h
+
+
+_server_keep = {}
+
+
+def tp_server_add_stream(s, nchan, f_lo_mhz, bw_mhz, t_samp_s, dm_list, dtype, block_nsamp, cand_capacity):
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    d = tp_stream_desc(nchan, len(dm), f_lo_mhz, bw_mhz, t_samp_s, dm.ctypes.data, dtype, block_nsamp,
+                       cand_capacity, 0)
+    sid = ctypes.c_int()
+    _check(lib().tp_server_add_stream(s, ctypes.byref(d), ctypes.byref(sid)))
+    return sid.value
+
+
+def tp_server_submit(s, stream_id, block, arrival_s, nsamp=None):
+    """``block`` must stay alive until the request is done (keep a reference)."""
+    if nsamp is None:
+        nsamp = block.shape[-1]
+    rid = _check(lib().tp_server_submit(s, stream_id, _addr(block), int(nsamp), float(arrival_s)))
+    _server_keep.setdefault(s.value, []).append(block)
+    return rid
+
+
+def tp_server_end_stream(s, stream_id):
+    return _check(lib().tp_server_end_stream(s, stream_id))
+
+
+def tp_server_run(s, time_limit_s=1e9):
+    return _check(lib().tp_server_run(s, float(time_limit_s)))
+
+
+def tp_server_results(s):
+    n = ctypes.c_int()
+    _check(lib().tp_server_results(s, None, 0, ctypes.byref(n)))
+    out = np.zeros(max(n.value, 1), SERVE_RESULT_DTYPE)
+    _check(lib().tp_server_results(s, out.ctypes.data, n.value, ctypes.byref(n)))
+    return out[:n.value]
+
+
+def tp_server_candidates(s, request, cap=1 << 20):
+    out = np.zeros(max(cap, 1), CAND_DTYPE)
+    n = ctypes.c_int()
+    _check(lib().tp_server_candidates(s, request, out.ctypes.data, cap, ctypes.byref(n)))
+    return out[:min(n.value, cap)]
+
+
+def tp_server_destroy(s):
+    rc = _check(lib().tp_server_destroy(s))
+    _server_keep.pop(s.value, None)
+    return rc

@@ -121,7 +121,8 @@ struct Beam {
   int64_t dpitch = 0;
   cudaStream_t stream = nullptr;
   bool own_event = false;
-  cudaEvent_t ev_detect = nullptr;
+  cudaEvent_t ev_detect = nullptr;  // the beam's last detection finished
+  cudaEvent_t ev_pushed = nullptr;  // the beam's last push finished (its own stream)
   // device buffers
   void* win[2] = {nullptr, nullptr};
   void* chunk_sums = nullptr;
@@ -375,6 +376,7 @@ void free_beam(Beam* b) {
   b->ev_pool.clear();
   b->ev_pending.clear();
   if (b->ev_detect) cudaEventDestroy(b->ev_detect);
+  if (b->ev_pushed) cudaEventDestroy(b->ev_pushed);
   for (void* p : b->allocs) cudaFree(p);
   b->allocs.clear();
 }
@@ -618,6 +620,13 @@ size_t batch_bytes(const BatchPlan& bp) { return bp.args.size() * sizeof(DedispA
 
 // Issue RFI + batched dedispersion + detection for a planned batch; batch
 // arguments at `d_args` (device) must already hold the plan's arguments.
+// The engine stream waits for the pushes of beams that have their own stream.
+int wait_pushes(tp_engine* e, const BatchPlan& bp) {
+  for (Beam* b : bp.beams)
+    if (b->stream && b->stream != e->stream) TP_CUDA_TRY(cudaStreamWaitEvent(e->stream, b->ev_pushed, 0));
+  return TP_OK;
+}
+
 int issue_batch(tp_engine* e, BatchPlan& bp, void* d_args, bool detect) {
   cudaStream_t s = e->stream;
   for (Beam* b : bp.beams) {
@@ -738,6 +747,12 @@ int tp_sync(tp_engine* e) {
   TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
   for (Beam* b : e->beams)
     if (b && b->stream) TP_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return TP_OK;
+}
+
+int tp_engine_stream(const tp_engine* e, void** stream) {
+  if (!e || !stream) return set_error(TP_EINVAL, "engine or stream is NULL");
+  *stream = e->stream;
   return TP_OK;
 }
 
@@ -938,6 +953,7 @@ int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capac
     return cuda_error(ce, "cudaMemset");
   }
   ce = cudaEventCreateWithFlags(&b->ev_detect, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ev_pushed, cudaEventDisableTiming);
   if (ce != cudaSuccess) {
     free_beam(b);
     delete b;
@@ -1027,7 +1043,8 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
   const tp_plan* p = b->plan;
   if (!buf) return set_error(TP_EINVAL, "buf is NULL");
   if (nsamp < 1 || nsamp > b->B) return set_error(TP_EINVAL, "nsamp %d not in [1, %d]", nsamp, b->B);
-  if (b->state == kReady) return set_error(TP_EBUSY, "beam %d: previous block not dedispersed", beam);
+  if (b->state == kReady || b->state == kDedispersed)
+    return set_error(TP_EBUSY, "beam %d: previous block not yet through detection", beam);
   const int64_t dmax = p->max_delay;
   if (b->pushed == 0 && nsamp <= dmax)
     return set_error(TP_EINVAL, "first block (%d samples) must exceed the largest delay %lld", nsamp,
@@ -1037,6 +1054,9 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
   cudaStream_t s = beam_stream(e, b);
   const cudaMemcpyKind kind = buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t dpitch = (size_t)b->pitch * es;
+  // on its own stream, a push must not overwrite the window, t0 or buffers
+  // while the beam's previous batch may still run on the engine stream
+  if (s != e->stream && b->pushed > 0) TP_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_detect, 0));
   prof_record(e, b, 0, s);
   if (b->pushed == 0) {
     b->cur = 0;
@@ -1061,6 +1081,7 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
     b->t0_abs = b->pushed - dmax;
   }
   TP_CUDA_TRY(cudaMemcpyAsync(b->d_t0, &b->t0_abs, 8, cudaMemcpyHostToDevice, s));
+  TP_CUDA_TRY(cudaEventRecord(b->ev_pushed, s));
   prof_record(e, b, 1, s);
   b->pushed += nsamp;
   b->state = kReady;
@@ -1080,6 +1101,8 @@ int tp_dedisperse(tp_engine* e, int beam) {
   if (bp.beams.empty()) return set_error(TP_ENOTREADY, "no beam holds a new block");
   const size_t need = batch_bytes(bp);
   if (need > kBatchBytes) return set_error(TP_EINVAL, "batch of %zu beams too large", bp.beams.size());
+  int rc = wait_pushes(e, bp);
+  if (rc) return rc;
   pack_batch(bp, &e->h_batch);
   TP_CUDA_TRY(cudaMemcpyAsync(e->d_batch, e->h_batch.data(), need, cudaMemcpyHostToDevice, e->stream));
   return issue_batch(e, bp, e->d_batch, false);
@@ -1113,9 +1136,8 @@ int tp_run_ready(tp_engine* e, int use_graph, int* nbeams) {
   if (bp.beams.empty()) return set_error(TP_ENOTREADY, "no beam holds a new block");
   const size_t need = batch_bytes(bp);
   if (need > kBatchBytes) return set_error(TP_EINVAL, "batch of %zu beams too large", bp.beams.size());
-  for (Beam* b : bp.beams)
-    if (b->stream && b->stream != e->stream)
-      return set_error(TP_EINVAL, "batched beams run on the engine stream (beam %d has its own)", b->id);
+  int rc0 = wait_pushes(e, bp);
+  if (rc0) return rc0;
   if (!use_graph) {
     pack_batch(bp, &e->h_batch);
     TP_CUDA_TRY(cudaMemcpyAsync(e->d_batch, e->h_batch.data(), need, cudaMemcpyHostToDevice, e->stream));
