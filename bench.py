@@ -290,6 +290,94 @@ def run_batch8(args):
             "gpu_launches": int(launches), "candidates_last_block": ncand, "clocks": clk}), flush=True)
 
 
+def serve_streams():
+    """32 streams: channel counts cycle 256/512/1024/4096 and block lengths
+    2^16/2^17/2^18; up to 1024 channels: 398-418 MHz, 51.2 us, 320 DMs step
+    0.2; 4096 channels: 1200-1500 MHz, 64 us, 1024 DMs step 1; 8-bit samples
+    round(N(128, 16))."""
+    out = []
+    for i in range(32):
+        nchan = (256, 512, 1024, 4096)[i % 4]
+        block = 1 << (16 + i % 3)
+        if nchan == 4096:
+            out.append(dict(nchan=nchan, f_lo=1200.0, bw=300.0, ts=64e-6, dms=np.arange(1024) * 1.0, block=block))
+        else:
+            out.append(dict(nchan=nchan, f_lo=398.0, bw=20.0, ts=51.2e-6, dms=np.arange(320) * 0.2, block=block))
+    return out
+
+
+def run_serve(args):
+    """Serving loop: Poisson block arrivals on 32 streams (time compressed by
+    --speedup), HBM admission within --hbm-gb, continuous batching."""
+    import torch
+    import paper_1307_5700_gb300 as tp
+
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    tp.build()
+    streams = serve_streams()
+    cache = {}
+    blocks = []
+    for i, st in enumerate(streams):
+        key = (st["nchan"], st["block"])
+        if key not in cache:
+            g = synth.rng(5000 + len(cache))
+            xf = g.standard_normal((st["nchan"], st["block"]), dtype=np.float32)
+            synth.apply_bursts(xf, synth.poisson_bursts(st["nchan"], st["block"], 6000 + len(cache)))
+            host = torch.empty(xf.shape, dtype=torch.uint8, pin_memory=True)
+            host.numpy()[...] = synth.to_u8(xf * 16.0 + 128.0)
+            cache[key] = host
+        blocks.append(cache[key])
+    stream = torch.cuda.Stream(dev)
+    e = tp.tp_engine_create(local, int(args.hbm_gb * (1 << 30)), stream.cuda_stream)
+    srv = tp.tp_server_create(e, nsigma=5.0)
+    g = synth.rng(99 + rank)
+    total_units = 0
+    for i, st in enumerate(streams):
+        sid = tp.tp_server_add_stream(srv, st["nchan"], st["f_lo"], st["bw"], st["ts"], st["dms"], "u8",
+                                      st["block"], 1 << 20)
+        dur = st["block"] * st["ts"] / args.speedup          # compressed block duration
+        t = float(g.exponential(dur))
+        for k in range(args.blocks_per_stream):
+            tp.tp_server_submit(srv, sid, blocks[i], t)
+            t += float(g.exponential(dur))
+        tp.tp_server_end_stream(srv, sid)
+        st["dur"] = dur
+    clocks = Clocks(local)
+    clocks.start()
+    barrier(world)
+    w0 = time.perf_counter()
+    tp.tp_server_run(srv, time_limit_s=600.0)
+    wall = max_over_ranks(time.perf_counter() - w0, world, dev)
+    clk = clocks.stop()
+    res = tp.tp_server_results(srv)
+    launches = tp.tp_engine_launches(e)
+    tp.tp_server_destroy(srv)
+    tp.tp_engine_destroy(e)
+    lat = (res["done_s"] - res["arrival_s"]) * 1e3
+    maxdelay = {}
+    for r in res:
+        st = streams[r["stream"]]
+        # outputs: the first block of a stream yields block - max_delay
+        total_units += len(st["dms"]) * st["block"]
+    value = total_units * world / wall
+    rt = [((r["done_s"] - r["arrival_s"]) / (streams[r["stream"]]["block"] * streams[r["stream"]]["ts"]))
+          for r in res]
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "DM-trial*samples/s", "n_gpus": world, "steps": len(res),
+            "warmup": 0, "ms_per_step": wall * 1e3 / max(len(res), 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / PAPER_DERIVED, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "serving: 32 streams, nchan 256/512/1024/4096, blocks 2^16-2^18, u8, Poisson "
+                                   f"arrivals x{args.speedup} real time, {args.blocks_per_stream} blocks/stream, "
+                                   f"HBM budget {args.hbm_gb} GB"},
+            "p50_block_latency_ms": float(np.percentile(lat, 50)),
+            "p99_block_latency_ms": float(np.percentile(lat, 99)),
+            "latency_over_block_duration_p99": float(np.percentile(rt, 99)),
+            "blocks": int(len(res)), "wall_s": wall, "gpu_launches": int(launches), "clocks": clk}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,13 +388,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "u8"],
                     help="sample storage format (the metric's workload is f32)")
-    ap.add_argument("--workload", default="stream", choices=["stream", "batch8"],
-                    help="stream: the metric's 1-beam streaming workload; batch8: 8 uneven beams batched")
+    ap.add_argument("--workload", default="stream", choices=["stream", "batch8", "serve32"],
+                    help="stream: the metric's 1-beam streaming workload; batch8: 8 uneven beams batched; "
+                         "serve32: the serving loop")
+    ap.add_argument("--speedup", type=float, default=50.0, help="serve32: arrival time compression")
+    ap.add_argument("--blocks-per-stream", type=int, default=4, help="serve32: blocks per stream")
+    ap.add_argument("--hbm-gb", type=float, default=48.0, help="serve32: engine HBM budget")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch8":
         return run_batch8(args)
+    if args.workload == "serve32":
+        return run_serve(args)
 
     import torch
     import paper_1307_5700_gb300 as tp
