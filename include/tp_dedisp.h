@@ -176,6 +176,12 @@ int tp_beam_set_bandpass(tp_engine *e, int beam, const double *mu, const double 
  * beam's previous detection (which may run on the engine stream). */
 int tp_push_block(tp_engine *e, int beam, const void *buf, int nsamp, int buf_is_device);
 
+/* Mark the beam's current window as not yet processed, so that tp_dedisperse
+ * runs on it again (for instance after tp_plan_set_shape); the next push
+ * still continues the stream from this window.  TP_ENOTREADY if the beam holds
+ * no block. */
+int tp_beam_rewind(tp_engine *e, int beam);
+
 /* A1-A5 on the beam's current window (async).  beam = -1 processes every beam
  * holding a new block in one batched launch per stage.  TP_ENOTREADY if no
  * block is waiting. */

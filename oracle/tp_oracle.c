@@ -320,12 +320,13 @@ void orc_spectrum_mask_float(const void *x, int dtype, int nchan, int64_t nsamp,
   double v = 0.0;
   for (int c = 0; c < nchan; ++c) v += sigma[c] * sigma[c];
   const double thr = tau_s * sqrt(v);
-  for (int64_t t = 0; t < nsamp; ++t) {
-    double m = 0.0;
-    for (int c = 0; c < nchan; ++c)
-      if (!chunk_flag[(int64_t)c * nchunk + t / W]) m += sample(x, dtype, (int64_t)c * pitch + t) - mu[c];
-    spec_flag[t] = (uint8_t)(m > thr);
-  }
+  /* m[t] accumulates channel c = 0, 1, ... in order for every t */
+  double *m = (double *)calloc((size_t)nsamp, sizeof(double));
+  for (int c = 0; c < nchan; ++c)
+    for (int64_t t = 0; t < nsamp; ++t)
+      if (!chunk_flag[(int64_t)c * nchunk + t / W]) m[t] += sample(x, dtype, (int64_t)c * pitch + t) - mu[c];
+  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)(m[t] > thr);
+  free(m);
 }
 
 /* 8-bit samples, block statistics, exact: multiplied through by N the test is
@@ -342,12 +343,12 @@ void orc_spectrum_mask_u8(const uint8_t *x, int nchan, int64_t nsamp, int64_t pi
     vlo += (uint64_t)V[c] & 0xFFFFFu;
   }
   const double thr = tau_s * sqrt((double)vhi * 1048576.0 + (double)vlo);
-  for (int64_t t = 0; t < nsamp; ++t) {
-    int64_t m = 0;
-    for (int c = 0; c < nchan; ++c)
-      if (!chunk_flag[(int64_t)c * nchunk + t / W]) m += nsamp * sample_u8(x, (int64_t)c * pitch + t) - S[c];
-    spec_flag[t] = (uint8_t)((double)m > thr);
-  }
+  int64_t *m = (int64_t *)calloc((size_t)nsamp, sizeof(int64_t));
+  for (int c = 0; c < nchan; ++c)
+    for (int64_t t = 0; t < nsamp; ++t)
+      if (!chunk_flag[(int64_t)c * nchunk + t / W]) m[t] += nsamp * sample_u8(x, (int64_t)c * pitch + t) - S[c];
+  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)((double)m[t] > thr);
+  free(m);
 }
 
 /* 8-bit samples with external bandpass b_c and spread sigma_c. */
@@ -358,12 +359,12 @@ void orc_spectrum_mask_u8_ext(const uint8_t *x, int nchan, int64_t nsamp, int64_
   double v = 0.0;
   for (int c = 0; c < nchan; ++c) v += sigma[c] * sigma[c];
   const double thr = tau_s * sqrt(v);
-  for (int64_t t = 0; t < nsamp; ++t) {
-    int64_t m = 0;
-    for (int c = 0; c < nchan; ++c)
-      if (!chunk_flag[(int64_t)c * nchunk + t / W]) m += sample_u8(x, (int64_t)c * pitch + t) - b[c];
-    spec_flag[t] = (uint8_t)((double)m > thr);
-  }
+  int64_t *m = (int64_t *)calloc((size_t)nsamp, sizeof(int64_t));
+  for (int c = 0; c < nchan; ++c)
+    for (int64_t t = 0; t < nsamp; ++t)
+      if (!chunk_flag[(int64_t)c * nchunk + t / W]) m[t] += sample_u8(x, (int64_t)c * pitch + t) - b[c];
+  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)((double)m[t] > thr);
+  free(m);
 }
 
 /* ---- A4: substitution (R7) --------------------------------------------------- */

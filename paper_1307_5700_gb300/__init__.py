@@ -48,6 +48,7 @@ EXPORTS = (
     "tp_version", "tp_plan_shapes", "tp_plan_set_shape", "tp_autotune", "tp_channel_stats_noalloc",
     "tp_run_ready", "tp_engine_stream", "tp_server_create", "tp_server_add_stream", "tp_server_submit",
     "tp_server_end_stream", "tp_server_run", "tp_server_results", "tp_server_candidates", "tp_server_destroy",
+    "tp_beam_rewind",
 )
 
 
@@ -120,6 +121,7 @@ _SIGS = {
     "tp_server_results": (_i, [_vp, _vp, _i, _vp]),
     "tp_server_candidates": (_i, [_vp, _i, _vp, _i, _vp]),
     "tp_server_destroy": (_i, [_vp]),
+    "tp_beam_rewind": (_i, [_vp, _i]),
     "tp_last_error_string": (ctypes.c_char_p, []),
     "tp_version": (_i, []),
 }
@@ -471,3 +473,7 @@ def tp_server_destroy(s):
     rc = _check(lib().tp_server_destroy(s))
     _server_keep.pop(s.value, None)
     return rc
+
+
+def tp_beam_rewind(e, beam):
+    return _check(lib().tp_beam_rewind(e, beam))

@@ -993,6 +993,16 @@ int tp_beam_close(tp_engine* e, int beam) {
   return TP_OK;
 }
 
+int tp_beam_rewind(tp_engine* e, int beam) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->nsamp_win == 0) return set_error(TP_ENOTREADY, "beam %d holds no block", beam);
+  b->state = kReady;
+  return TP_OK;
+}
+
 int tp_beam_set_stream(tp_engine* e, int beam, void* cuda_stream) {
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
