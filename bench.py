@@ -40,6 +40,10 @@ BLOCK = 1 << 17
 DMS = np.arange(640) * 0.2
 NBUF = 3  # distinct synthetic blocks cycled through
 PAPER_DERIVED = 6.5e7  # DM-trial.samples/s per GPU derived from the paper's Table 1
+# DRAM bytes (read + write) of one dedispersion launch of this workload, from
+# the ncu capture summarised in profiles/dedisperse_kernel_stream1024_640dm_f32.md,
+# per kernel shape; a shape without a capture reports null.
+TRAFFIC_BY_SHAPE = {("f32", 12): 533.664e6 + 306.476e6}
 METRIC = "DM-trial*samples/s per GB300 (real-time beams sustained, p99 block latency alongside)"
 WORKLOAD = "stream: 1 beam, 1024 ch 398-418 MHz, 51.2 us, 640 DMs 0-127.8 step 0.2, FP32, 2^17-sample blocks"
 
@@ -474,8 +478,8 @@ def main():
     adds = len(DMS) * NCHAN * BLOCK
     achieved = adds / (dd_ms / 1e3) / 1e12
     peak = 152 * 128 * 2.070e9 / 1e12
-    roof = {"kernel": "dedisperse_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+    roof = {"kernel": f"dedisperse_kernel (shape {best})", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": TRAFFIC_BY_SHAPE.get((args.dtype, int(best))),
             "ms_per_launch": dd_ms,
             "note": "FP32 adds (1 add = 1 flop) per launch = ndm*nchan*T; peak = 152 SMs x 128 FP32 lanes x 2070 MHz",
             "stage_ms_per_block": {"push": stage_ms[0] / max(nstage, 1), "a1_a3": stage_ms[1] / max(nstage, 1),
