@@ -2,25 +2,30 @@
 //
 //   D[d][t] = sum_{c=0}^{nchan-1} y[c][t + delay[d][c]],   0 <= t < T,
 //
-// over the substituted, bandpass-corrected series y written by the A3/A4
-// kernel (FP32; exact small integers for 8-bit data).
+// over the series staged by the A3/A4 kernel: FP32 y for FP32 data, else the
+// stored samples x~ in their own format (binary16, bfloat16, 8-bit), whose
+// sum of bandpass values the epilogue subtracts.
 //
-// Work decomposition.  A CTA owns a tile of consecutive DM trials (up to 8
-// groups of K) x TT = 32 S output samples.  Warps 0-7 are consumers: warp w
-// owns group w, lane l owns the S consecutive outputs t0 + l S .. + S - 1 of
-// each of the K DMs.  Warp 8 is the producer: for each pipeline stage (kNC
-// channels) it stages the stage's delays for the tile's DMs into shared memory
-// and copies, per channel, the samples the tile needs,
+// Work decomposition.  A CTA owns a tile of consecutive DM trials (up to
+// NCONS groups of K) x TT = 32 S output samples.  Consumer warp w owns group
+// w; lane l owns the S consecutive outputs t0 + l S .. + S - 1 of each of the
+// K DMs.  The last warp is the producer: for each pipeline stage (kNC
+// channels) it stages the stage's delays for the tile's DMs and copies, per
+// channel, the samples the tile needs,
 // [t0 + delay[d_first][c], t0 + TT + delay[d_last][c]) rounded out to 16 B,
 // with cp.async.bulk onto a "full" mbarrier; consumers release a stage on an
-// "empty" mbarrier (kStages stages in flight, no CTA-wide barrier).
-// A consumer lane loads a register window of S + spread + 4 samples with
-// 128-bit shared loads (only as many quads as this channel's spread needs) and
-// adds it into the K x S accumulators at each DM's offset inside the window:
-// the offsets are warp-uniform run-time values, so each DM jumps through a
-// table (brx.idx) into one of OMAX + 1 unrolled add sequences
-// (dispatch_gen.cuh).  Every sample loaded from shared memory thus feeds up to
-// K adds from registers.  Each (d, t) adds its channels in index order (FP32).
+// "empty" mbarrier (STAGES stages in flight, no CTA-wide barrier).
+//
+// Consumers (ALGO 1) read each DM's S samples straight from shared memory at
+// that DM's offset: FP32, one 32-bit load per add; 16-bit, S/2 + 1 words, a
+// half-word shift for odd offsets, mixed-precision FP32 adds; 8-bit, S/4 + 1
+// words, a byte funnel shift and two byte permutes per word that spread four
+// samples into two words of 16-bit lanes, summed as packed integers (two
+// channels per add) and folded into 32-bit sums every 256 channels.  ALGO 0
+// instead loads one register window per channel and adds it at each DM's
+// in-window offset through an indexed branch (brx.idx) into unrolled add
+// sequences (dispatch_gen.cuh), reusing each loaded sample for K trials.
+// Each (d, t) adds its channels in index order (FP32, or exact integers).
 // Every mbarrier wait is bounded; a wait that gives up records TP_ETIMEOUT in
 // the beam's status word and the CTA leaves after letting its copies land.
 //
@@ -37,7 +42,9 @@ namespace tp {
 namespace {
 
 constexpr int kNC = 4;                              // channels per pipeline stage
-constexpr int kStages = 4;                          // pipeline depth
+constexpr int kStages = 4;                          // pipeline depth (8-bit data: kStagesU8)
+constexpr int kStagesU8 = 8;
+constexpr int kDelRing = 8;                         // stages of delays prefetched ahead
 constexpr long long kSpinLimit = 1LL << 24;         // bounded mbarrier waits
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -73,6 +80,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
+// 4-byte asynchronous global -> shared copy; zero-fills when !valid (the
+// source is not read then)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -97,12 +111,24 @@ __device__ __forceinline__ void add_pair_h(float& acc0, float& acc1, unsigned pr
 
 // Staged sample formats.
 constexpr int kModeF32 = 0;   // FP32 y (float data)
-constexpr int kModeF16 = 1;   // binary16 x~ (binary16 data, and 8-bit data widened exactly)
+constexpr int kModeF16 = 1;   // binary16 x~
 constexpr int kModeBF16 = 2;  // bfloat16 x~
+constexpr int kModeU8 = 3;    // 8-bit x~, summed as packed 16-bit integers
+
+// 8-bit mode: channels summed into packed 16-bit lanes before they are folded
+// into the 32-bit sums (256 x 255 < 2^16, so no lane can carry into the next)
+constexpr int kU8FoldStages = 256 / kNC;
+
+// Samples 1 and 3 of a word of four 8-bit samples (first sample in the low
+// byte), as two 16-bit lanes.
+__device__ __forceinline__ unsigned odd_u8(unsigned w) { return __byte_perm(w, 0u, 0x4341u); }
+
+// acc + x + y, the packed 8-bit accumulation step (one three-input add)
+__device__ __forceinline__ unsigned add3_u8(unsigned acc, unsigned x, unsigned y) { return acc + x + y; }
 
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO>
 struct Shape {
-  static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
+  static constexpr int EB = MODE == kModeF32 ? 4 : (MODE == kModeU8 ? 1 : 2);  // bytes per sample
   static constexpr int QS = 16 / EB;                                          // samples per 16 B
   static constexpr int TT = 32 * S;                                           // outputs per tile
   static constexpr int L = (S + OMAX + 1 + QS - 1) / QS * QS;                 // window samples
@@ -110,14 +136,20 @@ struct Shape {
   static constexpr int ROW = (TT + kMaxOverhang + OMAX + 2 * QS + 63) / 64 * 64;  // staged samples
   static constexpr int ROWB = ROW * EB;
   static constexpr int THREADS = (NCONS + 1) * 32;                            // + one producer warp
-  static constexpr size_t data_bytes = (size_t)kStages * kNC * ROWB;
-  static constexpr size_t del_bytes = sizeof(int) * kStages * kNC * 32;
-  static constexpr size_t info_bytes = sizeof(int4) * kStages * kNC * NCONS;
-  static constexpr size_t smem = data_bytes + del_bytes + info_bytes + 16 * kStages;
+  static constexpr int STAGES = MODE == kModeU8 ? kStagesU8 : kStages;
+  static constexpr size_t data_bytes = (size_t)STAGES * kNC * ROWB;
+  static constexpr size_t del_bytes = sizeof(int) * kDelRing * kNC * 32;
+  // 8-bit mode: per (stage, consumer warp) K int4 of word offsets (one per
+  // channel of the stage) and one int4 of byte shifts; else one int4 per
+  // (stage, channel, consumer warp)
+  static constexpr size_t info_bytes =
+      MODE == kModeU8 ? sizeof(int4) * STAGES * NCONS * (K + 1) : sizeof(int4) * STAGES * kNC * NCONS;
+  static constexpr size_t smem = data_bytes + del_bytes + info_bytes + 16 * STAGES;
   // no bank conflicts: register windows (ALGO 0) start an odd number of 16-byte
   // units apart, direct 32-bit loads (ALGO 1) an odd number of words apart
   static_assert(ALGO == 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
   static_assert(ALGO == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
+  static_assert(MODE != kModeU8 || (ALGO == 1 && S % 4 == 0), "8-bit loads take whole words");
 };
 
 // Per (stage, channel, consumer warp) the producer writes an int4:
@@ -143,19 +175,22 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   const DedispArgs& a = ba.beams[bi];
   const int local = (int)blockIdx.x - ba.cta_start[bi];
   constexpr int TT = Sh::TT, LR = Sh::LR, ROWB = Sh::ROWB, EB = Sh::EB, QS = Sh::QS;
+  static_assert(MODE != kModeU8 || K <= 4, "8-bit shifts of a warp's DMs are packed in one int4");
   static_assert(NCONS * K <= 32, "a producer lane holds one DM of the tile");
   static_assert(OMAX < 256, "offsets are packed in bytes");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char* srow = smem_raw;                                                     // [kStages][kNC][ROWB]
-  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);                       // [kStages][kNC][32]
-  int4* sinfo = reinterpret_cast<int4*>(smem_raw + Sh::data_bytes + Sh::del_bytes);      // [kStages][kNC][NCONS]
+  constexpr int STAGES = Sh::STAGES;
+  unsigned char* srow = smem_raw;                                                     // [STAGES][kNC][ROWB]
+  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);                       // [kDelRing][kNC][32]
+  int4* sinfo = reinterpret_cast<int4*>(smem_raw + Sh::data_bytes + Sh::del_bytes);      // [STAGES][kNC][NCONS]
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes);
-  uint64_t* empty = full + kStages;
+  uint64_t* empty = full + STAGES;
 
   const int tile = local % a.ntiles;
   const int tt = local / a.ntiles;
   const DmTile dt = a.tiles[tile];
   const int64_t t0 = (int64_t)tt * TT;
+  const int t0m = (int)(t0 & 15);  // t0 mod 16 (staged rows start on 16-byte units)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchan = a.nchan;
   const int nstage = (nchan + kNC - 1) / kNC;
@@ -163,7 +198,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   const unsigned char* ybytes = static_cast<const unsigned char*>(a.y);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < STAGES; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], NCONS);
     }
@@ -173,36 +208,62 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 
   if (warp == NCONS) {
     // ---------------------------------------------------------------- producer
-    // lane j < nd holds delayT[c][d0 + j] for the kNC channels of a stage
+    // delays: lane j < nd copies delayT[c][d0 + j] for the kNC channels of a
+    // stage into a ring of kDelRing stages, kDelRing - 1 stages ahead of use
     const int32_t* __restrict__ dT = a.delayT;
-    auto fetch = [&](int i, int (&v)[kNC]) {
+    auto prefetch = [&](int st) {
+      int* slot = sdel + (st % kDelRing) * kNC * 32;
 #pragma unroll
       for (int ci = 0; ci < kNC; ++ci) {
-        const int c = i * kNC + ci;
-        v[ci] = (c < nchan && lane < dt.nd) ? __ldg(dT + (int64_t)c * a.dtpitch + dt.d0 + lane) : 0;
+        const int c = st * kNC + ci;
+        const bool v = st < nstage && c < nchan && lane < dt.nd;
+        cp_async4(slot + ci * 32 + lane, v ? dT + (int64_t)c * a.dtpitch + dt.d0 + lane : dT, v);
       }
+      asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    int cur[kNC], nxt[kNC];
-    if (nstage > 0) fetch(0, cur);
+#pragma unroll
+    for (int st = 0; st < kDelRing - 1; ++st) prefetch(st);
     bool ok = true;
     int issued = 0;
     for (int i = 0; i < nstage; ++i) {
-      if (i + 1 < nstage) fetch(i + 1, nxt);
-      const int buf = i % kStages;
-      if (i >= kStages) {
+      __syncwarp();  // every lane is done with the slot the next prefetch reuses
+      prefetch(i + kDelRing - 1);
+      asm volatile("cp.async.wait_group %0;" ::"n"(kDelRing - 1) : "memory");
+      __syncwarp();
+      const int buf = i % STAGES;
+      if (i >= STAGES) {
         bool got = false;
-        if (lane == 0) got = mbar_wait_bounded(&empty[buf], (unsigned)(((i / kStages) - 1) & 1));
+        if (lane == 0) got = mbar_wait_bounded(&empty[buf], (unsigned)(((i / STAGES) - 1) & 1));
         if (!__shfl_sync(0xffffffffu, got, 0)) {
           ok = false;
           break;
         }
       }
-      int* del = sdel + buf * kNC * 32;
+      const int* del = sdel + (i % kDelRing) * kNC * 32;
+      if constexpr (MODE == kModeU8) {
+        // per (channel, consumer warp, DM of its group): byte offset in the
+        // stage's rows of the word holding lane 0's first sample, and the
+        // byte shift of that sample inside the word (in bits)
+        // (lane g = w K + j handles DM g of the tile for every channel)
+        if (lane < NCONS * K) {
+          const int w = lane / K, j = lane % K;
+          const int jj = lane < last ? lane : last;
+          int off[kNC];
+          unsigned shifts = 0;
 #pragma unroll
-      for (int ci = 0; ci < kNC; ++ci) del[ci * 32 + lane] = cur[ci];
-      __syncwarp();
+          for (int ci = 0; ci < kNC; ++ci) {
+            const int lo = del[ci * 32];
+            const int o = del[ci * 32 + jj] - lo + ((t0m + lo) & (QS - 1));  // t0 + delay - row start
+            off[ci] = (buf * kNC + ci) * ROWB + (o & ~3);
+            shifts |= (unsigned)((o & 3) * 8) << (8 * ci);
+          }
+          int4* e = sinfo + (buf * NCONS + w) * (K + 1);
+          e[j] = make_int4(off[0], off[1], off[2], off[3]);
+          reinterpret_cast<unsigned*>(e + K)[j] = shifts;
+        }
+      }
       // window geometry of every (channel, consumer warp) pair of the stage
-      for (int p = lane; p < kNC * NCONS; p += 32) {
+      for (int p = lane; MODE != kModeU8 && p < kNC * NCONS; p += 32) {
         const int ci = p / NCONS, w = p % NCONS;
         const int g0 = w * K < last ? w * K : last;
         const int lo = del[ci * 32];
@@ -235,42 +296,27 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
         sinfo[(buf * kNC + ci) * NCONS + w] =
             make_int4((buf * kNC + ci) * ROWB + (aw & ~(QS - 1)) * EB, offs, (S + omax + QS - 1) / QS, 0);
       }
-      unsigned bytes[kNC];
-      unsigned total = 0;
-#pragma unroll
-      for (int ci = 0; ci < kNC; ++ci) {
-        const int lo = __shfl_sync(0xffffffffu, cur[ci], 0);
-        const int hi = __shfl_sync(0xffffffffu, cur[ci], last);
-        const int c = i * kNC + ci;
-        bytes[ci] = 0;
-        if (c < nchan) {
-          const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
-          const int64_t end = t0 + TT + hi + QS;
-          bytes[ci] = (unsigned)((((end - base) * EB) + 15) & ~int64_t(15));
-          total += bytes[ci];
-        }
+      // lane ci < kNC copies the stage's channel ci: samples
+      // [t0 + lo, t0 + TT + hi + QS) rounded out to 16-byte units
+      unsigned nb = 0;
+      int64_t src = 0;
+      if (lane < kNC && i * kNC + lane < nchan) {
+        const int lo = del[lane * 32], hi = del[lane * 32 + last];
+        const int head = (t0m + lo) & (QS - 1);  // row start = t0 + lo - head
+        nb = (unsigned)(((TT + hi - lo + QS + head) * EB + 15) & ~15);
+        src = ((int64_t)(i * kNC + lane) * a.ypitch + t0 + lo - head) * EB;
       }
+      const unsigned total = __reduce_add_sync(0xffffffffu, nb);
+      if (lane == 0) mbar_arrive_expect_tx(&full[buf], total);
       __syncwarp();
-      if (lane == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(&full[buf], total);
-#pragma unroll
-        for (int ci = 0; ci < kNC; ++ci) {
-          if (!bytes[ci]) continue;
-          const int c = i * kNC + ci;
-          const int64_t base = (t0 + cur[ci]) & ~int64_t(QS - 1);
-          bulk_g2s(srow + (buf * kNC + ci) * ROWB, ybytes + ((int64_t)c * a.ypitch + base) * EB, bytes[ci],
-                   &full[buf]);
-        }
-      }
+      if (nb) bulk_g2s(srow + (buf * kNC + lane) * ROWB, ybytes + src, nb, &full[buf]);
       ++issued;
-#pragma unroll
-      for (int ci = 0; ci < kNC; ++ci) cur[ci] = nxt[ci];
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     // let every issued copy land before the CTA can exit
     if (lane == 0) {
-      for (int k = issued - 1; k >= 0 && k >= issued - kStages; --k)
-        if (!mbar_wait_bounded(&full[k % kStages], (unsigned)((k / kStages) & 1))) ok = false;
+      for (int k = issued - 1; k >= 0 && k >= issued - STAGES; --k)
+        if (!mbar_wait_bounded(&full[k % STAGES], (unsigned)((k / STAGES) & 1))) ok = false;
       if (!ok) atomicExch(a.status, TP_ETIMEOUT);
     }
     return;
@@ -285,19 +331,102 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   for (int j = 0; j < K; ++j)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[j][s] = 0.f;
+  // 8-bit mode: for the lane's outputs 4m .. 4m + 3, aw[j][m] sums the words
+  // of their four samples (mod 2^32) and ao[j][m] the odd samples 4m + 1,
+  // 4m + 3 as 16-bit lanes; the even samples' lanes are aw - 256 ao (exact:
+  // no lane sum reaches 2^16 within kU8FoldStages stages), folded into the
+  // 32-bit sums sum32 every kU8FoldStages stages
+  constexpr int PW = MODE == kModeU8 ? S / 4 : 1;
+  constexpr int S32 = MODE == kModeU8 ? S : 1;
+  unsigned aw[K][PW], ao[K][PW];
+  int sum32[K][S32];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int m = 0; m < PW; ++m) aw[j][m] = 0u, ao[j][m] = 0u;
+#pragma unroll
+    for (int s = 0; s < S32; ++s) sum32[j][s] = 0;
+  }
+  auto fold = [&]() {
+    if constexpr (MODE == kModeU8) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int m = 0; m < S / 4; ++m) {
+          const unsigned od = ao[j][m];
+          const unsigned ev = aw[j][m] - (od << 8);
+          sum32[j][4 * m] += (int)(ev & 0xffffu);
+          sum32[j][4 * m + 2] += (int)(ev >> 16);
+          sum32[j][4 * m + 1] += (int)(od & 0xffffu);
+          sum32[j][4 * m + 3] += (int)(od >> 16);
+          aw[j][m] = 0u;
+          ao[j][m] = 0u;
+        }
+    }
+  };
   using WT = typename std::conditional<MODE == kModeF32, float, unsigned>::type;
   WT w[ALGO == 0 ? LR : 4];
 #pragma unroll
   for (int q = 0; q < (ALGO == 0 ? LR : 4); ++q) w[q] = 0;
+  // the staged words holding samples 4m .. 4m + 3 (m <= S / 4) of the lane's
+  // outputs for one DM and channel, given lane 0's word offset
+  const int lane_bytes = lane * S;
+  auto load_words = [&](int off, unsigned (&wv)[S / 4 + 1]) {
+    const unsigned* r = reinterpret_cast<const unsigned*>(srow + off + lane_bytes);
+#pragma unroll
+    for (int k = 0; k <= S / 4; ++k) wv[k] = r[k];
+  };
 
   for (int i = 0; i < nstage; ++i) {
-    const int buf = i % kStages;
-    if (!mbar_wait_bounded(&full[buf], (unsigned)((i / kStages) & 1))) {
+    const int buf = i % STAGES;
+    if (!mbar_wait_bounded(&full[buf], (unsigned)((i / STAGES) & 1))) {
       if (lane == 0) atomicExch(a.status, TP_ETIMEOUT);
       return;
     }
     const int nc = nchan - i * kNC < kNC ? nchan - i * kNC : kNC;
-    if (live && ALGO == 1) {
+    if constexpr (MODE == kModeU8) {
+      // direct loads of each DM's words, aligned to the lane's outputs by a
+      // byte funnel shift; two channels at a time so that each accumulator
+      // takes both in one three-input add
+      if (live) {
+        const int4* e = sinfo + (buf * NCONS + warp) * (K + 1);
+        const int4 shv = e[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const int4 ad = e[j];
+          const unsigned shj = (unsigned)(j == 0 ? shv.x : j == 1 ? shv.y : j == 2 ? shv.z : shv.w);
+#pragma unroll
+          for (int ci = 0; ci < kNC; ci += 2) {
+            if (ci >= nc) break;
+            const int offa = ci == 0 ? ad.x : ad.z;
+            const unsigned sa = shj >> (8 * ci);
+            unsigned wa[S / 4 + 1];
+            load_words(offa, wa);
+            if (ci + 1 < nc) {
+              const int offb = ci == 0 ? ad.y : ad.w;
+              const unsigned sb = shj >> (8 * ci + 8);
+              unsigned wb[S / 4 + 1];
+              load_words(offb, wb);
+#pragma unroll
+              for (int m = 0; m < S / 4; ++m) {
+                const unsigned fa = __funnelshift_r(wa[m], wa[m + 1], sa);
+                const unsigned fb = __funnelshift_r(wb[m], wb[m + 1], sb);
+                aw[j][m] = add3_u8(aw[j][m], fa, fb);
+                ao[j][m] = add3_u8(ao[j][m], odd_u8(fa), odd_u8(fb));
+              }
+            } else {
+#pragma unroll
+              for (int m = 0; m < S / 4; ++m) {
+                const unsigned fa = __funnelshift_r(wa[m], wa[m + 1], sa);
+                aw[j][m] += fa;
+                ao[j][m] += odd_u8(fa);
+              }
+            }
+          }
+        }
+      }
+      if (i % kU8FoldStages == kU8FoldStages - 1) fold();
+    } else if (live && ALGO == 1) {
       // direct loads: each DM reads its own S samples at its own offset
       for (int ci = 0; ci < nc; ++ci) {
         const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
@@ -357,8 +486,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
     if (lane == 0) mbar_arrive(&empty[buf]);
   }
 
-  // epilogue: 16-bit modes accumulated the stored samples x~; subtract the
-  // block's sum of bandpass values (exact integers for 8-bit data)
+  // epilogue: 16-bit and 8-bit modes accumulated the stored samples x~;
+  // subtract the block's sum of bandpass values (exact integers for 8-bit data)
+  fold();
   if (!live) return;
   const bool is_int = a.dtype == TP_U8;
   float bhi = 0.f, blo = 0.f;
@@ -379,7 +509,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       long long s1 = 0, s2 = 0;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const int v = __float2int_rn(acc[j][s]) - bint;
+        const int v = (MODE == kModeU8 ? sum32[j][MODE == kModeU8 ? s : 0] : __float2int_rn(acc[j][s])) - bint;
         if (tl + s < a.nout) {
           Drow[tl + s] = v;
           s1 += v;
@@ -444,6 +574,8 @@ template <int K, int S, int OMAX, int NCONS, int EB, int ALGO, int MINB>
 cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t s) {
   if constexpr (EB == 4) {
     return launch_mode<K, S, OMAX, NCONS, kModeF32, ALGO, MINB>(ba, ctas, s);
+  } else if constexpr (EB == 1) {
+    return launch_mode<K, S, OMAX, NCONS, kModeU8, ALGO, MINB>(ba, ctas, s);
   } else {
     if (dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16, ALGO, MINB>(ba, ctas, s);
     return launch_mode<K, S, OMAX, NCONS, kModeF16, ALGO, MINB>(ba, ctas, s);
@@ -456,7 +588,8 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
 // OMAX, consumer warps).  The planner keeps the shapes whose K-trial groups
 // all spread by at most OMAX - 3 samples; the autotuner (or the first
 // feasible shape) picks among them.
-// EB = bytes per staged sample: 4 for FP32 data, 2 for 16-bit and 8-bit data.
+// EB = bytes per staged sample: 4 for FP32 data, 2 for 16-bit data, 1 for
+// 8-bit data.
 // ALGO 0: register window + jump-table shifted adds (reuse across the K DMs);
 // ALGO 1: direct shared loads per DM (no offset bound, OMAX unused).
 // MINB: CTAs per SM the register allocation is sized for.
@@ -477,7 +610,14 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
   X(13, 4, 15, 0, 8, 4, 1, 2)        \
   X(14, 2, 26, 0, 8, 2, 1, 2)        \
   X(15, 4, 22, 0, 8, 2, 1, 1)        \
-  X(16, 2, 22, 0, 16, 2, 1, 1)
+  X(16, 2, 22, 0, 16, 2, 1, 1)        \
+  X(17, 2, 20, 0, 8, 1, 1, 2)        \
+  X(18, 2, 28, 0, 15, 1, 1, 1)       \
+  X(19, 1, 36, 0, 16, 1, 1, 1)       \
+  X(20, 4, 20, 0, 8, 1, 1, 1)        \
+  X(21, 2, 36, 0, 8, 1, 1, 1)        \
+  X(22, 1, 44, 0, 15, 1, 1, 1)       \
+  X(23, 3, 28, 0, 10, 1, 1, 1)
 
 #define TP_SHAPE_ENTRY(i, K, S, O, N, EB, A, M) {K, S, O, N, EB, A},
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};

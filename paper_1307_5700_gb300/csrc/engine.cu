@@ -48,6 +48,10 @@ size_t dtype_size(int dtype) {
   }
 }
 
+// bytes per sample of the staged series y (A4 output): FP32 y for FP32 data,
+// the stored samples x~ in their own format otherwise
+int staged_bytes(int dtype) { return (int)dtype_size(dtype); }
+
 // Nearest value of a 16-bit storage format (ties to even), from the format's
 // definition; the same rule the statistics kernel applies on the device.
 static double round_to_format(double v, int sig, int emin, double maxv) {
@@ -266,8 +270,8 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
 // while the tile's delay spread stays within kMaxOverhang.
 bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype, int sh,
                 std::vector<DmTile>* tiles) {
-  const int EB = dtype == TP_F32 ? 4 : 2;
-  if (kShapes[sh].EB != EB) return false;
+  if (kShapes[sh].EB != staged_bytes(dtype)) return false;
+  const int EB = kShapes[sh].EB;
   // per-beam buffers (partial sums, staging padding) are sized for tiles of
   // kMinTileT..kMaxTileT outputs
   if (shape_tile_t(sh) < kMinTileT || shape_tile_t(sh) > kMaxTileT) return false;
@@ -278,6 +282,10 @@ bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype
       const int d1 = std::min(d0 + K, ndm) - 1;
       if (spread(delay, nchan, d0, d1) + residue > kShapes[sh].OMAX) return false;
     }
+  // the staging rows hold a tile's outputs plus at most kMaxOverhang samples
+  // of delay spread, which a single group must respect too
+  for (int d0 = 0; d0 < ndm; d0 += K)
+    if (spread(delay, nchan, d0, std::min(d0 + K, ndm) - 1) > kMaxOverhang) return false;
   tiles->clear();
   int d0 = 0;
   while (d0 < ndm) {
@@ -345,7 +353,7 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->spec_bits, (size_t)((nmax + 31) / 32) * 4);
   add((void**)&b->spec_nflag, 4);
   add((void**)&b->spec_thr, 8);
-  const size_t yb = p->dtype == TP_F32 ? 4 : 2;
+  const size_t yb = (size_t)staged_bytes(p->dtype);
   add((void**)&b->y, nc * (size_t)ypitch * yb);
   add((void**)&b->b16, nc * 2);
   add((void**)&b->bsum, 8);
@@ -945,7 +953,7 @@ int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capac
     b->allocs.push_back(ptr);
     *it.first = ptr;
   }
-  cudaError_t ce = cudaMemset(b->y, 0, (size_t)p->nchan * b->ypitch * (p->dtype == TP_F32 ? 4 : 2));
+  cudaError_t ce = cudaMemset(b->y, 0, (size_t)p->nchan * b->ypitch * (size_t)staged_bytes(p->dtype));
   if (ce == cudaSuccess) ce = cudaMemset(b->status, 0, 4);
   if (ce != cudaSuccess) {
     free_beam(b);

@@ -532,8 +532,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   for (int r = 0; r < 4; ++r) sflag[r] = (word >> (4 * q + r)) & 1u;
 
   // pass 2: y (FP32 data: x - mu, flagged -> 0) or the stored samples x~
-  // (16-bit data: flagged -> b16; 8-bit data: widened to binary16, exact,
-  // flagged -> b)
+  // in their own format (16-bit data: flagged -> b16; 8-bit data: flagged -> b)
   if (valid == 0) return;
   for (int c = g; c < a.nchan; c += 32) {
     const bool any = a.chan_nflag[c] != 0;
@@ -554,15 +553,22 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
       } else {
         for (int r = 0; r < valid; ++r) dst[r] = o[r];
       }
+    } else if constexpr (DT == TP_U8) {
+      const uint8_t* src = static_cast<const uint8_t*>(a.x) + (int64_t)c * a.pitch + tq;
+      const unsigned b = (unsigned)a.bint[c];
+      uint8_t* dst = static_cast<uint8_t*>(yv) + (int64_t)c * ypitch + tq;
+      if (valid == 4) {
+        const unsigned u = __ldg(reinterpret_cast<const unsigned*>(src));
+        unsigned o = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) o |= (fl[r] ? b : ((u >> (8 * r)) & 0xffu)) << (8 * r);
+        *reinterpret_cast<unsigned*>(dst) = o;
+      } else {
+        for (int r = 0; r < valid; ++r) dst[r] = fl[r] ? (uint8_t)b : __ldg(src + r);
+      }
     } else {
       unsigned short h[4];
-      if constexpr (DT == TP_U8) {
-        float v[4];
-        load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
-        const float b = (float)a.bint[c];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) h[r] = __half_as_ushort(__float2half_rn(fl[r] ? b : v[r]));
-      } else {
+      {
         const unsigned short* src = static_cast<const unsigned short*>(a.x) + (int64_t)c * a.pitch + tq;
         const unsigned short b = a.b16[c];
         if (valid == 4) {

@@ -58,8 +58,8 @@ struct DmTile {
 };
 
 struct DedispArgs {
-  const void* y;          // staged series [nchan][ypitch]: FP32 y, or 16-bit x~
-  int64_t ypitch;         // samples per channel row (>= window + tile + 16)
+  const void* y;          // staged series [nchan][ypitch]: FP32 y, or x~ in its storage format
+  int64_t ypitch;         // samples per row (>= window + tile + 16)
   const double* bsum;     // 16-bit modes: sum over channels of the bandpass values
   int nchan;
   int64_t nout;           // T
@@ -97,7 +97,7 @@ struct KernelShape {
   int EB;     // bytes per staged sample (4: FP32 y; 2: 16-bit x~)
   int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads
 };
-constexpr int kNumShapes = 17;
+constexpr int kNumShapes = 24;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
@@ -128,7 +128,7 @@ struct DetectArgs {
 
 // Dedispersion tiling constants (shared by the planner and the kernel).
 constexpr int kMinTileT = 256;      // smallest output tile any shape may use (sizes buffers)
-constexpr int kMaxTileT = 896;      // largest output tile of any shape
+constexpr int kMaxTileT = 1408;     // largest output tile of any shape
 constexpr int kMaxOverhang = 512;   // max delay spread inside a CTA tile
 constexpr int kDetectT = 4096;      // samples per detection CTA
 
