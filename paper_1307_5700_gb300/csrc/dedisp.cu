@@ -113,22 +113,15 @@ __device__ __forceinline__ void add_pair_h(float& acc0, float& acc1, unsigned pr
 constexpr int kModeF32 = 0;   // FP32 y (float data)
 constexpr int kModeF16 = 1;   // binary16 x~
 constexpr int kModeBF16 = 2;  // bfloat16 x~
-constexpr int kModeU8 = 3;    // 8-bit x~, summed as packed 16-bit integers
+constexpr int kModeU8 = 3;    // 8-bit x~ widened to 16 bits, summed as packed 16-bit integers
 
 // 8-bit mode: channels summed into packed 16-bit lanes before they are folded
 // into the 32-bit sums (256 x 255 < 2^16, so no lane can carry into the next)
 constexpr int kU8FoldStages = 256 / kNC;
 
-// Samples 1 and 3 of a word of four 8-bit samples (first sample in the low
-// byte), as two 16-bit lanes.
-__device__ __forceinline__ unsigned odd_u8(unsigned w) { return __byte_perm(w, 0u, 0x4341u); }
-
-// acc + x + y, the packed 8-bit accumulation step (one three-input add)
-__device__ __forceinline__ unsigned add3_u8(unsigned acc, unsigned x, unsigned y) { return acc + x + y; }
-
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO>
 struct Shape {
-  static constexpr int EB = MODE == kModeF32 ? 4 : (MODE == kModeU8 ? 1 : 2);  // bytes per sample
+  static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
   static constexpr int QS = 16 / EB;                                          // samples per 16 B
   static constexpr int TT = 32 * S;                                           // outputs per tile
   static constexpr int L = (S + OMAX + 1 + QS - 1) / QS * QS;                 // window samples
@@ -147,9 +140,10 @@ struct Shape {
   static constexpr size_t smem = data_bytes + del_bytes + info_bytes + 16 * STAGES;
   // no bank conflicts: register windows (ALGO 0) start an odd number of 16-byte
   // units apart, direct 32-bit loads (ALGO 1) an odd number of words apart
-  static_assert(ALGO == 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
+  static_assert(ALGO >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
+  static_assert(ALGO != 2 || (MODE != kModeU8 && K == 2), "DM-pair windows: float data, two trials per warp");
   static_assert(ALGO == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
-  static_assert(MODE != kModeU8 || (ALGO == 1 && S % 4 == 0), "8-bit loads take whole words");
+  static_assert(MODE != kModeU8 || ALGO == 1, "8-bit data use direct loads");
 };
 
 // Per (stage, channel, consumer warp) the producer writes an int4:
@@ -242,8 +236,8 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       const int* del = sdel + (i % kDelRing) * kNC * 32;
       if constexpr (MODE == kModeU8) {
         // per (channel, consumer warp, DM of its group): byte offset in the
-        // stage's rows of the word holding lane 0's first sample, and the
-        // byte shift of that sample inside the word (in bits)
+        // stage's rows of the word holding lane 0's first sample, and that
+        // sample's shift inside the word (0 or 16 bits)
         // (lane g = w K + j handles DM g of the tile for every channel)
         if (lane < NCONS * K) {
           const int w = lane / K, j = lane % K;
@@ -254,8 +248,8 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
           for (int ci = 0; ci < kNC; ++ci) {
             const int lo = del[ci * 32];
             const int o = del[ci * 32 + jj] - lo + ((t0m + lo) & (QS - 1));  // t0 + delay - row start
-            off[ci] = (buf * kNC + ci) * ROWB + (o & ~3);
-            shifts |= (unsigned)((o & 3) * 8) << (8 * ci);
+            off[ci] = (buf * kNC + ci) * ROWB + (o & ~1) * EB;
+            shifts |= (unsigned)((o & 1) * 16) << (8 * ci);
           }
           int4* e = sinfo + (buf * NCONS + w) * (K + 1);
           e[j] = make_int4(off[0], off[1], off[2], off[3]);
@@ -270,7 +264,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
         const int dw = del[ci * 32 + g0];
         const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
         const int aw = (int)(t0 + dw - base);
-        if constexpr (ALGO == 1) {
+        if constexpr (ALGO >= 1) {
           // sample offset, in the staged row, of each DM's first output of lane 0
           int o[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -331,19 +325,17 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   for (int j = 0; j < K; ++j)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[j][s] = 0.f;
-  // 8-bit mode: for the lane's outputs 4m .. 4m + 3, aw[j][m] sums the words
-  // of their four samples (mod 2^32) and ao[j][m] the odd samples 4m + 1,
-  // 4m + 3 as 16-bit lanes; the even samples' lanes are aw - 256 ao (exact:
-  // no lane sum reaches 2^16 within kU8FoldStages stages), folded into the
-  // 32-bit sums sum32 every kU8FoldStages stages
-  constexpr int PW = MODE == kModeU8 ? S / 4 : 1;
+  // 8-bit mode: pk[j][m] holds outputs 2m, 2m + 1 of DM j as 16-bit lanes
+  // (exact: no lane sum reaches 2^16 within kU8FoldStages stages), folded
+  // into the 32-bit sums sum32 every kU8FoldStages stages
+  constexpr int PW = MODE == kModeU8 ? S / 2 : 1;
   constexpr int S32 = MODE == kModeU8 ? S : 1;
-  unsigned aw[K][PW], ao[K][PW];
+  unsigned pk[K][PW];
   int sum32[K][S32];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
 #pragma unroll
-    for (int m = 0; m < PW; ++m) aw[j][m] = 0u, ao[j][m] = 0u;
+    for (int m = 0; m < PW; ++m) pk[j][m] = 0u;
 #pragma unroll
     for (int s = 0; s < S32; ++s) sum32[j][s] = 0;
   }
@@ -352,15 +344,10 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 #pragma unroll
       for (int j = 0; j < K; ++j)
 #pragma unroll
-        for (int m = 0; m < S / 4; ++m) {
-          const unsigned od = ao[j][m];
-          const unsigned ev = aw[j][m] - (od << 8);
-          sum32[j][4 * m] += (int)(ev & 0xffffu);
-          sum32[j][4 * m + 2] += (int)(ev >> 16);
-          sum32[j][4 * m + 1] += (int)(od & 0xffffu);
-          sum32[j][4 * m + 3] += (int)(od >> 16);
-          aw[j][m] = 0u;
-          ao[j][m] = 0u;
+        for (int m = 0; m < S / 2; ++m) {
+          sum32[j][2 * m] += (int)(pk[j][m] & 0xffffu);
+          sum32[j][2 * m + 1] += (int)(pk[j][m] >> 16);
+          pk[j][m] = 0u;
         }
     }
   };
@@ -368,13 +355,18 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   WT w[ALGO == 0 ? LR : 4];
 #pragma unroll
   for (int q = 0; q < (ALGO == 0 ? LR : 4); ++q) w[q] = 0;
-  // the staged words holding samples 4m .. 4m + 3 (m <= S / 4) of the lane's
-  // outputs for one DM and channel, given lane 0's word offset
-  const int lane_bytes = lane * S;
-  auto load_words = [&](int off, unsigned (&wv)[S / 4 + 1]) {
+  // the staged words of the lane's outputs 2m, 2m + 1 for one DM and channel,
+  // given lane 0's word offset and the half-word shift of its first sample
+  const int lane_bytes = lane * S * EB;
+  constexpr int NW = MODE == kModeU8 ? S / 2 + 1 : 1;
+  auto load_words = [&](int off, unsigned sh, unsigned (&wv)[NW]) {
     const unsigned* r = reinterpret_cast<const unsigned*>(srow + off + lane_bytes);
 #pragma unroll
-    for (int k = 0; k <= S / 4; ++k) wv[k] = r[k];
+    for (int k = 0; k < NW; ++k) wv[k] = r[k];
+    if (sh) {
+#pragma unroll
+      for (int k = 0; k + 1 < NW; ++k) wv[k] = __funnelshift_r(wv[k], wv[k + 1], 16u);
+    }
   };
 
   for (int i = 0; i < nstage; ++i) {
@@ -385,9 +377,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
     }
     const int nc = nchan - i * kNC < kNC ? nchan - i * kNC : kNC;
     if constexpr (MODE == kModeU8) {
-      // direct loads of each DM's words, aligned to the lane's outputs by a
-      // byte funnel shift; two channels at a time so that each accumulator
-      // takes both in one three-input add
+      // direct loads of each DM's words (a half-word funnel shift for odd
+      // offsets); two channels at a time so that each accumulator takes both
+      // in one three-input add
       if (live) {
         const int4* e = sinfo + (buf * NCONS + warp) * (K + 1);
         const int4 shv = e[K];
@@ -398,34 +390,40 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 #pragma unroll
           for (int ci = 0; ci < kNC; ci += 2) {
             if (ci >= nc) break;
-            const int offa = ci == 0 ? ad.x : ad.z;
-            const unsigned sa = shj >> (8 * ci);
-            unsigned wa[S / 4 + 1];
-            load_words(offa, wa);
+            unsigned wa[NW];
+            load_words(ci == 0 ? ad.x : ad.z, (shj >> (8 * ci)) & 0xffu, wa);
             if (ci + 1 < nc) {
-              const int offb = ci == 0 ? ad.y : ad.w;
-              const unsigned sb = shj >> (8 * ci + 8);
-              unsigned wb[S / 4 + 1];
-              load_words(offb, wb);
+              unsigned wb[NW];
+              load_words(ci == 0 ? ad.y : ad.w, (shj >> (8 * ci + 8)) & 0xffu, wb);
 #pragma unroll
-              for (int m = 0; m < S / 4; ++m) {
-                const unsigned fa = __funnelshift_r(wa[m], wa[m + 1], sa);
-                const unsigned fb = __funnelshift_r(wb[m], wb[m + 1], sb);
-                aw[j][m] = add3_u8(aw[j][m], fa, fb);
-                ao[j][m] = add3_u8(ao[j][m], odd_u8(fa), odd_u8(fb));
-              }
+              for (int m = 0; m < S / 2; ++m) pk[j][m] = pk[j][m] + wa[m] + wb[m];
             } else {
 #pragma unroll
-              for (int m = 0; m < S / 4; ++m) {
-                const unsigned fa = __funnelshift_r(wa[m], wa[m + 1], sa);
-                aw[j][m] += fa;
-                ao[j][m] += odd_u8(fa);
-              }
+              for (int m = 0; m < S / 2; ++m) pk[j][m] += wa[m];
             }
           }
         }
       }
       if (i % kU8FoldStages == kU8FoldStages - 1) fold();
+    } else if (live && ALGO == 2) {
+      if constexpr (ALGO == 2) {
+        // one window per channel for the warp's two trials: S + d samples
+        // at the first trial's offset, d = the second trial's extra delay
+        const unsigned sbase = smem_u32(srow) + (unsigned)(lane * S * EB);
+        for (int ci = 0; ci < nc; ++ci) {
+          const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
+          const int o0 = inf.y & 0xffff, o1 = (inf.y >> 16) & 0xffff;
+          int d = o1 - o0;
+          // the planner bounds d by OMAX; the clamp keeps the indexed branch
+          // inside its table whatever the delays hold
+          d = d < 0 ? 0 : (d > OMAX ? OMAX : d);
+          if constexpr (MODE == kModeF32)
+            add_pair<S, OMAX>(d, sbase + (unsigned)(inf.x + o0 * 4), acc[0], acc[1]);
+          else
+            add_pair16<S, OMAX, MODE == kModeBF16 ? 1 : 0>((o0 & 1) * (OMAX + 1) + d,
+                                                           sbase + (unsigned)(inf.x + (o0 & ~1) * 2), acc[0], acc[1]);
+        }
+      }
     } else if (live && ALGO == 1) {
       // direct loads: each DM reads its own S samples at its own offset
       for (int ci = 0; ci < nc; ++ci) {
@@ -570,11 +568,11 @@ cudaError_t launch_mode(const BatchArgs& ba, int ctas, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int K, int S, int OMAX, int NCONS, int EB, int ALGO, int MINB>
+template <int K, int S, int OMAX, int NCONS, int FMT, int ALGO, int MINB>
 cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t s) {
-  if constexpr (EB == 4) {
+  if constexpr (FMT == 4) {
     return launch_mode<K, S, OMAX, NCONS, kModeF32, ALGO, MINB>(ba, ctas, s);
-  } else if constexpr (EB == 1) {
+  } else if constexpr (FMT == 3) {
     return launch_mode<K, S, OMAX, NCONS, kModeU8, ALGO, MINB>(ba, ctas, s);
   } else {
     if (dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16, ALGO, MINB>(ba, ctas, s);
@@ -588,10 +586,11 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
 // OMAX, consumer warps).  The planner keeps the shapes whose K-trial groups
 // all spread by at most OMAX - 3 samples; the autotuner (or the first
 // feasible shape) picks among them.
-// EB = bytes per staged sample: 4 for FP32 data, 2 for 16-bit data, 1 for
-// 8-bit data.
+// FMT = staging format: 4 FP32 y (FP32 data), 2 16-bit float x~ (binary16 and
+// bfloat16 data), 3 8-bit x~ widened to 16-bit integers.
 // ALGO 0: register window + jump-table shifted adds (reuse across the K DMs);
-// ALGO 1: direct shared loads per DM (no offset bound, OMAX unused).
+// ALGO 1: direct shared loads per DM (no offset bound, OMAX unused);
+// ALGO 2: DM pairs sharing one window, second trial's extra delay <= OMAX.
 // MINB: CTAs per SM the register allocation is sized for.
 #define TP_SHAPES(X)                 \
   X(0, 4, 20, 36, 8, 4, 0, 1)        \
@@ -611,15 +610,21 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
   X(14, 2, 26, 0, 8, 2, 1, 2)        \
   X(15, 4, 22, 0, 8, 2, 1, 1)        \
   X(16, 2, 22, 0, 16, 2, 1, 1)        \
-  X(17, 2, 20, 0, 8, 1, 1, 2)        \
-  X(18, 2, 28, 0, 15, 1, 1, 1)       \
-  X(19, 1, 36, 0, 16, 1, 1, 1)       \
-  X(20, 4, 20, 0, 8, 1, 1, 1)        \
-  X(21, 2, 36, 0, 8, 1, 1, 1)        \
-  X(22, 1, 44, 0, 15, 1, 1, 1)       \
-  X(23, 3, 28, 0, 10, 1, 1, 1)
+  X(17, 2, 18, 0, 8, 3, 1, 2)        \
+  X(18, 2, 26, 0, 15, 3, 1, 1)       \
+  X(19, 1, 38, 0, 15, 3, 1, 1)       \
+  X(20, 4, 18, 0, 8, 3, 1, 1)        \
+  X(21, 2, 34, 0, 8, 3, 1, 1)        \
+  X(22, 1, 42, 0, 15, 3, 1, 1)       \
+  X(23, 3, 26, 0, 10, 3, 1, 1)       \
+  X(24, 2, 25, 11, 15, 4, 2, 1)      \
+  X(25, 2, 25, 11, 8, 4, 2, 2)       \
+  X(26, 2, 21, 15, 8, 4, 2, 2)       \
+  X(27, 2, 29, 11, 15, 4, 2, 1)      \
+  X(28, 2, 26, 11, 15, 2, 2, 1)      \
+  X(29, 2, 22, 11, 8, 2, 2, 2)
 
-#define TP_SHAPE_ENTRY(i, K, S, O, N, EB, A, M) {K, S, O, N, EB, A},
+#define TP_SHAPE_ENTRY(i, K, S, O, N, F, A, M) {K, S, O, N, F, A},
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};
 #undef TP_SHAPE_ENTRY
 
@@ -627,8 +632,8 @@ int shape_tile_t(int shape) { return 32 * kShapes[shape].S; }
 
 cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s) {
   switch (shape) {
-#define TP_SHAPE_CASE(i, K, S, O, N, EB, A, M) \
-  case i: return launch_shape<K, S, O, N, EB, A, M>(ba, dtype, ctas, s);
+#define TP_SHAPE_CASE(i, K, S, O, N, F, A, M) \
+  case i: return launch_shape<K, S, O, N, F, A, M>(ba, dtype, ctas, s);
     TP_SHAPES(TP_SHAPE_CASE)
 #undef TP_SHAPE_CASE
     default: return cudaErrorInvalidValue;

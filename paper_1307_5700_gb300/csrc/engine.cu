@@ -49,8 +49,12 @@ size_t dtype_size(int dtype) {
 }
 
 // bytes per sample of the staged series y (A4 output): FP32 y for FP32 data,
-// the stored samples x~ in their own format otherwise
-int staged_bytes(int dtype) { return (int)dtype_size(dtype); }
+// the stored samples x~ in their own 16-bit format, or 8-bit samples widened
+// to 16-bit integers
+int staged_bytes(int dtype) { return dtype == TP_F32 ? 4 : 2; }
+
+// the kernel-shape staging format (KernelShape::FMT) a dtype needs
+int staged_format(int dtype) { return dtype == TP_F32 ? 4 : (dtype == TP_U8 ? 3 : 2); }
 
 // Nearest value of a 16-bit storage format (ties to even), from the format's
 // definition; the same rule the statistics kernel applies on the device.
@@ -270,13 +274,22 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
 // while the tile's delay spread stays within kMaxOverhang.
 bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype, int sh,
                 std::vector<DmTile>* tiles) {
-  if (kShapes[sh].EB != staged_bytes(dtype)) return false;
-  const int EB = kShapes[sh].EB;
+  if (kShapes[sh].FMT != staged_format(dtype)) return false;
+  const int EB = staged_bytes(dtype);
   // per-beam buffers (partial sums, staging padding) are sized for tiles of
   // kMinTileT..kMaxTileT outputs
   if (shape_tile_t(sh) < kMinTileT || shape_tile_t(sh) > kMaxTileT) return false;
   const int K = kShapes[sh].K;
   const int residue = 16 / EB - 1;  // in-window offset of a 16-byte aligned copy
+  if (kShapes[sh].ALGO == 2)
+    // tiles start on even trials, so the pairs are (2i, 2i + 1): the second
+    // trial's delay may exceed the first's by 0 .. OMAX in every channel
+    for (int d0 = 0; d0 + 1 < ndm; d0 += 2) {
+      const int32_t* a = &delay[(size_t)d0 * nchan];
+      const int32_t* b = &delay[(size_t)(d0 + 1) * nchan];
+      for (int c = 0; c < nchan; ++c)
+        if (b[c] < a[c] || b[c] - a[c] > kShapes[sh].OMAX) return false;
+    }
   if (kShapes[sh].ALGO == 0)
     for (int d0 = 0; d0 < ndm; d0 += K) {
       const int d1 = std::min(d0 + K, ndm) - 1;

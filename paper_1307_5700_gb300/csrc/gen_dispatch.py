@@ -86,6 +86,88 @@ def emit16(S, OMAX, kind):
     return "\n".join(lines)
 
 
+# (S, OMAX) pairs of the FP32 DM-pair shapes (ALGO 2).
+PAIRS = [(25, 11), (21, 15), (29, 11)]
+
+
+def emit_pair(S, OMAX):
+    """Two consecutive DM trials whose delays in a channel differ by d in
+    [0, OMAX]: loads the S + d staged samples at lane 0's offset for the first
+    trial (plus the lane's own offset, folded into the address), then
+    a0[s] += w[s] and a1[s] += w[s + d].  One indexed branch per call."""
+    lines = []
+    lines.append(f"template <>\n__device__ __forceinline__ void add_pair<{S}, {OMAX}>(int d, unsigned addr, float (&a0)[{S}], float (&a1)[{S}]) {{")
+    body = ["{"]
+    body.append(f".reg .f32 w<{S + OMAX}>;")
+    body.append("tbl: .branchtargets " + ", ".join(f"C{d}" for d in range(OMAX + 1)) + ";")
+    ia = 2 * S
+    idx = 2 * S + 1
+    body.append(f"brx.idx.uni %{idx}, tbl;")
+    for d in range(OMAX + 1):
+        body.append(f"C{d}:")
+        for k in range(S + d):
+            body.append(f"ld.shared.f32 w{k}, [%{ia}+{4 * k}];")
+        for s_ in range(S):
+            body.append(f"add.f32 %{s_}, %{s_}, w{s_};")
+            body.append(f"add.f32 %{S + s_}, %{S + s_}, w{s_ + d};")
+        if d != OMAX:
+            body.append("bra.uni CEND;")
+    body.append("CEND:")
+    body.append("}")
+    asm = "\\n\"\n      \"".join(body)
+    outs = ", ".join([f'"+f"(a0[{s_}])' for s_ in range(S)] + [f'"+f"(a1[{s_}])' for s_ in range(S)])
+    ins = f'"r"(addr), "r"(d)'
+    lines.append(f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins}\n      : "memory");')
+    lines.append("}\n")
+    return "\n".join(lines)
+
+
+# (S, OMAX) of the 16-bit DM-pair shapes (ALGO 2): S = 2 mod 4 so that lanes
+# start an odd number of words apart.
+PAIRS16 = [(26, 11), (22, 11)]
+
+
+def emit_pair16(S, OMAX, kind):
+    """16-bit version of emit_pair: samples two per 32-bit word (low half
+    first); block index r (OMAX + 1) + d, with r the first trial's half-word
+    offset inside its first word."""
+    op = "add.rn.f32.f16" if kind == 0 else "add.rn.f32.bf16"
+    nwmax = (1 + OMAX + S + 1) // 2
+    lines = []
+    lines.append(f"template <>\n__device__ __forceinline__ void add_pair16<{S}, {OMAX}, {kind}>(int b, unsigned addr, float (&a0)[{S}], float (&a1)[{S}]) {{")
+    body = ["{"]
+    body.append(f".reg .b32 w<{nwmax}>;")
+    body.append(f".reg .b16 lo<{nwmax}>, hi<{nwmax}>;")
+    nb = 2 * (OMAX + 1)
+    body.append("tbl: .branchtargets " + ", ".join(f"C{b}" for b in range(nb)) + ";")
+    ia = 2 * S
+    idx = 2 * S + 1
+    body.append(f"brx.idx.uni %{idx}, tbl;")
+    for b in range(nb):
+        r, d = b // (OMAX + 1), b % (OMAX + 1)
+        nw = (r + d + S + 1) // 2
+        body.append(f"C{b}:")
+        for k in range(nw):
+            body.append(f"ld.shared.b32 w{k}, [%{ia}+{4 * k}];")
+        for k in range(nw):
+            body.append(f"mov.b32 {{lo{k}, hi{k}}}, w{k};")
+        def half(h):
+            return f"lo{h >> 1}" if h % 2 == 0 else f"hi{h >> 1}"
+        for s_ in range(S):
+            body.append(f"{op} %{s_}, {half(r + s_)}, %{s_};")
+            body.append(f"{op} %{S + s_}, {half(r + d + s_)}, %{S + s_};")
+        if b != nb - 1:
+            body.append("bra.uni CEND;")
+    body.append("CEND:")
+    body.append("}")
+    asm = "\\n\"\n      \"".join(body)
+    outs = ", ".join([f'"+f"(a0[{s_}])' for s_ in range(S)] + [f'"+f"(a1[{s_}])' for s_ in range(S)])
+    ins = f'"r"(addr), "r"(b)'
+    lines.append(f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins}\n      : "memory");')
+    lines.append("}\n")
+    return "\n".join(lines)
+
+
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
     out = [
@@ -99,6 +181,15 @@ def main():
         "template <int S, int L, int OMAX>",
         "__device__ __forceinline__ void add_shifted(int o, float (&acc)[S], const float (&w)[L]);",
         "",
+        "// two consecutive DM trials from one window of staged FP32 samples",
+        "template <int S, int OMAX>",
+        "__device__ __forceinline__ void add_pair(int d, unsigned addr, float (&a0)[S], float (&a1)[S]);",
+        "",
+        "// the same for 16-bit samples (kind 0 = binary16, 1 = bfloat16), block",
+        "// index = first trial's half-word offset r * (OMAX + 1) + d",
+        "template <int S, int OMAX, int KIND>",
+        "__device__ __forceinline__ void add_pair16(int b, unsigned addr, float (&a0)[S], float (&a1)[S]);",
+        "",
         "// 16-bit samples, two per register; kind 0 = binary16, 1 = bfloat16.",
         "template <int S, int LR, int OMAX, int KIND>",
         "__device__ __forceinline__ void add_shifted_h(int o, float (&acc)[S], const unsigned (&w)[LR]);",
@@ -109,6 +200,11 @@ def main():
     for S, OMAX in SHAPES16:
         for kind in (0, 1):
             out.append(emit16(S, OMAX, kind))
+    for S, OMAX in PAIRS:
+        out.append(emit_pair(S, OMAX))
+    for S, OMAX in PAIRS16:
+        for kind in (0, 1):
+            out.append(emit_pair16(S, OMAX, kind))
     out.append("}  // namespace tp")
     with open(os.path.join(here, "dispatch_gen.cuh"), "w") as f:
         f.write("\n".join(out) + "\n")

@@ -532,7 +532,8 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   for (int r = 0; r < 4; ++r) sflag[r] = (word >> (4 * q + r)) & 1u;
 
   // pass 2: y (FP32 data: x - mu, flagged -> 0) or the stored samples x~
-  // in their own format (16-bit data: flagged -> b16; 8-bit data: flagged -> b)
+  // (16-bit data: flagged -> b16; 8-bit data: flagged -> b, widened to 16-bit
+  // integers)
   if (valid == 0) return;
   for (int c = g; c < a.nchan; c += 32) {
     const bool any = a.chan_nflag[c] != 0;
@@ -554,17 +555,18 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
         for (int r = 0; r < valid; ++r) dst[r] = o[r];
       }
     } else if constexpr (DT == TP_U8) {
+      // 8-bit data: x~ (flagged -> b) widened to 16-bit integers
       const uint8_t* src = static_cast<const uint8_t*>(a.x) + (int64_t)c * a.pitch + tq;
       const unsigned b = (unsigned)a.bint[c];
-      uint8_t* dst = static_cast<uint8_t*>(yv) + (int64_t)c * ypitch + tq;
+      unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
+      unsigned h[4];
       if (valid == 4) {
         const unsigned u = __ldg(reinterpret_cast<const unsigned*>(src));
-        unsigned o = 0;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) o |= (fl[r] ? b : ((u >> (8 * r)) & 0xffu)) << (8 * r);
-        *reinterpret_cast<unsigned*>(dst) = o;
+        for (int r = 0; r < 4; ++r) h[r] = fl[r] ? b : ((u >> (8 * r)) & 0xffu);
+        *reinterpret_cast<uint2*>(dst) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
       } else {
-        for (int r = 0; r < valid; ++r) dst[r] = fl[r] ? (uint8_t)b : __ldg(src + r);
+        for (int r = 0; r < valid; ++r) dst[r] = (unsigned short)(fl[r] ? b : __ldg(src + r));
       }
     } else {
       unsigned short h[4];

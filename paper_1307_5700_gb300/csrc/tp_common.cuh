@@ -94,10 +94,11 @@ struct KernelShape {
   int S;      // consecutive outputs per lane (tile = 32 S samples)
   int OMAX;   // largest in-window offset the kernel handles
   int NCONS;  // consumer warps per CTA (DM groups per tile)
-  int EB;     // bytes per staged sample (4: FP32 y; 2: 16-bit x~)
-  int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads
+  int FMT;    // staged series: 4 = FP32 y, 2 = 16-bit float x~, 3 = 8-bit x~ as 16-bit integers
+  int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads;
+              // 2: DM pairs sharing one window
 };
-constexpr int kNumShapes = 24;
+constexpr int kNumShapes = 30;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
@@ -128,7 +129,7 @@ struct DetectArgs {
 
 // Dedispersion tiling constants (shared by the planner and the kernel).
 constexpr int kMinTileT = 256;      // smallest output tile any shape may use (sizes buffers)
-constexpr int kMaxTileT = 1408;     // largest output tile of any shape
+constexpr int kMaxTileT = 1472;     // largest output tile of any shape
 constexpr int kMaxOverhang = 512;   // max delay spread inside a CTA tile
 constexpr int kDetectT = 4096;      // samples per detection CTA
 
