@@ -390,8 +390,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "u8"],
-                    help="sample storage format (the metric's workload is f32)")
+    ap.add_argument("--dtype", default=None, choices=["f32", "f16", "bf16", "u8"],
+                    help="sample storage format (default: f32 for the metric's stream workload, binary16 for "
+                         "batch8)")
     ap.add_argument("--workload", default="stream", choices=["stream", "batch8", "serve32"],
                     help="stream: the metric's 1-beam streaming workload; batch8: 8 uneven beams batched; "
                          "serve32: the serving loop")
@@ -399,6 +400,8 @@ def main():
     ap.add_argument("--blocks-per-stream", type=int, default=4, help="serve32: blocks per stream")
     ap.add_argument("--hbm-gb", type=float, default=48.0, help="serve32: engine HBM budget")
     args = ap.parse_args()
+    if args.dtype is None:
+        args.dtype = "f16" if args.workload == "batch8" else "f32"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch8":

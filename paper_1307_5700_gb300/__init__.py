@@ -361,7 +361,7 @@ def tp_engine_launches(e):
 def tp_plan_shapes(p):
     """(current shape, feasible flags per shape)."""
     sh = ctypes.c_int()
-    feas = np.zeros(32, np.int32)
+    feas = np.zeros(64, np.int32)
     n = _check(lib().tp_plan_shapes(p, ctypes.byref(sh), feas.ctypes.data, len(feas)))
     return sh.value, feas[:n].astype(bool)
 
@@ -373,7 +373,7 @@ def tp_plan_set_shape(p, shape):
 def tp_autotune(e, beam, reps=3):
     """(best shape, ms per launch for every shape; -1 where infeasible)."""
     best = ctypes.c_int()
-    ms = np.zeros(32, np.float32)
+    ms = np.full(64, -1.0, np.float32)
     _check(lib().tp_autotune(e, beam, int(reps), ctypes.byref(best), ms.ctypes.data, len(ms)))
     return best.value, ms
 

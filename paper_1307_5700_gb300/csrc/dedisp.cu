@@ -126,7 +126,10 @@ struct Shape {
   static constexpr int TT = 32 * S;                                           // outputs per tile
   static constexpr int L = (S + OMAX + 1 + QS - 1) / QS * QS;                 // window samples
   static constexpr int LR = L * EB / 4;                                       // window registers
-  static constexpr int ROW = (TT + kMaxOverhang + OMAX + 2 * QS + 63) / 64 * 64;  // staged samples
+  // largest in-row offset of a warp's last trial past its first (ALGO 3: three
+  // steps of at most OMAX + 1)
+  static constexpr int OSPAN = ALGO == 3 ? 3 * (OMAX + 1) : OMAX;
+  static constexpr int ROW = (TT + kMaxOverhang + OSPAN + 2 * QS + 63) / 64 * 64;  // staged samples
   static constexpr int ROWB = ROW * EB;
   static constexpr int THREADS = (NCONS + 1) * 32;                            // + one producer warp
   static constexpr int STAGES = MODE == kModeU8 ? kStagesU8 : kStages;
@@ -142,6 +145,7 @@ struct Shape {
   // units apart, direct 32-bit loads (ALGO 1) an odd number of words apart
   static_assert(ALGO >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
   static_assert(ALGO != 2 || (MODE != kModeU8 && K == 2), "DM-pair windows: float data, two trials per warp");
+  static_assert(ALGO != 3 || (MODE == kModeF32 && K == 4), "DM-quad windows: FP32 data, four trials per warp");
   static_assert(ALGO == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
   static_assert(MODE != kModeU8 || ALGO == 1, "8-bit data use direct loads");
 };
@@ -264,7 +268,35 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
         const int dw = del[ci * 32 + g0];
         const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
         const int aw = (int)(t0 + dw - base);
-        if constexpr (ALGO >= 1) {
+        if constexpr (ALGO == 3) {
+          // four trials sharing one window: the steps e_j = o_j - o_{j-1}
+          // between consecutive trials are m or m + 1 (the planner checks
+          // this); block index m * 8 + bits.  Trials past the tile's last DM
+          // take step m; their sums are never stored.
+          int o[4], nreal = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const bool real = g0 + j <= last;
+            o[j] = real ? del[ci * 32 + g0 + j] - dw : 0;
+            nreal += real ? 1 : 0;
+          }
+          int m = 1 << 30;
+#pragma unroll
+          for (int j = 1; j < 4; ++j)
+            if (j < nreal) m = min(m, o[j] - o[j - 1]);
+          if (nreal < 2) m = 0;
+          m = m < 0 ? 0 : (m > OMAX ? OMAX : m);
+          int bits = 0;
+#pragma unroll
+          for (int j = 1; j < 4; ++j) {
+            // out-of-pattern steps are clamped so the branch stays inside its
+            // table whatever the delays hold
+            const int e = j < nreal ? o[j] - o[j - 1] - m : 0;
+            bits |= (e > 0 ? 1 : 0) << (j - 1);
+          }
+          sinfo[(buf * kNC + ci) * NCONS + w] = make_int4((buf * kNC + ci) * ROWB + aw * EB, m * 8 + bits, 0, 0);
+          continue;
+        } else if constexpr (ALGO >= 1) {
           // sample offset, in the staged row, of each DM's first output of lane 0
           int o[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -422,6 +454,16 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
           else
             add_pair16<S, OMAX, MODE == kModeBF16 ? 1 : 0>((o0 & 1) * (OMAX + 1) + d,
                                                            sbase + (unsigned)(inf.x + (o0 & ~1) * 2), acc[0], acc[1]);
+        }
+      }
+    } else if (live && ALGO == 3) {
+      if constexpr (ALGO == 3) {
+        // one window per channel for the warp's four trials, at the first
+        // trial's offset
+        const unsigned sbase = smem_u32(srow) + (unsigned)(lane * S * EB);
+        for (int ci = 0; ci < nc; ++ci) {
+          const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
+          add_quad<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc);
         }
       }
     } else if (live && ALGO == 1) {
@@ -590,7 +632,9 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
 // bfloat16 data), 3 8-bit x~ widened to 16-bit integers.
 // ALGO 0: register window + jump-table shifted adds (reuse across the K DMs);
 // ALGO 1: direct shared loads per DM (no offset bound, OMAX unused);
-// ALGO 2: DM pairs sharing one window, second trial's extra delay <= OMAX.
+// ALGO 2: DM pairs sharing one window, second trial's extra delay <= OMAX;
+// ALGO 3: DM quads sharing one window, steps between consecutive trials m or
+// m + 1 with m <= OMAX.
 // MINB: CTAs per SM the register allocation is sized for.
 #define TP_SHAPES(X)                 \
   X(0, 4, 20, 36, 8, 4, 0, 1)        \
@@ -622,7 +666,10 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
   X(26, 2, 21, 15, 8, 4, 2, 2)       \
   X(27, 2, 29, 11, 15, 4, 2, 1)      \
   X(28, 2, 26, 11, 15, 2, 2, 1)      \
-  X(29, 2, 22, 11, 8, 2, 2, 2)
+  X(29, 2, 22, 11, 8, 2, 2, 2)        \
+  X(30, 4, 25, 9, 8, 4, 3, 1)        \
+  X(31, 4, 31, 9, 8, 4, 3, 1)        \
+  X(32, 4, 23, 9, 8, 4, 3, 1)
 
 #define TP_SHAPE_ENTRY(i, K, S, O, N, F, A, M) {K, S, O, N, F, A},
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};

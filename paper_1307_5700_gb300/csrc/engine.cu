@@ -290,6 +290,21 @@ bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype
       for (int c = 0; c < nchan; ++c)
         if (b[c] < a[c] || b[c] - a[c] > kShapes[sh].OMAX) return false;
     }
+  if (kShapes[sh].ALGO == 3)
+    // quads (4i .. 4i + 3): in every channel the steps between consecutive
+    // trials of a quad are m or m + 1 for one m in 0 .. OMAX
+    for (int d0 = 0; d0 + 1 < ndm; d0 += K) {
+      const int d1 = std::min(d0 + K, ndm) - 1;
+      for (int c = 0; c < nchan; ++c) {
+        int lo = 1 << 30, hi = -1;
+        for (int d = d0 + 1; d <= d1; ++d) {
+          const int e = delay[(size_t)d * nchan + c] - delay[(size_t)(d - 1) * nchan + c];
+          lo = std::min(lo, e);
+          hi = std::max(hi, e);
+        }
+        if (lo < 0 || hi - lo > 1 || lo > kShapes[sh].OMAX) return false;
+      }
+    }
   if (kShapes[sh].ALGO == 0)
     for (int d0 = 0; d0 < ndm; d0 += K) {
       const int d1 = std::min(d0 + K, ndm) - 1;

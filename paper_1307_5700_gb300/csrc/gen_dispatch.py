@@ -168,6 +168,59 @@ def emit_pair16(S, OMAX, kind):
     return "\n".join(lines)
 
 
+# (S, MMAX) of the FP32 DM-quad shapes (ALGO 3): S odd (lanes start an odd
+# number of words apart), consecutive-trial delay steps m or m + 1, m <= MMAX.
+QUADS = [(25, 9), (31, 9), (23, 9)]
+
+
+def quad_steps(b):
+    """Block index b = m * 8 + bits -> offsets (0, o1, o2, o3) of the four
+    trials: o_j - o_{j-1} = m + bit j-1 of `bits`."""
+    m, bits = b // 8, b % 8
+    o = [0]
+    for j in range(3):
+        o.append(o[-1] + m + ((bits >> j) & 1))
+    return o
+
+
+def emit_quad(S, MMAX):
+    """Four consecutive DM trials sharing one window: loads the S + o3 staged
+    samples from lane 0's offset for the first trial (plus the lane's own
+    offset, folded into the address) and adds a_j[s] += w[s + o_j].  One
+    indexed branch per call; the window is loaded in order and each sample is
+    added into every trial that uses it, so only a few window registers are
+    live at a time."""
+    nb = 8 * (MMAX + 1)
+    lines = []
+    lines.append(f"template <>\n__device__ __forceinline__ void add_quad<{S}, {MMAX}>(int b, unsigned addr, float (&a)[4][{S}]) {{")
+    body = ["{"]
+    body.append(f".reg .f32 w<{S + 3 * (MMAX + 1)}>;")
+    body.append("tbl: .branchtargets " + ", ".join(f"C{b}" for b in range(nb)) + ";")
+    ia = 4 * S
+    idx = 4 * S + 1
+    body.append(f"brx.idx.uni %{idx}, tbl;")
+    for b in range(nb):
+        o = quad_steps(b)
+        body.append(f"C{b}:")
+        for k in range(S + o[3]):
+            body.append(f"ld.shared.f32 w{k}, [%{ia}+{4 * k}];")
+            for j in range(4):
+                s_ = k - o[j]
+                if 0 <= s_ < S:
+                    r = j * S + s_
+                    body.append(f"add.f32 %{r}, %{r}, w{k};")
+        if b != nb - 1:
+            body.append("bra.uni CEND;")
+    body.append("CEND:")
+    body.append("}")
+    asm = "\\n\"\n      \"".join(body)
+    outs = ", ".join(f'"+f"(a[{j}][{s_}])' for j in range(4) for s_ in range(S))
+    ins = f'"r"(addr), "r"(b)'
+    lines.append(f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins}\n      : "memory");')
+    lines.append("}\n")
+    return "\n".join(lines)
+
+
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
     out = [
@@ -184,6 +237,12 @@ def main():
         "// two consecutive DM trials from one window of staged FP32 samples",
         "template <int S, int OMAX>",
         "__device__ __forceinline__ void add_pair(int d, unsigned addr, float (&a0)[S], float (&a1)[S]);",
+        "",
+        "// four consecutive DM trials from one window of staged FP32 samples;",
+        "// block index = m * 8 + bits (trial j's offset exceeds trial j - 1's by",
+        "// m + bit j - 1)",
+        "template <int S, int MMAX>",
+        "__device__ __forceinline__ void add_quad(int b, unsigned addr, float (&a)[4][S]);",
         "",
         "// the same for 16-bit samples (kind 0 = binary16, 1 = bfloat16), block",
         "// index = first trial's half-word offset r * (OMAX + 1) + d",
@@ -205,6 +264,8 @@ def main():
     for S, OMAX in PAIRS16:
         for kind in (0, 1):
             out.append(emit_pair16(S, OMAX, kind))
+    for S, MMAX in QUADS:
+        out.append(emit_quad(S, MMAX))
     out.append("}  // namespace tp")
     with open(os.path.join(here, "dispatch_gen.cuh"), "w") as f:
         f.write("\n".join(out) + "\n")

@@ -96,9 +96,9 @@ struct KernelShape {
   int NCONS;  // consumer warps per CTA (DM groups per tile)
   int FMT;    // staged series: 4 = FP32 y, 2 = 16-bit float x~, 3 = 8-bit x~ as 16-bit integers
   int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads;
-              // 2: DM pairs sharing one window
+              // 2: DM pairs sharing one window; 3: DM quads sharing one window
 };
-constexpr int kNumShapes = 30;
+constexpr int kNumShapes = 33;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 

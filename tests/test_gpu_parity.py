@@ -215,6 +215,46 @@ def test_ragged_shapes(dtype):
     check_block(g, o, x, dtype, od, rfi, 3.5)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16", "u8"])
+def test_every_shape_elementwise(dtype):
+    """Every kernel shape the plan admits, element by element against the
+    oracle: 256 channels over 398-418 MHz, 62 DM trials of step 0.2 (the last
+    group of four trials is incomplete), a window that is not a multiple of
+    any tile and spans several DM tiles and time tiles."""
+    nchan, nsamp = 256, 7777
+    dms = np.arange(62) * 0.2
+    f_lo, bw, ts = 398.0, 20.0, 51.2e-6
+    od, dmax = O.delay_table(nchan, f_lo, bw, ts, dms)
+    xf = synth.noise(nchan, nsamp, 7101, mean=128.0 if dtype == "u8" else 0.0, std=16.0 if dtype == "u8" else 1.0)
+    synth.add_pulse(xf, od[40].astype(np.float64) + 2500, 20.0, 160.0 if dtype == "u8" else 10.0 / 16)
+    xf[17, 3000:3400] += 200.0 if dtype == "u8" else 12.0
+    x = {"f32": lambda a: a, "u8": synth.to_u8, "f16": synth.to_f16, "bf16": synth.to_bf16_bits}[dtype](xf)
+    rfi = O.RfiParams()
+    o = O.search_block(x, dtype, od, dmax, rfi=rfi)
+    g = GpuBeam(nchan, f_lo, bw, ts, dms, dtype, rfi=rfi)
+    try:
+        g.open(nsamp)
+        first = g.run(x)
+        _, feasible = tp.tp_plan_shapes(g.plan)
+        shapes = [int(s) for s in np.nonzero(feasible)[0]]
+        assert len(shapes) >= 2
+        for sh in shapes:
+            tp.tp_plan_set_shape(g.plan, sh)
+            tp.tp_beam_rewind(g.e, g.beam)
+            tp.tp_dedisperse(g.e, g.beam)
+            tp.tp_detect(g.e, g.beam)
+            cands, n, rc = tp.tp_get_candidates(g.e, g.beam, g.cap)
+            r = dict(first, candidates=cands, n_candidates=n, rc=rc,
+                     D=tp.tp_get_series(g.e, g.beam, ndm=len(dms), is_int=dtype == "u8"))
+            r["row_mu"], r["row_sigma"] = tp.tp_get_series_stats(g.e, g.beam, len(dms))
+            try:
+                check_block(r, o, x, dtype, od, rfi, 5.0)
+            except AssertionError as exc:
+                raise AssertionError(f"shape {sh}: {exc}") from exc
+    finally:
+        g.close()
+
+
 def test_degenerate_dm0_single_channel():
     for nchan, dms in [(1, np.array([0.0])), (64, np.array([0.0])), (3, np.array([0.0, 0.0, 1.0]))]:
         x = synth.noise(nchan, 1500, 8001 + nchan)
