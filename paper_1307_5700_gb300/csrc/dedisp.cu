@@ -132,22 +132,26 @@ struct Shape {
   static constexpr int ROW = (TT + kMaxOverhang + OSPAN + 2 * QS + 63) / 64 * 64;  // staged samples
   static constexpr int ROWB = ROW * EB;
   static constexpr int THREADS = (NCONS + 1) * 32;                            // + one producer warp
-  static constexpr int STAGES = MODE == kModeU8 ? kStagesU8 : kStages;
+  static constexpr int DW = NCONS * K <= 32 ? 32 : 64;                        // delays staged per channel
+  static constexpr int STAGES = MODE == kModeU8 && ALGO == 1 ? kStagesU8 : kStages;
   static constexpr size_t data_bytes = (size_t)STAGES * kNC * ROWB;
-  static constexpr size_t del_bytes = sizeof(int) * kDelRing * kNC * 32;
+  static constexpr size_t del_bytes = sizeof(int) * kDelRing * kNC * DW;
   // 8-bit mode: per (stage, consumer warp) K int4 of word offsets (one per
   // channel of the stage) and one int4 of byte shifts; else one int4 per
   // (stage, channel, consumer warp)
-  static constexpr size_t info_bytes =
-      MODE == kModeU8 ? sizeof(int4) * STAGES * NCONS * (K + 1) : sizeof(int4) * STAGES * kNC * NCONS;
-  static constexpr size_t smem = data_bytes + del_bytes + info_bytes + 16 * STAGES;
+  static constexpr size_t info_bytes = MODE == kModeU8 && ALGO == 1 ? sizeof(int4) * STAGES * NCONS * (K + 1)
+                                                                     : sizeof(int4) * STAGES * kNC * NCONS;
+  // 8-bit DM quads: the 32-bit sums of every consumer thread, [warp][K S][32]
+  static constexpr size_t fold_bytes = MODE == kModeU8 && ALGO == 3 ? sizeof(int) * NCONS * K * S * 32 : 0;
+  static constexpr size_t smem = data_bytes + del_bytes + info_bytes + fold_bytes + 16 * STAGES;
+  static_assert(smem <= 227 * 1024, "shared memory per CTA");
   // no bank conflicts: register windows (ALGO 0) start an odd number of 16-byte
   // units apart, direct 32-bit loads (ALGO 1) an odd number of words apart
   static_assert(ALGO >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
   static_assert(ALGO != 2 || (MODE != kModeU8 && K == 2), "DM-pair windows: float data, two trials per warp");
-  static_assert(ALGO != 3 || (MODE == kModeF32 && K == 4), "DM-quad windows: FP32 data, four trials per warp");
+  static_assert(ALGO != 3 || K == 4, "DM-quad windows: four trials per warp");
   static_assert(ALGO == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
-  static_assert(MODE != kModeU8 || ALGO == 1, "8-bit data use direct loads");
+  static_assert(MODE != kModeU8 || ALGO == 1 || ALGO == 3, "8-bit data: direct loads or DM quads");
 };
 
 // Per (stage, channel, consumer warp) the producer writes an int4:
@@ -174,14 +178,17 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   const int local = (int)blockIdx.x - ba.cta_start[bi];
   constexpr int TT = Sh::TT, LR = Sh::LR, ROWB = Sh::ROWB, EB = Sh::EB, QS = Sh::QS;
   static_assert(MODE != kModeU8 || K <= 4, "8-bit shifts of a warp's DMs are packed in one int4");
-  static_assert(NCONS * K <= 32, "a producer lane holds one DM of the tile");
+  static_assert(NCONS * K <= 64, "a producer lane holds at most two DMs of the tile");
   static_assert(OMAX < 256, "offsets are packed in bytes");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int STAGES = Sh::STAGES;
   unsigned char* srow = smem_raw;                                                     // [STAGES][kNC][ROWB]
-  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);                       // [kDelRing][kNC][32]
+  constexpr int DW = Sh::DW;
+  int* sdel = reinterpret_cast<int*>(smem_raw + Sh::data_bytes);                       // [kDelRing][kNC][DW]
   int4* sinfo = reinterpret_cast<int4*>(smem_raw + Sh::data_bytes + Sh::del_bytes);      // [STAGES][kNC][NCONS]
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes);
+  int* sfold = reinterpret_cast<int*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes +
+                                               Sh::fold_bytes);
   uint64_t* empty = full + STAGES;
 
   const int tile = local % a.ntiles;
@@ -206,16 +213,20 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 
   if (warp == NCONS) {
     // ---------------------------------------------------------------- producer
-    // delays: lane j < nd copies delayT[c][d0 + j] for the kNC channels of a
-    // stage into a ring of kDelRing stages, kDelRing - 1 stages ahead of use
+    // delays: lane l copies delayT[c][d0 + j] for j = l, l + 32 < nd and
+    // the kNC channels of a stage into a ring of kDelRing stages,
+    // kDelRing - 1 stages ahead of use
     const int32_t* __restrict__ dT = a.delayT;
     auto prefetch = [&](int st) {
-      int* slot = sdel + (st % kDelRing) * kNC * 32;
+      int* slot = sdel + (st % kDelRing) * kNC * DW;
 #pragma unroll
       for (int ci = 0; ci < kNC; ++ci) {
         const int c = st * kNC + ci;
-        const bool v = st < nstage && c < nchan && lane < dt.nd;
-        cp_async4(slot + ci * 32 + lane, v ? dT + (int64_t)c * a.dtpitch + dt.d0 + lane : dT, v);
+#pragma unroll
+        for (int h = 0; h < DW; h += 32) {
+          const bool v = st < nstage && c < nchan && lane + h < dt.nd;
+          cp_async4(slot + ci * DW + h + lane, v ? dT + (int64_t)c * a.dtpitch + dt.d0 + h + lane : dT, v);
+        }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
@@ -237,21 +248,21 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
           break;
         }
       }
-      const int* del = sdel + (i % kDelRing) * kNC * 32;
-      if constexpr (MODE == kModeU8) {
+      const int* del = sdel + (i % kDelRing) * kNC * DW;
+      if constexpr (MODE == kModeU8 && ALGO == 1) {
         // per (channel, consumer warp, DM of its group): byte offset in the
         // stage's rows of the word holding lane 0's first sample, and that
         // sample's shift inside the word (0 or 16 bits)
         // (lane g = w K + j handles DM g of the tile for every channel)
-        if (lane < NCONS * K) {
-          const int w = lane / K, j = lane % K;
-          const int jj = lane < last ? lane : last;
+        for (int g = lane; g < NCONS * K; g += 32) {
+          const int w = g / K, j = g % K;
+          const int jj = g < last ? g : last;
           int off[kNC];
           unsigned shifts = 0;
 #pragma unroll
           for (int ci = 0; ci < kNC; ++ci) {
-            const int lo = del[ci * 32];
-            const int o = del[ci * 32 + jj] - lo + ((t0m + lo) & (QS - 1));  // t0 + delay - row start
+            const int lo = del[ci * DW];
+            const int o = del[ci * DW + jj] - lo + ((t0m + lo) & (QS - 1));  // t0 + delay - row start
             off[ci] = (buf * kNC + ci) * ROWB + (o & ~1) * EB;
             shifts |= (unsigned)((o & 1) * 16) << (8 * ci);
           }
@@ -261,11 +272,11 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
         }
       }
       // window geometry of every (channel, consumer warp) pair of the stage
-      for (int p = lane; MODE != kModeU8 && p < kNC * NCONS; p += 32) {
+      for (int p = lane; (MODE != kModeU8 || ALGO == 3) && p < kNC * NCONS; p += 32) {
         const int ci = p / NCONS, w = p % NCONS;
         const int g0 = w * K < last ? w * K : last;
-        const int lo = del[ci * 32];
-        const int dw = del[ci * 32 + g0];
+        const int lo = del[ci * DW];
+        const int dw = del[ci * DW + g0];
         const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
         const int aw = (int)(t0 + dw - base);
         if constexpr (ALGO == 3) {
@@ -277,7 +288,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const bool real = g0 + j <= last;
-            o[j] = real ? del[ci * 32 + g0 + j] - dw : 0;
+            o[j] = real ? del[ci * DW + g0 + j] - dw : 0;
             nreal += real ? 1 : 0;
           }
           int m = 1 << 30;
@@ -294,7 +305,11 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
             const int e = j < nreal ? o[j] - o[j - 1] - m : 0;
             bits |= (e > 0 ? 1 : 0) << (j - 1);
           }
-          sinfo[(buf * kNC + ci) * NCONS + w] = make_int4((buf * kNC + ci) * ROWB + aw * EB, m * 8 + bits, 0, 0);
+          // 16-bit samples: the window starts on the word holding the first
+          // trial's first sample, r half-words before it
+          const int r = EB == 2 ? (aw & 1) : 0;
+          sinfo[(buf * kNC + ci) * NCONS + w] =
+              make_int4((buf * kNC + ci) * ROWB + (aw - r) * EB, (r * (OMAX + 1) + m) * 8 + bits, 0, 0);
           continue;
         } else if constexpr (ALGO >= 1) {
           // sample offset, in the staged row, of each DM's first output of lane 0
@@ -302,7 +317,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 #pragma unroll
           for (int j = 0; j < K; ++j) {
             const int jj = g0 + j <= last ? g0 + j : last;
-            o[j] = (int)(t0 + del[ci * 32 + jj] - base);
+            o[j] = (int)(t0 + del[ci * DW + jj] - base);
           }
           sinfo[(buf * kNC + ci) * NCONS + w] =
               make_int4((buf * kNC + ci) * ROWB, o[0] | (o[1] << 16), o[2] | (o[3] << 16), 0);
@@ -312,7 +327,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 #pragma unroll
         for (int j = 0; j < K; ++j) {
           const int jj = g0 + j <= last ? g0 + j : last;
-          int o = (aw & (QS - 1)) + del[ci * 32 + jj] - dw;
+          int o = (aw & (QS - 1)) + del[ci * DW + jj] - dw;
           // the planner bounds o by OMAX; the clamp keeps the indexed branch
           // inside its table whatever the delays hold
           o = o < 0 ? 0 : (o > OMAX ? OMAX : o);
@@ -327,7 +342,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       unsigned nb = 0;
       int64_t src = 0;
       if (lane < kNC && i * kNC + lane < nchan) {
-        const int lo = del[lane * 32], hi = del[lane * 32 + last];
+        const int lo = del[lane * DW], hi = del[lane * DW + last];
         const int head = (t0m + lo) & (QS - 1);  // row start = t0 + lo - head
         nb = (unsigned)(((TT + hi - lo + QS + head) * EB + 15) & ~15);
         src = ((int64_t)(i * kNC + lane) * a.ypitch + t0 + lo - head) * EB;
@@ -360,8 +375,27 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   // 8-bit mode: pk[j][m] holds outputs 2m, 2m + 1 of DM j as 16-bit lanes
   // (exact: no lane sum reaches 2^16 within kU8FoldStages stages), folded
   // into the 32-bit sums sum32 every kU8FoldStages stages
-  constexpr int PW = MODE == kModeU8 ? S / 2 : 1;
-  constexpr int S32 = MODE == kModeU8 ? S : 1;
+  constexpr bool U8D = MODE == kModeU8 && ALGO == 1;  // 8-bit direct loads
+  constexpr bool U8Q = MODE == kModeU8 && ALGO == 3;  // 8-bit DM quads
+  constexpr int PW = U8D ? S / 2 : 1;
+  constexpr int S32 = U8D ? S : 1;
+  // 8-bit DM quads: qe[j][i] holds outputs 2i, 2i + 1 of DM j, qf[j][i]
+  // outputs 2i - 1, 2i (16-bit lanes, low first), folded every kU8FoldStages
+  // stages into this thread's 32-bit sums in shared memory
+  constexpr int QH = U8Q ? S / 2 : 1;
+  unsigned qe[K][QH], qf[K][QH + 1];
+  int* myfold = sfold + (size_t)warp * K * S * 32 + lane;  // [j S + s][32]
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int q = 0; q < QH; ++q) qe[j][q] = 0u;
+#pragma unroll
+    for (int q = 0; q <= QH; ++q) qf[j][q] = 0u;
+  }
+  if constexpr (U8Q) {
+#pragma unroll
+    for (int q = 0; q < K * S; ++q) myfold[q * 32] = 0;
+  }
   unsigned pk[K][PW];
   int sum32[K][S32];
 #pragma unroll
@@ -372,7 +406,21 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
     for (int s = 0; s < S32; ++s) sum32[j][s] = 0;
   }
   auto fold = [&]() {
-    if constexpr (MODE == kModeU8) {
+    if constexpr (U8Q) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+#pragma unroll
+        for (int q = 0; q < QH; ++q) {
+          myfold[(j * S + 2 * q) * 32] += (int)(qe[j][q] & 0xffffu) + (int)(qf[j][q] >> 16);
+          myfold[(j * S + 2 * q + 1) * 32] += (int)(qe[j][q] >> 16) + (int)(qf[j][q + 1] & 0xffffu);
+        }
+#pragma unroll
+        for (int q = 0; q < QH; ++q) qe[j][q] = 0u;
+#pragma unroll
+        for (int q = 0; q <= QH; ++q) qf[j][q] = 0u;
+      }
+    }
+    if constexpr (U8D) {
 #pragma unroll
       for (int j = 0; j < K; ++j)
 #pragma unroll
@@ -408,7 +456,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       return;
     }
     const int nc = nchan - i * kNC < kNC ? nchan - i * kNC : kNC;
-    if constexpr (MODE == kModeU8) {
+    if constexpr (U8D) {
       // direct loads of each DM's words (a half-word funnel shift for odd
       // offsets); two channels at a time so that each accumulator takes both
       // in one three-input add
@@ -436,7 +484,6 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
           }
         }
       }
-      if (i % kU8FoldStages == kU8FoldStages - 1) fold();
     } else if (live && ALGO == 2) {
       if constexpr (ALGO == 2) {
         // one window per channel for the warp's two trials: S + d samples
@@ -463,7 +510,12 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
         const unsigned sbase = smem_u32(srow) + (unsigned)(lane * S * EB);
         for (int ci = 0; ci < nc; ++ci) {
           const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
-          add_quad<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc);
+          if constexpr (MODE == kModeF32)
+            add_quad<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc);
+          else if constexpr (MODE == kModeU8)
+            add_quad8<S, OMAX>(inf.y, sbase + (unsigned)inf.x, qe, qf);
+          else
+            add_quad16<S, OMAX, MODE == kModeBF16 ? 1 : 0>(inf.y, sbase + (unsigned)inf.x, acc);
         }
       }
     } else if (live && ALGO == 1) {
@@ -524,6 +576,8 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[buf]);
+    if constexpr (MODE == kModeU8)
+      if (i % kU8FoldStages == kU8FoldStages - 1) fold();
   }
 
   // epilogue: 16-bit and 8-bit modes accumulated the stored samples x~;
@@ -549,7 +603,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       long long s1 = 0, s2 = 0;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const int v = (MODE == kModeU8 ? sum32[j][MODE == kModeU8 ? s : 0] : __float2int_rn(acc[j][s])) - bint;
+        const int v = (U8D ? sum32[j][U8D ? s : 0] : U8Q ? myfold[(j * S + s) * 32] : __float2int_rn(acc[j][s])) - bint;
         if (tl + s < a.nout) {
           Drow[tl + s] = v;
           s1 += v;
@@ -669,7 +723,16 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
   X(29, 2, 22, 11, 8, 2, 2, 2)        \
   X(30, 4, 25, 9, 8, 4, 3, 1)        \
   X(31, 4, 31, 9, 8, 4, 3, 1)        \
-  X(32, 4, 23, 9, 8, 4, 3, 1)
+  X(32, 4, 23, 9, 8, 4, 3, 1)        \
+  X(33, 4, 31, 9, 11, 4, 3, 1)       \
+  X(34, 4, 25, 9, 11, 4, 3, 1)       \
+  X(35, 4, 25, 9, 15, 4, 3, 1)       \
+  X(36, 4, 26, 9, 8, 2, 3, 1)        \
+  X(37, 4, 26, 9, 11, 2, 3, 1)       \
+  X(38, 4, 30, 9, 11, 2, 3, 1)       \
+  X(39, 4, 26, 16, 7, 3, 3, 1)       \
+  X(40, 4, 18, 16, 11, 3, 3, 1)      \
+  X(41, 4, 22, 16, 7, 3, 3, 1)
 
 #define TP_SHAPE_ENTRY(i, K, S, O, N, F, A, M) {K, S, O, N, F, A},
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};

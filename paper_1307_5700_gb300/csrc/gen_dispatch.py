@@ -221,6 +221,92 @@ def emit_quad(S, MMAX):
     return "\n".join(lines)
 
 
+# (S, MMAX) of the 16-bit float DM-quad shapes: S = 2 mod 4.
+QUADS16 = [(26, 9), (30, 9)]
+# (S, MMAX) of the 8-bit DM-quad shapes: S = 2 mod 4.
+QUADS8 = [(26, 16), (22, 16), (18, 16)]
+
+
+def _asm_fn(signature, body, outs, ins):
+    asm = "\\n\"\n      \"".join(body)
+    return (f"template <>\n__device__ __forceinline__ {signature} {{\n"
+            f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins}\n      : "memory");\n}}\n')
+
+
+def emit_quad16(S, MMAX, kind):
+    """16-bit float version of emit_quad: samples two per 32-bit word (low
+    half first); block index (r (MMAX + 1) + m) 8 + bits, r = the first
+    trial's half-word offset inside its first word."""
+    op = "add.rn.f32.f16" if kind == 0 else "add.rn.f32.bf16"
+    nwmax = (1 + 3 * (MMAX + 1) + S + 1) // 2
+    nb = 2 * 8 * (MMAX + 1)
+    body = ["{", f".reg .b32 w<{nwmax}>;", f".reg .b16 lo<{nwmax}>, hi<{nwmax}>;",
+            "tbl: .branchtargets " + ", ".join(f"C{b}" for b in range(nb)) + ";",
+            f"brx.idx.uni %{4 * S + 1}, tbl;"]
+    for b in range(nb):
+        r, mb = b // (8 * (MMAX + 1)), b % (8 * (MMAX + 1))
+        p = [r + o for o in quad_steps(mb)]
+        nw = (p[3] + S - 1) // 2 + 1
+        body.append(f"C{b}:")
+        for k in range(nw):
+            body.append(f"ld.shared.b32 w{k}, [%{4 * S}+{4 * k}];")
+            body.append(f"mov.b32 {{lo{k}, hi{k}}}, w{k};")
+            for h in (2 * k, 2 * k + 1):
+                for j in range(4):
+                    s_ = h - p[j]
+                    if 0 <= s_ < S:
+                        half = f"lo{k}" if h % 2 == 0 else f"hi{k}"
+                        body.append(f"{op} %{j * S + s_}, {half}, %{j * S + s_};")
+        if b != nb - 1:
+            body.append("bra.uni CEND;")
+    body += ["CEND:", "}"]
+    outs = ", ".join(f'"+f"(a[{j}][{s_}])' for j in range(4) for s_ in range(S))
+    return _asm_fn(f"void add_quad16<{S}, {MMAX}, {kind}>(int b, unsigned addr, float (&a)[4][{S}])", body, outs,
+                   '"r"(addr), "r"(b)')
+
+
+def emit_quad8(S, MMAX):
+    """8-bit samples staged as 16-bit integers, two per word.  Four trials
+    share one window; block index (r (MMAX + 1) + m) 8 + bits as in
+    emit_quad16.  Trial j's first sample sits p_j = r + o_j half-words into
+    the window.  Even p_j: word p_j / 2 + i holds its outputs (2i, 2i + 1)
+    and goes into e[j][i]; odd p_j: word (p_j - 1) / 2 + i holds its outputs
+    (2i - 1, 2i) and goes into f[j][i] (i = 0 .. S / 2; the outputs -1 and S
+    are never read).  Each add sums two 16-bit lanes; no lane carries into
+    the next while at most 256 channels are summed."""
+    H = S // 2
+    nb = 2 * 8 * (MMAX + 1)
+    nwmax = (1 + 3 * (MMAX + 1) + S + 1) // 2 + 1
+    ne = 4 * H
+    body = ["{", f".reg .b32 w<{nwmax}>;",
+            "tbl: .branchtargets " + ", ".join(f"C{b}" for b in range(nb)) + ";",
+            f"brx.idx.uni %{ne + 4 * (H + 1) + 1}, tbl;"]
+    ia = ne + 4 * (H + 1)
+    for b in range(nb):
+        r, mb = b // (8 * (MMAX + 1)), b % (8 * (MMAX + 1))
+        p = [r + o for o in quad_steps(mb)]
+        uses = {}
+        for j in range(4):
+            if p[j] % 2 == 0:
+                for i in range(H):
+                    uses.setdefault(p[j] // 2 + i, []).append(j * H + i)
+            else:
+                for i in range(H + 1):
+                    uses.setdefault((p[j] - 1) // 2 + i, []).append(ne + j * (H + 1) + i)
+        body.append(f"C{b}:")
+        for k in range(max(uses) + 1):
+            body.append(f"ld.shared.b32 w{k}, [%{ia}+{4 * k}];")
+            for op_ in uses.get(k, []):
+                body.append(f"add.u32 %{op_}, %{op_}, w{k};")
+        if b != nb - 1:
+            body.append("bra.uni CEND;")
+    body += ["CEND:", "}"]
+    outs = ", ".join([f'"+r"(e[{j}][{i}])' for j in range(4) for i in range(H)] +
+                     [f'"+r"(f[{j}][{i}])' for j in range(4) for i in range(H + 1)])
+    return _asm_fn(f"void add_quad8<{S}, {MMAX}>(int b, unsigned addr, unsigned (&e)[4][{H}], "
+                   f"unsigned (&f)[4][{H + 1}])", body, outs, '"r"(addr), "r"(b)')
+
+
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
     out = [
@@ -244,6 +330,18 @@ def main():
         "template <int S, int MMAX>",
         "__device__ __forceinline__ void add_quad(int b, unsigned addr, float (&a)[4][S]);",
         "",
+        "// four trials, 16-bit float samples (kind 0 = binary16, 1 = bfloat16);",
+        "// block index = (r * (MMAX + 1) + m) * 8 + bits, r = the first trial's",
+        "// half-word offset in its first word",
+        "template <int S, int MMAX, int KIND>",
+        "__device__ __forceinline__ void add_quad16(int b, unsigned addr, float (&a)[4][S]);",
+        "",
+        "// four trials, 8-bit samples widened to 16-bit integers: e holds output",
+        "// pairs (2i, 2i + 1), f output pairs (2i - 1, 2i), two 16-bit lanes a word",
+        "template <int S, int MMAX>",
+        "__device__ __forceinline__ void add_quad8(int b, unsigned addr, unsigned (&e)[4][S / 2],",
+        "                                          unsigned (&f)[4][S / 2 + 1]);",
+        "",
         "// the same for 16-bit samples (kind 0 = binary16, 1 = bfloat16), block",
         "// index = first trial's half-word offset r * (OMAX + 1) + d",
         "template <int S, int OMAX, int KIND>",
@@ -266,6 +364,11 @@ def main():
             out.append(emit_pair16(S, OMAX, kind))
     for S, MMAX in QUADS:
         out.append(emit_quad(S, MMAX))
+    for S, MMAX in QUADS16:
+        for kind in (0, 1):
+            out.append(emit_quad16(S, MMAX, kind))
+    for S, MMAX in QUADS8:
+        out.append(emit_quad8(S, MMAX))
     out.append("}  // namespace tp")
     with open(os.path.join(here, "dispatch_gen.cuh"), "w") as f:
         f.write("\n".join(out) + "\n")
