@@ -240,12 +240,11 @@ def run_batch8(args):
     for b, hb in zip(beams, dev_blocks):
         tp.tp_push_block(e, b, hb[0])
     tp.tp_run_ready(e, use_graph=False)
-    tuned = {}
-    for nd, b in zip(BATCH_DMS, beams):
-        if nd not in tuned:
-            tuned[nd] = tp.tp_autotune(e, b, reps=1)[0]
-    # the autotune overwrote those series: process the block again with the
-    # chosen shapes
+    # one kernel shape for the whole batch, tuned on the batched launch itself
+    best, shape_ms = tp.tp_autotune_batch(e, reps=1)
+    tuned = {str(nd): int(best) for nd in sorted(set(BATCH_DMS))}
+    # the autotune overwrote the series: process the block again with the
+    # chosen shape
     tp.tp_run_ready(e, use_graph=False)
     units_per_step = sum(BATCH_DMS) * BLOCK
 
@@ -287,7 +286,8 @@ def run_batch8(args):
             "vs_baseline": value / PAPER_DERIVED, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": f"batch: 8 beams x 1024 ch, DM trials {BATCH_DMS} step 0.2, {args.dtype}, "
                                    "2^17-sample blocks, graph-replayed batched launch",
-                       "kernel_shapes": {str(k): int(v) for k, v in tuned.items()}},
+                       "kernel_shapes": tuned,
+                       "autotune_ms": {str(i): round(float(v), 3) for i, v in enumerate(shape_ms) if v >= 0}},
             "realtime_beams": value / (len(DMS) / TSAMP),
             "adds_per_s": adds * args.steps * world / (ms / 1e3),
             "frac_of_fp32_add_peak": adds * args.steps / (ms / 1e3) / (152 * 128 * 2.070e9),

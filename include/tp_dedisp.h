@@ -256,6 +256,18 @@ int tp_plan_set_shape(tp_plan *p, int shape);
  * received a block. */
 int tp_autotune(tp_engine *e, int beam, int reps, int *best, float *ms, int n);
 
+/* Batch form of tp_autotune for the batched launch of tp_run_ready: for every
+ * shape feasible for all beams that have received a block, time `reps`
+ * launches of the dedispersion kernel over all of those beams at once (one
+ * launch, the layout tp_run_ready uses), select the fastest for every beam's
+ * plan, and return it in *best and the milliseconds per launch in ms[shape]
+ * (-1 where not timed; n entries).  A shape's speed on one beam does not
+ * predict its speed in a batch (instruction-cache behaviour differs with the
+ * number of CTAs in flight), hence a separate tuner.  The beams must share one
+ * sample format.  Blocks; the series are overwritten (run the batch again
+ * before detection).  TP_ENOTREADY if no beam has received a block. */
+int tp_autotune_batch(tp_engine *e, int reps, int *best, float *ms, int n);
+
 /* ---- tracing -------------------------------------------------------------------- */
 
 /* Enable (1) or disable (0) per-stage CUDA-event timing on every beam of the

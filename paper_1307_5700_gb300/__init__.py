@@ -48,7 +48,7 @@ EXPORTS = (
     "tp_version", "tp_plan_shapes", "tp_plan_set_shape", "tp_autotune", "tp_channel_stats_noalloc",
     "tp_run_ready", "tp_engine_stream", "tp_server_create", "tp_server_add_stream", "tp_server_submit",
     "tp_server_end_stream", "tp_server_run", "tp_server_results", "tp_server_candidates", "tp_server_destroy",
-    "tp_beam_rewind",
+    "tp_beam_rewind", "tp_autotune_batch",
 )
 
 
@@ -109,6 +109,7 @@ _SIGS = {
     "tp_plan_shapes": (_i, [_vp, _vp, _vp, _i]),
     "tp_plan_set_shape": (_i, [_vp, _i]),
     "tp_autotune": (_i, [_vp, _i, _i, _vp, _vp, _i]),
+    "tp_autotune_batch": (_i, [_vp, _i, _vp, _vp, _i]),
     "tp_channel_stats_noalloc": (_i, [_vp, _i, _i, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                      _vp]),
     "tp_run_ready": (_i, [_vp, _i, _vp]),
@@ -375,6 +376,14 @@ def tp_autotune(e, beam, reps=3):
     best = ctypes.c_int()
     ms = np.full(64, -1.0, np.float32)
     _check(lib().tp_autotune(e, beam, int(reps), ctypes.byref(best), ms.ctypes.data, len(ms)))
+    return best.value, ms
+
+
+def tp_autotune_batch(e, reps=2):
+    """(best shape, ms per batched launch for every shape; -1 where not timed)."""
+    best = ctypes.c_int()
+    ms = np.full(64, -1.0, np.float32)
+    _check(lib().tp_autotune_batch(e, int(reps), ctypes.byref(best), ms.ctypes.data, len(ms)))
     return best.value, ms
 
 

@@ -507,7 +507,10 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       if constexpr (ALGO == 3) {
         // one window per channel for the warp's four trials, at the first
         // trial's offset
+        // (one call site: the loop stays rolled so the jump table is emitted
+        // once)
         const unsigned sbase = smem_u32(srow) + (unsigned)(lane * S * EB);
+#pragma unroll 1
         for (int ci = 0; ci < nc; ++ci) {
           const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
           if constexpr (MODE == kModeF32)

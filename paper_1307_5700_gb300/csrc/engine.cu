@@ -48,13 +48,22 @@ size_t dtype_size(int dtype) {
   }
 }
 
-// bytes per sample of the staged series y (A4 output): FP32 y for FP32 data,
-// the stored samples x~ in their own 16-bit format, or 8-bit samples widened
-// to 16-bit integers
-int staged_bytes(int dtype) { return dtype == TP_F32 ? 4 : 2; }
+// bytes per sample of the staged series y (A4 output) in the format of kernel
+// shape format `fmt`: FP32 y (FP32 data, or 16-bit float data staged as
+// x~ - b in FP32), the stored samples x~ in their own 16-bit format, or 8-bit
+// samples widened to 16-bit integers
+int staged_bytes_fmt(int fmt) { return fmt == 4 ? 4 : 2; }
 
-// the kernel-shape staging format (KernelShape::FMT) a dtype needs
+// the kernel-shape staging formats (KernelShape::FMT) a dtype can use: its
+// own, and FP32 staging for 16-bit float data
 int staged_format(int dtype) { return dtype == TP_F32 ? 4 : (dtype == TP_U8 ? 3 : 2); }
+bool format_ok(int dtype, int fmt) {
+  return fmt == staged_format(dtype) || (fmt == 4 && (dtype == TP_F16 || dtype == TP_BF16));
+}
+
+// bytes per sample the staged series buffer is allocated with (room for
+// every format the dtype can use)
+int staged_bytes_alloc(int dtype) { return dtype == TP_U8 ? 2 : 4; }
 
 // Nearest value of a 16-bit storage format (ties to even), from the format's
 // definition; the same rule the statistics kernel applies on the device.
@@ -272,10 +281,17 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
 // consecutive trials spreads by at most OMAX - (16 / bytes per sample - 1)
 // samples in every channel; tiles pack up to NCONS consecutive groups
 // while the tile's delay spread stays within kMaxOverhang.
+// Kernel shapes in order of preference when no autotuning has run: DM quads,
+// then DM pairs, then direct loads, then register windows (the order of their
+// launch times on a 1024-channel, 640-trial, 2^17-sample block).
+constexpr int kShapePreference[kNumShapes] = {33, 34, 31, 30, 32, 35, 39, 41, 40, 27, 25, 26, 24, 28,
+                                              29, 22, 18, 19, 12, 13, 14, 15, 16, 17, 23, 21, 20, 8,
+                                              10, 1,  2,  5,  0,  3,  6,  4,  7,  9,  11, 36, 37, 38};
+
 bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype, int sh,
                 std::vector<DmTile>* tiles) {
-  if (kShapes[sh].FMT != staged_format(dtype)) return false;
-  const int EB = staged_bytes(dtype);
+  if (!format_ok(dtype, kShapes[sh].FMT)) return false;
+  const int EB = staged_bytes_fmt(kShapes[sh].FMT);
   // per-beam buffers (partial sums, staging padding) are sized for tiles of
   // kMinTileT..kMaxTileT outputs
   if (shape_tile_t(sh) < kMinTileT || shape_tile_t(sh) > kMaxTileT) return false;
@@ -381,7 +397,7 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->spec_bits, (size_t)((nmax + 31) / 32) * 4);
   add((void**)&b->spec_nflag, 4);
   add((void**)&b->spec_thr, 8);
-  const size_t yb = (size_t)staged_bytes(p->dtype);
+  const size_t yb = (size_t)staged_bytes_alloc(p->dtype);
   add((void**)&b->y, nc * (size_t)ypitch * yb);
   add((void**)&b->b16, nc * 2);
   add((void**)&b->bsum, 8);
@@ -493,6 +509,7 @@ RfiArgs rfi_args(const tp_plan* p, Beam* b) {
   a.spec_bits = b->spec_bits;
   a.spec_nflag = b->spec_nflag;
   a.spec_thr = b->spec_thr;
+  a.stage_f32 = (p->dtype == TP_F16 || p->dtype == TP_BF16) && kShapes[p->shape].FMT == 4;
   return a;
 }
 
@@ -882,7 +899,6 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
   for (int sh = 0; sh < kNumShapes; ++sh) {
     p->feasible[sh] = make_tiles(p->h_delay, ndm, nchan, dtype, sh, &p->shape_tiles[sh]);
     if (!p->feasible[sh]) continue;
-    if (p->shape < 0) p->shape = sh;
     const size_t bts = p->shape_tiles[sh].size() * sizeof(DmTile);
     if ((ce = cudaMalloc(&p->d_shape_tiles[sh], bts)) != cudaSuccess) return fail(cuda_error(ce, "cudaMalloc(tiles)"));
     if ((ce = cudaMemcpy(p->d_shape_tiles[sh], p->shape_tiles[sh].data(), bts, cudaMemcpyHostToDevice)) !=
@@ -890,6 +906,13 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
       return fail(cuda_error(ce, "copy tiles"));
     tb += bts;
   }
+  // default shape (until tp_autotune or tp_plan_set_shape): the first
+  // feasible one in an order of measured speed on the 1024-channel band
+  for (int sh : kShapePreference)
+    if (p->feasible[sh]) {
+      p->shape = sh;
+      break;
+    }
   if (p->shape < 0) return fail(set_error(TP_EINVAL, "no kernel shape fits this DM list"));
   p->h_tiles = p->shape_tiles[p->shape];
   p->d_tiles = p->d_shape_tiles[p->shape];
@@ -981,7 +1004,7 @@ int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capac
     b->allocs.push_back(ptr);
     *it.first = ptr;
   }
-  cudaError_t ce = cudaMemset(b->y, 0, (size_t)p->nchan * b->ypitch * (size_t)staged_bytes(p->dtype));
+  cudaError_t ce = cudaMemset(b->y, 0, (size_t)p->nchan * b->ypitch * (size_t)staged_bytes_alloc(p->dtype));
   if (ce == cudaSuccess) ce = cudaMemset(b->status, 0, 4);
   if (ce != cudaSuccess) {
     free_beam(b);
@@ -1408,6 +1431,80 @@ int tp_plan_set_shape(tp_plan* p, int shape) {
   p->shape = shape;
   p->h_tiles = p->shape_tiles[shape];
   p->d_tiles = p->d_shape_tiles[shape];
+  return TP_OK;
+}
+
+int tp_autotune_batch(tp_engine* e, int reps, int* best, float* ms, int n) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  std::vector<Beam*> bs;
+  for (Beam* b : e->beams)
+    if (b && b->nsamp_win > 0) bs.push_back(b);
+  if (bs.empty()) return set_error(TP_ENOTREADY, "no beam has received a block");
+  const size_t need = bs.size() * sizeof(DedispArgs) + 2 * sizeof(int) + bs.size() * sizeof(int) + 16;
+  if (need > kBatchBytes) return set_error(TP_EINVAL, "batch of %zu beams too large", bs.size());
+  // every earlier block of every beam is finished before the timing runs
+  for (Beam* b : bs) TP_CUDA_TRY(cudaStreamSynchronize(beam_stream(e, b)));
+  TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
+  cudaStream_t s = e->stream;
+  cudaEvent_t e0, e1;
+  TP_CUDA_TRY(cudaEventCreate(&e0));
+  TP_CUDA_TRY(cudaEventCreate(&e1));
+  reps = reps < 1 ? 1 : reps;
+  int bestsh = -1;
+  float bestms = 0.f;
+  std::vector<unsigned char> buf;
+  for (int sh = 0; sh < kNumShapes; ++sh) {
+    if (ms && sh < n) ms[sh] = -1.f;
+    bool ok = true;
+    for (Beam* b : bs) ok = ok && b->plan->feasible[sh];
+    if (!ok) continue;
+    // one launch over every beam with shape sh (bfloat16 beams take their own
+    // launch in tp_run_ready; the timing treats the whole set as one group)
+    std::vector<DedispArgs> args;
+    std::vector<int> cta{0};
+    for (Beam* b : bs) {
+      DedispArgs da = dedisp_args(b->plan, b);
+      da.shape = sh;
+      da.tiles = b->plan->d_shape_tiles[sh];
+      da.ntiles = (int)b->plan->shape_tiles[sh].size();
+      da.ntt = (int)((b->nout + shape_tile_t(sh) - 1) / shape_tile_t(sh));
+      if (da.ntt > b->ntt_max) ok = false;
+      args.push_back(da);
+      cta.push_back(cta.back() + da.ntiles * da.ntt);
+    }
+    if (!ok) continue;
+    buf.resize(args.size() * sizeof(DedispArgs) + cta.size() * sizeof(int));
+    std::memcpy(buf.data(), args.data(), args.size() * sizeof(DedispArgs));
+    std::memcpy(buf.data() + args.size() * sizeof(DedispArgs), cta.data(), cta.size() * sizeof(int));
+    TP_CUDA_TRY(cudaMemcpyAsync(e->d_batch, buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
+    BatchArgs ba{static_cast<const DedispArgs*>(e->d_batch),
+                 reinterpret_cast<const int*>(static_cast<unsigned char*>(e->d_batch) +
+                                              args.size() * sizeof(DedispArgs)),
+                 (int)args.size()};
+    const int dtype = bs[0]->plan->dtype;
+    TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s));  // warm-up
+    TP_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s));
+    TP_CUDA_TRY(cudaEventRecord(e1, s));
+    TP_CUDA_TRY(cudaEventSynchronize(e1));
+    e->launches += 1 + reps;
+    float t = 0.f;
+    TP_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+    t /= reps;
+    if (ms && sh < n) ms[sh] = t;
+    if (bestsh < 0 || t < bestms) bestsh = sh, bestms = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bestsh < 0) return set_error(TP_EINVAL, "no kernel shape is feasible for every beam");
+  for (Beam* b : bs) {
+    // the timing runs overwrote the series: each beam must be dedispersed again
+    if (b->state >= kDedispersed) b->state = kReady;
+    tp_plan_set_shape(const_cast<tp_plan*>(b->plan), bestsh);
+  }
+  if (best) *best = bestsh;
   return TP_OK;
 }
 

@@ -46,6 +46,18 @@ __device__ __forceinline__ float load_as_float<TP_BF16>(const void* x, int64_t i
   return __uint_as_float((unsigned)h << 16);
 }
 
+// value of 16-bit storage bits (exact in FP32)
+template <int DT>
+__device__ __forceinline__ float bits_to_float(unsigned short h) {
+  if constexpr (DT == TP_F16) {
+    float f;
+    asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
+    return f;
+  } else {
+    return __uint_as_float((unsigned)h << 16);
+  }
+}
+
 __device__ __forceinline__ unsigned load_u8(const void* x, int64_t i) {
   return __ldg(static_cast<const unsigned char*>(x) + i);
 }
@@ -582,6 +594,22 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) h[r] = fl[r] ? b : h[r];
+      }
+      if (a.stage_f32) {
+        // FP32 staging (for the FP32 kernel shapes): y = x~ - b, one rounding
+        // of the difference of two exactly converted stored values; flagged
+        // samples give exactly 0
+        const float bf = bits_to_float<DT>(a.b16[c]);
+        float o[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) o[r] = bits_to_float<DT>(h[r]) - bf;
+        float* dst = static_cast<float*>(yv) + (int64_t)c * ypitch + tq;
+        if (valid == 4) {
+          *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+          for (int r = 0; r < valid; ++r) dst[r] = o[r];
+        }
+        continue;
       }
       unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
       if (valid == 4) {

@@ -49,6 +49,7 @@ struct RfiArgs {
   uint32_t* spec_bits;    // [ceil(N_s/32)] spectrum flags
   int* spec_nflag;        // [1] flagged spectra
   double* spec_thr;       // [1] spectrum threshold (per-block constant)
+  int stage_f32;          // 16-bit data: stage y = x~ - b in FP32 (for the FP32 kernel shapes)
 };
 
 // A tile of consecutive DM trials processed by one dedispersion CTA.
@@ -94,7 +95,8 @@ struct KernelShape {
   int S;      // consecutive outputs per lane (tile = 32 S samples)
   int OMAX;   // largest in-window offset the kernel handles
   int NCONS;  // consumer warps per CTA (DM groups per tile)
-  int FMT;    // staged series: 4 = FP32 y, 2 = 16-bit float x~, 3 = 8-bit x~ as 16-bit integers
+  int FMT;    // staged series: 4 = FP32 y (FP32 data, or 16-bit float data staged as
+              // FP32 x~ - b), 2 = 16-bit float x~, 3 = 8-bit x~ as 16-bit integers
   int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads;
               // 2: DM pairs sharing one window; 3: DM quads sharing one window
 };

@@ -90,3 +90,45 @@ def test_batch_and_graph_equal_solo(dtype):
         _, mass = O.dedisperse_points(blocks[1][0], dtype, o["stats"], o["chunk_flag"], o["spec_flag"], 256,
                                       od, dd, tt)
         assert np.all(np.abs(D.astype(np.float64) - o["D"]).ravel() <= 1e-5 * mass)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_batch_autotune_keeps_results(dtype):
+    """tp_autotune_batch picks a shape every plan admits; the batch run with
+    it gives the solo series exactly (every shape adds each output's channels
+    in index order, FP32 or exact integers) and the same candidates."""
+    import torch
+    tp.build()
+    B = 6000
+    blocks = [_blocks(dtype, 300 * (i + 1), 1, B) for i in range(len(PLANS))]
+    solo = _run("solo", dtype, blocks, B)
+    stream = torch.cuda.Stream()
+    e = tp.tp_engine_create(0, 0, stream.cuda_stream)
+    try:
+        plans = [tp.tp_create_plan(e, NCHAN, F_LO, BW, TS, dms, dtype, None, 4.0) for dms in PLANS]
+        beams = [tp.tp_beam_open(e, p, B, 1 << 16) for p in plans]
+        for b, bl in zip(beams, blocks):
+            tp.tp_push_block(e, b, bl[0])
+        tp.tp_run_ready(e, use_graph=False)
+        best, ms = tp.tp_autotune_batch(e, reps=1)
+        for p in plans:
+            cur, feas = tp.tp_plan_shapes(p)
+            assert cur == best and feas[best]
+            assert ms[best] > 0 and all(ms[s] < 0 or ms[s] >= ms[best] for s in range(len(feas)))
+        assert tp.tp_run_ready(e, use_graph=True) == len(beams)
+        for i, (b, dms) in enumerate(zip(beams, PLANS)):
+            c, n, rc = tp.tp_get_candidates(e, b, 1 << 16)
+            D = tp.tp_get_series(e, b, ndm=len(dms), is_int=dtype == "u8")
+            assert np.array_equal(D, solo[0][i][1]), i
+            # the row statistics sum per-time-tile partials, whose grouping
+            # follows the shape's tile length: snr may differ in the last bits
+            ref = solo[0][i][0]
+            for f in ("beam", "dm_idx", "t_abs", "value"):
+                assert np.array_equal(c[f], ref[f]), (i, f)
+            np.testing.assert_allclose(c["snr"], ref["snr"], rtol=1e-6)
+        for b in beams:
+            tp.tp_beam_close(e, b)
+        for p in plans:
+            tp.tp_plan_destroy(p)
+    finally:
+        tp.tp_engine_destroy(e)
