@@ -1127,10 +1127,14 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
   // while the beam's previous batch may still run on the engine stream
   if (s != e->stream && b->pushed > 0) TP_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_detect, 0));
   prof_record(e, b, 0, s);
+  int nk = 0;  // copy kernels launched
   if (b->pushed == 0) {
     b->cur = 0;
-    TP_CUDA_TRY(cudaMemcpy2DAsync(b->win[0], dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
-                                  kind, s));
+    if (buf_is_device)
+      TP_CUDA_TRY(copy_rows(b->win[0], dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan, s, &nk));
+    else
+      TP_CUDA_TRY(cudaMemcpy2DAsync(b->win[0], dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
+                                    kind, s));
     b->nsamp_win = nsamp;
     b->nout = nsamp - dmax;
     b->t0_abs = 0;
@@ -1139,16 +1143,20 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
     char* dst = static_cast<char*>(b->win[nxt]);
     if (dmax > 0) {
       const char* src = static_cast<const char*>(b->win[b->cur]) + (size_t)(b->nsamp_win - dmax) * es;
-      TP_CUDA_TRY(cudaMemcpy2DAsync(dst, dpitch, src, dpitch, (size_t)dmax * es, p->nchan,
-                                    cudaMemcpyDeviceToDevice, s));
+      TP_CUDA_TRY(copy_rows(dst, dpitch, src, dpitch, (size_t)dmax * es, p->nchan, s, &nk));
     }
-    TP_CUDA_TRY(cudaMemcpy2DAsync(dst + (size_t)dmax * es, dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es,
-                                  p->nchan, kind, s));
+    if (buf_is_device)
+      TP_CUDA_TRY(copy_rows(dst + (size_t)dmax * es, dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
+                            s, &nk));
+    else
+      TP_CUDA_TRY(cudaMemcpy2DAsync(dst + (size_t)dmax * es, dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es,
+                                    p->nchan, kind, s));
     b->cur = nxt;
     b->nsamp_win = dmax + nsamp;
     b->nout = nsamp;
     b->t0_abs = b->pushed - dmax;
   }
+  e->launches += (uint64_t)nk;
   TP_CUDA_TRY(cudaMemcpyAsync(b->d_t0, &b->t0_abs, 8, cudaMemcpyHostToDevice, s));
   TP_CUDA_TRY(cudaEventRecord(b->ev_pushed, s));
   prof_record(e, b, 1, s);

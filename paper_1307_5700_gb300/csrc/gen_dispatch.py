@@ -216,7 +216,7 @@ def emit_quad(S, MMAX):
     asm = "\\n\"\n      \"".join(body)
     outs = ", ".join(f'"+f"(a[{j}][{s_}])' for j in range(4) for s_ in range(S))
     ins = f'"r"(addr), "r"(b)'
-    lines.append(f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins});')
+    lines.append(f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins}\n      : "memory");')
     lines.append("}\n")
     return "\n".join(lines)
 
@@ -227,14 +227,10 @@ QUADS16 = [(26, 9), (30, 9)]
 QUADS8 = [(26, 16), (22, 16), (18, 16)]
 
 
-# The DM-quad blocks read shared memory without a "memory" clobber: every
-# ordering they need (after the stage's "full" barrier wait, before its
-# "empty" arrive) comes from those volatile mbarrier statements, and leaving
-# the clobber out lets the compiler schedule the surrounding loads freely.
 def _asm_fn(signature, body, outs, ins):
     asm = "\\n\"\n      \"".join(body)
     return (f"template <>\n__device__ __forceinline__ {signature} {{\n"
-            f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins});\n}}\n')
+            f'  asm volatile(\n      "{asm}\\n"\n      : {outs}\n      : {ins}\n      : "memory");\n}}\n')
 
 
 def emit_quad16(S, MMAX, kind):

@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "tp_common.cuh"
 
@@ -26,6 +27,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kChunkBatch = 4;  // W_c = 256 chunks summed per warp and iteration
 
 template <int DT>
 __device__ __forceinline__ float load_as_float(const void* x, int64_t i);
@@ -159,7 +161,46 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
   const bool vec = (a.W % 128) == 0;
 
   double tot_s = 0.0, tot_q = 0.0;  // lane-0 accumulators of this warp
-  for (int k = warp; k < a.nchunk; k += kWarps) {
+  // W = 256 (one sub-chunk per chunk): kChunkBatch full chunks per warp and
+  // iteration, every load issued before the sums (the same FP32 summation
+  // order per chunk as the general loop below); the rest (a short last
+  // chunk) falls through to the general loop
+  int kstart = warp;
+  if (vec && a.W == 256) {
+    const int nfull = (int)(a.nsamp / 256);
+    int k = warp;
+    for (; k + (kChunkBatch - 1) * kWarps < nfull; k += kChunkBatch * kWarps) {
+      float e[kChunkBatch][2][4];
+      bool ok[kChunkBatch][2][4];
+#pragma unroll
+      for (int u = 0; u < kChunkBatch; ++u) {
+        const int64_t lo = (int64_t)(k + u * kWarps) * 256;
+        load4<DT>(a.x, row + lo + 4 * lane, row + lo + 256, p, e[u][0], ok[u][0]);
+        load4<DT>(a.x, row + lo + 128 + 4 * lane, row + lo + 256, p, e[u][1], ok[u][1]);
+      }
+#pragma unroll
+      for (int u = 0; u < kChunkBatch; ++u) {
+        float fs = 0.f, fq = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            fs += e[u][h][r];
+            fq += e[u][h][r] * e[u][h][r];
+          }
+        fs = warp_sum_f(fs);
+        fq = warp_sum_f(fq);
+        const double cs = 0.0 + (double)fs, cq = 0.0 + (double)fq;
+        if (lane == 0) {
+          chunk_sums[(int64_t)c * a.nchunk + k + u * kWarps] = make_double2(cs, cq);
+          tot_s += cs;
+          tot_q += cq;
+        }
+      }
+    }
+    kstart = k;
+  }
+  for (int k = kstart; k < a.nchunk; k += kWarps) {
     const int64_t lo = (int64_t)k * a.W;
     const int64_t hi = lo + a.W < a.nsamp ? lo + a.W : a.nsamp;
     double cs = 0.0, cq = 0.0;
@@ -472,20 +513,29 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
     if constexpr (!kU8) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       float part[4] = {0.f, 0.f, 0.f, 0.f};
-      int n = 0;
-      for (int c = g; c < a.nchan; c += 32) {
-        float v[4];
-        load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
-        const float mh = a.mu_hi[c], ml = a.mu_lo[c];
-        const bool any = a.chan_nflag[c] != 0;
-        const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
+      // channels g, g + 32, ... in groups of 8: the group's loads are issued
+      // together, its FP32 partial sums flushed to FP64 after the group
+      for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
+        float v[8][4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (r < valid && !(any && cf[kk[r]])) part[r] += (v[r] - mh) - ml;
-        if (++n == 8) {
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + 32 * u;
+          if (c < a.nchan) load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + 32 * u;
+          if (c >= a.nchan) break;
+          const float mh = a.mu_hi[c], ml = a.mu_lo[c];
+          const bool any = a.chan_nflag[c] != 0;
+          const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (r < valid && !(any && cf[kk[r]])) part[r] += (v[u][r] - mh) - ml;
+        }
+        if (c0 + 32 * 7 < a.nchan) {
 #pragma unroll
           for (int r = 0; r < 4; ++r) acc[r] += (double)part[r], part[r] = 0.f;
-          n = 0;
         }
       }
 #pragma unroll
@@ -547,6 +597,67 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   // (16-bit data: flagged -> b16; 8-bit data: flagged -> b, widened to 16-bit
   // integers)
   if (valid == 0) return;
+  if (valid == 4) {
+    // full 4-sample quads: raw loads of 4 channels (c, c + 32, c + 64,
+    // c + 96) issued together, then substitution and stores
+    using Raw = typename std::conditional<DT == TP_F32, float4,
+                                          typename std::conditional<DT == TP_U8, unsigned, uint2>::type>::type;
+    for (int c0 = g; c0 < a.nchan; c0 += 32 * 4) {
+      Raw raw[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u;
+        if (c < a.nchan) raw[u] = __ldg(reinterpret_cast<const Raw*>(static_cast<const char*>(a.x) +
+                                                                    ((int64_t)c * a.pitch + tq) * sizeof(Raw) / 4));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u;
+        if (c >= a.nchan) break;
+        const bool any = a.chan_nflag[c] != 0;
+        const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
+        bool fl[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) fl[r] = sflag[r] || (any && cf[kk[r]]);
+        if constexpr (DT == TP_F32) {
+          const float v[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
+          const float mh = a.mu_hi[c], ml = a.mu_lo[c];
+          float o[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - mh) - ml;
+          *reinterpret_cast<float4*>(static_cast<float*>(yv) + (int64_t)c * ypitch + tq) =
+              make_float4(o[0], o[1], o[2], o[3]);
+        } else if constexpr (DT == TP_U8) {
+          const unsigned b = (unsigned)a.bint[c];
+          unsigned h[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) h[r] = fl[r] ? b : ((raw[u] >> (8 * r)) & 0xffu);
+          *reinterpret_cast<uint2*>(static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq) =
+              make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+        } else {
+          const unsigned short b = a.b16[c];
+          unsigned short h[4] = {(unsigned short)(raw[u].x & 0xffff), (unsigned short)(raw[u].x >> 16),
+                                 (unsigned short)(raw[u].y & 0xffff), (unsigned short)(raw[u].y >> 16)};
+#pragma unroll
+          for (int r = 0; r < 4; ++r) h[r] = fl[r] ? b : h[r];
+          if (a.stage_f32) {
+            // FP32 staging (for the FP32 kernel shapes): y = x~ - b, one
+            // rounding of the difference of two exactly converted stored
+            // values; flagged samples give exactly 0
+            const float bf = bits_to_float<DT>(b);
+            *reinterpret_cast<float4*>(static_cast<float*>(yv) + (int64_t)c * ypitch + tq) =
+                make_float4(bits_to_float<DT>(h[0]) - bf, bits_to_float<DT>(h[1]) - bf,
+                            bits_to_float<DT>(h[2]) - bf, bits_to_float<DT>(h[3]) - bf);
+          } else {
+            *reinterpret_cast<uint2*>(static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq) =
+                make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16));
+          }
+        }
+      }
+    }
+    return;
+  }
+  // the window's last, partial quad
   for (int c = g; c < a.nchan; c += 32) {
     const bool any = a.chan_nflag[c] != 0;
     const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
@@ -622,7 +733,50 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   }
 }
 
+// Pitched row copy in 16-byte units: CTA (x, y) copies kThreads kCopyUnroll
+// consecutive units of rows y, y + gridDim.y, ...; all loads of a thread are
+// issued before its stores.
+constexpr int kCopyUnroll = 4;
+
+__global__ void __launch_bounds__(kThreads) copy_rows_kernel(int4* __restrict__ dst, int64_t dpitch,
+                                                             const int4* __restrict__ src, int64_t spitch,
+                                                             int64_t row_units, int nrows) {
+  constexpr int64_t span = (int64_t)kThreads * kCopyUnroll;
+  for (int r = blockIdx.y; r < nrows; r += gridDim.y) {
+    const int4* s = src + (int64_t)r * spitch;
+    int4* d = dst + (int64_t)r * dpitch;
+    for (int64_t base = (int64_t)blockIdx.x * span + threadIdx.x; base < row_units; base += (int64_t)gridDim.x * span) {
+      int4 v[kCopyUnroll];
+#pragma unroll
+      for (int u = 0; u < kCopyUnroll; ++u) {
+        const int64_t i = base + (int64_t)u * kThreads;
+        if (i < row_units) v[u] = __ldcs(s + i);
+      }
+#pragma unroll
+      for (int u = 0; u < kCopyUnroll; ++u) {
+        const int64_t i = base + (int64_t)u * kThreads;
+        if (i < row_units) d[i] = v[u];
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int nrows,
+                      cudaStream_t s, int* kernels) {
+  if (nrows <= 0 || row_bytes == 0) return cudaSuccess;
+  const bool vec = ((uintptr_t)dst | (uintptr_t)src | dpitch | spitch | row_bytes) % 16 == 0;
+  if (!vec) return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row_bytes, nrows, cudaMemcpyDeviceToDevice, s);
+  const int64_t units = (int64_t)(row_bytes / 16);
+  const int64_t span = (int64_t)kThreads * kCopyUnroll;
+  const int64_t gx = (units + span - 1) / span;
+  const dim3 grid((unsigned)(gx < 1024 ? gx : 1024), (unsigned)(nrows < 65535 ? nrows : 65535));
+  copy_rows_kernel<<<grid, kThreads, 0, s>>>(static_cast<int4*>(dst), (int64_t)(dpitch / 16),
+                                             static_cast<const int4*>(src), (int64_t)(spitch / 16), units, nrows);
+  if (kernels) ++*kernels;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void* y, int64_t ypitch,
                        cudaStream_t s) {

@@ -144,6 +144,12 @@ double external_spectrum_threshold(const double* sigma, int nchan, double tau_s)
 cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s);
 cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s);
+// Device-to-device copy of nrows rows of row_bytes bytes (pitched); a
+// 16-byte vector kernel when every address, pitch and the row length are
+// multiples of 16 bytes, else cudaMemcpy2DAsync.
+// *kernels (may be NULL) is incremented when the kernel ran.
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int nrows,
+                      cudaStream_t s, int* kernels);
 
 size_t dtype_size(int dtype);
 
