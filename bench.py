@@ -43,7 +43,10 @@ PAPER_DERIVED = 6.5e7  # DM-trial.samples/s per GPU derived from the paper's Tab
 # DRAM bytes (read + write) of one dedispersion launch of this workload, from
 # the ncu capture summarised in profiles/dedisperse_kernel_stream1024_640dm_f32.md,
 # per kernel shape; a shape without a capture reports null.
-TRAFFIC_BY_SHAPE = {("f32", 12): 533.664e6 + 306.476e6}
+# DRAM bytes (read + write) of one dedispersion launch of this workload, per
+# (sample format, kernel shape), from an ncu capture of the timed launch
+# (profiles/dedisperse_kernel_dm_quads_stream1024_640dm_f32.md)
+TRAFFIC_BY_SHAPE = {("f32", 33): 584.843264e6 + 331.993600e6}
 METRIC = "DM-trial*samples/s per GB300 (real-time beams sustained, p99 block latency alongside)"
 WORKLOAD = "stream: 1 beam, 1024 ch 398-418 MHz, 51.2 us, 640 DMs 0-127.8 step 0.2, FP32, 2^17-sample blocks"
 
@@ -240,18 +243,28 @@ def run_batch8(args):
     for b, hb in zip(beams, dev_blocks):
         tp.tp_push_block(e, b, hb[0])
     tp.tp_run_ready(e, use_graph=False)
-    # one kernel shape for the whole batch, tuned on the batched launch itself
-    best, shape_ms = tp.tp_autotune_batch(e, reps=1)
+    if args.shape is None:
+        # one kernel shape for the whole batch, tuned on the batched launch itself
+        best, shape_ms = tp.tp_autotune_batch(e, reps=1)
+        # the autotune overwrote the series: process the block again with the
+        # chosen shape
+        tp.tp_run_ready(e, use_graph=False)
+    else:
+        best, shape_ms = args.shape, np.full(1, -1.0)
+        for p in plans.values():
+            tp.tp_plan_set_shape(p, best)
     tuned = {str(nd): int(best) for nd in sorted(set(BATCH_DMS))}
-    # the autotune overwrote the series: process the block again with the
-    # chosen shape
-    tp.tp_run_ready(e, use_graph=False)
     units_per_step = sum(BATCH_DMS) * BLOCK
 
     def step(k):
         for b, hb in zip(beams, dev_blocks):
             tp.tp_push_block(e, b, hb[(k + 1) % 2])
-        tp.tp_run_ready(e, use_graph=True)
+        if args.per_beam:
+            for b in beams:
+                tp.tp_dedisperse(e, b)
+                tp.tp_detect(e, b)
+        else:
+            tp.tp_run_ready(e, use_graph=True)
 
     for k in range(args.warmup):
         step(k)
@@ -285,7 +298,8 @@ def run_batch8(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value / PAPER_DERIVED, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": f"batch: 8 beams x 1024 ch, DM trials {BATCH_DMS} step 0.2, {args.dtype}, "
-                                   "2^17-sample blocks, graph-replayed batched launch",
+                                   "2^17-sample blocks, " + ("per-beam launches" if args.per_beam else
+                                                             "graph-replayed batched launch"),
                        "kernel_shapes": tuned,
                        "autotune_ms": {str(i): round(float(v), 3) for i, v in enumerate(shape_ms) if v >= 0}},
             "realtime_beams": value / (len(DMS) / TSAMP),
@@ -399,6 +413,10 @@ def main():
     ap.add_argument("--speedup", type=float, default=50.0, help="serve32: arrival time compression")
     ap.add_argument("--blocks-per-stream", type=int, default=4, help="serve32: blocks per stream")
     ap.add_argument("--hbm-gb", type=float, default=48.0, help="serve32: engine HBM budget")
+    ap.add_argument("--shape", type=int, default=None,
+                    help="stream / batch8: use this kernel shape instead of autotuning")
+    ap.add_argument("--per-beam", action="store_true",
+                    help="batch8: per-beam dedisperse/detect calls instead of the batched launch")
     args = ap.parse_args()
     if args.dtype is None:
         args.dtype = "f16" if args.workload == "batch8" else "f32"
@@ -429,10 +447,14 @@ def main():
     # first block of the stream fills the overlap tail; not timed
     tp.tp_push_block(e, beam, dev_blocks[0])
     tp.tp_dedisperse(e, beam)
-    # autotune the dedispersion kernel shape on this plan's geometry
-    best, shape_ms = tp.tp_autotune(e, beam, reps=2)
+    if args.shape is None:
+        # autotune the dedispersion kernel shape on this plan's geometry
+        best, shape_ms = tp.tp_autotune(e, beam, reps=2)
+        tp.tp_dedisperse(e, beam)
+    else:
+        best, shape_ms = args.shape, np.full(1, -1.0)
+        tp.tp_plan_set_shape(plan, best)
     tune = {str(i): round(float(v), 3) for i, v in enumerate(shape_ms) if v >= 0}
-    tp.tp_dedisperse(e, beam)
     tp.tp_detect(e, beam)
     tp.tp_get_candidates(e, beam, 0)
 

@@ -735,7 +735,9 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
   X(38, 4, 30, 9, 11, 2, 3, 1)       \
   X(39, 4, 26, 16, 7, 3, 3, 1)       \
   X(40, 4, 18, 16, 11, 3, 3, 1)      \
-  X(41, 4, 22, 16, 7, 3, 3, 1)
+  X(41, 4, 22, 16, 7, 3, 3, 1)        \
+  X(42, 4, 41, 9, 7, 4, 3, 1)        \
+  X(43, 4, 30, 16, 7, 3, 3, 1)
 
 #define TP_SHAPE_ENTRY(i, K, S, O, N, F, A, M) {K, S, O, N, F, A},
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};

@@ -170,7 +170,7 @@ def emit_pair16(S, OMAX, kind):
 
 # (S, MMAX) of the FP32 DM-quad shapes (ALGO 3): S odd (lanes start an odd
 # number of words apart), consecutive-trial delay steps m or m + 1, m <= MMAX.
-QUADS = [(25, 9), (31, 9), (23, 9)]
+QUADS = [(25, 9), (31, 9), (23, 9), (41, 9)]
 
 
 def quad_steps(b):
@@ -224,7 +224,7 @@ def emit_quad(S, MMAX):
 # (S, MMAX) of the 16-bit float DM-quad shapes: S = 2 mod 4.
 QUADS16 = [(26, 9), (30, 9)]
 # (S, MMAX) of the 8-bit DM-quad shapes: S = 2 mod 4.
-QUADS8 = [(26, 16), (22, 16), (18, 16)]
+QUADS8 = [(26, 16), (22, 16), (18, 16), (30, 16)]
 
 
 def _asm_fn(signature, body, outs, ins):

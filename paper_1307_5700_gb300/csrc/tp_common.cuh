@@ -100,7 +100,7 @@ struct KernelShape {
   int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads;
               // 2: DM pairs sharing one window; 3: DM quads sharing one window
 };
-constexpr int kNumShapes = 42;
+constexpr int kNumShapes = 44;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
