@@ -70,6 +70,11 @@ def lib():
             "orc_series_stats_int": (None, [_p, _i, _i64, _p, _p, _p, _p]),
             "orc_candidates_float": (_i64, [_p, _i, _i64, _p, _p, _d, _i, _i64, _p, _i64]),
             "orc_candidates_int": (_i64, [_p, _i, _i64, _p, _p, _d, _i, _i64, _p, _i64]),
+            "orc_median_float": (None, [_p, _i, _i64, _i, _p]),
+            "orc_median_int": (None, [_p, _i, _i64, _i, _p]),
+            "orc_detrend_float": (None, [_p, _i, _i64, _p, _p, _p]),
+            "orc_detrend_int": (None, [_p, _i, _i64, _p, _p, _p, _p]),
+            "orc_candidates_detrend": (_i64, [_p, _i, _i, _i64, _p, _p, _p, _d, _i, _i64, _p, _i64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -326,6 +331,72 @@ def candidates(D, mu, sigma, nsigma, beam=0, t0=0, cap=None):
         n = lib().orc_candidates_float(_ptr(D), ndm, T, _ptr(mu), _ptr(sigma), nsigma, beam, t0,
                                        _ptr(out), cap)
     return out[:min(n, cap)], int(n)
+
+
+# ---- post-processing (Sec. 2.2.3) ------------------------------------------------
+
+def median_filter(D, w):
+    """Eq. 2 with the median: each value replaced by the median of the w values
+    centred on it, the ends of the series repeating (R11).  w odd, 1 <= w <= 63."""
+    if w % 2 != 1 or not 1 <= w <= 63:
+        raise ValueError("median width must be odd, 1..63")
+    D = np.ascontiguousarray(D)
+    ndm, T = D.shape
+    if D.dtype == np.int64:
+        out = np.empty_like(D)
+        lib().orc_median_int(_ptr(D), ndm, T, w, _ptr(out))
+        return out
+    D = _c(D, np.float64)
+    out = np.empty_like(D)
+    lib().orc_median_float(_ptr(D), ndm, T, w, _ptr(out))
+    return out
+
+
+def detrend(D):
+    """Least-squares line mean + beta * (2t - (T - 1)) per series and the
+    residual's population deviation (R11); for int64 series also the exact
+    sums (Sy, Suy, Syy)."""
+    D = np.ascontiguousarray(D)
+    ndm, T = D.shape
+    mean = np.empty(ndm, np.float64)
+    beta = np.empty(ndm, np.float64)
+    sigma = np.empty(ndm, np.float64)
+    if D.dtype == np.int64:
+        sums = np.empty((ndm, 3), np.int64)
+        lib().orc_detrend_int(_ptr(D), ndm, T, _ptr(sums), _ptr(mean), _ptr(beta), _ptr(sigma))
+        return dict(mean=mean, beta=beta, sigma=sigma, sums=sums)
+    D = _c(D, np.float64)
+    lib().orc_detrend_float(_ptr(D), ndm, T, _ptr(mean), _ptr(beta), _ptr(sigma))
+    return dict(mean=mean, beta=beta, sigma=sigma)
+
+
+def candidates_detrend(D, mean, beta, sigma, nsigma, beam=0, t0=0, cap=None):
+    """Candidates of detrended series: residual >= nsigma * sigma, (d, t) order."""
+    D = np.ascontiguousarray(D)
+    ndm, T = D.shape
+    if cap is None:
+        cap = ndm * T
+    out = np.zeros(max(int(cap), 1), CAND_DTYPE)
+    is_int = D.dtype == np.int64
+    if not is_int:
+        D = _c(D, np.float64)
+    n = lib().orc_candidates_detrend(_ptr(D), int(is_int), ndm, T, _ptr(_c(mean, np.float64)),
+                                     _ptr(_c(beta, np.float64)), _ptr(_c(sigma, np.float64)), nsigma, beam, t0,
+                                     _ptr(out), cap)
+    return out[:min(n, cap)], int(n)
+
+
+def post_process(D, median_width=1, detrend_on=False, nsigma=5.0, beam=0, t0=0, cap=None):
+    """A6-A7 with the optional post-processing of Sec. 2.2.3: the median
+    filter, then either the detrended detection or the plain one."""
+    Y = median_filter(D, median_width) if median_width > 1 else D
+    if detrend_on:
+        st = detrend(Y)
+        cands, n = candidates_detrend(Y, st["mean"], st["beta"], st["sigma"], nsigma, beam=beam, t0=t0, cap=cap)
+    else:
+        st = series_stats(Y)
+        cands, n = candidates(Y, st["mu"], st["sigma"], nsigma, beam=beam, t0=t0, cap=cap)
+    return dict(Y=Y, stats=st, candidates=cands, n_candidates=n)
 
 
 # ---- the whole block -------------------------------------------------------------

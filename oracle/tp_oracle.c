@@ -43,6 +43,12 @@
  *   R8  the detection threshold of Sec. 2.3 is (D - mu_d) >= nsigma * sigma_d
  *       on each dedispersed series, with sigma_d the population standard
  *       deviation of the series; a series with sigma_d = 0 yields nothing.
+ *   R11 post-processing (Sec. 2.2.3), optional: the median filter of Eq. 2
+ *       replaces y_m by the median of the w = 2h + 1 values centred on m
+ *       (odd w; positions beyond the ends of the block's series take the end
+ *       value); detrending fits a least-squares line in t to each series and
+ *       normalises the residual by its population standard deviation, and the
+ *       detection test becomes residual >= nsigma * that deviation.
  */
 #include <math.h>
 #include <stdint.h>
@@ -591,6 +597,133 @@ int64_t orc_candidates_int(const int64_t *D, int ndm, int64_t T, const double *m
           out[n].dm_idx = d;
           out[n].t_abs = t0 + t;
           out[n].snr = (float)((v - mu[d]) / sigma[d]);
+          out[n].value = (float)v;
+        }
+        ++n;
+      }
+    }
+  }
+  return n;
+}
+
+/* ---- Post-processing (Sec. 2.2.3) ------------------------------------------- */
+
+/* Median filter, Eq. 2 with the median as the operation (R11): out[d][m] is the
+ * median of D[d][clamp(m + i)], i = -h .. h, clamp to [0, T - 1]; the w = 2h + 1
+ * values are sorted by insertion and the middle one taken. */
+void orc_median_float(const double *D, int ndm, int64_t T, int w, double *out) {
+  const int h = w / 2;
+  double v[64];
+  for (int d = 0; d < ndm; ++d)
+    for (int64_t m = 0; m < T; ++m) {
+      for (int i = 0; i < w; ++i) {
+        int64_t j = m - h + i;
+        j = j < 0 ? 0 : (j > T - 1 ? T - 1 : j);
+        double x = D[(int64_t)d * T + j];
+        int k = i;
+        while (k > 0 && v[k - 1] > x) {
+          v[k] = v[k - 1];
+          --k;
+        }
+        v[k] = x;
+      }
+      out[(int64_t)d * T + m] = v[h];
+    }
+}
+
+void orc_median_int(const int64_t *D, int ndm, int64_t T, int w, int64_t *out) {
+  const int h = w / 2;
+  int64_t v[64];
+  for (int d = 0; d < ndm; ++d)
+    for (int64_t m = 0; m < T; ++m) {
+      for (int i = 0; i < w; ++i) {
+        int64_t j = m - h + i;
+        j = j < 0 ? 0 : (j > T - 1 ? T - 1 : j);
+        int64_t x = D[(int64_t)d * T + j];
+        int k = i;
+        while (k > 0 && v[k - 1] > x) {
+          v[k] = v[k - 1];
+          --k;
+        }
+        v[k] = x;
+      }
+      out[(int64_t)d * T + m] = v[h];
+    }
+}
+
+/* Detrending (R11): least-squares line y ~ mean + beta * u_t with the centred
+ * abscissa u_t = 2t - (T - 1) (sum_t u_t = 0, so the intercept is the mean and
+ * the slope decouples), from the sums
+ *   Sy = sum y,  Suy = sum u y,  Syy = sum y^2,  Suu = sum u^2 = (T-1) T (T+1) / 3,
+ *   mean = Sy / T,  beta = Suy / Suu,
+ *   RSS = Syy - Sy Sy / T - Suy Suy / Suu  (the least-squares residual identity),
+ *   sigma_r = sqrt(max(RSS, 0) / T).
+ * Float series: the sums in binary64 in t order.  Integer series: the sums
+ * exactly in int64, then the same binary64 formula. */
+static void detrend_from_sums(double Sy, double Suy, double Syy, int64_t T, double *mean, double *beta,
+                              double *sigma) {
+  const double Tn = (double)T;
+  const double Suu = (double)(((T - 1) * T * (T + 1)) / 3);
+  const double m = Sy / Tn;
+  const double b = T > 1 ? Suy / Suu : 0.0;
+  double rss = Syy - Sy * Sy / Tn;
+  if (T > 1) rss = rss - Suy * Suy / Suu;
+  *mean = m;
+  *beta = b;
+  *sigma = sqrt((rss > 0.0 ? rss : 0.0) / Tn);
+}
+
+void orc_detrend_float(const double *D, int ndm, int64_t T, double *mean, double *beta, double *sigma) {
+  for (int d = 0; d < ndm; ++d) {
+    const double *r = D + (int64_t)d * T;
+    double sy = 0.0, suy = 0.0, syy = 0.0;
+    for (int64_t t = 0; t < T; ++t) {
+      sy += r[t];
+      suy += (double)(2 * t - (T - 1)) * r[t];
+      syy += r[t] * r[t];
+    }
+    detrend_from_sums(sy, suy, syy, T, &mean[d], &beta[d], &sigma[d]);
+  }
+}
+
+void orc_detrend_int(const int64_t *D, int ndm, int64_t T, int64_t *sums, double *mean, double *beta,
+                     double *sigma) {
+  for (int d = 0; d < ndm; ++d) {
+    const int64_t *r = D + (int64_t)d * T;
+    int64_t sy = 0, suy = 0, syy = 0;
+    for (int64_t t = 0; t < T; ++t) {
+      sy += r[t];
+      suy += (2 * t - (T - 1)) * r[t];
+      syy += r[t] * r[t];
+    }
+    sums[3 * d] = sy;
+    sums[3 * d + 1] = suy;
+    sums[3 * d + 2] = syy;
+    detrend_from_sums((double)sy, (double)suy, (double)syy, T, &mean[d], &beta[d], &sigma[d]);
+  }
+}
+
+/* Candidates of detrended series (R11): residual r = y - (mean + beta u_t),
+ * a detection when sigma > 0 and r >= nsigma * sigma; snr = r / sigma.  D is
+ * binary64 (float data) or int64 (is_int). */
+int64_t orc_candidates_detrend(const void *D, int is_int, int ndm, int64_t T, const double *mean,
+                               const double *beta, const double *sigma, double nsigma, int beam, int64_t t0,
+                               orc_candidate *out, int64_t cap) {
+  int64_t n = 0;
+  for (int d = 0; d < ndm; ++d) {
+    if (!(sigma[d] > 0.0)) continue;
+    const double thr = nsigma * sigma[d];
+    for (int64_t t = 0; t < T; ++t) {
+      const int64_t i = (int64_t)d * T + t;
+      const double v = is_int ? (double)((const int64_t *)D)[i] : ((const double *)D)[i];
+      const double lin = mean[d] + beta[d] * (double)(2 * t - (T - 1));
+      const double r = v - lin;
+      if (r >= thr) {
+        if (n < cap) {
+          out[n].beam = beam;
+          out[n].dm_idx = d;
+          out[n].t_abs = t0 + t;
+          out[n].snr = (float)(r / sigma[d]);
           out[n].value = (float)v;
         }
         ++n;
