@@ -138,6 +138,22 @@ int tp_plan_destroy(tp_plan *p);
 /* Sizes of a plan (any pointer may be NULL). */
 int tp_plan_info(const tp_plan *p, int *nchan, int *ndm, int *max_delay, int *dtype);
 
+/* Post-processing of the dedispersed series before detection (Sec. 2.2.3,
+ * "Post-Processing"), both off by default:
+ *   median_width w (odd, 1..9; 1 = off): the median filter of Eq. 2 with the
+ *     median as the operation -- each value of a block's series is replaced by
+ *     the median of the w values centred on it, positions beyond the ends of
+ *     the series taking the end value (an exact selection of a stored value);
+ *   detrend (0 or 1): a least-squares line mean + beta u_t, u_t = 2t - (T - 1),
+ *     is fitted to each (filtered) series, and a candidate is a sample whose
+ *     residual y - (mean + beta u_t) is >= nsigma times the residual's
+ *     population standard deviation (snr = residual / deviation); without it
+ *     the detection of Sec. 2.3 runs on the (filtered) series as before.
+ * Call before any beam of the plan is opened (TP_EBUSY otherwise; the
+ * filtered series is part of a beam's footprint).  TP_EINVAL for an even or
+ * out-of-range width. */
+int tp_plan_set_postprocess(tp_plan *p, int median_width, int detrend);
+
 /* Copy the delay table (ndm x nchan int32, row = DM) to host memory `out`
  * holding `count` elements.  Blocks. */
 int tp_get_delay_table(const tp_plan *p, int32_t *out, size_t count);
@@ -232,8 +248,19 @@ int tp_get_bandpass(tp_engine *e, int beam, double *mu, double *sigma, int nchan
  * byte per window sample).  Any pointer may be NULL.  Blocks. */
 int tp_get_masks(tp_engine *e, int beam, uint8_t *chunk_flag, uint8_t *chunk_raw, uint8_t *spec_flag);
 
-/* Series statistics mu_d, sigma_d (host, ndm doubles each). */
+/* Series statistics mu_d, sigma_d (host, ndm doubles each); with detrending
+ * the line's mean and the residual deviation. */
 int tp_get_series_stats(tp_engine *e, int beam, double *mu, double *sigma, int ndm);
+
+/* The series the detection ran on (ndm x nout, row-major, float32 or int32):
+ * the median-filtered series when the plan filters, else D.  Blocks;
+ * TP_ENOTREADY before the beam's detection. */
+int tp_get_processed_series(tp_engine *e, int beam, void *out, size_t bytes, int out_is_device);
+
+/* Detrending line and residual deviation per series (host, ndm doubles each;
+ * any pointer may be NULL): the line is mean + beta (2t - (T - 1)).  Blocks;
+ * TP_EINVAL when the plan does not detrend, TP_ENOTREADY before detection. */
+int tp_get_detrend(tp_engine *e, int beam, double *mean, double *beta, double *sigma, int ndm);
 
 /* ---- kernel shapes and autotuning -------------------------------------------------
  * The dedispersion kernel is compiled for several register tilings ("shapes":

@@ -48,7 +48,8 @@ EXPORTS = (
     "tp_version", "tp_plan_shapes", "tp_plan_set_shape", "tp_autotune", "tp_channel_stats_noalloc",
     "tp_run_ready", "tp_engine_stream", "tp_server_create", "tp_server_add_stream", "tp_server_submit",
     "tp_server_end_stream", "tp_server_run", "tp_server_results", "tp_server_candidates", "tp_server_destroy",
-    "tp_beam_rewind", "tp_autotune_batch",
+    "tp_beam_rewind", "tp_autotune_batch", "tp_plan_set_postprocess", "tp_get_processed_series",
+    "tp_get_detrend",
 )
 
 
@@ -110,6 +111,9 @@ _SIGS = {
     "tp_plan_set_shape": (_i, [_vp, _i]),
     "tp_autotune": (_i, [_vp, _i, _i, _vp, _vp, _i]),
     "tp_autotune_batch": (_i, [_vp, _i, _vp, _vp, _i]),
+    "tp_plan_set_postprocess": (_i, [_vp, _i, _i]),
+    "tp_get_processed_series": (_i, [_vp, _i, _vp, ctypes.c_size_t, _i]),
+    "tp_get_detrend": (_i, [_vp, _i, _vp, _vp, _vp, _i]),
     "tp_channel_stats_noalloc": (_i, [_vp, _i, _i, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                      _vp]),
     "tp_run_ready": (_i, [_vp, _i, _vp]),
@@ -377,6 +381,32 @@ def tp_autotune(e, beam, reps=3):
     ms = np.full(64, -1.0, np.float32)
     _check(lib().tp_autotune(e, beam, int(reps), ctypes.byref(best), ms.ctypes.data, len(ms)))
     return best.value, ms
+
+
+def tp_plan_set_postprocess(p, median_width=1, detrend=False):
+    """Median filter width (odd, 1 = off) and detrending for the plan's beams
+    (before any beam is opened; see tp_dedisp.h)."""
+    return _check(lib().tp_plan_set_postprocess(p, int(median_width), int(bool(detrend))))
+
+
+def tp_get_processed_series(e, beam, out=None, ndm=None, is_int=False):
+    """The series the detection ran on (median-filtered, or D)."""
+    info = tp_beam_info(e, beam)
+    if out is None:
+        out = np.empty((ndm, info["nout"]), np.int32 if is_int else np.float32)
+    nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+    is_dev = bool(getattr(out, "is_cuda", False))
+    _check(lib().tp_get_processed_series(e, beam, _addr(out), nbytes, int(is_dev)))
+    return out
+
+
+def tp_get_detrend(e, beam, ndm):
+    """(mean, beta, sigma) of the detrending line mean + beta (2t - (T - 1))."""
+    mean = np.empty(ndm, np.float64)
+    beta = np.empty(ndm, np.float64)
+    sigma = np.empty(ndm, np.float64)
+    _check(lib().tp_get_detrend(e, beam, mean.ctypes.data, beta.ctypes.data, sigma.ctypes.data, ndm))
+    return mean, beta, sigma
 
 
 def tp_autotune_batch(e, reps=2):

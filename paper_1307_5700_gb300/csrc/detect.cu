@@ -15,9 +15,24 @@
 //   scan  : one CTA turns the counts into offsets (row-major in (d, block));
 //   write : each CTA ranks its hits in t order (ballots + a 128-entry scan) and
 //           writes records at offset + rank, keeping those below the capacity.
+//
+// Optional post-processing of Sec. 2.2.3 (median filter of Eq. 2, detrending
+// and normalisation).  post_kernel (one CTA per (d, 4096 samples)) replaces
+// each value by the median of the w values centred on it -- the series ends
+// repeat -- selected with min/max exchanges (an exact selection of a stored
+// value), writes the filtered series M, and sums per tile y, (t - t_c) y and
+// y^2 (FP32 over a thread's 16 values, FP64 above; exact int64 for 8-bit
+// data).  With detrending, row_stats fits the least-squares line
+// y ~ mean + beta u_t, u_t = 2t - (T - 1), from those sums,
+//   mean = Sy / T, beta = Suy / Suu, Suu = (T-1) T (T+1) / 3,
+//   RSS = Syy - Sy Sy / T - Suy Suy / Suu, sigma = sqrt(max(RSS, 0) / T),
+// and a sample is a candidate when y - (mean + beta u_t) >= nsigma sigma,
+// evaluated in binary64 in that order whenever an FP32 pre-test cannot
+// decide it with a wide margin.
 #include <cfloat>
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "tp_common.cuh"
 
@@ -31,10 +46,243 @@ constexpr int kPer = kDetectT / kThreads;  // 16 samples per thread
 
 __device__ __forceinline__ bool passes(double v, double mu, double thr) { return __dsub_rn(v, mu) >= thr; }
 
+// detrended residual y - (mean + beta u), binary64 in the order written
+__device__ __forceinline__ double residual(double v, double mean, double beta, double u) {
+  return __dsub_rn(v, __dadd_rn(mean, __dmul_rn(beta, u)));
+}
+
+// compare-exchange: lo = min, hi = max (exact selections)
+__device__ __forceinline__ void cx(float& lo, float& hi) {
+  const float a = fminf(lo, hi), b = fmaxf(lo, hi);
+  lo = a, hi = b;
+}
+__device__ __forceinline__ void cx(int& lo, int& hi) {
+  const int a = min(lo, hi), b = max(lo, hi);
+  lo = a, hi = b;
+}
+
+// median of v[0 .. W) (W odd): odd-even transposition sort, middle element
+template <int W, typename V>
+__device__ __forceinline__ V median_of(V (&v)[W]) {
+#pragma unroll
+  for (int pass = 0; pass < W; ++pass)
+#pragma unroll
+    for (int i = pass & 1; i + 1 < W; i += 2) cx(v[i], v[i + 1]);
+  return v[W / 2];
+}
+
+constexpr int kPostHalo = kMaxMedianWidth / 2;
+
+// Post-processing of one (d, 4096-sample tile): median filter (W > 1) and the
+// tile's sums {y, (t - t_c) y, y^2}, t_c = tile start + 2048.
+template <bool INT, int W>
+__global__ void __launch_bounds__(kThreads) post_kernel(DetectArgs a) {
+  using V = typename std::conditional<INT, int, float>::type;
+  const int d = blockIdx.y;
+  const int64_t t0 = (int64_t)blockIdx.x * kDetectT;
+  const int64_t T = a.nout;
+  const V* row = static_cast<const V*>(a.D) + (int64_t)d * a.dpitch;
+  constexpr int H = W / 2;
+  __shared__ V s_v[kDetectT + 2 * kPostHalo];
+  if constexpr (W > 1) {
+    for (int i = threadIdx.x; i < kDetectT + 2 * H; i += kThreads) {
+      int64_t t = t0 - H + i;
+      t = t < 0 ? 0 : (t > T - 1 ? T - 1 : t);
+      s_v[i] = row[t];
+    }
+    __syncthreads();
+  }
+  V* mrow = static_cast<V*>(a.M) + (int64_t)d * a.dpitch;
+  const int64_t tc = t0 + kDetectT / 2;
+  float fs = 0.f, fd = 0.f, fq = 0.f;
+  long long is = 0, id = 0, iq = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t tb = t0 + 1024 * r + 4 * threadIdx.x;
+    V y[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if constexpr (W > 1) {
+        V w[W];
+        const int j = (int)(tb + e - t0);
+#pragma unroll
+        for (int k = 0; k < W; ++k) w[k] = s_v[j + k];
+        y[e] = median_of<W>(w);
+      } else {
+        y[e] = tb + e < T ? row[tb + e] : V(0);
+      }
+    }
+    if constexpr (W > 1) {
+      if (tb + 3 < T) {
+        if constexpr (INT)
+          *reinterpret_cast<int4*>(mrow + tb) = make_int4(y[0], y[1], y[2], y[3]);
+        else
+          *reinterpret_cast<float4*>(mrow + tb) = make_float4(y[0], y[1], y[2], y[3]);
+      } else {
+        for (int e = 0; e < 4; ++e)
+          if (tb + e < T) mrow[tb + e] = y[e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (tb + e >= T) continue;
+      const int dt = (int)(tb + e - tc);
+      if constexpr (INT) {
+        is += y[e];
+        id += (long long)dt * y[e];
+        iq += (long long)y[e] * y[e];
+      } else {
+        fs += y[e];
+        fd += (float)dt * y[e];
+        fq += y[e] * y[e];
+      }
+    }
+  }
+  __shared__ double s_f[3][kWarps];
+  __shared__ long long s_i[3][kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (INT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      is += __shfl_xor_sync(0xffffffffu, is, o);
+      id += __shfl_xor_sync(0xffffffffu, id, o);
+      iq += __shfl_xor_sync(0xffffffffu, iq, o);
+    }
+    if (lane == 0) s_i[0][warp] = is, s_i[1][warp] = id, s_i[2][warp] = iq;
+  } else {
+    double ds = fs, dd = fd, dq = fq;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ds += __shfl_xor_sync(0xffffffffu, ds, o);
+      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+      dq += __shfl_xor_sync(0xffffffffu, dq, o);
+    }
+    if (lane == 0) s_f[0][warp] = ds, s_f[1][warp] = dd, s_f[2][warp] = dq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int64_t slot = ((int64_t)d * a.nblk_t + blockIdx.x) * 3;
+    if constexpr (INT) {
+      long long x = 0, y = 0, z = 0;
+      for (int w = 0; w < kWarps; ++w) x += s_i[0][w], y += s_i[1][w], z += s_i[2][w];
+      long long* o = static_cast<long long*>(a.post_part) + slot;
+      o[0] = x, o[1] = y, o[2] = z;
+    } else {
+      double x = 0, y = 0, z = 0;
+      for (int w = 0; w < kWarps; ++w) x += s_f[0][w], y += s_f[1][w], z += s_f[2][w];
+      double* o = static_cast<double*>(a.post_part) + slot;
+      o[0] = x, o[1] = y, o[2] = z;
+    }
+  }
+}
+
+template <bool INT>
+cudaError_t launch_post(const DetectArgs& a, cudaStream_t s) {
+  const dim3 grid((unsigned)a.nblk_t, (unsigned)a.ndm);
+  switch (a.median_width) {
+    case 1: post_kernel<INT, 1><<<grid, kThreads, 0, s>>>(a); break;
+    case 3: post_kernel<INT, 3><<<grid, kThreads, 0, s>>>(a); break;
+    case 5: post_kernel<INT, 5><<<grid, kThreads, 0, s>>>(a); break;
+    case 7: post_kernel<INT, 7><<<grid, kThreads, 0, s>>>(a); break;
+    case 9: post_kernel<INT, 9><<<grid, kThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Post-processed rows: sums of the post_kernel tiles (tile order, exact for
+// int data), then the plain statistics or the detrending line of R11.
+__device__ void row_stats_post(const DetectArgs& a, int d) {
+  __shared__ double s_f[3][kThreads];
+  __shared__ long long s_i[3][kThreads];
+  const int64_t T = a.nout;
+  double sy = 0.0, suy = 0.0, syy = 0.0;
+  long long iy = 0, iuy = 0, iyy = 0;
+  for (int b = threadIdx.x; b < a.nblk_t; b += kThreads) {
+    // u_t = 2t - (T - 1) = 2 (t - t_c) + (2 t_c - (T - 1))
+    const long long uc = 2LL * ((long long)b * kDetectT + kDetectT / 2) - (T - 1);
+    const int64_t slot = ((int64_t)d * a.nblk_t + b) * 3;
+    if (a.is_int) {
+      const long long* o = static_cast<const long long*>(a.post_part) + slot;
+      iy += o[0];
+      iuy += 2 * o[1] + uc * o[0];
+      iyy += o[2];
+    } else {
+      const double* o = static_cast<const double*>(a.post_part) + slot;
+      sy += o[0];
+      suy += 2.0 * o[1] + (double)uc * o[0];
+      syy += o[2];
+    }
+  }
+  s_f[0][threadIdx.x] = sy, s_f[1][threadIdx.x] = suy, s_f[2][threadIdx.x] = syy;
+  s_i[0][threadIdx.x] = iy, s_i[1][threadIdx.x] = iuy, s_i[2][threadIdx.x] = iyy;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        s_f[k][threadIdx.x] += s_f[k][threadIdx.x + o];
+        s_i[k][threadIdx.x] += s_i[k][threadIdx.x + o];
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double Sy = a.is_int ? (double)s_i[0][0] : s_f[0][0];
+  const double Suy = a.is_int ? (double)s_i[1][0] : s_f[1][0];
+  const double Syy = a.is_int ? (double)s_i[2][0] : s_f[2][0];
+  const double Tn = (double)T;
+  double m, sig, beta = 0.0;
+  if (a.detrend) {
+    const double Suu = (double)(((T - 1) * T * (T + 1)) / 3);
+    m = __ddiv_rn(Sy, Tn);
+    beta = T > 1 ? __ddiv_rn(Suy, Suu) : 0.0;
+    double rss = __dsub_rn(Syy, __ddiv_rn(__dmul_rn(Sy, Sy), Tn));
+    if (T > 1) rss = __dsub_rn(rss, __ddiv_rn(__dmul_rn(Suy, Suy), Suu));
+    sig = __dsqrt_rn(__ddiv_rn(rss > 0.0 ? rss : 0.0, Tn));
+  } else {
+    m = __ddiv_rn(Sy, Tn);
+    const double var = __dsub_rn(__ddiv_rn(Syy, Tn), __dmul_rn(m, m));
+    sig = __dsqrt_rn(var > 0.0 ? var : 0.0);
+  }
+  a.row_mu[d] = m;
+  a.row_sigma[d] = sig;
+  a.row_beta[d] = beta;
+}
+
 __global__ void __launch_bounds__(kThreads) row_stats_kernel(DetectArgs a) {
   const int d = blockIdx.x;
   __shared__ double s_a[kThreads], s_b[kThreads];
   __shared__ long long s_ia[kThreads], s_ib[kThreads];
+  if (a.median_width > 1 || a.detrend) {
+    row_stats_post(a, d);
+    __syncthreads();
+    if (threadIdx.x != 0 || a.detrend) return;
+    // plain statistics of the filtered series: the thresholds below
+    const double m = a.row_mu[d], sig = a.row_sigma[d];
+    const double thr = __dmul_rn(a.nsigma, sig);
+    if (!(sig > 0.0)) {
+      a.row_thr_f[d] = __int_as_float(0x7f800000);
+      a.row_thr_i[d] = INT_MAX;
+      return;
+    }
+    float f = (float)__dadd_rn(m, thr);
+    if (passes((double)f, m, thr)) {
+      for (int it = 0; it < 64; ++it) {
+        const float g = nextafterf(f, -FLT_MAX);
+        if (g == f || !passes((double)g, m, thr)) break;
+        f = g;
+      }
+    } else {
+      for (int it = 0; it < 64 && !passes((double)f, m, thr); ++it) f = nextafterf(f, FLT_MAX);
+    }
+    a.row_thr_f[d] = f;
+    const double c = ceil(__dadd_rn(m, thr));
+    long long i = c > 2147483647.0 ? 2147483647LL : (c < -2147483648.0 ? -2147483648LL : (long long)c);
+    while (i > INT_MIN && passes((double)(i - 1), m, thr)) --i;
+    while (i < INT_MAX && !passes((double)i, m, thr)) ++i;
+    a.row_thr_i[d] = (int)i;
+    return;
+  }
   if (a.is_int) {
     long long x = 0, y = 0;
     const longlong2* p = static_cast<const longlong2*>(a.row_part) + (int64_t)d * a.ntt;
@@ -108,20 +356,61 @@ __global__ void __launch_bounds__(kThreads) row_stats_kernel(DetectArgs a) {
   a.row_thr_i[d] = (int)i;
 }
 
+// the series the detection reads: the median-filtered one, else D
+__device__ __forceinline__ const void* det_series(const DetectArgs& a) { return a.median_width > 1 ? a.M : a.D; }
+
+// Detrended test of one sample: an FP32 pre-test decides unless the residual
+// lies within a margin of the threshold far wider than its FP32 rounding
+// (a few units in 2^-24 of |y| + |mean| + |beta u| + thr), then the binary64
+// test in the oracle's operation order.
+__device__ __forceinline__ bool detrend_hit(double v, int64_t t, int64_t T, double mean, double beta, double thr,
+                                            float m32, float b32, float thr32) {
+  const float u32 = (float)(2 * t - (T - 1));
+  const float y32 = (float)v;
+  const float bu = b32 * u32;
+  const float r32 = y32 - (m32 + bu);
+  const float guard = 1e-5f * (fabsf(y32) + fabsf(m32) + fabsf(bu) + thr32);
+  if (r32 > thr32 + guard) return true;
+  if (r32 < thr32 - guard) return false;
+  return residual(v, mean, beta, (double)(2 * t - (T - 1))) >= thr;
+}
+
 __global__ void __launch_bounds__(kThreads) detect_count(DetectArgs a) {
   const int d = blockIdx.y;
   const int64_t t0 = (int64_t)blockIdx.x * kDetectT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float tf = a.row_thr_f[d];
   const int ti = a.row_thr_i[d];
+  const void* S = det_series(a);
+  // detrended rows: line and threshold (sigma = 0: nothing passes)
+  double mean = 0.0, beta = 0.0, thr = 0.0;
+  float m32 = 0.f, b32 = 0.f, thr32 = 0.f;
+  bool live = true;
+  if (a.detrend) {
+    mean = a.row_mu[d];
+    beta = a.row_beta[d];
+    const double sig = a.row_sigma[d];
+    live = sig > 0.0;
+    thr = __dmul_rn(a.nsigma, sig);
+    m32 = (float)mean, b32 = (float)beta, thr32 = (float)thr;
+  }
   int cnt = 0;
   // thread handles 4 runs of 4 consecutive samples: t = t0 + 1024 r + 4 tid + e
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int64_t tb = t0 + 1024 * r + 4 * threadIdx.x;
     bool hit[4] = {false, false, false, false};
-    if (a.is_int) {
-      const int* row = static_cast<const int*>(a.D) + (int64_t)d * a.dpitch;
+    if (a.detrend) {
+      if (live)
+        for (int e = 0; e < 4; ++e) {
+          const int64_t t = tb + e;
+          if (t >= a.nout) break;
+          const double v = a.is_int ? (double)static_cast<const int*>(S)[(int64_t)d * a.dpitch + t]
+                                    : (double)static_cast<const float*>(S)[(int64_t)d * a.dpitch + t];
+          hit[e] = detrend_hit(v, t, a.nout, mean, beta, thr, m32, b32, thr32);
+        }
+    } else if (a.is_int) {
+      const int* row = static_cast<const int*>(S) + (int64_t)d * a.dpitch;
       if (tb + 3 < a.nout) {
         const int4 v = *reinterpret_cast<const int4*>(row + tb);
         hit[0] = v.x >= ti, hit[1] = v.y >= ti, hit[2] = v.z >= ti, hit[3] = v.w >= ti;
@@ -129,7 +418,7 @@ __global__ void __launch_bounds__(kThreads) detect_count(DetectArgs a) {
         for (int e = 0; e < 4; ++e) hit[e] = tb + e < a.nout && row[tb + e] >= ti;
       }
     } else {
-      const float* row = static_cast<const float*>(a.D) + (int64_t)d * a.dpitch;
+      const float* row = static_cast<const float*>(S) + (int64_t)d * a.dpitch;
       if (tb + 3 < a.nout) {
         const float4 v = *reinterpret_cast<const float4*>(row + tb);
         hit[0] = v.x >= tf, hit[1] = v.y >= tf, hit[2] = v.z >= tf, hit[3] = v.w >= tf;
@@ -222,6 +511,8 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
   }
   __syncthreads();
   const double mu = a.row_mu[d], sigma = a.row_sigma[d];
+  const double beta = a.detrend ? a.row_beta[d] : 0.0;
+  const void* S = det_series(a);
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const uint32_t w = words[j];
@@ -230,13 +521,14 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
       const uint64_t pos = base + rank;
       if (pos < (uint64_t)a.cap) {
         const int64_t t = t0 + 32 * ((int64_t)j * kWarps + warp) + lane;
-        const double v = a.is_int ? (double)static_cast<const int*>(a.D)[(int64_t)d * a.dpitch + t]
-                                  : (double)static_cast<const float*>(a.D)[(int64_t)d * a.dpitch + t];
+        const double v = a.is_int ? (double)static_cast<const int*>(S)[(int64_t)d * a.dpitch + t]
+                                  : (double)static_cast<const float*>(S)[(int64_t)d * a.dpitch + t];
         tp_candidate r;
         r.beam = a.beam;
         r.dm_idx = d;
         r.t_abs = *a.t0_abs + t;
-        r.snr = (float)__ddiv_rn(__dsub_rn(v, mu), sigma);
+        const double res = a.detrend ? residual(v, mu, beta, (double)(2 * t - (a.nout - 1))) : __dsub_rn(v, mu);
+        r.snr = (float)__ddiv_rn(res, sigma);
         r.value = (float)v;
         a.cand[pos] = r;
       }
@@ -247,8 +539,13 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
 }  // namespace
 
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (a.median_width > 1 || a.detrend) {
+    e = a.is_int ? launch_post<true>(a, s) : launch_post<false>(a, s);
+    if (e != cudaSuccess) return e;
+  }
   row_stats_kernel<<<a.ndm, kThreads, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)a.nblk_t, (unsigned)a.ndm);
   detect_count<<<grid, kThreads, 0, s>>>(a);

@@ -164,6 +164,9 @@ struct Beam {
   double* bsum = nullptr;
   int* status = nullptr;
   void* D = nullptr;
+  void* M = nullptr;          // median-filtered series (plans with median_width > 1)
+  void* post_part = nullptr;  // post-processing tile sums
+  double* row_beta = nullptr;
   void* row_part = nullptr;
   double* row_mu = nullptr;
   double* row_sigma = nullptr;
@@ -210,6 +213,8 @@ struct tp_plan {
   std::vector<double> dm;
   tp_rfi_params rfi{};
   double nsigma = 5.0;
+  int median_width = 1;  // post-processing (Sec. 2.2.3): median filter width, 1 = off
+  int detrend = 0;       // post-processing: least-squares detrending
   int32_t* d_delay = nullptr;
   int32_t* d_delayT = nullptr;  // [nchan][ndm]
   std::vector<int32_t> h_delay;
@@ -405,6 +410,9 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add(&b->d_args, sizeof(DedispArgs) + 16);
   add((void**)&b->d_t0, 8);
   add(&b->D, nd * (size_t)dpitch * 4);
+  if (p->median_width > 1) add(&b->M, nd * (size_t)dpitch * 4);
+  add(&b->post_part, nd * (size_t)nblk * 24);
+  add((void**)&b->row_beta, nd * 8);
   add(&b->row_part, nd * (size_t)ntt * 16);
   add((void**)&b->row_mu, nd * 8);
   add((void**)&b->row_sigma, nd * 8);
@@ -611,8 +619,13 @@ int issue_detect(tp_engine* e, Beam* b, cudaStream_t s) {
   a.cand = b->cand;
   a.cap = b->cap;
   a.n_total = b->n_total;
+  a.median_width = p->median_width;
+  a.detrend = p->detrend;
+  a.M = b->M;
+  a.post_part = b->post_part;
+  a.row_beta = b->row_beta;
   TP_CUDA_TRY(launch_detect(a, s));
-  e->launches += 4;
+  e->launches += (p->median_width > 1 || p->detrend) ? 5 : 4;
   prof_record(e, b, 5, s);
   TP_CUDA_TRY(cudaEventRecord(b->ev_detect, s));
   b->state = kDetected;
@@ -1422,6 +1435,53 @@ int tp_engine_launches(const tp_engine* e, uint64_t* n) {
 }  // extern "C"
 
 extern "C" {
+
+int tp_plan_set_postprocess(tp_plan* p, int median_width, int detrend) {
+  if (!p) return set_error(TP_EINVAL, "plan is NULL");
+  std::lock_guard<std::recursive_mutex> lk(p->e->mu);
+  if (median_width < 1 || median_width > kMaxMedianWidth || median_width % 2 == 0)
+    return set_error(TP_EINVAL, "median width %d: odd, 1..%d", median_width, kMaxMedianWidth);
+  if (detrend != 0 && detrend != 1) return set_error(TP_EINVAL, "detrend must be 0 or 1");
+  if (p->users > 0) return set_error(TP_EBUSY, "plan is used by %d open beams", p->users);
+  p->median_width = median_width;
+  p->detrend = detrend;
+  return TP_OK;
+}
+
+int tp_get_processed_series(tp_engine* e, int beam, void* out, size_t bytes, int out_is_device) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->state != kDetected) return set_error(TP_ENOTREADY, "beam %d has no detected block", beam);
+  const size_t row = (size_t)b->nout * 4;
+  if (!out || bytes < row * (size_t)b->plan->ndm) return set_error(TP_EINVAL, "output buffer too small");
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  const void* src = b->plan->median_width > 1 ? b->M : b->D;
+  TP_CUDA_TRY(cudaMemcpy2DAsync(out, row, src, (size_t)b->dpitch * 4, row, b->plan->ndm,
+                                out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+}
+
+int tp_get_detrend(tp_engine* e, int beam, double* mean, double* beta, double* sigma, int ndm) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->state != kDetected) return set_error(TP_ENOTREADY, "beam %d has no detected block", beam);
+  if (!b->plan->detrend) return set_error(TP_EINVAL, "the beam's plan does not detrend");
+  if (ndm < b->plan->ndm) return set_error(TP_EINVAL, "ndm %d < %d", ndm, b->plan->ndm);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  const size_t nb = (size_t)b->plan->ndm * 8;
+  if (mean) TP_CUDA_TRY(cudaMemcpyAsync(mean, b->row_mu, nb, cudaMemcpyDeviceToHost, s));
+  if (beta) TP_CUDA_TRY(cudaMemcpyAsync(beta, b->row_beta, nb, cudaMemcpyDeviceToHost, s));
+  if (sigma) TP_CUDA_TRY(cudaMemcpyAsync(sigma, b->row_sigma, nb, cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+}
 
 int tp_plan_shapes(const tp_plan* p, int* shape, int* feasible, int n) {
   if (!p) return set_error(TP_EINVAL, "plan is NULL");

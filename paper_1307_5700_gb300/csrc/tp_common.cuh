@@ -127,7 +127,19 @@ struct DetectArgs {
   tp_candidate* cand;
   int cap;
   unsigned long long* n_total;  // [1]
+  // post-processing (Sec. 2.2.3): median width (1 = off), detrending; when
+  // either is on, post_kernel reads D, writes the median-filtered series to M
+  // (median_width > 1) and the per-(DM, 4096-sample tile) sums to post_part,
+  // and the detection runs on M (or D)
+  int median_width;
+  int detrend;
+  void* M;                // [ndm][dpitch] like D
+  void* post_part;        // [ndm][nblk_t] x 3: float data double {Sy, Sdy, Syy}, int data long long
+  double* row_beta;       // [ndm] detrending slope per unit of u = 2t - (T - 1)
 };
+
+// Largest median-filter width of the post-processing.
+constexpr int kMaxMedianWidth = 9;
 
 // Dedispersion tiling constants (shared by the planner and the kernel).
 constexpr int kMinTileT = 256;      // smallest output tile any shape may use (sizes buffers)
