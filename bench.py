@@ -415,6 +415,9 @@ def main():
     ap.add_argument("--hbm-gb", type=float, default=48.0, help="serve32: engine HBM budget")
     ap.add_argument("--shape", type=int, default=None,
                     help="stream / batch8: use this kernel shape instead of autotuning")
+    ap.add_argument("--median", type=int, default=1,
+                    help="stream: median filter width of the post-processing (odd, 1 = off)")
+    ap.add_argument("--detrend", action="store_true", help="stream: detrended detection (post-processing)")
     ap.add_argument("--per-beam", action="store_true",
                     help="batch8: per-beam dedisperse/detect calls instead of the batched launch")
     args = ap.parse_args()
@@ -438,6 +441,8 @@ def main():
     e = tp.tp_engine_create(local, 0, stream)
     rfi = tp.tp_rfi_defaults()
     plan = tp.tp_create_plan(e, NCHAN, F_LO, BW, TSAMP, DMS, args.dtype, rfi, 5.0)
+    if args.median > 1 or args.detrend:
+        tp.tp_plan_set_postprocess(plan, args.median, args.detrend)
     delays = tp.tp_get_delay_table(plan)
     max_delay = tp.tp_plan_info(plan)["max_delay"]
     beam = tp.tp_beam_open(e, plan, BLOCK, 1 << 20)
@@ -506,7 +511,10 @@ def main():
     roof = {"kernel": f"dedisperse_kernel (shape {best})", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": TRAFFIC_BY_SHAPE.get((args.dtype, int(best))),
             "ms_per_launch": dd_ms,
-            "note": "FP32 adds (1 add = 1 flop) per launch = ndm*nchan*T; peak = 152 SMs x 128 FP32 lanes x 2070 MHz",
+            "note": ("adds per launch = ndm*nchan*T (1 add = 1 op); peak = 152 SMs x 128 lanes x 2070 MHz "
+                     + ("(integer adds issue at the FP32 rate; the 8-bit kernel adds two 16-bit lanes per "
+                        "instruction, so against its packed peak of 2x this figure frac halves)"
+                        if args.dtype == "u8" else "FP32 adds")),
             "stage_ms_per_block": {"push": stage_ms[0] / max(nstage, 1), "a1_a3": stage_ms[1] / max(nstage, 1),
                                    "a4_a5": dd_ms, "a6_a7": stage_ms[3] / max(nstage, 1)}}
 
@@ -563,6 +571,7 @@ def main():
                        "overlap": int(max_delay), "beams_per_gpu": 1,
                        "l2": "inputs larger than L2 (562 MB window per block, 3 distinct blocks cycled)",
                        "parallelism": f"replicas x{world}", "kernel_shape": int(best),
+                       "postprocess": {"median_width": args.median, "detrend": bool(args.detrend)},
                        "autotune_ms": tune},
             "realtime_beams": value / (len(DMS) / TSAMP),
             "p50_block_latency_ms": float(np.percentile(per_block, 50)),

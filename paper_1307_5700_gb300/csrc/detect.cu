@@ -85,7 +85,21 @@ __global__ void __launch_bounds__(kThreads) post_kernel(DetectArgs a) {
   constexpr int H = W / 2;
   __shared__ V s_v[kDetectT + 2 * kPostHalo];
   if constexpr (W > 1) {
-    for (int i = threadIdx.x; i < kDetectT + 2 * H; i += kThreads) {
+    // s_v[i] = value at t0 - H + i, positions beyond the series taking the
+    // end value: 16-byte loads for the tile, clamped loads for the halos
+    using V4 = typename std::conditional<INT, int4, float4>::type;
+    for (int q = threadIdx.x; q < kDetectT / 4; q += kThreads) {
+      const int64_t t = t0 + 4 * q;
+      if (t + 3 < T) {
+        const V4 v = *reinterpret_cast<const V4*>(row + t);
+        s_v[H + 4 * q] = v.x, s_v[H + 4 * q + 1] = v.y, s_v[H + 4 * q + 2] = v.z, s_v[H + 4 * q + 3] = v.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s_v[H + 4 * q + e] = row[t + e < T ? t + e : T - 1];
+      }
+    }
+    if (threadIdx.x < 2 * H) {
+      const int i = threadIdx.x < H ? threadIdx.x : kDetectT + threadIdx.x;
       int64_t t = t0 - H + i;
       t = t < 0 ? 0 : (t > T - 1 ? T - 1 : t);
       s_v[i] = row[t];
@@ -359,20 +373,18 @@ __global__ void __launch_bounds__(kThreads) row_stats_kernel(DetectArgs a) {
 // the series the detection reads: the median-filtered one, else D
 __device__ __forceinline__ const void* det_series(const DetectArgs& a) { return a.median_width > 1 ? a.M : a.D; }
 
-// Detrended test of one sample: an FP32 pre-test decides unless the residual
-// lies within a margin of the threshold far wider than its FP32 rounding
-// (a few units in 2^-24 of |y| + |mean| + |beta u| + thr), then the binary64
-// test in the oracle's operation order.
-__device__ __forceinline__ bool detrend_hit(double v, int64_t t, int64_t T, double mean, double beta, double thr,
-                                            float m32, float b32, float thr32) {
-  const float u32 = (float)(2 * t - (T - 1));
-  const float y32 = (float)v;
-  const float bu = b32 * u32;
-  const float r32 = y32 - (m32 + bu);
-  const float guard = 1e-5f * (fabsf(y32) + fabsf(m32) + fabsf(bu) + thr32);
-  if (r32 > thr32 + guard) return true;
-  if (r32 < thr32 - guard) return false;
-  return residual(v, mean, beta, (double)(2 * t - (T - 1))) >= thr;
+// Detrended test of one sample in FP32: 1 = pass, 0 = fail, 2 = undecided.
+// The FP32 residual y - (mean + beta u) is within a few units in 2^-24 of
+// |y| + |mean| + |beta u| + thr of the exact one; the margin below is far
+// wider, so only samples inside it are undecided and take the binary64 test
+// (in the oracle's operation order).  u is exact in FP32 (|u| < 2^24).
+__device__ __forceinline__ int detrend_hit32(float y, float u, float m32, float b32, float thr32) {
+  const float bu = b32 * u;
+  const float r32 = y - (m32 + bu);
+  const float guard = 1e-5f * (fabsf(y) + fabsf(m32) + fabsf(bu) + thr32);
+  if (r32 > thr32 + guard) return 1;
+  if (r32 < thr32 - guard) return 0;
+  return 2;
 }
 
 __global__ void __launch_bounds__(kThreads) detect_count(DetectArgs a) {
@@ -401,14 +413,37 @@ __global__ void __launch_bounds__(kThreads) detect_count(DetectArgs a) {
     const int64_t tb = t0 + 1024 * r + 4 * threadIdx.x;
     bool hit[4] = {false, false, false, false};
     if (a.detrend) {
-      if (live)
-        for (int e = 0; e < 4; ++e) {
-          const int64_t t = tb + e;
-          if (t >= a.nout) break;
-          const double v = a.is_int ? (double)static_cast<const int*>(S)[(int64_t)d * a.dpitch + t]
-                                    : (double)static_cast<const float*>(S)[(int64_t)d * a.dpitch + t];
-          hit[e] = detrend_hit(v, t, a.nout, mean, beta, thr, m32, b32, thr32);
+      if (live && tb < a.nout) {
+        float y[4];
+        const int64_t base = (int64_t)d * a.dpitch + tb;
+        if (tb + 3 < a.nout) {
+          if (a.is_int) {
+            const int4 v = *reinterpret_cast<const int4*>(static_cast<const int*>(S) + base);
+            y[0] = (float)v.x, y[1] = (float)v.y, y[2] = (float)v.z, y[3] = (float)v.w;
+          } else {
+            const float4 v = *reinterpret_cast<const float4*>(static_cast<const float*>(S) + base);
+            y[0] = v.x, y[1] = v.y, y[2] = v.z, y[3] = v.w;
+          }
+        } else {
+          for (int e = 0; e < 4; ++e)
+            y[e] = tb + e < a.nout ? (a.is_int ? (float)static_cast<const int*>(S)[base + e]
+                                               : static_cast<const float*>(S)[base + e])
+                                   : 0.f;
         }
+        const float u0 = (float)(2 * tb - (a.nout - 1));
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (tb + e >= a.nout) break;
+          const int h = detrend_hit32(y[e], u0 + 2.f * e, m32, b32, thr32);
+          if (h == 2) {
+            const double v = a.is_int ? (double)static_cast<const int*>(S)[base + e]
+                                      : (double)static_cast<const float*>(S)[base + e];
+            hit[e] = residual(v, mean, beta, (double)(2 * (tb + e) - (a.nout - 1))) >= thr;
+          } else {
+            hit[e] = h == 1;
+          }
+        }
+      }
     } else if (a.is_int) {
       const int* row = static_cast<const int*>(S) + (int64_t)d * a.dpitch;
       if (tb + 3 < a.nout) {
