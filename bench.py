@@ -51,12 +51,23 @@ METRIC = "DM-trial*samples/s per GB300 (real-time beams sustained, p99 block lat
 WORKLOAD = "stream: 1 beam, 1024 ch 398-418 MHz, 51.2 us, 640 DMs 0-127.8 step 0.2, FP32, 2^17-sample blocks"
 
 
+def _raw(h):
+    """A host block as an array torch can hold: bfloat16 bits as int16,
+    complex int16 voltages as one int32 per sample."""
+    if h.dtype == np.uint16:
+        return h.view(np.int16)
+    if h.dtype.names:
+        return h.view(np.int32)
+    return h
+
+
 def make_block(seed, delay, max_delay, dtype="f32"):
     """One synthetic block: noise, 16 pulses on random trials, RFI bursts;
     FP32 N(0,1) by default, stored as binary16 / bfloat16, or as 8-bit
-    round(N(128, 16))."""
+    round(N(128, 16)); complex int16 voltages whose power carries the same
+    pulses and bursts on a unit envelope."""
     g = synth.rng(seed)
-    x = synth.noise(NCHAN, BLOCK, seed)
+    x = synth.noise(NCHAN, BLOCK, seed) if dtype != "c16" else np.ones((NCHAN, BLOCK), np.float32)
     for _ in range(16):
         d = int(g.integers(min(25, delay.shape[0] - 1), min(601, delay.shape[0])))
         t = int(g.integers(0, BLOCK - int(delay[d].max()) - 200))
@@ -70,6 +81,8 @@ def make_block(seed, delay, max_delay, dtype="f32"):
         return synth.to_bf16_bits(x)
     if dtype == "u8":
         return synth.to_u8(x * 16.0 + 128.0)
+    if dtype == "c16":
+        return synth.complex_voltage(np.maximum(x, 0.05), seed + 11, sigma=30.0)
     return x
 
 
@@ -404,7 +417,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--dtype", default=None, choices=["f32", "f16", "bf16", "u8"],
+    ap.add_argument("--dtype", default=None, choices=["f32", "f16", "bf16", "u8", "c16"],
                     help="sample storage format (default: f32 for the metric's stream workload, binary16 for "
                          "batch8)")
     ap.add_argument("--workload", default="stream", choices=["stream", "batch8", "serve32"],
@@ -448,7 +461,7 @@ def main():
     beam = tp.tp_beam_open(e, plan, BLOCK, 1 << 20)
 
     host = [make_block(2000 + 17 * rank + i, delays, max_delay, args.dtype) for i in range(NBUF)]
-    dev_blocks = [torch.from_numpy(h.view(np.int16) if h.dtype == np.uint16 else h).to(dev) for h in host]
+    dev_blocks = [torch.from_numpy(_raw(h)).to(dev) for h in host]
     # first block of the stream fills the overlap tail; not timed
     tp.tp_push_block(e, beam, dev_blocks[0])
     tp.tp_dedisperse(e, beam)
@@ -522,10 +535,11 @@ def main():
     e2e = None
     if not args.no_e2e:
         pinned = []
-        tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.int16, "u8": torch.uint8}[args.dtype]
+        tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.int16, "u8": torch.uint8,
+               "c16": torch.int32}[args.dtype]
         for h in host:
             t = torch.empty(h.shape, dtype=tdt, pin_memory=True)
-            t.numpy()[...] = h.view(t.numpy().dtype)
+            t.numpy()[...] = _raw(h).view(t.numpy().dtype)
             pinned.append(t)
         cand_buf_cap = 1 << 20
         ncand = []
@@ -566,7 +580,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_DERIVED,
             "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("FP32", {"f32": "FP32", "f16": "binary16", "bf16": "bfloat16",
-                                                               "u8": "8-bit"}[args.dtype]),
+                                                               "u8": "8-bit",
+                                                               "c16": "complex int16 voltages detected as power"
+                                                               }[args.dtype]),
                        "nchan": NCHAN, "ndm": len(DMS), "block": BLOCK,
                        "overlap": int(max_delay), "beams_per_gpu": 1,
                        "l2": "inputs larger than L2 (562 MB window per block, 3 distinct blocks cycled)",

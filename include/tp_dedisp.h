@@ -53,6 +53,10 @@ extern "C" {
 #define TP_F16 1  /* IEEE binary16; FP32 accumulation                          */
 #define TP_BF16 2 /* bfloat16; FP32 accumulation                               */
 #define TP_F32 3  /* IEEE binary32; FP32 accumulation                          */
+#define TP_C16 4  /* complex voltage, int16 real then int16 imaginary part (4 bytes
+                     a sample): detected as power |v|^2 = re^2 + im^2 on load by the
+                     statistics and staging kernels (Sec. 2, "power calculation";
+                     Sec. 1.1: 16 bits per complex component); FP32 accumulation */
 
 /* ---- bandpass statistics modes ---------------------------------------------- */
 #define TP_STATS_BLOCK 0    /* measured on each block's window (default)       */

@@ -19,7 +19,9 @@ import numpy as np
 
 from . import build as _build
 
-DTYPE_CODES = {"u8": 0, "f16": 1, "bf16": 2, "f32": 3}
+DTYPE_CODES = {"u8": 0, "f16": 1, "bf16": 2, "f32": 3, "c16": 4}
+# complex voltage samples: int16 real part, then int16 imaginary part
+C16 = np.dtype([("re", "<i2"), ("im", "<i2")])
 
 STATS_BLOCK = 0
 STATS_EXTERNAL = 1
@@ -100,7 +102,7 @@ def _c(a, dt):
 
 def _input(x, dtype):
     code = DTYPE_CODES[dtype]
-    want = {"u8": np.uint8, "f16": np.float16, "bf16": np.uint16, "f32": np.float32}[dtype]
+    want = {"u8": np.uint8, "f16": np.float16, "bf16": np.uint16, "f32": np.float32, "c16": C16}[dtype]
     x = np.ascontiguousarray(x)
     if x.dtype != want:
         raise TypeError(f"dtype {dtype} needs a {np.dtype(want)} array, got {x.dtype}")
@@ -286,7 +288,7 @@ def dedisperse_points(x, dtype, stats, chunk_flag, spec_flag, W, delay, d_idx, t
     args = (_ptr(x), code, nchan, nsamp, nsamp, _ptr(stats["b"]), _ptr(cf), _ptr(sf), W,
             _ptr(delay), _ptr(d_idx), _ptr(t_idx), n)
     lib().orc_dedisperse_points_float(*args, _ptr(out))
-    if dtype == "f32":
+    if dtype in ("f32", "c16"):
         lib().orc_abs_mass_points_float(*args, _ptr(mass))
     else:  # FP32 accumulation of the stored 16-bit samples: bounded by sum |x~|
         lib().orc_stored_mass_points(*args, _ptr(mass))

@@ -43,6 +43,9 @@
  *   R8  the detection threshold of Sec. 2.3 is (D - mu_d) >= nsigma * sigma_d
  *       on each dedispersed series, with sigma_d the population standard
  *       deviation of the series; a series with sigma_d = 0 yields nothing.
+ *   R12 complex voltages (Sec. 1.1: 16 bits per complex component) are detected
+ *       as power |v|^2 = re^2 + im^2 ("power calculation", Sec. 2); the power
+ *       series then takes the binary32 path (bandpass value mu_c itself).
  *   R11 post-processing (Sec. 2.2.3), optional: the median filter of Eq. 2
  *       replaces y_m by the median of the w = 2h + 1 values centred on m
  *       (odd w; positions beyond the ends of the block's series take the end
@@ -62,6 +65,7 @@
 #define ORC_F16 1
 #define ORC_BF16 2
 #define ORC_F32 3
+#define ORC_C16 4 /* complex voltage, int16 real and imaginary parts */
 
 #define ORC_STATS_BLOCK 0
 #define ORC_STATS_EXTERNAL 1
@@ -115,6 +119,12 @@ static double sample(const void *x, int dtype, int64_t i) {
     return half_bits_to_double(((const uint16_t *)x)[i]);
   case ORC_BF16:
     return bf16_bits_to_double(((const uint16_t *)x)[i]);
+  case ORC_C16: {
+    /* power of the complex voltage (R12), exact in binary64 */
+    const double re = (double)((const int16_t *)x)[2 * i];
+    const double im = (double)((const int16_t *)x)[2 * i + 1];
+    return re * re + im * im;
+  }
   default:
     return (double)((const float *)x)[i];
   }

@@ -34,7 +34,8 @@ TP_EBOUNDS = -9
 TP_EOVERFLOW = -10
 
 TP_U8, TP_F16, TP_BF16, TP_F32 = 0, 1, 2, 3
-DTYPES = {"u8": TP_U8, "f16": TP_F16, "bf16": TP_BF16, "f32": TP_F32}
+TP_C16 = 4
+DTYPES = {"u8": TP_U8, "f16": TP_F16, "bf16": TP_BF16, "f32": TP_F32, "c16": TP_C16}
 TP_STATS_BLOCK, TP_STATS_EXTERNAL = 0, 1
 
 # Every entry point of include/tp_dedisp.h (checked by the tests).

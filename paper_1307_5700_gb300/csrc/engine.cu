@@ -43,7 +43,8 @@ size_t dtype_size(int dtype) {
     case TP_U8: return 1;
     case TP_F16:
     case TP_BF16: return 2;
-    case TP_F32: return 4;
+    case TP_F32:
+    case TP_C16: return 4;
     default: return 0;
   }
 }
@@ -56,7 +57,7 @@ int staged_bytes_fmt(int fmt) { return fmt == 4 ? 4 : 2; }
 
 // the kernel-shape staging formats (KernelShape::FMT) a dtype can use: its
 // own, and FP32 staging for 16-bit float data
-int staged_format(int dtype) { return dtype == TP_F32 ? 4 : (dtype == TP_U8 ? 3 : 2); }
+int staged_format(int dtype) { return dtype == TP_F32 || dtype == TP_C16 ? 4 : (dtype == TP_U8 ? 3 : 2); }
 bool format_ok(int dtype, int fmt) {
   return fmt == staged_format(dtype) || (fmt == 4 && (dtype == TP_F16 || dtype == TP_BF16));
 }

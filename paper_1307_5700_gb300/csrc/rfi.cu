@@ -48,6 +48,22 @@ __device__ __forceinline__ float load_as_float<TP_BF16>(const void* x, int64_t i
   return __uint_as_float((unsigned)h << 16);
 }
 
+// Power |v|^2 = re^2 + im^2 of a complex voltage sample (int16 real part in
+// the low half, imaginary in the high half): exact in 32-bit unsigned
+// integers, one rounding to FP32 (none below 2^24).
+__device__ __forceinline__ float c16_power(int v) {
+  const int re = (short)(v & 0xffff), im = v >> 16;
+  return (float)((unsigned)(re * re) + (unsigned)(im * im));
+}
+template <>
+__device__ __forceinline__ float load_as_float<TP_C16>(const void* x, int64_t i) {
+  return c16_power(__ldg(static_cast<const int*>(x) + i));
+}
+
+// sample formats staged as FP32 y = x - mu (binary32 data, complex-voltage power)
+template <int DT>
+constexpr bool kStagedF32 = DT == TP_F32 || DT == TP_C16;
+
 // value of 16-bit storage bits (exact in FP32)
 template <int DT>
 __device__ __forceinline__ float bits_to_float(unsigned short h) {
@@ -111,6 +127,9 @@ __device__ __forceinline__ void load4(const void* x, int64_t i, int64_t lim, flo
     if constexpr (DT == TP_F32) {
       const float4 v = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(x) + i));
       e[0] = v.x - p, e[1] = v.y - p, e[2] = v.z - p, e[3] = v.w - p;
+    } else if constexpr (DT == TP_C16) {
+      const int4 v = __ldg(reinterpret_cast<const int4*>(static_cast<const int*>(x) + i));
+      e[0] = c16_power(v.x) - p, e[1] = c16_power(v.y) - p, e[2] = c16_power(v.z) - p, e[3] = c16_power(v.w) - p;
     } else {
       const uint2 v = __ldg(reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(x) + i));
       const unsigned short h[4] = {(unsigned short)(v.x & 0xffff), (unsigned short)(v.x >> 16),
@@ -269,7 +288,7 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
       const float hi = (float)mu;
       a.mu_hi[c] = hi;
       a.mu_lo[c] = (float)(mu - (double)hi);
-      if (DT != TP_F32) a.b16[c] = storage_bits(DT, mu);
+      if (DT == TP_F16 || DT == TP_BF16) a.b16[c] = storage_bits(DT, mu);
       m = mu - (double)p;
     }
     s_m = m;
@@ -399,7 +418,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a,
   if (threadIdx.x == 0) *a.spec_nflag = 0;
   // sum of the bandpass values (16-bit and 8-bit staging subtract it once)
   double bs = 0.0;
-  if (a.dtype != TP_F32)
+  if (a.dtype == TP_U8 || a.dtype == TP_F16 || a.dtype == TP_BF16)
     for (int c = threadIdx.x; c < a.nchan; c += kThreads)
       bs += a.dtype == TP_U8 ? (double)a.bint[c] : storage_value(a.dtype, a.b16[c]);
   s_b[threadIdx.x] = bs;
@@ -461,6 +480,9 @@ __device__ __forceinline__ void load_quad(const void* x, int64_t i, int64_t vali
     if constexpr (DT == TP_F32) {
       const float4 f = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(x) + i));
       v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
+    } else if constexpr (DT == TP_C16) {
+      const int4 f = __ldg(reinterpret_cast<const int4*>(static_cast<const int*>(x) + i));
+      v[0] = c16_power(f.x), v[1] = c16_power(f.y), v[2] = c16_power(f.z), v[3] = c16_power(f.w);
     } else if constexpr (DT == TP_U8) {
       const unsigned w = __ldg(reinterpret_cast<const unsigned*>(static_cast<const unsigned char*>(x) + i));
 #pragma unroll
@@ -600,8 +622,10 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   if (valid == 4) {
     // full 4-sample quads: raw loads of 4 channels (c, c + 32, c + 64,
     // c + 96) issued together, then substitution and stores
-    using Raw = typename std::conditional<DT == TP_F32, float4,
-                                          typename std::conditional<DT == TP_U8, unsigned, uint2>::type>::type;
+    using Raw = typename std::conditional<
+        DT == TP_F32, float4,
+        typename std::conditional<DT == TP_C16, int4,
+                                  typename std::conditional<DT == TP_U8, unsigned, uint2>::type>::type>::type;
     for (int c0 = g; c0 < a.nchan; c0 += 32 * 4) {
       Raw raw[4];
 #pragma unroll
@@ -619,8 +643,13 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
         bool fl[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) fl[r] = sflag[r] || (any && cf[kk[r]]);
-        if constexpr (DT == TP_F32) {
-          const float v[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
+        if constexpr (kStagedF32<DT>) {
+          float v[4];
+          if constexpr (DT == TP_C16)
+            v[0] = c16_power(raw[u].x), v[1] = c16_power(raw[u].y), v[2] = c16_power(raw[u].z),
+            v[3] = c16_power(raw[u].w);
+          else
+            v[0] = raw[u].x, v[1] = raw[u].y, v[2] = raw[u].z, v[3] = raw[u].w;
           const float mh = a.mu_hi[c], ml = a.mu_lo[c];
           float o[4];
 #pragma unroll
@@ -664,7 +693,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
     bool fl[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) fl[r] = sflag[r] || (any && cf[kk[r]]);
-    if constexpr (DT == TP_F32) {
+    if constexpr (kStagedF32<DT>) {
       float v[4];
       load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
       const float mh = a.mu_hi[c], ml = a.mu_lo[c];
@@ -786,6 +815,8 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void*
     chunk_stats_float<TP_F16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
   else if (a.dtype == TP_BF16)
     chunk_stats_float<TP_BF16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
+  else if (a.dtype == TP_C16)
+    chunk_stats_float<TP_C16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
   else
     chunk_stats_float<TP_F32><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
   cudaError_t e = cudaGetLastError();
@@ -802,7 +833,9 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void*
   if (e != cudaSuccess) return e;
   spectrum_threshold_kernel<<<1, kThreads, 0, s>>>(a, ext_thr);
   const unsigned blocks = (unsigned)((a.nsamp + 31) / 32);
-  if (a.dtype == TP_U8)
+  if (a.dtype == TP_C16)
+    spectrum_substitute_kernel<TP_C16><<<blocks, kThreads, 0, s>>>(a, y, ypitch);
+  else if (a.dtype == TP_U8)
     spectrum_substitute_kernel<TP_U8><<<blocks, kThreads, 0, s>>>(a, y, ypitch);
   else if (a.dtype == TP_F16)
     spectrum_substitute_kernel<TP_F16><<<blocks, kThreads, 0, s>>>(a, y, ypitch);
@@ -823,6 +856,8 @@ cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_
     chunk_stats_float<TP_F16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
   else if (a.dtype == TP_BF16)
     chunk_stats_float<TP_BF16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
+  else if (a.dtype == TP_C16)
+    chunk_stats_float<TP_C16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
   else
     chunk_stats_float<TP_F32><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
   cudaError_t e = cudaGetLastError();

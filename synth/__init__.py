@@ -113,6 +113,30 @@ def bf16_bits_to_f32(h):
     return (h.astype(np.uint32) << 16).view(np.float32)
 
 
+# complex voltage samples of the beamformer output (Sec. 1.1: 16 bits for each
+# complex component): int16 real part, then int16 imaginary part
+C16 = np.dtype([("re", "<i2"), ("im", "<i2")])
+
+
+def complex_voltage(envelope, seed, sigma=20.0):
+    """Complex int16 voltages shaped like ``envelope`` (nchan, nsamp): each
+    component is N(0, 1) * sigma * sqrt(envelope), rounded and clipped to
+    int16, so the expected power follows the envelope (a pulse or an RFI
+    burst drawn into the envelope raises the voltage variance there)."""
+    g = rng(seed)
+    amp = np.sqrt(np.maximum(np.asarray(envelope, np.float32), np.float32(0.0)))
+    amp *= np.float32(sigma)
+    out = np.empty(amp.shape + (2,), np.int16)
+    v = np.empty(amp.shape, np.float32)
+    for k in range(2):  # real, then imaginary part
+        g.standard_normal(amp.shape, dtype=np.float32, out=v)
+        v *= amp
+        np.rint(v, out=v)
+        np.clip(v, -32768, 32767, out=v)
+        out[..., k] = v
+    return out.view(C16)[..., 0]
+
+
 # ---- workload recipes --------------------------------------------------------------
 # Band of the paper's receiver (Sec. 1.1): 1024 channels over 398-418 MHz, 51.2 us.
 BAND_1024 = dict(nchan=1024, f_lo=398.0, bw=20.0, t_samp=51.2e-6)

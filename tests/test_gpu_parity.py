@@ -39,6 +39,8 @@ def _mass_all(x, dtype, st, cf, sf, W, delay, T):
 def _as_f64(x, dtype):
     if dtype == "bf16":
         return synth.bf16_bits_to_f32(x).astype(np.float64)
+    if dtype == "c16":  # power of the complex voltages
+        return x["re"].astype(np.float64) ** 2 + x["im"].astype(np.float64) ** 2
     return x.astype(np.float64)
 
 
@@ -253,6 +255,54 @@ def test_every_shape_elementwise(dtype):
                 raise AssertionError(f"shape {sh}: {exc}") from exc
     finally:
         g.close()
+
+
+def _voltage_block(nchan, nsamp, od, seed):
+    env = np.ones((nchan, nsamp), np.float32)
+    d = min(40, od.shape[0] - 1)
+    synth.add_pulse(env, od[d].astype(np.float64) + nsamp // 2, 20.0, 2.5)
+    env[33:35, 1000:1700] += 30.0     # narrowband RFI
+    env[:, 3333] += 10.0              # broadband spike
+    return synth.complex_voltage(env, seed, sigma=30.0)
+
+
+def test_power_detection_c16():
+    """Complex int16 voltages detected as power on the device, against the
+    oracle (float bars: masks identical, D within 1e-5 of the summed
+    magnitude, candidates outside the borderline band)."""
+    nchan, nsamp = 192, 7001
+    dms = np.arange(62) * 0.2
+    od, dmax = O.delay_table(nchan, 398.0, 20.0, 51.2e-6, dms)
+    x = _voltage_block(nchan, nsamp, od, 8123)
+    rfi = O.RfiParams()
+    g, o, _ = run_both(x, "c16", nchan, 398.0, 20.0, 51.2e-6, dms, rfi, nsigma=5.0)
+    assert o["chunk_flag"].any() and o["n_candidates"] > 0
+    check_block(g, o, x, "c16", od, rfi, 5.0)
+
+
+def test_power_detection_equals_float_on_power():
+    """The device's power of complex voltages (exact below 2^24) makes the
+    whole chain bit-identical to the binary32 chain on that power."""
+    nchan, nsamp = 160, 6000
+    dms = np.arange(40) * 0.4
+    od, dmax = O.delay_table(nchan, 398.0, 20.0, 51.2e-6, dms)
+    x = _voltage_block(nchan, nsamp, od, 8124)
+    p = (x["re"].astype(np.int64) ** 2 + x["im"].astype(np.int64) ** 2)
+    assert p.max() < 2 ** 24
+    pf = p.astype(np.float32)
+    out = []
+    for dtype, data in (("c16", x), ("f32", pf)):
+        gb = GpuBeam(nchan, 398.0, 20.0, 51.2e-6, dms, dtype, nsigma=4.5, cap=1 << 18)
+        try:
+            tp.tp_plan_set_shape(gb.plan, int(np.nonzero(tp.tp_plan_shapes(gb.plan)[1])[0][-1]))
+            out.append(gb.run(data))
+        finally:
+            gb.close()
+    a, b = out
+    for k in ("D", "mu", "sigma", "chunk_flag", "chunk_raw", "spec_flag", "row_mu", "row_sigma"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["n_candidates"] == b["n_candidates"] > 0
+    assert np.array_equal(a["candidates"], b["candidates"])
 
 
 def test_degenerate_dm0_single_channel():
