@@ -179,7 +179,11 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
   const float p = s_pivot;
   const bool vec = (a.W % 128) == 0;
 
-  double tot_s = 0.0, tot_q = 0.0;  // lane-0 accumulators of this warp
+  // W <= 256: every chunk is one FP32 sub-chunk and its sums are stored as
+  // float2 (no FP64 in the loops: FP64 is a small fraction of the FP32 rate
+  // on this part); wider chunks accumulate sub-chunks in FP64 (double2)
+  const bool single = a.W <= 256;
+  float2* sums32 = reinterpret_cast<float2*>(chunk_sums) + (int64_t)c * a.nchunk;
   // W = 256 (one sub-chunk per chunk): kChunkBatch full chunks per warp and
   // iteration, every load issued before the sums (the same FP32 summation
   // order per chunk as the general loop below); the rest (a short last
@@ -209,12 +213,7 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
           }
         fs = warp_sum_f(fs);
         fq = warp_sum_f(fq);
-        const double cs = 0.0 + (double)fs, cq = 0.0 + (double)fq;
-        if (lane == 0) {
-          chunk_sums[(int64_t)c * a.nchunk + k + u * kWarps] = make_double2(cs, cq);
-          tot_s += cs;
-          tot_q += cq;
-        }
+        if (lane == 0) sums32[k + u * kWarps] = make_float2(fs, fq);
       }
     }
     kstart = k;
@@ -250,18 +249,34 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
       }
       fs = warp_sum_f(fs);
       fq = warp_sum_f(fq);
-      cs += (double)fs;
-      cq += (double)fq;
+      if (single) {
+        if (lane == 0) sums32[k] = make_float2(fs, fq);
+      } else {
+        cs += (double)fs;
+        cq += (double)fq;
+      }
     }
-    if (lane == 0) {
-      chunk_sums[(int64_t)c * a.nchunk + k] = make_double2(cs, cq);
-      tot_s += cs;
-      tot_q += cq;
-    }
+    if (!single && lane == 0) chunk_sums[(int64_t)c * a.nchunk + k] = make_double2(cs, cq);
   }
-  if (lane == 0) {
-    s_tot[0][warp] = tot_s;
-    s_tot[1][warp] = tot_q;
+  __syncthreads();
+  // per-warp totals over the chunks k = w, w + kWarps, ... in that order (the
+  // order the warps summed them), one thread per warp slot
+  auto chunk_sum = [&](int k) -> double2 {
+    if (single) {
+      const float2 f = sums32[k];
+      return make_double2((double)f.x, (double)f.y);
+    }
+    return chunk_sums[(int64_t)c * a.nchunk + k];
+  };
+  if (threadIdx.x < kWarps) {
+    double tot_s = 0.0, tot_q = 0.0;
+    for (int k = threadIdx.x; k < a.nchunk; k += kWarps) {
+      const double2 v = chunk_sum(k);
+      tot_s += 0.0 + v.x;
+      tot_q += 0.0 + v.y;
+    }
+    s_tot[0][threadIdx.x] = tot_s;
+    s_tot[1][threadIdx.x] = tot_q;
   }
   __syncthreads();
 
@@ -300,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
   for (int k = threadIdx.x; k < a.nchunk; k += kThreads) {
     const int64_t lo = (int64_t)k * a.W;
     const int64_t n = (lo + a.W < a.nsamp ? lo + a.W : a.nsamp) - lo;
-    const double2 cs = chunk_sums[(int64_t)c * a.nchunk + k];
+    const double2 cs = chunk_sum(k);
     const double e = cs.x - (double)n * m;
     a.chunk_raw[(int64_t)c * a.nchunk + k] = (uint8_t)(e > tsig * sqrt((double)n));
   }
