@@ -73,6 +73,7 @@ def lib():
             "orc_candidates_float": (_i64, [_p, _i, _i64, _p, _p, _d, _i, _i64, _p, _i64]),
             "orc_candidates_int": (_i64, [_p, _i, _i64, _p, _p, _d, _i, _i64, _p, _i64]),
             "orc_median_float": (None, [_p, _i, _i64, _i, _p]),
+            "orc_channel_mask_fit": (None, [_p, _i, _i, _i64, _i64, _i, _d, _i, _p, _d, _p, _p]),
             "orc_median_int": (None, [_p, _i, _i64, _i, _p]),
             "orc_detrend_float": (None, [_p, _i, _i64, _p, _p, _p]),
             "orc_detrend_int": (None, [_p, _i, _i64, _p, _p, _p, _p]),
@@ -186,6 +187,62 @@ def external_stats(dtype, mu, sigma):
     return st
 
 
+def bandpass_fit(mu, order, tau_mask):
+    """Fitted bandpass of Sec. 2.2.1 "Bandpass Correction", reading R13.
+
+    1. The averaged bandpass is the block means mu_c.
+    2. High-power channels are masked before the fit: the local excess
+       e_c = mu_c - (mu_{c-1} + mu_{c+1}) / 2 (one neighbour at the band
+       edges) above tau_mask times 1.4826 * median_c |e_c| (the lower middle
+       element of the sorted values); a masked channel takes the mean of its
+       nearest unmasked neighbours on each side (one side at the edges).
+    3. Least squares with Legendre polynomials P_0 .. P_order of
+       x_c = (2c - (N - 1)) / (N - 1) (x = 0 for N = 1) gives b_c.
+    4. RMSE = sqrt(mean_c (b_c - interpolated mu_c)^2).
+    Returns dict(b, rmse, masked, mu_interp)."""
+    mu = _c(mu, np.float64)
+    n = len(mu)
+    if n == 1:
+        e = np.zeros(1)
+    else:
+        e = np.empty(n)
+        e[0] = mu[0] - mu[1]
+        e[-1] = mu[-1] - mu[-2]
+        e[1:-1] = mu[1:-1] - (mu[:-2] + mu[2:]) / 2.0
+    srt = np.sort(np.abs(e))
+    scale = 1.4826 * srt[(n - 1) // 2]
+    masked = e > tau_mask * scale
+    if masked.all():
+        masked[:] = False
+    mi = mu.copy()
+    good = np.nonzero(~masked)[0]
+    for c in np.nonzero(masked)[0]:
+        left = good[good < c]
+        right = good[good > c]
+        vals = ([mu[left[-1]]] if len(left) else []) + ([mu[right[0]]] if len(right) else [])
+        mi[c] = sum(vals) / len(vals)
+    xc = np.zeros(n) if n == 1 else (2.0 * np.arange(n) - (n - 1)) / (n - 1)
+    V = np.polynomial.legendre.legvander(xc, order)
+    coef = np.linalg.lstsq(V, mi, rcond=None)[0]
+    b = V @ coef
+    rmse = float(np.sqrt(np.mean((b - mi) ** 2)))
+    return dict(b=b, rmse=rmse, masked=masked, mu_interp=mi, coef=coef)
+
+
+def fit_stats(x, dtype, order, tau_mask):
+    """Block statistics with the fitted bandpass (R13): mu, sigma as measured,
+    b = the fit (8-bit data: the integer floor(fit + 1/2); 16-bit data: the fit
+    in the storage format), plus the fit products."""
+    st = bandpass(x, dtype)
+    fit = bandpass_fit(st["mu"], order, tau_mask)
+    out = dict(mu=st["mu"], sigma=st["sigma"], external=True, fit=fit)
+    if dtype == "u8":
+        out["b"] = np.floor(fit["b"] + 0.5).astype(np.int64)
+    else:
+        out["b"] = storage_bandpass(dtype, fit["b"])
+    return out
+
+
 def channel_mask(x, dtype, stats, rfi):
     x, code = _input(x, dtype)
     nchan, nsamp = x.shape
@@ -196,7 +253,11 @@ def channel_mask(x, dtype, stats, rfi):
     if not rfi.enable_channel:
         return raw, flag
     dil = int(bool(rfi.dilate_channels))
-    if dtype == "u8" and not stats["external"]:
+    if "fit" in stats:
+        lib().orc_channel_mask_fit(_ptr(x), code, nchan, nsamp, nsamp, W, rfi.tau_channel, dil,
+                                   _ptr(_c(stats["fit"]["b"], np.float64)), stats["fit"]["rmse"], _ptr(raw),
+                                   _ptr(flag))
+    elif dtype == "u8" and not stats["external"]:
         lib().orc_channel_mask_u8(_ptr(x), nchan, nsamp, nsamp, W, rfi.tau_channel, dil,
                                   _ptr(stats["S"]), _ptr(stats["V"]), _ptr(raw), _ptr(flag))
     elif dtype == "u8":
@@ -223,8 +284,10 @@ def spectrum_mask(x, dtype, stats, rfi, chunk_flag):
         lib().orc_spectrum_mask_u8_ext(_ptr(x), nchan, nsamp, nsamp, W, rfi.tau_spectrum,
                                        _ptr(stats["b"]), _ptr(stats["sigma"]), _ptr(cf), _ptr(spec))
     else:
+        # the spectrum stage subtracts the bandpass: the fitted one when fitted
+        ref = _c(stats["fit"]["b"], np.float64) if "fit" in stats else stats["mu"]
         lib().orc_spectrum_mask_float(_ptr(x), code, nchan, nsamp, nsamp, W, rfi.tau_spectrum,
-                                      _ptr(stats["mu"]), _ptr(stats["sigma"]), _ptr(cf), _ptr(spec))
+                                      _ptr(ref), _ptr(stats["sigma"]), _ptr(cf), _ptr(spec))
     return spec
 
 
@@ -404,15 +467,19 @@ def post_process(D, median_width=1, detrend_on=False, nsigma=5.0, beam=0, t0=0, 
 # ---- the whole block -------------------------------------------------------------
 
 def search_block(x, dtype, delay, max_delay, rfi=None, nsigma=5.0, beam=0, t0=0, stats=None,
-                 cand_cap=None, keep_series=True):
+                 cand_cap=None, keep_series=True, fit=None):
     """Run A1-A7 on one block window x (nchan, nsamp).  ``stats`` replaces the
-    measured bandpass when given (see ``external_stats``).  Returns every
+    measured bandpass when given (see ``external_stats``); ``fit`` = (order,
+    tau_mask) uses the fitted bandpass (``fit_stats``).  Returns every
     intermediate product."""
     rfi = rfi or RfiParams()
     x, _ = _input(x, dtype)
     nchan, nsamp = x.shape
     T = nsamp - max_delay
-    st = stats if stats is not None else bandpass(x, dtype)
+    if fit is not None:
+        st = fit_stats(x, dtype, fit[0], fit[1])
+    else:
+        st = stats if stats is not None else bandpass(x, dtype)
     raw, cflag = channel_mask(x, dtype, st, rfi)
     sflag = spectrum_mask(x, dtype, st, rfi, cflag)
     D = dedisperse(x, dtype, st, cflag, sflag, rfi.chunk_width, delay, T)

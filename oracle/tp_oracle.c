@@ -46,6 +46,11 @@
  *   R12 complex voltages (Sec. 1.1: 16 bits per complex component) are detected
  *       as power |v|^2 = re^2 + im^2 ("power calculation", Sec. 2); the power
  *       series then takes the binary32 path (bandpass value mu_c itself).
+ *   R13 optional fitted bandpass (Sec. 2.2.1 "Bandpass Correction"): the block
+ *       means mu_c with high-power channels replaced by their unmasked
+ *       neighbours' mean are fitted by least squares with a polynomial of
+ *       order p; b_c is the fit, and the channel stage compares chunk means
+ *       with b_c + tau_c * RMSE of the fit (see orc_channel_mask_fit).
  *   R11 post-processing (Sec. 2.2.3), optional: the median filter of Eq. 2
  *       replaces y_m by the median of the w = 2h + 1 values centred on m
  *       (odd w; positions beyond the ends of the block's series take the end
@@ -321,6 +326,25 @@ void orc_channel_mask_u8_ext(const uint8_t *x, int nchan, int64_t nsamp, int64_t
       int64_t e = 0;
       for (int64_t t = lo; t < hi; ++t) e += sample_u8(x, (int64_t)c * pitch + t) - b[c];
       raw[(int64_t)c * nchunk + k] = (uint8_t)((double)e > tau * sigma[c] * sqrt((double)(hi - lo)));
+    }
+  dilate(nchan, nchunk, raw, dilate_channels, flag);
+}
+
+/* Channel thresholding against a fitted bandpass (R13, Sec. 2.2.1 "Bandpass
+ * Correction" and Fig. 2): chunk k of channel c exceeds when
+ * sum_t (x - b_c) > tau * rmse * n_k, i.e. its mean lies above the fitted
+ * bandpass b_c by more than tau times the fit's RMSE; any sample format
+ * (8-bit samples are exact in binary64). */
+void orc_channel_mask_fit(const void *x, int dtype, int nchan, int64_t nsamp, int64_t pitch, int W,
+                          double tau, int dilate_channels, const double *b, double rmse, uint8_t *raw,
+                          uint8_t *flag) {
+  const int nchunk = (int)((nsamp + W - 1) / W);
+  for (int c = 0; c < nchan; ++c)
+    for (int k = 0; k < nchunk; ++k) {
+      int64_t lo = (int64_t)k * W, hi = lo + W < nsamp ? lo + W : nsamp;
+      double e = 0.0;
+      for (int64_t t = lo; t < hi; ++t) e += sample(x, dtype, (int64_t)c * pitch + t) - b[c];
+      raw[(int64_t)c * nchunk + k] = (uint8_t)(e > tau * rmse * (double)(hi - lo));
     }
   dilate(nchan, nchunk, raw, dilate_channels, flag);
 }
