@@ -158,6 +158,22 @@ int tp_plan_info(const tp_plan *p, int *nchan, int *ndm, int *max_delay, int *dt
  * out-of-range width. */
 int tp_plan_set_postprocess(tp_plan *p, int median_width, int detrend);
 
+/* Fitted bandpass (Sec. 2.2.1 "Bandpass Correction", with Fig. 2), in place
+ * of the plain block mean: order = p (0..8; -1 turns it off).  Per block the
+ * channel means are taken, channels whose mean exceeds the mean of its two
+ * neighbours (one at the band edges) by more than tau_mask * 1.4826 * the
+ * median absolute excess are masked and replaced by the mean of their
+ * nearest unmasked neighbours, the result is fitted by least squares with
+ * Legendre polynomials of the normalised channel index, and the fit b_c
+ * replaces the mean as the bandpass: a W_c chunk is flagged when its mean
+ * exceeds b_c + tau_channel * RMSE (the fit's root-mean-square error against
+ * the interpolated means, so tau_channel counts in RMSE units), flagged
+ * samples take b_c, and the spectrum stage subtracts b_c (8-bit data: the
+ * integer floor(b_c + 1/2); 16-bit data: b_c in the storage format).  Needs
+ * block statistics (TP_STATS_BLOCK) and at most 8192 channels (TP_EINVAL);
+ * call before any beam of the plan is opened (TP_EBUSY). */
+int tp_plan_set_bandpass_fit(tp_plan *p, int order, double tau_mask);
+
 /* Copy the delay table (ndm x nchan int32, row = DM) to host memory `out`
  * holding `count` elements.  Blocks. */
 int tp_get_delay_table(const tp_plan *p, int32_t *out, size_t count);
@@ -265,6 +281,11 @@ int tp_get_processed_series(tp_engine *e, int beam, void *out, size_t bytes, int
  * any pointer may be NULL): the line is mean + beta (2t - (T - 1)).  Blocks;
  * TP_EINVAL when the plan does not detrend, TP_ENOTREADY before detection. */
 int tp_get_detrend(tp_engine *e, int beam, double *mean, double *beta, double *sigma, int ndm);
+
+/* The fitted bandpass of the beam's current block: b_c (nchan doubles), the
+ * channels masked before the fit (nchan bytes, 1 = masked) and the fit's RMSE
+ * (any pointer may be NULL).  Blocks; TP_EINVAL when the plan does not fit. */
+int tp_get_bandpass_fit(tp_engine *e, int beam, double *bfit, uint8_t *masked, double *rmse, int nchan);
 
 /* ---- kernel shapes and autotuning -------------------------------------------------
  * The dedispersion kernel is compiled for several register tilings ("shapes":

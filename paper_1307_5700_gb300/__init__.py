@@ -50,7 +50,7 @@ EXPORTS = (
     "tp_run_ready", "tp_engine_stream", "tp_server_create", "tp_server_add_stream", "tp_server_submit",
     "tp_server_end_stream", "tp_server_run", "tp_server_results", "tp_server_candidates", "tp_server_destroy",
     "tp_beam_rewind", "tp_autotune_batch", "tp_plan_set_postprocess", "tp_get_processed_series",
-    "tp_get_detrend",
+    "tp_get_detrend", "tp_plan_set_bandpass_fit", "tp_get_bandpass_fit",
 )
 
 
@@ -115,6 +115,8 @@ _SIGS = {
     "tp_plan_set_postprocess": (_i, [_vp, _i, _i]),
     "tp_get_processed_series": (_i, [_vp, _i, _vp, ctypes.c_size_t, _i]),
     "tp_get_detrend": (_i, [_vp, _i, _vp, _vp, _vp, _i]),
+    "tp_plan_set_bandpass_fit": (_i, [_vp, _i, _d]),
+    "tp_get_bandpass_fit": (_i, [_vp, _i, _vp, _vp, _vp, _i]),
     "tp_channel_stats_noalloc": (_i, [_vp, _i, _i, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                      _vp]),
     "tp_run_ready": (_i, [_vp, _i, _vp]),
@@ -408,6 +410,21 @@ def tp_get_detrend(e, beam, ndm):
     sigma = np.empty(ndm, np.float64)
     _check(lib().tp_get_detrend(e, beam, mean.ctypes.data, beta.ctypes.data, sigma.ctypes.data, ndm))
     return mean, beta, sigma
+
+
+def tp_plan_set_bandpass_fit(p, order, tau_mask=5.0):
+    """Fitted bandpass of polynomial order ``order`` (-1: off) for the plan's
+    beams (before any beam is opened; see tp_dedisp.h)."""
+    return _check(lib().tp_plan_set_bandpass_fit(p, int(order), float(tau_mask)))
+
+
+def tp_get_bandpass_fit(e, beam, nchan):
+    """(b_c, masked channels, rmse) of the beam's current block."""
+    b = np.empty(nchan, np.float64)
+    m = np.empty(nchan, np.uint8)
+    r = ctypes.c_double()
+    _check(lib().tp_get_bandpass_fit(e, beam, b.ctypes.data, m.ctypes.data, ctypes.byref(r), nchan))
+    return b, m.astype(bool), r.value
 
 
 def tp_autotune_batch(e, reps=2):

@@ -166,6 +166,11 @@ struct Beam {
   int* status = nullptr;
   void* D = nullptr;
   void* M = nullptr;          // median-filtered series (plans with median_width > 1)
+  float* pivot = nullptr;     // fitted bandpass buffers
+  double* bfit = nullptr;
+  uint8_t* fit_masked = nullptr;
+  double* fit_work = nullptr;
+  double* rmse = nullptr;
   void* post_part = nullptr;  // post-processing tile sums
   double* row_beta = nullptr;
   void* row_part = nullptr;
@@ -214,6 +219,8 @@ struct tp_plan {
   std::vector<double> dm;
   tp_rfi_params rfi{};
   double nsigma = 5.0;
+  int fit_order = -1;    // fitted bandpass (Sec. 2.2.1): polynomial order, -1 = off
+  double tau_mask = 5.0; // fitted bandpass: high-power channel masking threshold
   int median_width = 1;  // post-processing (Sec. 2.2.3): median filter width, 1 = off
   int detrend = 0;       // post-processing: least-squares detrending
   int32_t* d_delay = nullptr;
@@ -403,6 +410,11 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->spec_bits, (size_t)((nmax + 31) / 32) * 4);
   add((void**)&b->spec_nflag, 4);
   add((void**)&b->spec_thr, 8);
+  add((void**)&b->pivot, nc * 4);
+  add((void**)&b->bfit, nc * 8);
+  add((void**)&b->fit_masked, nc);
+  add((void**)&b->fit_work, nc * 16);
+  add((void**)&b->rmse, 8);
   const size_t yb = (size_t)staged_bytes_alloc(p->dtype);
   add((void**)&b->y, nc * (size_t)ypitch * yb);
   add((void**)&b->b16, nc * 2);
@@ -519,6 +531,14 @@ RfiArgs rfi_args(const tp_plan* p, Beam* b) {
   a.spec_nflag = b->spec_nflag;
   a.spec_thr = b->spec_thr;
   a.stage_f32 = (p->dtype == TP_F16 || p->dtype == TP_BF16) && kShapes[p->shape].FMT == 4;
+  a.fit = p->fit_order >= 0 ? 1 : 0;
+  a.fit_order = p->fit_order;
+  a.tau_mask = p->tau_mask;
+  a.pivot = b->pivot;
+  a.bfit = b->bfit;
+  a.fit_masked = b->fit_masked;
+  a.fit_work = b->fit_work;
+  a.rmse = b->rmse;
   return a;
 }
 
@@ -1436,6 +1456,38 @@ int tp_engine_launches(const tp_engine* e, uint64_t* n) {
 }  // extern "C"
 
 extern "C" {
+
+int tp_plan_set_bandpass_fit(tp_plan* p, int order, double tau_mask) {
+  if (!p) return set_error(TP_EINVAL, "plan is NULL");
+  std::lock_guard<std::recursive_mutex> lk(p->e->mu);
+  if (order < -1 || order > kMaxFitOrder) return set_error(TP_EINVAL, "fit order %d: -1 (off) .. %d", order, kMaxFitOrder);
+  if (order >= 0) {
+    if (!(tau_mask > 0.0) || !std::isfinite(tau_mask)) return set_error(TP_EINVAL, "tau_mask must be > 0");
+    if (p->rfi.stats_mode != TP_STATS_BLOCK) return set_error(TP_EINVAL, "the fit needs block statistics");
+    if (p->nchan > kMaxFitChannels) return set_error(TP_EINVAL, "the fit takes at most %d channels", kMaxFitChannels);
+  }
+  if (p->users > 0) return set_error(TP_EBUSY, "plan is used by %d open beams", p->users);
+  p->fit_order = order;
+  p->tau_mask = tau_mask;
+  return TP_OK;
+}
+
+int tp_get_bandpass_fit(tp_engine* e, int beam, double* bfit, uint8_t* masked, double* rmse, int nchan) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->plan->fit_order < 0) return set_error(TP_EINVAL, "the beam's plan does not fit its bandpass");
+  if (b->state < kDedispersed) return set_error(TP_ENOTREADY, "beam %d has no processed block", beam);
+  if (nchan != b->plan->nchan) return set_error(TP_EINVAL, "nchan %d != %d", nchan, b->plan->nchan);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  if (bfit) TP_CUDA_TRY(cudaMemcpyAsync(bfit, b->bfit, (size_t)nchan * 8, cudaMemcpyDeviceToHost, s));
+  if (masked) TP_CUDA_TRY(cudaMemcpyAsync(masked, b->fit_masked, (size_t)nchan, cudaMemcpyDeviceToHost, s));
+  if (rmse) TP_CUDA_TRY(cudaMemcpyAsync(rmse, b->rmse, 8, cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  return TP_OK;
+}
 
 int tp_plan_set_postprocess(tp_plan* p, int median_width, int detrend) {
   if (!p) return set_error(TP_EINVAL, "plan is NULL");

@@ -308,9 +308,11 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
     }
     s_m = m;
     s_sig = sig;
+    if (a.fit) a.pivot[c] = p;
   }
   __syncthreads();
-  if (!a.enable_channel) return;
+  // with the fitted bandpass the chunk test waits for the fit (fit_chunk_test)
+  if (!a.enable_channel || a.fit) return;
   const double m = s_m, tsig = a.tau_c * s_sig;
   for (int k = threadIdx.x; k < a.nchunk; k += kThreads) {
     const int64_t lo = (int64_t)k * a.W;
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_u8(RfiArgs a, longlong2*
     }
   }
   __syncthreads();
-  if (!a.enable_channel) return;
+  if (!a.enable_channel || a.fit) return;
   const long long N = a.nsamp, S = s_S, V = s_V, b = s_b;
   const bool ext = a.stats_mode == TP_STATS_EXTERNAL;
   const double tsig = ext ? __dmul_rn(a.tau_c, a.sigma[c]) : 0.0;
@@ -449,8 +451,9 @@ __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a,
   }
   double v = 0.0;
   unsigned long long hi = 0, lo = 0;
+  const bool fit = a.fit;
   for (int c = threadIdx.x; c < a.nchan; c += kThreads) {
-    if (a.dtype == TP_U8) {
+    if (a.dtype == TP_U8 && !fit) {
       const unsigned long long V = (unsigned long long)a.V[c];
       hi += V >> 20;
       lo += V & 0xFFFFFull;
@@ -472,7 +475,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a,
   }
   if (threadIdx.x == 0) {
     double tot;
-    if (a.dtype == TP_U8)
+    if (a.dtype == TP_U8 && !fit)
       tot = __dadd_rn(__dmul_rn((double)s_hi[0], 1048576.0), (double)s_lo[0]);
     else
       tot = s_d[0];
@@ -578,7 +581,8 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
 #pragma unroll
       for (int r = 0; r < 4; ++r) s_f[g][4 * q + r] = acc[r] + (double)part[r];
     } else {
-      const bool ext = a.stats_mode == TP_STATS_EXTERNAL;
+      // external or fitted bandpass: sums of x - b_c (integer b_c)
+      const bool ext = a.stats_mode == TP_STATS_EXTERNAL || a.fit;
       int sx[4] = {0, 0, 0, 0};
       long long sS[4] = {0, 0, 0, 0};
       for (int c = g; c < a.nchan; c += 32) {
@@ -777,6 +781,212 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   }
 }
 
+// ---- fitted bandpass (Sec. 2.2.1 "Bandpass Correction") ---------------------------
+//
+// bandpass_fit_kernel (one CTA): local excess of each block mean over its
+// neighbours' mean, e_c = mu_c - (mu_{c-1} + mu_{c+1}) / 2 (one neighbour at
+// the band edges); channels with e_c > tau_mask * 1.4826 * median |e| (the
+// lower middle of the sorted values, from a bitonic sort in shared memory)
+// are masked and take the mean of their nearest unmasked neighbours; the
+// result is fitted by least squares with Legendre polynomials P_0 .. P_p of
+// x_c = (2c - (N - 1)) / (N - 1) (normal equations in binary64, Gaussian
+// elimination with partial pivoting); b_c and the RMSE of the fit go to the
+// beam, and b_c replaces the block mean as the value the spectrum and staging
+// stages subtract (8-bit data: floor(b_c + 1/2); 16-bit data: b_c in the
+// storage format).
+constexpr int kFitThreads = 1024;
+
+__global__ void __launch_bounds__(kFitThreads) bandpass_fit_kernel(RfiArgs a) {
+  extern __shared__ double s_sort[];  // next power of two >= nchan
+  const int N = a.nchan;
+  int P = 1;
+  while (P < N) P <<= 1;
+  const double* mu = a.mu;
+  double* e = a.fit_work;
+  double* mi = a.fit_work + N;
+  for (int c = threadIdx.x; c < P; c += kFitThreads) {
+    double v = INFINITY;
+    if (c < N) {
+      double x;
+      if (N == 1) x = 0.0;
+      else if (c == 0) x = __dsub_rn(mu[0], mu[1]);
+      else if (c == N - 1) x = __dsub_rn(mu[N - 1], mu[N - 2]);
+      else x = __dsub_rn(mu[c], __ddiv_rn(__dadd_rn(mu[c - 1], mu[c + 1]), 2.0));
+      e[c] = x;
+      v = fabs(x);
+    }
+    s_sort[c] = v;
+  }
+  __syncthreads();
+  // bitonic sort of s_sort[0 .. P), ascending
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += kFitThreads) {
+        const int l = i ^ j;
+        if (l > i) {
+          const double x = s_sort[i], y = s_sort[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) s_sort[i] = y, s_sort[l] = x;
+        }
+      }
+      __syncthreads();
+    }
+  __shared__ double s_thr;
+  __shared__ int s_nmask;
+  if (threadIdx.x == 0) {
+    s_thr = __dmul_rn(a.tau_mask, __dmul_rn(1.4826, s_sort[(N - 1) / 2]));
+    s_nmask = 0;
+  }
+  __syncthreads();
+  const double thr = s_thr;
+  int nm = 0;
+  for (int c = threadIdx.x; c < N; c += kFitThreads) nm += e[c] > thr ? 1 : 0;
+  atomicAdd(&s_nmask, nm);
+  __syncthreads();
+  const bool none = s_nmask == N;  // every channel masked: mask none
+  for (int c = threadIdx.x; c < N; c += kFitThreads) a.fit_masked[c] = (uint8_t)(!none && e[c] > thr);
+  __syncthreads();
+  // interpolation of masked channels from their nearest unmasked neighbours
+  for (int c = threadIdx.x; c < N; c += kFitThreads) {
+    double v = mu[c];
+    if (a.fit_masked[c]) {
+      int l = c - 1, r = c + 1;
+      while (l >= 0 && a.fit_masked[l]) --l;
+      while (r < N && a.fit_masked[r]) ++r;
+      if (l >= 0 && r < N) v = __ddiv_rn(__dadd_rn(mu[l], mu[r]), 2.0);
+      else if (l >= 0) v = mu[l];
+      else if (r < N) v = mu[r];
+    }
+    mi[c] = v;
+  }
+  __syncthreads();
+  // normal equations: G[j][k] = sum_c P_j P_k (k <= j), r[j] = sum_c P_j mi_c
+  const int p = a.fit_order, np1 = p + 1;
+  constexpr int kG = (kMaxFitOrder + 1) * (kMaxFitOrder + 2) / 2;
+  double g[kG + kMaxFitOrder + 1];
+#pragma unroll
+  for (int i = 0; i < kG + kMaxFitOrder + 1; ++i) g[i] = 0.0;
+  const double half = N > 1 ? (double)(N - 1) : 1.0;
+  for (int c = threadIdx.x; c < N; c += kFitThreads) {
+    double L[kMaxFitOrder + 1];
+    const double x = N > 1 ? __ddiv_rn((double)(2 * c - (N - 1)), half) : 0.0;
+    L[0] = 1.0;
+    if (p >= 1) L[1] = x;
+    for (int i = 2; i <= p; ++i)
+      L[i] = __ddiv_rn(__dsub_rn(__dmul_rn(__dmul_rn(L[i - 1], x), (double)(2 * i - 1)),
+                                 __dmul_rn(L[i - 2], (double)(i - 1))),
+                       (double)i);
+    int q = 0;
+    for (int j = 0; j < np1; ++j)
+      for (int k = 0; k <= j; ++k) g[q++] += L[j] * L[k];
+    for (int j = 0; j < np1; ++j) g[kG + j] += L[j] * mi[c];
+  }
+  __shared__ double s_g[kFitThreads / 32][kG + kMaxFitOrder + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = 0; i < kG + kMaxFitOrder + 1; ++i) {
+    double v = g[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_g[warp][i] = v;
+  }
+  __syncthreads();
+  __shared__ double s_coef[kMaxFitOrder + 1];
+  if (threadIdx.x == 0) {
+    double A[kMaxFitOrder + 1][kMaxFitOrder + 2];
+    for (int j = 0, q = 0; j < np1; ++j)
+      for (int k = 0; k <= j; ++k, ++q) {
+        double v = 0.0;
+        for (int w = 0; w < kFitThreads / 32; ++w) v += s_g[w][q];
+        A[j][k] = v;
+        A[k][j] = v;
+      }
+    for (int j = 0; j < np1; ++j) {
+      double v = 0.0;
+      for (int w = 0; w < kFitThreads / 32; ++w) v += s_g[w][kG + j];
+      A[j][np1] = v;
+    }
+    // Gaussian elimination with partial pivoting
+    for (int col = 0; col < np1; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < np1; ++r)
+        if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+      if (piv != col)
+        for (int k = 0; k <= np1; ++k) {
+          const double t = A[col][k];
+          A[col][k] = A[piv][k];
+          A[piv][k] = t;
+        }
+      const double d = A[col][col];
+      for (int r = col + 1; r < np1; ++r) {
+        const double f = d != 0.0 ? A[r][col] / d : 0.0;
+        for (int k = col; k <= np1; ++k) A[r][k] -= f * A[col][k];
+      }
+    }
+    for (int j = np1 - 1; j >= 0; --j) {
+      double v = A[j][np1];
+      for (int k = j + 1; k < np1; ++k) v -= A[j][k] * s_coef[k];
+      s_coef[j] = A[j][j] != 0.0 ? v / A[j][j] : 0.0;
+    }
+  }
+  __syncthreads();
+  // fitted values, RMSE, and the values the later stages subtract
+  double ss = 0.0;
+  for (int c = threadIdx.x; c < N; c += kFitThreads) {
+    double L[kMaxFitOrder + 1];
+    const double x = N > 1 ? __ddiv_rn((double)(2 * c - (N - 1)), half) : 0.0;
+    L[0] = 1.0;
+    if (p >= 1) L[1] = x;
+    for (int i = 2; i <= p; ++i)
+      L[i] = __ddiv_rn(__dsub_rn(__dmul_rn(__dmul_rn(L[i - 1], x), (double)(2 * i - 1)),
+                                 __dmul_rn(L[i - 2], (double)(i - 1))),
+                       (double)i);
+    double b = 0.0;
+    for (int j = 0; j < np1; ++j) b += s_coef[j] * L[j];
+    a.bfit[c] = b;
+    const double r = b - mi[c];
+    ss += r * r;
+    const float hi = (float)b;
+    a.mu_hi[c] = hi;
+    a.mu_lo[c] = (float)(b - (double)hi);
+    if (a.dtype == TP_U8) a.bint[c] = (int)floor(__dadd_rn(b, 0.5));
+    if (a.dtype == TP_F16 || a.dtype == TP_BF16) a.b16[c] = storage_bits(a.dtype, b);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  __shared__ double s_ss[kFitThreads / 32];
+  if (lane == 0) s_ss[warp] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kFitThreads / 32; ++w) t += s_ss[w];
+    *a.rmse = __dsqrt_rn(__ddiv_rn(t, (double)N));
+  }
+}
+
+// Chunk test against the fitted bandpass (one CTA per channel): chunk k
+// exceeds when sum(x - b_c) > tau_c * rmse * n_k (float chunk sums are
+// relative to the channel's pivot; 8-bit ones are exact integers).
+__global__ void __launch_bounds__(kThreads) fit_chunk_test_kernel(RfiArgs a, const void* chunk_sums) {
+  const int c = blockIdx.x;
+  const double b = a.bfit[c];
+  const double tr = __dmul_rn(a.tau_c, *a.rmse);
+  const bool single = a.W <= 256;
+  for (int k = threadIdx.x; k < a.nchunk; k += kThreads) {
+    const int64_t lo = (int64_t)k * a.W;
+    const int64_t n = (lo + a.W < a.nsamp ? lo + a.W : a.nsamp) - lo;
+    const int64_t idx = (int64_t)c * a.nchunk + k;
+    double ex;
+    if (a.dtype == TP_U8) {
+      ex = __dsub_rn((double)static_cast<const longlong2*>(chunk_sums)[idx].x, __dmul_rn((double)n, b));
+    } else {
+      const double cs = single ? (double)static_cast<const float2*>(chunk_sums)[idx].x
+                               : static_cast<const double2*>(chunk_sums)[idx].x;
+      ex = __dsub_rn(cs, __dmul_rn((double)n, __dsub_rn(b, (double)a.pivot[c])));
+    }
+    a.chunk_raw[idx] = (uint8_t)(ex > __dmul_rn(tr, (double)n));
+  }
+}
+
 // Pitched row copy in 16-byte units: CTA (x, y) copies kThreads kCopyUnroll
 // consecutive units of rows y, y + gridDim.y, ...; all loads of a thread are
 // issued before its stores.
@@ -837,6 +1047,21 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void*
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t nflag_bytes = (int64_t)a.nchan * a.nchunk;
+  if (a.fit) {
+    int P = 1;
+    while (P < a.nchan) P <<= 1;
+    const size_t sm = sizeof(double) * (size_t)P;
+    e = cudaFuncSetAttribute(bandpass_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    bandpass_fit_kernel<<<1, kFitThreads, sm, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.enable_channel) {
+      fit_chunk_test_kernel<<<a.nchan, kThreads, 0, s>>>(a, chunk_sums);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
   if (a.enable_channel) {
     dilate_kernel<<<(a.nchan + kWarps - 1) / kWarps, kThreads, 0, s>>>(a);
   } else {

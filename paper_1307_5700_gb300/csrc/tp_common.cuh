@@ -50,7 +50,22 @@ struct RfiArgs {
   int* spec_nflag;        // [1] flagged spectra
   double* spec_thr;       // [1] spectrum threshold (per-block constant)
   int stage_f32;          // 16-bit data: stage y = x~ - b in FP32 (for the FP32 kernel shapes)
+  // fitted bandpass (Sec. 2.2.1 "Bandpass Correction"): fit = 1 turns it on
+  // (0, the zero-initialised value, leaves the block statistics); the chunk
+  // test then uses the fit b_c of order fit_order and its RMSE
+  int fit;
+  int fit_order;
+  double tau_mask;        // high-power channel masking before the fit
+  float* pivot;           // [nchan] per-channel pivot of the float chunk sums
+  double* bfit;           // [nchan] fitted bandpass b_c
+  uint8_t* fit_masked;    // [nchan] channels masked before the fit
+  double* fit_work;       // [2 nchan] local excess e_c, interpolated bandpass
+  double* rmse;           // [1] RMSE of the fit
 };
+
+// Largest polynomial order and channel count of the fitted bandpass.
+constexpr int kMaxFitOrder = 8;
+constexpr int kMaxFitChannels = 8192;
 
 // A tile of consecutive DM trials processed by one dedispersion CTA.
 struct DmTile {
