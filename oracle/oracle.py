@@ -490,3 +490,119 @@ def search_block(x, dtype, delay, max_delay, rfi=None, nsigma=5.0, beam=0, t0=0,
     if keep_series:
         out["D"] = D
     return out
+
+
+# ---- clustering and classification of the detections (Sec. 2.3) -------------------
+
+@dataclass
+class ClusterParams:
+    """Parameters of the clustering and classification stage (reading R14)."""
+    t_eps: int = 20          # T_t: neighbourhood half-extent in samples
+    dm_eps: int = 3          # DM_t: neighbourhood half-extent in DM trials
+    snr_eps: float = 5.0     # SNR_t: neighbourhood half-extent in SNR
+    min_pts: int = 5         # MinPts (the point itself included)
+    smooth: int = 3          # k of the moving average of the DM-SNR signature (odd)
+    rmse_max: float = 0.4    # largest RMSE of the normalised signature against Eq. 3
+    dm_min: float = 1.0      # clusters peaking below this DM are broadband RFI
+
+
+def dbscan(d, t, snr, prm):
+    """DBSCAN (Sec. 2.3, Ester et al.) of detections (d, t, snr) with the box
+    neighbourhood |d_q - d_p| <= dm_eps, |t_q - t_p| <= t_eps,
+    |snr_q - snr_p| <= snr_eps (the point itself included).  Core points have
+    at least min_pts neighbours; clusters are the connected groups of core
+    points (core points in each other's neighbourhood); a border point (not
+    core, with a core neighbour) joins the cluster of its lowest-index core
+    neighbour; the rest is noise (-1).  Clusters are numbered 0, 1, ... in
+    the order of their lowest-index core point.  Plain O(N^2) search.
+    Returns (labels, core)."""
+    d = np.asarray(d, np.int64)
+    t = np.asarray(t, np.int64)
+    s = np.asarray(snr, np.float64)
+    n = len(d)
+    nb = []
+    for p in range(n):
+        m = (np.abs(d - d[p]) <= prm.dm_eps) & (np.abs(t - t[p]) <= prm.t_eps) & \
+            (np.abs(s - s[p]) <= prm.snr_eps)
+        nb.append(np.nonzero(m)[0])
+    core = np.array([len(x) >= prm.min_pts for x in nb], bool)
+    comp = -np.ones(n, np.int64)
+    for p in range(n):                       # components of the core graph, by search
+        if not core[p] or comp[p] >= 0:
+            continue
+        comp[p] = p
+        stack = [p]
+        while stack:
+            q = stack.pop()
+            for r in nb[q]:
+                if core[r] and comp[r] < 0:
+                    comp[r] = p
+                    stack.append(r)
+    labels = -np.ones(n, np.int64)
+    roots = sorted({int(comp[p]) for p in range(n) if core[p]})
+    rank = {r: i for i, r in enumerate(roots)}
+    for p in range(n):
+        if core[p]:
+            labels[p] = rank[int(comp[p])]
+        else:
+            cn = [int(q) for q in nb[p] if core[q]]
+            if cn:
+                labels[p] = rank[int(comp[min(cn)])]
+    return labels, core
+
+
+def eq3_ratio(ddm, width_ms, bw_mhz, f_ghz):
+    """Eq. 3-4: measured / true peak flux of a Gaussian pulse of FWHM width_ms
+    dedispersed with a DM error ddm, rectangular band of bw_mhz at f_ghz:
+    (sqrt(pi) / 2) erf(zeta) / zeta, zeta = 6.91e-3 ddm bw / (W f^3); 1 at 0."""
+    from math import erf, pi, sqrt
+    z = 6.91e-3 * abs(ddm) * bw_mhz / (width_ms * f_ghz ** 3)
+    if z == 0.0:
+        return 1.0
+    return sqrt(pi) / 2.0 * erf(z) / z
+
+
+def classify(d, t, snr, labels, dm_list, t_samp, bw_mhz, f_ghz, prm):
+    """The classification steps of Sec. 2.3 for every cluster (reading R14):
+    1. the DM-SNR signature: per DM trial of the cluster, its largest SNR;
+    2. a centred moving average of prm.smooth trials over the trials from the
+       cluster's lowest to its highest (trials without detections count 0;
+       at the ends the average is over the trials available);
+    3. d* = the trial with the most detections (ties: the lowest trial), and
+       its largest SNR; d* with DM below prm.dm_min is broadband RFI;
+    4. the width: (last - first detection time at d* + 1) samples, in ms;
+    5. the smoothed signature divided by its largest value;
+    6. Eq. 3 with dDM = DM_d - DM_{d*};
+    7. the RMSE of 5 against 6 over the cluster's trials;
+    8. a candidate when not broadband RFI and RMSE <= prm.rmse_max.
+    Returns one dict per cluster, in cluster order."""
+    d = np.asarray(d, np.int64)
+    t = np.asarray(t, np.int64)
+    s = np.asarray(snr, np.float64)
+    out = []
+    k = prm.smooth
+    for c in range(int(labels.max()) + 1 if len(labels) else 0):
+        m = labels == c
+        dc, tc, sc = d[m], t[m], s[m]
+        lo, hi = int(dc.min()), int(dc.max())
+        nd = hi - lo + 1
+        sig = np.zeros(nd)
+        cnt = np.zeros(nd, np.int64)
+        for di, si in zip(dc, sc):
+            sig[di - lo] = max(sig[di - lo], si)
+            cnt[di - lo] += 1
+        sm = np.empty(nd)
+        for i in range(nd):
+            a, b = max(0, i - k // 2), min(nd, i + k // 2 + 1)
+            sm[i] = sig[a:b].sum() / (b - a)
+        ds = lo + int(np.argmax(cnt))
+        rfi = dm_list[ds] < prm.dm_min
+        ts = tc[dc == ds]
+        width_ms = float(ts.max() - ts.min() + 1) * t_samp * 1e3
+        norm = sm / sm.max()
+        model = np.array([eq3_ratio(dm_list[lo + i] - dm_list[ds], width_ms, bw_mhz, f_ghz) for i in range(nd)])
+        rmse = float(np.sqrt(np.mean((norm - model) ** 2)))
+        out.append(dict(cluster=c, n=int(m.sum()), d_lo=lo, d_hi=hi, d_star=ds, snr_max=float(sc.max()),
+                        t_first=int(tc.min()), t_last=int(tc.max()), width_ms=width_ms, rmse=rmse,
+                        broadband=bool(rfi), candidate=bool((not rfi) and rmse <= prm.rmse_max)))
+    return out
