@@ -94,6 +94,31 @@ typedef struct tp_candidate {
   float value;    /* D[dm_idx][t]                                               */
 } tp_candidate;
 
+/* Clustering of a block's detections (Sec. 2.3), see tp_plan_set_clustering. */
+typedef struct tp_cluster_params {
+  int32_t t_eps;     /* T_t: neighbourhood half-extent in samples (>= 0)          */
+  int32_t dm_eps;    /* DM_t: neighbourhood half-extent in DM trials (>= 0)       */
+  double snr_eps;    /* SNR_t: neighbourhood half-extent in SNR (>= 0)            */
+  int32_t min_pts;   /* MinPts: neighbours of a core point, itself included (>= 1) */
+  int32_t smooth;    /* k of the DM-SNR moving average (odd, >= 1)                */
+  double rmse_max;   /* largest RMSE against Eq. 3 of a candidate cluster          */
+  double dm_min;     /* clusters peaking below this DM (pc cm^-3) are broadband RFI */
+} tp_cluster_params;
+
+/* One cluster of detections and its classification.  48 bytes. */
+typedef struct tp_cluster {
+  int32_t label;     /* cluster number (clusters numbered by their lowest-index core detection) */
+  int32_t n;         /* detections in the cluster                                */
+  int32_t d_lo, d_hi; /* DM trial range                                          */
+  int32_t d_star;    /* trial with the most detections                           */
+  int32_t flags;     /* bit 0: candidate; bit 1: broadband RFI (d_star below dm_min) */
+  int64_t t_first, t_last; /* first and last detection (stream sample index)     */
+  float snr_max;     /* largest SNR                                              */
+  float width_ms;    /* (last - first detection time at d_star + 1) samples, ms  */
+  float rmse;        /* RMSE of the normalised DM-SNR signature against Eq. 3    */
+  float reserved;
+} tp_cluster;
+
 typedef struct tp_engine tp_engine;
 typedef struct tp_plan tp_plan;
 
@@ -173,6 +198,33 @@ int tp_plan_set_postprocess(tp_plan *p, int median_width, int detrend);
  * block statistics (TP_STATS_BLOCK) and at most 8192 channels (TP_EINVAL);
  * call before any beam of the plan is opened (TP_EBUSY). */
 int tp_plan_set_bandpass_fit(tp_plan *p, int order, double tau_mask);
+
+/* Clustering and classification of every block's detections (Sec. 2.3:
+ * DBSCAN of the (time, DM, intensity) triplets, then each cluster's DM-SNR
+ * signature against the incorrect-dedispersion model of Eq. 3-4), run on the
+ * device after the detection; params = NULL turns it off.
+ *   Neighbourhood of a detection p: the detections q with |t_q - t_p| <=
+ *   t_eps, |d_q - d_p| <= dm_eps, |snr_q - snr_p| <= snr_eps (p included);
+ *   core detections have >= min_pts neighbours; clusters are the connected
+ *   groups of core detections; a detection that is not core but has a core
+ *   neighbour joins the cluster of its lowest-index core neighbour (records
+ *   in (dm_idx, t_abs) order); the rest is noise.  Clusters are numbered in
+ *   the order of their lowest-index core detection.  (The paper's FDBSCAN is
+ *   an approximation of this clustering for a CPU; the device computes it
+ *   exactly.)
+ *   Classification of each cluster: the largest SNR per DM trial, its
+ *   centred moving average over `smooth` trials (fewer at the ends), d* =
+ *   the trial with the most detections (ties: the lowest), broadband RFI
+ *   when DM(d*) < dm_min, the width (last - first detection time at d* + 1)
+ *   samples, the averaged signature divided by its maximum, Eq. 3 for
+ *   dDM = DM(d) - DM(d*) with the band's width and centre frequency, and the
+ *   RMSE of the two over the cluster's trials; a candidate when not
+ *   broadband RFI and RMSE <= rmse_max.
+ * Clustering works on the stored detections (the first cand_capacity in
+ * (d, t) order) and keeps at most min(cand_capacity, 65536) clusters.  Call
+ * before any beam of the plan is opened (TP_EBUSY).  TP_EINVAL for invalid
+ * parameters. */
+int tp_plan_set_clustering(tp_plan *p, const tp_cluster_params *params);
 
 /* Copy the delay table (ndm x nchan int32, row = DM) to host memory `out`
  * holding `count` elements.  Blocks. */
@@ -286,6 +338,17 @@ int tp_get_detrend(tp_engine *e, int beam, double *mean, double *beta, double *s
  * channels masked before the fit (nchan bytes, 1 = masked) and the fit's RMSE
  * (any pointer may be NULL).  Blocks; TP_EINVAL when the plan does not fit. */
 int tp_get_bandpass_fit(tp_engine *e, int beam, double *bfit, uint8_t *masked, double *rmse, int nchan);
+
+/* The clusters of the beam's last detected block (host): min(cap, n) records
+ * in cluster order; *n receives the number of clusters, *truncated (may be
+ * NULL) 1 when more clusters than the beam keeps were found.  Blocks;
+ * TP_EINVAL when the plan does not cluster, TP_ENOTREADY before detection. */
+int tp_get_clusters(tp_engine *e, int beam, tp_cluster *out, int cap, int *n, int *truncated);
+
+/* Cluster number of each of the first min(cap, stored) detections of the
+ * last detected block (-1: noise), in the order of tp_get_candidates.
+ * Blocks; *n receives the number of stored detections. */
+int tp_get_candidate_labels(tp_engine *e, int beam, int32_t *labels, int cap, int *n);
 
 /* ---- kernel shapes and autotuning -------------------------------------------------
  * The dedispersion kernel is compiled for several register tilings ("shapes":

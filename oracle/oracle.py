@@ -556,7 +556,7 @@ def eq3_ratio(ddm, width_ms, bw_mhz, f_ghz):
     dedispersed with a DM error ddm, rectangular band of bw_mhz at f_ghz:
     (sqrt(pi) / 2) erf(zeta) / zeta, zeta = 6.91e-3 ddm bw / (W f^3); 1 at 0."""
     from math import erf, pi, sqrt
-    z = 6.91e-3 * abs(ddm) * bw_mhz / (width_ms * f_ghz ** 3)
+    z = 6.91e-3 * abs(ddm) * bw_mhz / (width_ms * (f_ghz * f_ghz * f_ghz))
     if z == 0.0:
         return 1.0
     return sqrt(pi) / 2.0 * erf(z) / z

@@ -50,7 +50,8 @@ EXPORTS = (
     "tp_run_ready", "tp_engine_stream", "tp_server_create", "tp_server_add_stream", "tp_server_submit",
     "tp_server_end_stream", "tp_server_run", "tp_server_results", "tp_server_candidates", "tp_server_destroy",
     "tp_beam_rewind", "tp_autotune_batch", "tp_plan_set_postprocess", "tp_get_processed_series",
-    "tp_get_detrend", "tp_plan_set_bandpass_fit", "tp_get_bandpass_fit",
+    "tp_get_detrend", "tp_plan_set_bandpass_fit", "tp_get_bandpass_fit", "tp_plan_set_clustering",
+    "tp_get_clusters", "tp_get_candidate_labels",
 )
 
 
@@ -74,6 +75,18 @@ class tp_candidate(ctypes.Structure):
 
 CAND_DTYPE = np.dtype([("beam", np.int32), ("dm_idx", np.int32), ("t_abs", np.int64),
                        ("snr", np.float32), ("value", np.float32)])
+
+
+class tp_cluster_params(ctypes.Structure):
+    _fields_ = [("t_eps", ctypes.c_int32), ("dm_eps", ctypes.c_int32), ("snr_eps", ctypes.c_double),
+                ("min_pts", ctypes.c_int32), ("smooth", ctypes.c_int32), ("rmse_max", ctypes.c_double),
+                ("dm_min", ctypes.c_double)]
+
+
+CLUSTER_DTYPE = np.dtype([("label", np.int32), ("n", np.int32), ("d_lo", np.int32), ("d_hi", np.int32),
+                          ("d_star", np.int32), ("flags", np.int32), ("t_first", np.int64), ("t_last", np.int64),
+                          ("snr_max", np.float32), ("width_ms", np.float32), ("rmse", np.float32),
+                          ("reserved", np.float32)])
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -116,6 +129,9 @@ _SIGS = {
     "tp_get_processed_series": (_i, [_vp, _i, _vp, ctypes.c_size_t, _i]),
     "tp_get_detrend": (_i, [_vp, _i, _vp, _vp, _vp, _i]),
     "tp_plan_set_bandpass_fit": (_i, [_vp, _i, _d]),
+    "tp_plan_set_clustering": (_i, [_vp, _vp]),
+    "tp_get_clusters": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "tp_get_candidate_labels": (_i, [_vp, _i, _vp, _i, _vp]),
     "tp_get_bandpass_fit": (_i, [_vp, _i, _vp, _vp, _vp, _i]),
     "tp_channel_stats_noalloc": (_i, [_vp, _i, _i, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                      _vp]),
@@ -425,6 +441,34 @@ def tp_get_bandpass_fit(e, beam, nchan):
     r = ctypes.c_double()
     _check(lib().tp_get_bandpass_fit(e, beam, b.ctypes.data, m.ctypes.data, ctypes.byref(r), nchan))
     return b, m.astype(bool), r.value
+
+
+def tp_plan_set_clustering(p, t_eps=20, dm_eps=3, snr_eps=5.0, min_pts=5, smooth=3, rmse_max=0.4, dm_min=1.0,
+                           enable=True):
+    """Clustering and classification of every block's detections (Sec. 2.3;
+    see tp_dedisp.h); enable=False turns it off."""
+    if not enable:
+        return _check(lib().tp_plan_set_clustering(p, None))
+    prm = tp_cluster_params(int(t_eps), int(dm_eps), float(snr_eps), int(min_pts), int(smooth), float(rmse_max),
+                            float(dm_min))
+    return _check(lib().tp_plan_set_clustering(p, ctypes.byref(prm)))
+
+
+def tp_get_clusters(e, beam, cap=1 << 16):
+    """(cluster records, number of clusters, truncated)."""
+    out = np.zeros(max(int(cap), 1), CLUSTER_DTYPE)
+    n = ctypes.c_int()
+    tr = ctypes.c_int()
+    _check(lib().tp_get_clusters(e, beam, out.ctypes.data, int(cap), ctypes.byref(n), ctypes.byref(tr)))
+    return out[:min(n.value, cap)], n.value, bool(tr.value)
+
+
+def tp_get_candidate_labels(e, beam, cap=1 << 20):
+    """Cluster number (-1: noise) of each stored detection, in record order."""
+    out = np.zeros(max(int(cap), 1), np.int32)
+    n = ctypes.c_int()
+    _check(lib().tp_get_candidate_labels(e, beam, out.ctypes.data, int(cap), ctypes.byref(n)))
+    return out[:min(n.value, cap)]
 
 
 def tp_autotune_batch(e, reps=2):

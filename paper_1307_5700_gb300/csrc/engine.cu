@@ -166,6 +166,20 @@ struct Beam {
   int* status = nullptr;
   void* D = nullptr;
   void* M = nullptr;          // median-filtered series (plans with median_width > 1)
+  // clustering buffers (plans that cluster)
+  int* cl_row_start = nullptr;
+  int* cl_core = nullptr;
+  int* cl_parent = nullptr;
+  int* cl_root = nullptr;
+  int* cl_rank = nullptr;
+  int* cl_label = nullptr;
+  int* cl_order = nullptr;
+  int* cl_count = nullptr;
+  int* cl_offset = nullptr;
+  int* cl_cursor = nullptr;
+  tp_cluster* clusters = nullptr;
+  int* n_clusters = nullptr;
+  int max_clusters = 0;
   float* pivot = nullptr;     // fitted bandpass buffers
   double* bfit = nullptr;
   uint8_t* fit_masked = nullptr;
@@ -221,6 +235,9 @@ struct tp_plan {
   double nsigma = 5.0;
   int fit_order = -1;    // fitted bandpass (Sec. 2.2.1): polynomial order, -1 = off
   double tau_mask = 5.0; // fitted bandpass: high-power channel masking threshold
+  bool cluster = false;  // clustering of the detections (Sec. 2.3)
+  tp_cluster_params cparams{};
+  double* d_dmlist = nullptr;  // [ndm] DM values on the device (classification)
   int median_width = 1;  // post-processing (Sec. 2.2.3): median filter width, 1 = off
   int detrend = 0;       // post-processing: least-squares detrending
   int32_t* d_delay = nullptr;
@@ -435,6 +452,18 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->blk_count, nd * (size_t)nblk * 4);
   add((void**)&b->blk_off, nd * (size_t)nblk * 4);
   add((void**)&b->cand, (size_t)cap * sizeof(tp_candidate));
+  if (p->cluster) {
+    const int mc = cap < kMaxClusters ? cap : kMaxClusters;
+    b->max_clusters = mc;
+    add((void**)&b->cl_row_start, ((size_t)nd + 1) * 4);
+    for (int** q : {&b->cl_core, &b->cl_parent, &b->cl_root, &b->cl_rank, &b->cl_label, &b->cl_order})
+      add((void**)q, (size_t)cap * 4);
+    add((void**)&b->cl_count, (size_t)mc * 4);
+    add((void**)&b->cl_offset, ((size_t)mc + 1) * 4);
+    add((void**)&b->cl_cursor, (size_t)mc * 4);
+    add((void**)&b->clusters, (size_t)mc * sizeof(tp_cluster));
+    add((void**)&b->n_clusters, 8);
+  }
   add((void**)&b->n_total, 8);
 }
 
@@ -647,6 +676,40 @@ int issue_detect(tp_engine* e, Beam* b, cudaStream_t s) {
   a.row_beta = b->row_beta;
   TP_CUDA_TRY(launch_detect(a, s));
   e->launches += (p->median_width > 1 || p->detrend) ? 5 : 4;
+  if (p->cluster) {
+    ClusterArgs c{};
+    c.cand = b->cand;
+    c.n_total = b->n_total;
+    c.cap = b->cap;
+    c.ndm = p->ndm;
+    c.dm = p->d_dmlist;
+    c.t_samp = p->t_samp;
+    c.bw_mhz = std::fabs(p->bw);
+    c.f_ghz = (p->f_lo + p->bw / 2.0) / 1e3;
+    c.t_eps = p->cparams.t_eps;
+    c.dm_eps = p->cparams.dm_eps;
+    c.snr_eps = (float)p->cparams.snr_eps;
+    c.min_pts = p->cparams.min_pts;
+    c.smooth = p->cparams.smooth;
+    c.rmse_max = p->cparams.rmse_max;
+    c.dm_min = p->cparams.dm_min;
+    c.row_start = b->cl_row_start;
+    c.core = b->cl_core;
+    c.parent = b->cl_parent;
+    c.root = b->cl_root;
+    c.rank = b->cl_rank;
+    c.label = b->cl_label;
+    c.order = b->cl_order;
+    c.max_clusters = b->max_clusters;
+    c.cl_count = b->cl_count;
+    c.cl_offset = b->cl_offset;
+    c.cl_cursor = b->cl_cursor;
+    c.clusters = b->clusters;
+    c.n_clusters = b->n_clusters;
+    c.truncated = b->n_clusters + 1;
+    TP_CUDA_TRY(launch_cluster(c, s));
+    e->launches += 9;
+  }
   prof_record(e, b, 5, s);
   TP_CUDA_TRY(cudaEventRecord(b->ev_detect, s));
   b->state = kDetected;
@@ -810,6 +873,7 @@ int tp_engine_destroy(tp_engine* e) {
       }
     e->beams.clear();
     for (tp_plan* p : e->plans) {
+      cudaFree(p->d_dmlist);
       cudaFree(p->d_delay);
       cudaFree(p->d_delayT);
       for (DmTile* t : p->d_shape_tiles) cudaFree(t);
@@ -895,6 +959,7 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
   auto fail = [&](int code) {
     cudaFree(d_dm);
     cudaFree(d_err);
+    cudaFree(p->d_dmlist);
     cudaFree(p->d_delay);
     cudaFree(p->d_delayT);
     for (DmTile* t : p->d_shape_tiles) cudaFree(t);
@@ -920,7 +985,7 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
   if ((ce = cudaMemcpyAsync(&herr, d_err, 4, cudaMemcpyDeviceToHost, e->stream)) != cudaSuccess)
     return fail(cuda_error(ce, "copy err"));
   if ((ce = cudaStreamSynchronize(e->stream)) != cudaSuccess) return fail(cuda_error(ce, "sync"));
-  cudaFree(d_dm);
+  p->d_dmlist = d_dm;  // kept for the classification of clusters
   d_dm = nullptr;
   cudaFree(d_err);
   d_err = nullptr;
@@ -972,6 +1037,7 @@ int tp_plan_destroy(tp_plan* p) {
   if (p->users > 0) return set_error(TP_EBUSY, "plan is used by %d open beams", p->users);
   DeviceGuard g(e->device);
   cudaStreamSynchronize(e->stream);
+  cudaFree(p->d_dmlist);
   cudaFree(p->d_delay);
   cudaFree(p->d_delayT);
   for (DmTile* t : p->d_shape_tiles) cudaFree(t);
@@ -1456,6 +1522,63 @@ int tp_engine_launches(const tp_engine* e, uint64_t* n) {
 }  // extern "C"
 
 extern "C" {
+
+int tp_plan_set_clustering(tp_plan* p, const tp_cluster_params* prm) {
+  if (!p) return set_error(TP_EINVAL, "plan is NULL");
+  std::lock_guard<std::recursive_mutex> lk(p->e->mu);
+  if (prm) {
+    if (prm->t_eps < 0 || prm->dm_eps < 0 || !(prm->snr_eps >= 0.0) || prm->min_pts < 1 || prm->smooth < 1 ||
+        prm->smooth % 2 == 0 || !std::isfinite(prm->rmse_max) || !std::isfinite(prm->dm_min) ||
+        !std::isfinite(prm->snr_eps))
+      return set_error(TP_EINVAL, "invalid clustering parameters");
+  }
+  if (p->users > 0) return set_error(TP_EBUSY, "plan is used by %d open beams", p->users);
+  p->cluster = prm != nullptr;
+  if (prm) p->cparams = *prm;
+  return TP_OK;
+}
+
+int tp_get_clusters(tp_engine* e, int beam, tp_cluster* out, int cap, int* n, int* truncated) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (!b->plan->cluster) return set_error(TP_EINVAL, "the beam's plan does not cluster");
+  if (b->state != kDetected) return set_error(TP_ENOTREADY, "beam %d has no detected block", beam);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  int hn[2] = {0, 0};
+  TP_CUDA_TRY(cudaMemcpyAsync(hn, b->n_clusters, 8, cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  const int k = cap < hn[0] ? (cap > 0 ? cap : 0) : hn[0];
+  if (k > 0 && out)
+    TP_CUDA_TRY(cudaMemcpyAsync(out, b->clusters, (size_t)k * sizeof(tp_cluster), cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (n) *n = hn[0];
+  if (truncated) *truncated = hn[1];
+  return TP_OK;
+}
+
+int tp_get_candidate_labels(tp_engine* e, int beam, int32_t* labels, int cap, int* n) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (!b->plan->cluster) return set_error(TP_EINVAL, "the beam's plan does not cluster");
+  if (b->state != kDetected) return set_error(TP_ENOTREADY, "beam %d has no detected block", beam);
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  unsigned long long tot = 0;
+  TP_CUDA_TRY(cudaMemcpyAsync(&tot, b->n_total, 8, cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  const int stored = tot < (unsigned long long)b->cap ? (int)tot : b->cap;
+  const int k = cap < stored ? (cap > 0 ? cap : 0) : stored;
+  if (k > 0 && labels)
+    TP_CUDA_TRY(cudaMemcpyAsync(labels, b->cl_label, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
+  TP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (n) *n = stored;
+  return TP_OK;
+}
 
 int tp_plan_set_bandpass_fit(tp_plan* p, int order, double tau_mask) {
   if (!p) return set_error(TP_EINVAL, "plan is NULL");

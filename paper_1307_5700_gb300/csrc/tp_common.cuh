@@ -153,6 +153,37 @@ struct DetectArgs {
   double* row_beta;       // [ndm] detrending slope per unit of u = 2t - (T - 1)
 };
 
+// Clustering of a block's detections (cluster.cu).
+struct ClusterArgs {
+  const tp_candidate* cand;           // (d, t)-ordered records
+  const unsigned long long* n_total;  // [1] detections found
+  int cap;                            // records stored
+  int ndm;
+  const double* dm;                   // [ndm] DM values
+  double t_samp, bw_mhz, f_ghz;
+  int64_t t_eps;
+  int dm_eps;
+  float snr_eps;
+  int min_pts, smooth;
+  double rmse_max, dm_min;
+  int* row_start;                     // [ndm + 1]
+  int* core;                          // [cap]
+  int* parent;                        // [cap]
+  int* root;                          // [cap]
+  int* rank;                          // [cap]
+  int* label;                         // [cap]
+  int* order;                         // [cap] records grouped by cluster
+  int max_clusters;
+  int* cl_count;                      // [max_clusters]
+  int* cl_offset;                     // [max_clusters + 1]
+  int* cl_cursor;                     // [max_clusters]
+  tp_cluster* clusters;               // [max_clusters]
+  int* n_clusters;                    // [1]
+  int* truncated;                     // [1]
+};
+cudaError_t launch_cluster(const ClusterArgs& a, cudaStream_t s);
+constexpr int kMaxClusters = 65536;  // clusters kept per block
+
 // Largest median-filter width of the post-processing.
 constexpr int kMaxMedianWidth = 9;
 
