@@ -431,6 +431,8 @@ def main():
     ap.add_argument("--median", type=int, default=1,
                     help="stream: median filter width of the post-processing (odd, 1 = off)")
     ap.add_argument("--detrend", action="store_true", help="stream: detrended detection (post-processing)")
+    ap.add_argument("--cluster", action="store_true",
+                    help="stream: cluster and classify every block's detections (Sec. 2.3)")
     ap.add_argument("--fit", type=int, default=-1,
                     help="stream: fitted bandpass of this polynomial order (-1 = block mean)")
     ap.add_argument("--per-beam", action="store_true",
@@ -462,6 +464,8 @@ def main():
         tp.tp_plan_set_postprocess(plan, args.median, args.detrend)
     if args.fit >= 0:
         tp.tp_plan_set_bandpass_fit(plan, args.fit, 5.0)
+    if args.cluster:
+        tp.tp_plan_set_clustering(plan)
     delays = tp.tp_get_delay_table(plan)
     max_delay = tp.tp_plan_info(plan)["max_delay"]
     beam = tp.tp_beam_open(e, plan, BLOCK, 1 << 20)
@@ -594,7 +598,7 @@ def main():
                        "l2": "inputs larger than L2 (562 MB window per block, 3 distinct blocks cycled)",
                        "parallelism": f"replicas x{world}", "kernel_shape": int(best),
                        "postprocess": {"median_width": args.median, "detrend": bool(args.detrend)},
-                       "bandpass_fit_order": args.fit,
+                       "bandpass_fit_order": args.fit, "clustering": bool(args.cluster),
                        "autotune_ms": tune},
             "realtime_beams": value / (len(DMS) / TSAMP),
             "p50_block_latency_ms": float(np.percentile(per_block, 50)),

@@ -223,7 +223,8 @@ int tp_plan_set_bandpass_fit(tp_plan *p, int order, double tau_mask);
  * Clustering works on the stored detections (the first cand_capacity in
  * (d, t) order) and keeps at most min(cand_capacity, 65536) clusters.  Call
  * before any beam of the plan is opened (TP_EBUSY).  TP_EINVAL for invalid
- * parameters. */
+ * parameters or a plan of more than 14336 DM trials (the classification
+ * keeps one cluster's signature in shared memory). */
 int tp_plan_set_clustering(tp_plan *p, const tp_cluster_params *params);
 
 /* Copy the delay table (ndm x nchan int32, row = DM) to host memory `out`

@@ -15,7 +15,7 @@
 // saves region queries on a CPU; on the sorted records a region query is two
 // binary searches per DM trial, so the exact clustering is kept.)
 //
-// Classification, one CTA per cluster: the largest SNR per DM trial (the
+// Classification, one CTA per cluster at a time: the largest SNR per DM trial (the
 // DM-SNR signature), its centred k-trial moving average, the trial d* with
 // the most detections (below dm_min: broadband RFI), the width there, the
 // signature normalised by its maximum, Eq. 3-4 for the DM errors to d*, and
@@ -86,12 +86,17 @@ __global__ void cl_core(ClusterArgs a) {
   a.parent[p] = p;
 }
 
+// Root of p's group, halving the path on the way (a non-root's parent is
+// set to its grandparent: an ancestor, so concurrent finds and the roots'
+// compare-and-swap links stay valid).
 __device__ __forceinline__ int find_root(int* parent, int p) {
   int r = p;
   for (int it = 0; it < (1 << 24); ++it) {  // bounded: a root is reached in fewer steps than points
     const int q = parent[r];
     if (q == r) return r;
-    r = q;
+    const int g = parent[q];
+    if (g != q) parent[r] = g;
+    r = g;
   }
   return r;
 }
@@ -106,12 +111,31 @@ __device__ void unite(int* parent, int u, int v) {
   }
 }
 
-__global__ void cl_union(ClusterArgs a) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= cand_count(a) || !a.core[p]) return;
-  for_neighbours(a, p, [&](int q) {
-    if (q < p && a.core[q]) unite(a.parent, p, q);
-  });
+// One warp per core point p (a fixed grid strides over the points), its
+// lanes splitting p's neighbours q < p: those lie in the trials up to p's
+// own (records are in (d, t) order), the links to higher neighbours are
+// made by those neighbours' warps.
+__global__ void __launch_bounds__(kThreads) cl_union(ClusterArgs a) {
+  const int n = cand_count(a);
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (kThreads / 32);
+  for (int p = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); p < n; p += warps) {
+    if (!a.core[p]) continue;
+    const tp_candidate cp = a.cand[p];
+    const int d0 = cp.dm_idx - a.dm_eps < 0 ? 0 : cp.dm_idx - a.dm_eps;
+    int rp = find_root(a.parent, p);  // may go stale; unite() re-checks
+    for (int d = d0; d <= cp.dm_idx; ++d) {
+      const int hi = d == cp.dm_idx ? p : a.row_start[d + 1];
+      for (int q = lower_t(a.cand, a.row_start[d], hi, cp.t_abs - a.t_eps) + lane; q < hi; q += 32) {
+        const tp_candidate cq = a.cand[q];
+        if (cq.t_abs > cp.t_abs + a.t_eps) break;
+        if (fabsf(cq.snr - cp.snr) <= a.snr_eps && a.core[q] && find_root(a.parent, q) != rp) {
+          unite(a.parent, p, q);
+          rp = find_root(a.parent, p);
+        }
+      }
+    }
+  }
 }
 
 // root of every point's cluster (-1: noise)
@@ -212,19 +236,33 @@ __device__ double eq3(double ddm, double width_ms, double bw_mhz, double f_ghz) 
   return sqrt(3.141592653589793) / 2.0 * erf(z) / z;
 }
 
-// One CTA per cluster; dynamic shared memory: 2 ints per DM trial.
-__global__ void __launch_bounds__(kThreads) cl_classify(ClusterArgs a) {
-  const int k = blockIdx.x;
-  if (k >= *a.n_clusters) return;
-  extern __shared__ int s_dm[];  // [ndm] max-SNR keys, [ndm] counts
-  int* s_sig = s_dm;
-  int* s_cnt = s_dm + a.ndm;
+// sum or maximum over the CTA (every thread gets the result)
+template <bool MAX>
+__device__ __forceinline__ double block_reduce(double v, double* s_red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = MAX ? (w > v ? w : v) : v + w;
+  }
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = s_red[0];
+  for (int i = 1; i < kThreads / 32; ++i) v = MAX ? (s_red[i] > v ? s_red[i] : v) : v + s_red[i];
+  __syncthreads();
+  return v;
+}
+
+// One cluster: dynamic shared memory holds [ndm] doubles (the smoothed
+// signature), then [ndm] max-SNR keys and [ndm] detection counts.
+__device__ void classify_one(const ClusterArgs& a, int k, double* s_v, int* s_sig, int* s_cnt) {
   const int b0 = a.cl_offset[k], b1 = a.cl_offset[k + 1];
   __shared__ int s_dlo, s_dhi, s_smax;
-  __shared__ long long s_t0, s_t1;
+  __shared__ long long s_t0, s_t1, s_w0, s_w1;
+  __shared__ unsigned long long s_best;
+  __shared__ double s_red[kThreads / 32];
   if (threadIdx.x == 0) {
     s_dlo = INT_MAX, s_dhi = -1, s_smax = fkey(-INFINITY);
-    s_t0 = LLONG_MAX, s_t1 = LLONG_MIN;
+    s_t0 = LLONG_MAX, s_t1 = LLONG_MIN, s_w0 = LLONG_MAX, s_w1 = LLONG_MIN;
+    s_best = 0;
   }
   __syncthreads();
   for (int i = b0 + threadIdx.x; i < b1; i += kThreads) {
@@ -245,17 +283,12 @@ __global__ void __launch_bounds__(kThreads) cl_classify(ClusterArgs a) {
     atomicAdd(&s_cnt[c.dm_idx - lo], 1);
   }
   __syncthreads();
-  __shared__ int s_dstar;
-  __shared__ long long s_w0, s_w1;
-  if (threadIdx.x == 0) {
-    int best = 0;
-    for (int i = 1; i < span; ++i)
-      if (s_cnt[i] > s_cnt[best]) best = i;
-    s_dstar = lo + best;
-    s_w0 = LLONG_MAX, s_w1 = LLONG_MIN;
-  }
+  // d*: the most detections, ties to the lowest trial
+  for (int i = threadIdx.x; i < span; i += kThreads)
+    if (s_cnt[i] > 0)
+      atomicMax(&s_best, ((unsigned long long)s_cnt[i] << 32) | (unsigned)(INT_MAX - i));
   __syncthreads();
-  const int ds = s_dstar;
+  const int ds = lo + (INT_MAX - (int)(unsigned)(s_best & 0xffffffffu));
   for (int i = b0 + threadIdx.x; i < b1; i += kThreads) {
     const tp_candidate c = a.cand[a.order[i]];
     if (c.dm_idx == ds) {
@@ -264,65 +297,80 @@ __global__ void __launch_bounds__(kThreads) cl_classify(ClusterArgs a) {
     }
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
   const double width_ms = (double)(s_w1 - s_w0 + 1) * a.t_samp * 1e3;
-  // centred moving average of the signature, its maximum, and the RMSE
-  // against Eq. 3 (sequential, in DM order)
+  // centred moving average of the signature (each trial's window summed in
+  // DM order), its maximum, and the RMSE against Eq. 3
   const int h = a.smooth / 2;
-  double smax = 0.0;
-  for (int i = 0; i < span; ++i) {
+  double vmax = 0.0;
+  for (int i = threadIdx.x; i < span; i += kThreads) {
     const int p0 = i - h < 0 ? 0 : i - h, p1 = i + h + 1 > span ? span : i + h + 1;
     double v = 0.0;
     for (int j = p0; j < p1; ++j) v += (double)fval(s_sig[j]);
     v /= (double)(p1 - p0);
-    smax = v > smax ? v : smax;
+    s_v[i] = v;
+    vmax = v > vmax ? v : vmax;
   }
-  double ss = 0.0;
+  const double smax = block_reduce<true>(vmax, s_red);
   const double dm_star = a.dm[ds];
-  for (int i = 0; i < span; ++i) {
-    const int p0 = i - h < 0 ? 0 : i - h, p1 = i + h + 1 > span ? span : i + h + 1;
-    double v = 0.0;
-    for (int j = p0; j < p1; ++j) v += (double)fval(s_sig[j]);
-    v /= (double)(p1 - p0);
-    const double r = v / smax - eq3(a.dm[lo + i] - dm_star, width_ms, a.bw_mhz, a.f_ghz);
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < span; i += kThreads) {
+    const double r = s_v[i] / smax - eq3(a.dm[lo + i] - dm_star, width_ms, a.bw_mhz, a.f_ghz);
     ss += r * r;
   }
-  const double rmse = sqrt(ss / (double)span);
-  const bool broadband = dm_star < a.dm_min;
-  tp_cluster r;
-  r.label = k;
-  r.n = b1 - b0;
-  r.d_lo = lo;
-  r.d_hi = s_dhi;
-  r.d_star = ds;
-  r.flags = (broadband ? 2 : 0) | ((!broadband && rmse <= a.rmse_max) ? 1 : 0);
-  r.t_first = s_t0;
-  r.t_last = s_t1;
-  r.snr_max = fval(s_smax);
-  r.width_ms = (float)width_ms;
-  r.rmse = (float)rmse;
-  r.reserved = 0.f;
-  a.clusters[k] = r;
+  ss = block_reduce<false>(ss, s_red);
+  if (threadIdx.x == 0) {
+    const double rmse = sqrt(ss / (double)span);
+    const bool broadband = dm_star < a.dm_min;
+    tp_cluster r;
+    r.label = k;
+    r.n = b1 - b0;
+    r.d_lo = lo;
+    r.d_hi = s_dhi;
+    r.d_star = ds;
+    r.flags = (broadband ? 2 : 0) | ((!broadband && rmse <= a.rmse_max) ? 1 : 0);
+    r.t_first = s_t0;
+    r.t_last = s_t1;
+    r.snr_max = fval(s_smax);
+    r.width_ms = (float)width_ms;
+    r.rmse = (float)rmse;
+    r.reserved = 0.f;
+    a.clusters[k] = r;
+  }
+  __syncthreads();
+}
+
+// A fixed grid strides over the clusters, one cluster per CTA at a time.
+__global__ void __launch_bounds__(kThreads) cl_classify(ClusterArgs a) {
+  extern __shared__ double s_dyn[];
+  double* s_v = s_dyn;
+  int* s_sig = reinterpret_cast<int*>(s_dyn + a.ndm);
+  int* s_cnt = s_sig + a.ndm;
+  const int n = *a.n_clusters;
+  for (int k = blockIdx.x; k < n; k += gridDim.x) classify_one(a, k, s_v, s_sig, s_cnt);
 }
 
 }  // namespace
 
 cudaError_t launch_cluster(const ClusterArgs& a, cudaStream_t s) {
   const unsigned gp = (unsigned)((a.cap + kThreads - 1) / kThreads);
-  cudaError_t e = cudaMemsetAsync(a.cl_count, 0, sizeof(int) * (size_t)a.max_clusters, s);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.cl_count, 0, sizeof(int) * (size_t)a.max_clusters, s);
   if (e != cudaSuccess) return e;
   cl_rows<<<(a.ndm + 1 + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
   cl_core<<<gp, kThreads, 0, s>>>(a);
-  cl_union<<<gp, kThreads, 0, s>>>(a);
+  cl_union<<<8 * sms, kThreads, 0, s>>>(a);
   cl_assign<<<gp, kThreads, 0, s>>>(a);
   cl_number<<<1, 1024, 0, s>>>(a);
   cl_label<<<gp, kThreads, 0, s>>>(a);
   cl_offsets<<<1, 1024, 0, s>>>(a);
   cl_scatter<<<gp, kThreads, 0, s>>>(a);
-  const size_t sm = sizeof(int) * 2 * (size_t)a.ndm;
+  const size_t sm = (sizeof(double) + 2 * sizeof(int)) * (size_t)a.ndm;
   e = cudaFuncSetAttribute(cl_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  cl_classify<<<(unsigned)a.max_clusters, kThreads, sm, s>>>(a);
+  const int grid = a.max_clusters < 4 * sms ? a.max_clusters : 4 * sms;
+  cl_classify<<<(unsigned)grid, kThreads, sm, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1532,6 +1532,8 @@ int tp_plan_set_clustering(tp_plan* p, const tp_cluster_params* prm) {
         !std::isfinite(prm->snr_eps))
       return set_error(TP_EINVAL, "invalid clustering parameters");
   }
+  if (prm && p->ndm > tp::kMaxClusterDm)
+    return set_error(TP_EINVAL, "clustering supports at most %d DM trials (plan has %d)", tp::kMaxClusterDm, p->ndm);
   if (p->users > 0) return set_error(TP_EBUSY, "plan is used by %d open beams", p->users);
   p->cluster = prm != nullptr;
   if (prm) p->cparams = *prm;

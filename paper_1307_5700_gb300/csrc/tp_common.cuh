@@ -183,6 +183,7 @@ struct ClusterArgs {
 };
 cudaError_t launch_cluster(const ClusterArgs& a, cudaStream_t s);
 constexpr int kMaxClusters = 65536;  // clusters kept per block
+constexpr int kMaxClusterDm = 14336;  // DM trials a clustering plan may have (shared memory)
 
 // Largest median-filter width of the post-processing.
 constexpr int kMaxMedianWidth = 9;

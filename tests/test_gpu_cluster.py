@@ -94,6 +94,21 @@ def test_many_small_clusters():
     _compare(r, labels, cl, ncl, dms, prm)
 
 
+def test_wide_cluster():
+    """A strong pulse over 400 fine DM trials: one cluster spans more trials
+    (263) than a classification CTA has threads."""
+    nchan, nsamp = 256, 16000
+    dms = np.arange(400) * 0.1
+    od, dmax = O.delay_table(nchan, F_LO, BW, TS, dms)
+    x = synth.noise(nchan, nsamp, 9)
+    synth.add_pulse(x, od[200].astype(np.float64) + 6000, 20.0, 120.0 / np.sqrt(nchan))
+    rfi = O.RfiParams(enable_channel=False, enable_spectrum=False)
+    prm = O.ClusterParams()
+    r, labels, cl, ncl, trunc = _run(x, "f32", nchan, dms, prm, 5.0, rfi)
+    ref = _compare(r, labels, cl, ncl, dms, prm)
+    assert max(k["d_hi"] - k["d_lo"] + 1 for k in ref) > 256
+
+
 def test_clustering_arguments():
     e = tp.tp_engine_create(0)
     try:
@@ -101,6 +116,10 @@ def test_clustering_arguments():
         for bad in (dict(t_eps=-1), dict(min_pts=0), dict(smooth=2), dict(snr_eps=float("nan"))):
             with pytest.raises(tp.TpError):
                 tp.tp_plan_set_clustering(p, **bad)
+        big = tp.tp_create_plan(e, 64, F_LO, BW, TS, np.arange(14337) * 0.01, "f32", None, 5.0)
+        with pytest.raises(tp.TpError):  # more DM trials than the classification holds
+            tp.tp_plan_set_clustering(big)
+        tp.tp_plan_destroy(big)
         b = tp.tp_beam_open(e, p, 4000, 1024)
         with pytest.raises(tp.TpError) as ei:
             tp.tp_plan_set_clustering(p)
