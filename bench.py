@@ -523,6 +523,11 @@ def main():
     stage_ms, nstage = tp.tp_get_stage_times(e, beam)
     tp.tp_set_profiling(e, False)
     per_block = np.array([s.elapsed_time(t) for s, t in zip(starts, ends)])
+    last_block = {"detections": int(tp.tp_get_candidates(e, beam, 0)[1])}
+    if args.cluster:  # what the clustering worked on (read after the timed region)
+        cl, ncl, trunc = tp.tp_get_clusters(e, beam)
+        last_block.update(clusters=int(ncl), candidate_clusters=int(np.count_nonzero(cl["flags"] & 1)),
+                          broadband_clusters=int(np.count_nonzero(cl["flags"] & 2)), truncated=bool(trunc))
     units = len(DMS) * BLOCK * args.steps * world
     value = units / (ms / 1e3)
 
@@ -599,6 +604,7 @@ def main():
                        "parallelism": f"replicas x{world}", "kernel_shape": int(best),
                        "postprocess": {"median_width": args.median, "detrend": bool(args.detrend)},
                        "bandpass_fit_order": args.fit, "clustering": bool(args.cluster),
+                       "last_block": last_block,
                        "autotune_ms": tune},
             "realtime_beams": value / (len(DMS) / TSAMP),
             "p50_block_latency_ms": float(np.percentile(per_block, 50)),
