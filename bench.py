@@ -46,7 +46,10 @@ PAPER_DERIVED = 6.5e7  # DM-trial.samples/s per GPU derived from the paper's Tab
 # DRAM bytes (read + write) of one dedispersion launch of this workload, per
 # (sample format, kernel shape), from an ncu capture of the timed launch
 # (profiles/dedisperse_kernel_dm_quads_stream1024_640dm_f32.md)
-TRAFFIC_BY_SHAPE = {("f32", 33): 584.843264e6 + 331.993600e6}
+# DRAM bytes of one dedispersion launch of this workload (ncu captures):
+# shape 33 dram__bytes_read.sum + dram__bytes_write.sum; shape 46
+# dram__bytes.sum.per_second x gpu__time_duration
+TRAFFIC_BY_SHAPE = {("f32", 33): 584.843264e6 + 331.993600e6, ("f32", 46): 175.55649461716e9 * 5.406816e-3}
 METRIC = "DM-trial*samples/s per GB300 (real-time beams sustained, p99 block latency alongside)"
 WORKLOAD = "stream: 1 beam, 1024 ch 398-418 MHz, 51.2 us, 640 DMs 0-127.8 step 0.2, FP32, 2^17-sample blocks"
 

@@ -221,6 +221,43 @@ def emit_quad(S, MMAX):
     return "\n".join(lines)
 
 
+# (S, MMAX) of the FP32 two-segment DM-quad shapes (ALGO 4): S odd.
+QUADS2 = [(15, 9), (21, 9), (23, 9), (19, 9)]
+
+
+def emit_quad2(S, MMAX):
+    """emit_quad for two output segments 32 S samples apart: the lane's
+    outputs s of segment 0 and of segment 1 share one 64-bit accumulator
+    (segment 0 in the low word), and each window sample of the two segments
+    (the second segment's window 128 S bytes after the first's) is packed
+    into one register pair, so a single add.rn.f32x2 adds both; each lane's
+    result is the same binary32 add as the scalar form."""
+    nb = 8 * (MMAX + 1)
+    nw = S + 3 * (MMAX + 1)
+    ia = 4 * S
+    body = ["{", f".reg .f32 u<{nw}>, v<{nw}>;", f".reg .b64 w<{nw}>;",
+            "tbl: .branchtargets " + ", ".join(f"C{b}" for b in range(nb)) + ";",
+            f"brx.idx.uni %{4 * S + 1}, tbl;"]
+    for b in range(nb):
+        o = quad_steps(b)
+        body.append(f"C{b}:")
+        for k in range(S + o[3]):
+            body.append(f"ld.shared.f32 u{k}, [%{ia}+{4 * k}];")
+            body.append(f"ld.shared.f32 v{k}, [%{ia}+{4 * k + 128 * S}];")
+            body.append(f"mov.b64 w{k}, {{u{k}, v{k}}};")
+            for j in range(4):
+                s_ = k - o[j]
+                if 0 <= s_ < S:
+                    r = j * S + s_
+                    body.append(f"add.rn.f32x2 %{r}, %{r}, w{k};")
+        if b != nb - 1:
+            body.append("bra.uni CEND;")
+    body += ["CEND:", "}"]
+    outs = ", ".join(f'"+l"(a[{j}][{s_}])' for j in range(4) for s_ in range(S))
+    return _asm_fn(f"void add_quad2<{S}, {MMAX}>(int b, unsigned addr, unsigned long long (&a)[4][{S}])", body,
+                   outs, '"r"(addr), "r"(b)')
+
+
 # (S, MMAX) of the 16-bit float DM-quad shapes: S = 2 mod 4.
 QUADS16 = [(26, 9), (30, 9)]
 # (S, MMAX) of the 8-bit DM-quad shapes: S = 2 mod 4.
@@ -330,6 +367,11 @@ def main():
         "template <int S, int MMAX>",
         "__device__ __forceinline__ void add_quad(int b, unsigned addr, float (&a)[4][S]);",
         "",
+        "// four trials and two output segments 32 S samples apart, FP32 samples;",
+        "// a[j][s] holds output s of both segments (segment 0 in the low word)",
+        "template <int S, int MMAX>",
+        "__device__ __forceinline__ void add_quad2(int b, unsigned addr, unsigned long long (&a)[4][S]);",
+        "",
         "// four trials, 16-bit float samples (kind 0 = binary16, 1 = bfloat16);",
         "// block index = (r * (MMAX + 1) + m) * 8 + bits, r = the first trial's",
         "// half-word offset in its first word",
@@ -364,6 +406,8 @@ def main():
             out.append(emit_pair16(S, OMAX, kind))
     for S, MMAX in QUADS:
         out.append(emit_quad(S, MMAX))
+    for S, MMAX in QUADS2:
+        out.append(emit_quad2(S, MMAX))
     for S, MMAX in QUADS16:
         for kind in (0, 1):
             out.append(emit_quad16(S, MMAX, kind))

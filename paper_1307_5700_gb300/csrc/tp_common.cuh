@@ -107,15 +107,17 @@ struct BatchArgs {
 // Register-tile shapes of the dedispersion kernel.
 struct KernelShape {
   int K;      // DM trials per warp
-  int S;      // consecutive outputs per lane (tile = 32 S samples)
+  int S;      // consecutive outputs per lane and segment (tile = 32 S samples; ALGO 4: 64 S,
+              // two segments)
   int OMAX;   // largest in-window offset the kernel handles
   int NCONS;  // consumer warps per CTA (DM groups per tile)
   int FMT;    // staged series: 4 = FP32 y (FP32 data, or 16-bit float data staged as
               // FP32 x~ - b), 2 = 16-bit float x~, 3 = 8-bit x~ as 16-bit integers
   int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads;
-              // 2: DM pairs sharing one window; 3: DM quads sharing one window
+              // 2: DM pairs sharing one window; 3: DM quads sharing one window;
+              // 4: DM quads over two output segments with paired FP32 adds
 };
-constexpr int kNumShapes = 44;
+constexpr int kNumShapes = 48;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
