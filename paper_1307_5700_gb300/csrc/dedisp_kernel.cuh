@@ -31,7 +31,10 @@
 // t0 + 32 S + l S (TT = 64 S): the same window sample of both segments sits
 // in one register pair and one add.rn.f32x2 updates both accumulators, which
 // halves the add instructions per output; every lane still rounds each add
-// to binary32 as the scalar form does.
+// to binary32 as the scalar form does.  ALGO 5 pairs a lane's own outputs
+// s and s + S / 2 instead (S odd, output 2 (S / 2) added alone): register
+// pair k holds window samples k and k + S / 2 of the one window, so each
+// sample is loaded once for both halves.
 // Each (d, t) adds its channels in index order (FP32, or exact integers).
 // Every mbarrier wait is bounded; a wait that gives up records TP_ETIMEOUT in
 // the beam's status word and the CTA leaves after letting its copies land.
@@ -161,7 +164,8 @@ struct Shape {
   static_assert(ALGO >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
   static_assert(ALGO != 2 || (MODE != kModeU8 && K == 2), "DM-pair windows: float data, two trials per warp");
   static_assert(ALGO < 3 || K == 4, "DM-quad windows: four trials per warp");
-  static_assert(ALGO != 4 || MODE == kModeF32, "two-segment DM quads: FP32 staging");
+  static_assert(ALGO < 4 || MODE == kModeF32, "paired-add DM quads: FP32 staging");
+  static_assert(ALGO != 5 || S % 2 == 1, "in-lane pairs: S = 2 (S / 2) + 1");
   static_assert(ALGO == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
   static_assert(MODE != kModeU8 || ALGO == 1 || ALGO == 3, "8-bit data: direct loads or DM quads");
 };
@@ -393,6 +397,17 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   for (int j = 0; j < K; ++j)
 #pragma unroll
     for (int s = 0; s < (ALGO == 4 ? S : 1); ++s) acc2[j][s] = 0ull;
+  // in-lane paired DM quads: outputs s and s + S / 2 of DM j packed in
+  // accp[j][s] (low word first), output 2 (S / 2) in acct[j]
+  constexpr int PH = ALGO == 5 ? S / 2 : 1;
+  unsigned long long accp[K][PH];
+  float acct[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    acct[j] = 0.f;
+#pragma unroll
+    for (int s = 0; s < PH; ++s) accp[j][s] = 0ull;
+  }
   // 8-bit mode: pk[j][m] holds outputs 2m, 2m + 1 of DM j as 16-bit lanes
   // (exact: no lane sum reaches 2^16 within kU8FoldStages stages), folded
   // into the 32-bit sums sum32 every kU8FoldStages stages
@@ -534,7 +549,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 #pragma unroll 1
         for (int ci = 0; ci < nc; ++ci) {
           const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
-          if constexpr (ALGO == 4)
+          if constexpr (ALGO == 5)
+            add_quadp<S, OMAX>(inf.y, sbase + (unsigned)inf.x, accp, acct);
+          else if constexpr (ALGO == 4)
             add_quad2<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc2);
           else if constexpr (MODE == kModeF32)
             add_quad<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc);
@@ -616,6 +633,10 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
     if constexpr (ALGO == 4) {
       const unsigned long long p = acc2[j][s];
       return __uint_as_float(seg ? (unsigned)(p >> 32) : (unsigned)p);
+    } else if constexpr (ALGO == 5) {
+      if (s == 2 * PH) return acct[j];
+      const unsigned long long p = accp[j][s < PH ? s : s - PH];
+      return __uint_as_float(s < PH ? (unsigned)p : (unsigned)(p >> 32));
     } else {
       return acc[j][s];
     }

@@ -14,7 +14,9 @@
 // ALGO 3: DM quads sharing one window, steps between consecutive trials m or
 // m + 1 with m <= OMAX;
 // ALGO 4: ALGO 3 over two output segments per lane (32 S samples apart), both
-// added by one paired FP32 add (FP32 staging only).
+// added by one paired FP32 add (FP32 staging only);
+// ALGO 5: ALGO 3 with the lane's outputs s and s + S / 2 added by one paired
+// FP32 add (S odd; FP32 staging only).
 // MINB: CTAs per SM the register allocation is sized for.
 #define TP_SHAPES(X)                 \
   X(0, 4, 20, 36, 8, 4, 0, 1)        \
@@ -64,7 +66,12 @@
   X(44, 4, 15, 9, 11, 4, 4, 1)       \
   X(45, 4, 21, 9, 7, 4, 4, 1)        \
   X(46, 4, 23, 9, 7, 4, 4, 1)        \
-  X(47, 4, 19, 9, 7, 4, 4, 1)
+  X(47, 4, 19, 9, 7, 4, 4, 1)        \
+  X(48, 4, 45, 9, 7, 4, 5, 1)        \
+  X(49, 4, 43, 9, 7, 4, 5, 1)        \
+  X(50, 4, 27, 9, 11, 4, 5, 1)       \
+  X(51, 4, 25, 9, 11, 4, 5, 1)       \
+  X(52, 4, 29, 9, 11, 4, 5, 1)
 
 namespace tp {
 constexpr int kDedispParts = 6;  // translation units the kernel instantiations are split over

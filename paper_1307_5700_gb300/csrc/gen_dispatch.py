@@ -258,6 +258,51 @@ def emit_quad2(S, MMAX):
                    outs, '"r"(addr), "r"(b)')
 
 
+# (S, MMAX) of the FP32 in-lane paired DM-quad shapes (ALGO 5): S odd.
+QUADSP = [(45, 9), (43, 9), (27, 9), (25, 9), (29, 9)]
+
+
+def emit_quadp(S, MMAX):
+    """emit_quad with the lane's outputs s and s + H paired (H = S // 2):
+    a[j][s] holds outputs s (low word) and s + H (high word) of trial j for
+    s < H, t[j] its output 2 H.  The window w[0 .. S + o3) is loaded once, in
+    order; pair k = (w[k], w[k + H]) is formed as soon as w[k + H] is loaded
+    and added into a[j][k - o_j] of every trial j with 0 <= k - o_j < H by
+    one add.rn.f32x2 (samples w[H .. H + o3) sit in two pairs; the assembler
+    copies them).  Each lane's result is the same binary32 add as the
+    scalar form."""
+    H = S // 2
+    nb = 8 * (MMAX + 1)
+    nw = S + 3 * (MMAX + 1)
+    ia = 4 * H + 4
+    body = ["{", f".reg .f32 w<{nw}>;", f".reg .b64 p<{nw}>;",
+            "tbl: .branchtargets " + ", ".join(f"C{b}" for b in range(nb)) + ";",
+            f"brx.idx.uni %{ia + 1}, tbl;"]
+    for b in range(nb):
+        o = quad_steps(b)
+        body.append(f"C{b}:")
+        for i in range(S + o[3]):
+            body.append(f"ld.shared.f32 w{i}, [%{ia}+{4 * i}];")
+            k = i - H
+            if k >= 0:
+                used = [j for j in range(4) if 0 <= k - o[j] < H]
+                if used:
+                    body.append(f"mov.b64 p{k}, {{w{k}, w{i}}};")
+                    for j in used:
+                        r = j * H + (k - o[j])
+                        body.append(f"add.rn.f32x2 %{r}, %{r}, p{k};")
+            for j in range(4):
+                if i - o[j] == 2 * H:
+                    body.append(f"add.rn.f32 %{4 * H + j}, %{4 * H + j}, w{i};")
+        if b != nb - 1:
+            body.append("bra.uni CEND;")
+    body += ["CEND:", "}"]
+    outs = ", ".join([f'"+l"(a[{j}][{s_}])' for j in range(4) for s_ in range(H)] +
+                     [f'"+f"(t[{j}])' for j in range(4)])
+    return _asm_fn(f"void add_quadp<{S}, {MMAX}>(int b, unsigned addr, unsigned long long (&a)[4][{H}], "
+                   f"float (&t)[4])", body, outs, '"r"(addr), "r"(b)')
+
+
 # (S, MMAX) of the 16-bit float DM-quad shapes: S = 2 mod 4.
 QUADS16 = [(26, 9), (30, 9)]
 # (S, MMAX) of the 8-bit DM-quad shapes: S = 2 mod 4.
@@ -372,6 +417,12 @@ def main():
         "template <int S, int MMAX>",
         "__device__ __forceinline__ void add_quad2(int b, unsigned addr, unsigned long long (&a)[4][S]);",
         "",
+        "// four trials, FP32 samples, the lane's outputs s and s + S / 2 paired in",
+        "// a[j][s] (low word first), output 2 (S / 2) in t[j]",
+        "template <int S, int MMAX>",
+        "__device__ __forceinline__ void add_quadp(int b, unsigned addr, unsigned long long (&a)[4][S / 2],",
+        "                                          float (&t)[4]);",
+        "",
         "// four trials, 16-bit float samples (kind 0 = binary16, 1 = bfloat16);",
         "// block index = (r * (MMAX + 1) + m) * 8 + bits, r = the first trial's",
         "// half-word offset in its first word",
@@ -408,6 +459,8 @@ def main():
         out.append(emit_quad(S, MMAX))
     for S, MMAX in QUADS2:
         out.append(emit_quad2(S, MMAX))
+    for S, MMAX in QUADSP:
+        out.append(emit_quadp(S, MMAX))
     for S, MMAX in QUADS16:
         for kind in (0, 1):
             out.append(emit_quad16(S, MMAX, kind))

@@ -115,9 +115,10 @@ struct KernelShape {
               // FP32 x~ - b), 2 = 16-bit float x~, 3 = 8-bit x~ as 16-bit integers
   int ALGO;   // 0: register window + shifted-add dispatch; 1: direct shared loads;
               // 2: DM pairs sharing one window; 3: DM quads sharing one window;
-              // 4: DM quads over two output segments with paired FP32 adds
+              // 4: DM quads over two output segments with paired FP32 adds;
+              // 5: DM quads with a lane's outputs s and s + S / 2 paired
 };
-constexpr int kNumShapes = 48;
+constexpr int kNumShapes = 53;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
