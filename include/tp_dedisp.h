@@ -265,6 +265,26 @@ int tp_beam_set_bandpass(tp_engine *e, int beam, const double *mu, const double 
  * beam's previous detection (which may run on the engine stream). */
 int tp_push_block(tp_engine *e, int beam, const void *buf, int nsamp, int buf_is_device);
 
+/* Double-buffered ingest (Sec. 2.1: the next GPU buffer is filled while the
+ * current one is processed).  tp_prefetch_block starts the host -> device
+ * copy of the next block's `nsamp` new samples per channel (`host_buf`,
+ * channel-major [nchan][nsamp] in the plan's dtype, pinned host memory for
+ * asynchrony) on a copy stream of the beam's own, straight into the window
+ * the next block will use, so the copy overlaps the current block's kernels;
+ * it may be called while the current block is still being processed.  The
+ * caller keeps `host_buf` unchanged until tp_push_prefetched has returned
+ * and the beam's stream has passed that point (tp_get_candidates of that
+ * block, for instance).  tp_push_prefetched then publishes the block like
+ * tp_push_block (its stream waits for the copy and moves the overlap tail);
+ * the two calls together are equivalent to tp_push_block with `host_buf`.
+ * Errors: tp_prefetch_block TP_EINVAL (size, NULL), TP_EBUSY (a prefetched
+ * block is already waiting); tp_push_prefetched TP_ENOTREADY (nothing
+ * prefetched), TP_EBUSY (the previous block has not been through
+ * tp_detect).  While a prefetched block waits, tp_push_block returns
+ * TP_EBUSY. */
+int tp_prefetch_block(tp_engine *e, int beam, const void *host_buf, int nsamp);
+int tp_push_prefetched(tp_engine *e, int beam);
+
 /* Mark the beam's current window as not yet processed, so that tp_dedisperse
  * runs on it again (for instance after tp_plan_set_shape); the next push
  * still continues the stream from this window.  TP_ENOTREADY if the beam holds

@@ -51,7 +51,7 @@ EXPORTS = (
     "tp_server_end_stream", "tp_server_run", "tp_server_results", "tp_server_candidates", "tp_server_destroy",
     "tp_beam_rewind", "tp_autotune_batch", "tp_plan_set_postprocess", "tp_get_processed_series",
     "tp_get_detrend", "tp_plan_set_bandpass_fit", "tp_get_bandpass_fit", "tp_plan_set_clustering",
-    "tp_get_clusters", "tp_get_candidate_labels",
+    "tp_get_clusters", "tp_get_candidate_labels", "tp_prefetch_block", "tp_push_prefetched",
 )
 
 
@@ -110,6 +110,8 @@ _SIGS = {
     "tp_beam_set_stream": (_i, [_vp, _i, _vp]),
     "tp_beam_set_bandpass": (_i, [_vp, _i, _vp, _vp, _i]),
     "tp_push_block": (_i, [_vp, _i, _vp, _i, _i]),
+    "tp_prefetch_block": (_i, [_vp, _i, _vp, _i]),
+    "tp_push_prefetched": (_i, [_vp, _i]),
     "tp_dedisperse": (_i, [_vp, _i]),
     "tp_detect": (_i, [_vp, _i]),
     "tp_get_candidates": (_i, [_vp, _i, _vp, _i, _vp]),
@@ -302,6 +304,21 @@ def tp_push_block(e, beam, buf, nsamp=None, buf_is_device=None):
     if buf_is_device is None:
         buf_is_device = bool(getattr(buf, "is_cuda", False))
     return _check(lib().tp_push_block(e, beam, _addr(buf), int(nsamp), int(bool(buf_is_device))))
+
+
+def tp_prefetch_block(e, beam, host_buf, nsamp=None):
+    """Start the copy of the next block from ``host_buf`` (a host numpy array
+    or pinned torch tensor, (nchan, nsamp)); the caller keeps it unchanged
+    until the block has been pushed and processed."""
+    if nsamp is None:
+        nsamp = host_buf.shape[-1]
+    if getattr(host_buf, "is_cuda", False):
+        raise ValueError("tp_prefetch_block takes a host buffer")
+    return _check(lib().tp_prefetch_block(e, beam, _addr(host_buf), int(nsamp)))
+
+
+def tp_push_prefetched(e, beam):
+    return _check(lib().tp_push_prefetched(e, beam))
 
 
 def tp_dedisperse(e, beam):

@@ -141,6 +141,14 @@ struct Beam {
   bool own_event = false;
   cudaEvent_t ev_detect = nullptr;  // the beam's last detection finished
   cudaEvent_t ev_pushed = nullptr;  // the beam's last push finished (its own stream)
+  // prefetch of the next block (tp_prefetch_block): host -> device copy of its
+  // new samples into the window the block after the current one will use, on
+  // a copy stream of the beam's own
+  cudaStream_t pf_stream = nullptr;
+  cudaEvent_t ev_win_free = nullptr;  // the last push copied its overlap tail out of the other window
+  cudaEvent_t ev_pf = nullptr;        // the pending prefetch's copy finished
+  bool pf_pending = false;
+  int pf_nsamp = 0;
   // device buffers
   void* win[2] = {nullptr, nullptr};
   void* chunk_sums = nullptr;
@@ -479,6 +487,12 @@ void free_beam(Beam* b) {
     }
   b->ev_pool.clear();
   b->ev_pending.clear();
+  if (b->pf_stream) {
+    cudaStreamSynchronize(b->pf_stream);  // a pending prefetch still reads the caller's buffer
+    cudaStreamDestroy(b->pf_stream);
+  }
+  if (b->ev_win_free) cudaEventDestroy(b->ev_win_free);
+  if (b->ev_pf) cudaEventDestroy(b->ev_pf);
   if (b->ev_detect) cudaEventDestroy(b->ev_detect);
   if (b->ev_pushed) cudaEventDestroy(b->ev_pushed);
   for (void* p : b->allocs) cudaFree(p);
@@ -1115,6 +1129,8 @@ int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capac
   }
   ce = cudaEventCreateWithFlags(&b->ev_detect, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ev_pushed, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ev_win_free, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ev_pf, cudaEventDisableTiming);
   if (ce != cudaSuccess) {
     free_beam(b);
     delete b;
@@ -1206,23 +1222,27 @@ int tp_beam_set_bandpass(tp_engine* e, int beam, const double* mu, const double*
   return TP_OK;
 }
 
-int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is_device) {
-  if (!e) return set_error(TP_EINVAL, "engine is NULL");
-  std::lock_guard<std::recursive_mutex> lk(e->mu);
-  Beam* b = get_beam(e, beam);
-  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
-  const tp_plan* p = b->plan;
-  if (!buf) return set_error(TP_EINVAL, "buf is NULL");
+namespace {
+
+// Checks shared by the pushes: the size, the beam's state and the first
+// block's length.
+int check_push(const Beam* b, int nsamp, int beam) {
   if (nsamp < 1 || nsamp > b->B) return set_error(TP_EINVAL, "nsamp %d not in [1, %d]", nsamp, b->B);
   if (b->state == kReady || b->state == kDedispersed)
     return set_error(TP_EBUSY, "beam %d: previous block not yet through detection", beam);
-  const int64_t dmax = p->max_delay;
-  if (b->pushed == 0 && nsamp <= dmax)
+  if (b->pushed == 0 && nsamp <= b->plan->max_delay)
     return set_error(TP_EINVAL, "first block (%d samples) must exceed the largest delay %lld", nsamp,
-                     (long long)dmax);
+                     (long long)b->plan->max_delay);
+  return TP_OK;
+}
+
+// Assembles the next window on stream s: the overlap tail of the current
+// window, then (unless the new samples are already in place) the new block
+// from `buf`; then publishes the block (t0, events, state).
+int assemble_window(tp_engine* e, Beam* b, cudaStream_t s, const void* buf, int nsamp, int buf_is_device) {
+  const tp_plan* p = b->plan;
+  const int64_t dmax = p->max_delay;
   const size_t es = dtype_size(p->dtype);
-  DeviceGuard g(e->device);
-  cudaStream_t s = beam_stream(e, b);
   const cudaMemcpyKind kind = buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t dpitch = (size_t)b->pitch * es;
   // on its own stream, a push must not overwrite the window, t0 or buffers
@@ -1232,9 +1252,9 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
   int nk = 0;  // copy kernels launched
   if (b->pushed == 0) {
     b->cur = 0;
-    if (buf_is_device)
+    if (buf && buf_is_device)
       TP_CUDA_TRY(copy_rows(b->win[0], dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan, s, &nk));
-    else
+    else if (buf)
       TP_CUDA_TRY(cudaMemcpy2DAsync(b->win[0], dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
                                     kind, s));
     b->nsamp_win = nsamp;
@@ -1247,10 +1267,10 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
       const char* src = static_cast<const char*>(b->win[b->cur]) + (size_t)(b->nsamp_win - dmax) * es;
       TP_CUDA_TRY(copy_rows(dst, dpitch, src, dpitch, (size_t)dmax * es, p->nchan, s, &nk));
     }
-    if (buf_is_device)
+    if (buf && buf_is_device)
       TP_CUDA_TRY(copy_rows(dst + (size_t)dmax * es, dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
                             s, &nk));
-    else
+    else if (buf)
       TP_CUDA_TRY(cudaMemcpy2DAsync(dst + (size_t)dmax * es, dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es,
                                     p->nchan, kind, s));
     b->cur = nxt;
@@ -1258,6 +1278,9 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
     b->nout = nsamp;
     b->t0_abs = b->pushed - dmax;
   }
+  // the other window is free once the tail has been copied out of it (and,
+  // earlier on this stream, the previous block's kernels have read it)
+  TP_CUDA_TRY(cudaEventRecord(b->ev_win_free, s));
   e->launches += (uint64_t)nk;
   TP_CUDA_TRY(cudaMemcpyAsync(b->d_t0, &b->t0_abs, 8, cudaMemcpyHostToDevice, s));
   TP_CUDA_TRY(cudaEventRecord(b->ev_pushed, s));
@@ -1265,6 +1288,70 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
   b->pushed += nsamp;
   b->state = kReady;
   return TP_OK;
+}
+
+}  // namespace
+
+int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is_device) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (!buf) return set_error(TP_EINVAL, "buf is NULL");
+  if (b->pf_pending) return set_error(TP_EBUSY, "beam %d has a prefetched block to push first", beam);
+  const int rc = check_push(b, nsamp, beam);
+  if (rc != TP_OK) return rc;
+  DeviceGuard g(e->device);
+  return assemble_window(e, b, beam_stream(e, b), buf, nsamp, buf_is_device);
+}
+
+int tp_prefetch_block(tp_engine* e, int beam, const void* host_buf, int nsamp) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (!host_buf) return set_error(TP_EINVAL, "buf is NULL");
+  if (b->pf_pending) return set_error(TP_EBUSY, "beam %d already holds a prefetched block", beam);
+  if (nsamp < 1 || nsamp > b->B) return set_error(TP_EINVAL, "nsamp %d not in [1, %d]", nsamp, b->B);
+  const tp_plan* p = b->plan;
+  if (b->pushed == 0 && nsamp <= p->max_delay)
+    return set_error(TP_EINVAL, "first block (%d samples) must exceed the largest delay %lld", nsamp,
+                     (long long)p->max_delay);
+  DeviceGuard g(e->device);
+  if (!b->pf_stream) TP_CUDA_TRY(cudaStreamCreateWithFlags(&b->pf_stream, cudaStreamNonBlocking));
+  const size_t es = dtype_size(p->dtype);
+  const size_t dpitch = (size_t)b->pitch * es;
+  // the window the next push assembles: win[0] for the first block, else
+  // the one the current block does not use, after the overlap tail
+  char* dst;
+  if (b->pushed == 0) {
+    dst = static_cast<char*>(b->win[0]);
+  } else {
+    dst = static_cast<char*>(b->win[b->cur ^ 1]) + (size_t)p->max_delay * es;
+    TP_CUDA_TRY(cudaStreamWaitEvent(b->pf_stream, b->ev_win_free, 0));
+  }
+  TP_CUDA_TRY(cudaMemcpy2DAsync(dst, dpitch, host_buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
+                                cudaMemcpyHostToDevice, b->pf_stream));
+  TP_CUDA_TRY(cudaEventRecord(b->ev_pf, b->pf_stream));
+  b->pf_pending = true;
+  b->pf_nsamp = nsamp;
+  return TP_OK;
+}
+
+int tp_push_prefetched(tp_engine* e, int beam) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (!b->pf_pending) return set_error(TP_ENOTREADY, "beam %d holds no prefetched block", beam);
+  const int rc = check_push(b, b->pf_nsamp, beam);
+  if (rc != TP_OK) return rc;
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  TP_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_pf, 0));
+  const int r = assemble_window(e, b, s, nullptr, b->pf_nsamp, 0);
+  if (r == TP_OK) b->pf_pending = false;
+  return r;
 }
 
 int tp_dedisperse(tp_engine* e, int beam) {

@@ -357,6 +357,89 @@ def test_streaming_equals_long_block():
             assert np.all(np.abs(Dcat - Do) <= TOL * mass)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_prefetched_stream_equals_pushed_stream(dtype):
+    """Double-buffered ingest: each block's copy is started while the
+    previous block is still being processed (its candidates not yet read);
+    every block's series, masks and candidates are bit-identical to the same
+    stream pushed block by block, and the stream matches the oracle."""
+    torch = pytest.importorskip("torch")
+    nchan, B, nblk = 128, 3000, 5
+    dms = np.arange(40) * 1.0
+    f_lo, bw, ts = 398.0, 20.0, 51.2e-6
+    od, dmax = O.delay_table(nchan, f_lo, bw, ts, dms)
+    xf = synth.noise(nchan, B * nblk, 9301, mean=128.0 if dtype == "u8" else 0.0, std=16.0 if dtype == "u8" else 1.0)
+    synth.add_pulse(xf, od[25].astype(np.float64) + 2 * B + 700, 15.0, 80.0 if dtype == "u8" else 5.0 / 8)
+    x = synth.to_u8(xf) if dtype == "u8" else xf
+    blocks = [np.ascontiguousarray(x[:, k * B:(k + 1) * B]) for k in range(nblk)]
+    # pinned host copies for the prefetching run (the first two pageable)
+    host = [b if k < 2 else torch.from_numpy(b).pin_memory() for k, b in enumerate(blocks)]
+
+    def collect(g):
+        cands, n, rc = tp.tp_get_candidates(g.e, g.beam, g.cap)
+        out = dict(candidates=cands, n_candidates=n, rc=rc, info=tp.tp_beam_info(g.e, g.beam),
+                   D=tp.tp_get_series(g.e, g.beam, ndm=len(dms), is_int=dtype == "u8"))
+        out["mu"], out["sigma"] = tp.tp_get_bandpass(g.e, g.beam, nchan)
+        out["chunk_flag"], out["chunk_raw"], out["spec_flag"] = tp.tp_get_masks(g.e, g.beam, nchan)
+        out["row_mu"], out["row_sigma"] = tp.tp_get_series_stats(g.e, g.beam, len(dms))
+        return out
+
+    ref = []
+    g = GpuBeam(nchan, f_lo, bw, ts, dms, dtype)
+    try:
+        g.open(B)
+        for b in blocks:
+            tp.tp_push_block(g.e, g.beam, b)
+            tp.tp_dedisperse(g.e, g.beam)
+            tp.tp_detect(g.e, g.beam)
+            ref.append(collect(g))
+    finally:
+        g.close()
+
+    got = []
+    g = GpuBeam(nchan, f_lo, bw, ts, dms, dtype)
+    try:
+        g.open(B)
+        with pytest.raises(tp.TpError) as ei:
+            tp.tp_push_prefetched(g.e, g.beam)
+        assert ei.value.code == tp.TP_ENOTREADY
+        tp.tp_prefetch_block(g.e, g.beam, host[0])
+        with pytest.raises(tp.TpError) as ei:
+            tp.tp_prefetch_block(g.e, g.beam, host[1])
+        assert ei.value.code == tp.TP_EBUSY
+        with pytest.raises(tp.TpError) as ei:
+            tp.tp_push_block(g.e, g.beam, blocks[0])
+        assert ei.value.code == tp.TP_EBUSY
+        tp.tp_push_prefetched(g.e, g.beam)
+        tp.tp_dedisperse(g.e, g.beam)
+        tp.tp_detect(g.e, g.beam)
+        for k in range(1, nblk + 1):
+            if k < nblk:
+                tp.tp_prefetch_block(g.e, g.beam, host[k])  # overlaps block k - 1
+            got.append(collect(g))
+            if k < nblk:
+                tp.tp_push_prefetched(g.e, g.beam)
+                tp.tp_dedisperse(g.e, g.beam)
+                tp.tp_detect(g.e, g.beam)
+    finally:
+        g.close()
+
+    for k, (r, q) in enumerate(zip(ref, got)):
+        assert r["info"]["t0_abs"] == q["info"]["t0_abs"], k
+        for f in ("D", "mu", "sigma", "chunk_flag", "chunk_raw", "spec_flag", "row_mu", "row_sigma"):
+            assert np.array_equal(r[f], q[f]), (k, f)
+        assert r["n_candidates"] == q["n_candidates"], k
+        for f in ("dm_idx", "t_abs", "snr", "value"):
+            assert np.array_equal(r["candidates"][f], q["candidates"][f]), (k, f)
+    # and the stream's last block against the oracle's search of its window
+    assert sum(r["n_candidates"] for r in got) > 0
+    last = got[-1]
+    w0 = last["info"]["t0_abs"]
+    win = np.ascontiguousarray(x[:, w0:w0 + dmax + B])
+    o = O.search_block(win, dtype, od, dmax, rfi=O.RfiParams(), t0=w0)
+    check_block(last, o, win, dtype, od, O.RfiParams(), 5.0, t0=w0)
+
+
 def test_candidate_capacity_and_truncation():
     nchan = 64
     dms = np.arange(16) * 2.0
