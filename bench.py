@@ -572,7 +572,7 @@ def main():
         # block k is processed; every block's copy and candidate read lie
         # inside the timed region
         w0 = time.perf_counter()
-        ne2e = max(4, args.steps // 4)
+        ne2e = max(8, args.steps)
         tp.tp_prefetch_block(e, beam, pinned[0])
         tp.tp_push_prefetched(e, beam)
         tp.tp_dedisperse(e, beam)
