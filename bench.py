@@ -44,12 +44,15 @@ PAPER_DERIVED = 6.5e7  # DM-trial.samples/s per GPU derived from the paper's Tab
 # the ncu capture summarised in profiles/dedisperse_kernel_stream1024_640dm_f32.md,
 # per kernel shape; a shape without a capture reports null.
 # DRAM bytes (read + write) of one dedispersion launch of this workload, per
-# (sample format, kernel shape), from an ncu capture of the timed launch
-# (profiles/dedisperse_kernel_dm_quads_stream1024_640dm_f32.md)
-# DRAM bytes of one dedispersion launch of this workload (ncu captures):
-# shape 33 dram__bytes_read.sum + dram__bytes_write.sum; shape 46
-# dram__bytes.sum.per_second x gpu__time_duration
+# (sample format, kernel shape), from ncu captures of the timed launch
+# (profiles/dedisperse_kernel_dm_quads_stream1024_640dm_f32.md: shape 33,
+# dram__bytes_read.sum + dram__bytes_write.sum;
+# profiles/dedisperse_kernel_dm_quads_f32x2_stream1024_640dm_f32.md: shape 46,
+# dram__bytes.sum.per_second x gpu__time_duration)
 TRAFFIC_BY_SHAPE = {("f32", 33): 584.843264e6 + 331.993600e6, ("f32", 46): 175.55649461716e9 * 5.406816e-3}
+# shared-memory data-path utilisation (l1tex__data_pipe_lsu_wavefronts as a
+# fraction of peak) in the same captures
+SMEM_FRAC_BY_SHAPE = {("f32", 46): 0.6806}
 METRIC = "DM-trial*samples/s per GB300 (real-time beams sustained, p99 block latency alongside)"
 WORKLOAD = "stream: 1 beam, 1024 ch 398-418 MHz, 51.2 us, 640 DMs 0-127.8 step 0.2, FP32, 2^17-sample blocks"
 
@@ -547,7 +550,11 @@ def main():
                         "instruction, so against its packed peak of 2x this figure frac halves)"
                         if args.dtype == "u8" else "FP32 adds")),
             "stage_ms_per_block": {"push": stage_ms[0] / max(nstage, 1), "a1_a3": stage_ms[1] / max(nstage, 1),
-                                   "a4_a5": dd_ms, "a6_a7": stage_ms[3] / max(nstage, 1)}}
+                                   "a4_a5": dd_ms, "a6_a7": stage_ms[3] / max(nstage, 1)},
+            # the second roof: each staged sample is read from shared memory
+            # once per window that covers it (128 bytes per clock per SM)
+            "shared_memory": {"peak_TBps": 152 * 128 * 2.070e9 / 1e12,
+                              "ncu_data_path_frac": SMEM_FRAC_BY_SHAPE.get((args.dtype, int(best)))}}
 
     # ---- end to end through the C ABI from pinned host buffers -------------------
     e2e = None
