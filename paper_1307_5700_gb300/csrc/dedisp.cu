@@ -18,7 +18,10 @@ static_assert(kDedispParts == 6, "one launch_dedisperse_part per unit");
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};
 #undef TP_SHAPE_ENTRY
 
-int shape_tile_t(int shape) { return (kShapes[shape].ALGO == 4 ? 64 : 32) * kShapes[shape].S; }
+int shape_tile_t(int shape) {
+  const int algo = kShapes[shape].ALGO;
+  return (algo == 4 || algo == 6 ? 64 : 32) * kShapes[shape].S;  // two output segments per lane
+}
 
 cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s) {
   if (shape < 0 || shape >= kNumShapes) return cudaErrorInvalidValue;

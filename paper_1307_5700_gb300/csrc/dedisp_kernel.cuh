@@ -34,7 +34,12 @@
 // to binary32 as the scalar form does.  ALGO 5 pairs a lane's own outputs
 // s and s + S / 2 instead (S odd, output 2 (S / 2) added alone): register
 // pair k holds window samples k and k + S / 2 of the one window, so each
-// sample is loaded once for both halves.
+// sample is loaded once for both halves.  ALGO 6 and 7 are ALGO 4 and 5
+// without the producer warp: its register share goes to an eighth consumer
+// warp, and consumer warp w also issues the delays and bulk copies of stages
+// w, w + NCONS, ... kLookRot stages ahead of their use, over kStagesRot
+// buffers, so that the warp that fills a buffer rarely waits for the others to
+// release it.
 // Each (d, t) adds its channels in index order (FP32, or exact integers).
 // Every mbarrier wait is bounded; a wait that gives up records TP_ETIMEOUT in
 // the beam's status word and the CTA leaves after letting its copies land.
@@ -57,6 +62,8 @@ namespace {
 constexpr int kNC = 4;                              // channels per pipeline stage
 constexpr int kStages = 4;                          // pipeline depth (8-bit data: kStagesU8)
 constexpr int kStagesU8 = 8;
+constexpr int kStagesRot = 6;                       // ALGO 6, 7: pipeline depth
+constexpr int kLookRot = 2;                         // ALGO 6, 7: stages issued ahead of use
 constexpr int kDelRing = 8;                         // stages of delays prefetched ahead
 constexpr long long kSpinLimit = 1LL << 24;         // bounded mbarrier waits
 
@@ -134,22 +141,26 @@ constexpr int kU8FoldStages = 256 / kNC;
 
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO>
 struct Shape {
+  // ALGO 6 and 7: the consumer schemes of ALGO 4 and 5 without a producer warp
+  // (every consumer warp issues the copies of every NCONS-th stage)
+  static constexpr bool ROT = ALGO >= 6;
+  static constexpr int AB = ROT ? ALGO - 2 : ALGO;
   static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
   static constexpr int QS = 16 / EB;                                          // samples per 16 B
-  static constexpr int NSEG = ALGO == 4 ? 2 : 1;                              // output segments per lane
+  static constexpr int NSEG = AB == 4 ? 2 : 1;                              // output segments per lane
   static constexpr int TT = 32 * S * NSEG;                                    // outputs per tile
   static constexpr int L = (S + OMAX + 1 + QS - 1) / QS * QS;                 // window samples
   static constexpr int LR = L * EB / 4;                                       // window registers
   // largest in-row offset of a warp's last trial past its first (ALGO 3, 4:
   // three steps of at most OMAX + 1)
-  static constexpr int OSPAN = ALGO >= 3 ? 3 * (OMAX + 1) : OMAX;
+  static constexpr int OSPAN = AB >= 3 ? 3 * (OMAX + 1) : OMAX;
   static constexpr int ROW = (TT + kMaxOverhang + OSPAN + 2 * QS + 63) / 64 * 64;  // staged samples
   static constexpr int ROWB = ROW * EB;
-  static constexpr int THREADS = (NCONS + 1) * 32;                            // + one producer warp
+  static constexpr int THREADS = (NCONS + (ROT ? 0 : 1)) * 32;               // + one producer warp
   static constexpr int DW = NCONS * K <= 32 ? 32 : 64;                        // delays staged per channel
-  static constexpr int STAGES = MODE == kModeU8 && ALGO == 1 ? kStagesU8 : kStages;
+  static constexpr int STAGES = MODE == kModeU8 && ALGO == 1 ? kStagesU8 : ROT ? kStagesRot : kStages;
   static constexpr size_t data_bytes = (size_t)STAGES * kNC * ROWB;
-  static constexpr size_t del_bytes = sizeof(int) * kDelRing * kNC * DW;
+  static constexpr size_t del_bytes = sizeof(int) * (ROT ? NCONS : kDelRing) * kNC * DW;  // ring, or a slot per warp
   // 8-bit mode: per (stage, consumer warp) K int4 of word offsets (one per
   // channel of the stage) and one int4 of byte shifts; else one int4 per
   // (stage, channel, consumer warp)
@@ -163,9 +174,9 @@ struct Shape {
   // units apart, direct 32-bit loads (ALGO 1) an odd number of words apart
   static_assert(ALGO >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
   static_assert(ALGO != 2 || (MODE != kModeU8 && K == 2), "DM-pair windows: float data, two trials per warp");
-  static_assert(ALGO < 3 || K == 4, "DM-quad windows: four trials per warp");
-  static_assert(ALGO < 4 || MODE == kModeF32, "paired-add DM quads: FP32 staging");
-  static_assert(ALGO != 5 || S % 2 == 1, "in-lane pairs: S = 2 (S / 2) + 1");
+  static_assert(AB < 3 || K == 4, "DM-quad windows: four trials per warp");
+  static_assert(AB < 4 || MODE == kModeF32, "paired-add DM quads: FP32 staging");
+  static_assert(AB != 5 || S % 2 == 1, "in-lane pairs: S = 2 (S / 2) + 1");
   static_assert(ALGO == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
   static_assert(MODE != kModeU8 || ALGO == 1 || ALGO == 3, "8-bit data: direct loads or DM quads");
 };
@@ -179,6 +190,8 @@ template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
 __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS, MINB)
     dedisperse_kernel(BatchArgs ba) {
   using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO>;
+  constexpr bool ROT = Sh::ROT;
+  constexpr int AB = Sh::AB;  // the consumer scheme
   // the CTA's beam: last b with cta_start[b] <= blockIdx.x
   int bi = 0;
   {
@@ -227,25 +240,135 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   }
   __syncthreads();
 
-  if (warp == NCONS) {
-    // ---------------------------------------------------------------- producer
-    // delays: lane l copies delayT[c][d0 + j] for j = l, l + 32 < nd and
-    // the kNC channels of a stage into a ring of kDelRing stages,
-    // kDelRing - 1 stages ahead of use
-    const int32_t* __restrict__ dT = a.delayT;
-    auto prefetch = [&](int st) {
-      int* slot = sdel + (st % kDelRing) * kNC * DW;
+  const int32_t* __restrict__ dT = a.delayT;
+  // delays of stage st into `slot`: lane l copies delayT[c][d0 + j] for
+  // j = l, l + 32 < nd and the kNC channels of the stage (one cp.async group)
+  auto prefetch_to = [&](int st, int* slot) {
 #pragma unroll
-      for (int ci = 0; ci < kNC; ++ci) {
-        const int c = st * kNC + ci;
+    for (int ci = 0; ci < kNC; ++ci) {
+      const int c = st * kNC + ci;
 #pragma unroll
-        for (int h = 0; h < DW; h += 32) {
-          const bool v = st < nstage && c < nchan && lane + h < dt.nd;
-          cp_async4(slot + ci * DW + h + lane, v ? dT + (int64_t)c * a.dtpitch + dt.d0 + h + lane : dT, v);
-        }
+      for (int h = 0; h < DW; h += 32) {
+        const bool v = st < nstage && c < nchan && lane + h < dt.nd;
+        cp_async4(slot + ci * DW + h + lane, v ? dT + (int64_t)c * a.dtpitch + dt.d0 + h + lane : dT, v);
       }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    };
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // stage i: the window geometry of its (channel, consumer warp) pairs and
+  // the bulk copies of its channels onto full[i % STAGES], from its delays
+  // `del` (one warp; the stage's buffer must have been released)
+  auto issue_stage = [&](int i, const int* del) {
+    const int buf = i % STAGES;
+    if constexpr (MODE == kModeU8 && AB == 1) {
+      // per (channel, consumer warp, DM of its group): byte offset in the
+      // stage's rows of the word holding lane 0's first sample, and that
+      // sample's shift inside the word (0 or 16 bits)
+      // (lane g = w K + j handles DM g of the tile for every channel)
+      for (int g = lane; g < NCONS * K; g += 32) {
+        const int w = g / K, j = g % K;
+        const int jj = g < last ? g : last;
+        int off[kNC];
+        unsigned shifts = 0;
+#pragma unroll
+        for (int ci = 0; ci < kNC; ++ci) {
+          const int lo = del[ci * DW];
+          const int o = del[ci * DW + jj] - lo + ((t0m + lo) & (QS - 1));  // t0 + delay - row start
+          off[ci] = (buf * kNC + ci) * ROWB + (o & ~1) * EB;
+          shifts |= (unsigned)((o & 1) * 16) << (8 * ci);
+        }
+        int4* e = sinfo + (buf * NCONS + w) * (K + 1);
+        e[j] = make_int4(off[0], off[1], off[2], off[3]);
+        reinterpret_cast<unsigned*>(e + K)[j] = shifts;
+      }
+    }
+    // window geometry of every (channel, consumer warp) pair of the stage
+    for (int p = lane; (MODE != kModeU8 || AB == 3) && p < kNC * NCONS; p += 32) {
+      const int ci = p / NCONS, w = p % NCONS;
+      const int g0 = w * K < last ? w * K : last;
+      const int lo = del[ci * DW];
+      const int dw = del[ci * DW + g0];
+      const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
+      const int aw = (int)(t0 + dw - base);
+      if constexpr (AB >= 3) {
+        // four trials sharing one window (AB 4: one per output segment,
+        // 32 S samples apart): the steps e_j = o_j - o_{j-1}
+        // between consecutive trials are m or m + 1 (the planner checks
+        // this); block index m * 8 + bits.  Trials past the tile's last DM
+        // take step m; their sums are never stored.
+        int o[4], nreal = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool real = g0 + j <= last;
+          o[j] = real ? del[ci * DW + g0 + j] - dw : 0;
+          nreal += real ? 1 : 0;
+        }
+        int m = 1 << 30;
+#pragma unroll
+        for (int j = 1; j < 4; ++j)
+          if (j < nreal) m = min(m, o[j] - o[j - 1]);
+        if (nreal < 2) m = 0;
+        m = m < 0 ? 0 : (m > OMAX ? OMAX : m);
+        int bits = 0;
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+          // out-of-pattern steps are clamped so the branch stays inside its
+          // table whatever the delays hold
+          const int e = j < nreal ? o[j] - o[j - 1] - m : 0;
+          bits |= (e > 0 ? 1 : 0) << (j - 1);
+        }
+        // 16-bit samples: the window starts on the word holding the first
+        // trial's first sample, r half-words before it
+        const int r = EB == 2 ? (aw & 1) : 0;
+        sinfo[(buf * kNC + ci) * NCONS + w] =
+            make_int4((buf * kNC + ci) * ROWB + (aw - r) * EB, (r * (OMAX + 1) + m) * 8 + bits, 0, 0);
+        continue;
+      } else if constexpr (AB >= 1) {
+        // sample offset, in the staged row, of each DM's first output of lane 0
+        int o[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const int jj = g0 + j <= last ? g0 + j : last;
+          o[j] = (int)(t0 + del[ci * DW + jj] - base);
+        }
+        sinfo[(buf * kNC + ci) * NCONS + w] =
+            make_int4((buf * kNC + ci) * ROWB, o[0] | (o[1] << 16), o[2] | (o[3] << 16), 0);
+        continue;
+      }
+      int offs = 0, omax = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const int jj = g0 + j <= last ? g0 + j : last;
+        int o = (aw & (QS - 1)) + del[ci * DW + jj] - dw;
+        // the planner bounds o by OMAX; the clamp keeps the indexed branch
+        // inside its table whatever the delays hold
+        o = o < 0 ? 0 : (o > OMAX ? OMAX : o);
+        offs |= o << (8 * j);
+        omax = o > omax ? o : omax;
+      }
+      sinfo[(buf * kNC + ci) * NCONS + w] =
+          make_int4((buf * kNC + ci) * ROWB + (aw & ~(QS - 1)) * EB, offs, (S + omax + QS - 1) / QS, 0);
+    }
+    // lane ci < kNC copies the stage's channel ci: samples
+    // [t0 + lo, t0 + TT + hi + QS) rounded out to 16-byte units
+    unsigned nb = 0;
+    int64_t src = 0;
+    if (lane < kNC && i * kNC + lane < nchan) {
+      const int lo = del[lane * DW], hi = del[lane * DW + last];
+      const int head = (t0m + lo) & (QS - 1);  // row start = t0 + lo - head
+      nb = (unsigned)(((TT + hi - lo + QS + head) * EB + 15) & ~15);
+      src = ((int64_t)(i * kNC + lane) * a.ypitch + t0 + lo - head) * EB;
+    }
+    const unsigned total = __reduce_add_sync(0xffffffffu, nb);
+    if (lane == 0) mbar_arrive_expect_tx(&full[buf], total);
+    __syncwarp();
+    if (nb) bulk_g2s(srow + (buf * kNC + lane) * ROWB, ybytes + src, nb, &full[buf]);
+  };
+
+  if (!ROT && warp == NCONS) {
+    // ---------------------------------------------------------------- producer
+    // delays in a ring of kDelRing stages, kDelRing - 1 stages ahead of use
+    auto prefetch = [&](int st) { prefetch_to(st, sdel + (st % kDelRing) * kNC * DW); };
 #pragma unroll
     for (int st = 0; st < kDelRing - 1; ++st) prefetch(st);
     bool ok = true;
@@ -264,110 +387,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
           break;
         }
       }
-      const int* del = sdel + (i % kDelRing) * kNC * DW;
-      if constexpr (MODE == kModeU8 && ALGO == 1) {
-        // per (channel, consumer warp, DM of its group): byte offset in the
-        // stage's rows of the word holding lane 0's first sample, and that
-        // sample's shift inside the word (0 or 16 bits)
-        // (lane g = w K + j handles DM g of the tile for every channel)
-        for (int g = lane; g < NCONS * K; g += 32) {
-          const int w = g / K, j = g % K;
-          const int jj = g < last ? g : last;
-          int off[kNC];
-          unsigned shifts = 0;
-#pragma unroll
-          for (int ci = 0; ci < kNC; ++ci) {
-            const int lo = del[ci * DW];
-            const int o = del[ci * DW + jj] - lo + ((t0m + lo) & (QS - 1));  // t0 + delay - row start
-            off[ci] = (buf * kNC + ci) * ROWB + (o & ~1) * EB;
-            shifts |= (unsigned)((o & 1) * 16) << (8 * ci);
-          }
-          int4* e = sinfo + (buf * NCONS + w) * (K + 1);
-          e[j] = make_int4(off[0], off[1], off[2], off[3]);
-          reinterpret_cast<unsigned*>(e + K)[j] = shifts;
-        }
-      }
-      // window geometry of every (channel, consumer warp) pair of the stage
-      for (int p = lane; (MODE != kModeU8 || ALGO == 3) && p < kNC * NCONS; p += 32) {
-        const int ci = p / NCONS, w = p % NCONS;
-        const int g0 = w * K < last ? w * K : last;
-        const int lo = del[ci * DW];
-        const int dw = del[ci * DW + g0];
-        const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
-        const int aw = (int)(t0 + dw - base);
-        if constexpr (ALGO >= 3) {
-          // four trials sharing one window (ALGO 4: one per output segment,
-          // 32 S samples apart): the steps e_j = o_j - o_{j-1}
-          // between consecutive trials are m or m + 1 (the planner checks
-          // this); block index m * 8 + bits.  Trials past the tile's last DM
-          // take step m; their sums are never stored.
-          int o[4], nreal = 0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const bool real = g0 + j <= last;
-            o[j] = real ? del[ci * DW + g0 + j] - dw : 0;
-            nreal += real ? 1 : 0;
-          }
-          int m = 1 << 30;
-#pragma unroll
-          for (int j = 1; j < 4; ++j)
-            if (j < nreal) m = min(m, o[j] - o[j - 1]);
-          if (nreal < 2) m = 0;
-          m = m < 0 ? 0 : (m > OMAX ? OMAX : m);
-          int bits = 0;
-#pragma unroll
-          for (int j = 1; j < 4; ++j) {
-            // out-of-pattern steps are clamped so the branch stays inside its
-            // table whatever the delays hold
-            const int e = j < nreal ? o[j] - o[j - 1] - m : 0;
-            bits |= (e > 0 ? 1 : 0) << (j - 1);
-          }
-          // 16-bit samples: the window starts on the word holding the first
-          // trial's first sample, r half-words before it
-          const int r = EB == 2 ? (aw & 1) : 0;
-          sinfo[(buf * kNC + ci) * NCONS + w] =
-              make_int4((buf * kNC + ci) * ROWB + (aw - r) * EB, (r * (OMAX + 1) + m) * 8 + bits, 0, 0);
-          continue;
-        } else if constexpr (ALGO >= 1) {
-          // sample offset, in the staged row, of each DM's first output of lane 0
-          int o[4] = {0, 0, 0, 0};
-#pragma unroll
-          for (int j = 0; j < K; ++j) {
-            const int jj = g0 + j <= last ? g0 + j : last;
-            o[j] = (int)(t0 + del[ci * DW + jj] - base);
-          }
-          sinfo[(buf * kNC + ci) * NCONS + w] =
-              make_int4((buf * kNC + ci) * ROWB, o[0] | (o[1] << 16), o[2] | (o[3] << 16), 0);
-          continue;
-        }
-        int offs = 0, omax = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-          const int jj = g0 + j <= last ? g0 + j : last;
-          int o = (aw & (QS - 1)) + del[ci * DW + jj] - dw;
-          // the planner bounds o by OMAX; the clamp keeps the indexed branch
-          // inside its table whatever the delays hold
-          o = o < 0 ? 0 : (o > OMAX ? OMAX : o);
-          offs |= o << (8 * j);
-          omax = o > omax ? o : omax;
-        }
-        sinfo[(buf * kNC + ci) * NCONS + w] =
-            make_int4((buf * kNC + ci) * ROWB + (aw & ~(QS - 1)) * EB, offs, (S + omax + QS - 1) / QS, 0);
-      }
-      // lane ci < kNC copies the stage's channel ci: samples
-      // [t0 + lo, t0 + TT + hi + QS) rounded out to 16-byte units
-      unsigned nb = 0;
-      int64_t src = 0;
-      if (lane < kNC && i * kNC + lane < nchan) {
-        const int lo = del[lane * DW], hi = del[lane * DW + last];
-        const int head = (t0m + lo) & (QS - 1);  // row start = t0 + lo - head
-        nb = (unsigned)(((TT + hi - lo + QS + head) * EB + 15) & ~15);
-        src = ((int64_t)(i * kNC + lane) * a.ypitch + t0 + lo - head) * EB;
-      }
-      const unsigned total = __reduce_add_sync(0xffffffffu, nb);
-      if (lane == 0) mbar_arrive_expect_tx(&full[buf], total);
-      __syncwarp();
-      if (nb) bulk_g2s(srow + (buf * kNC + lane) * ROWB, ybytes + src, nb, &full[buf]);
+      issue_stage(i, sdel + (i % kDelRing) * kNC * DW);
       ++issued;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -392,14 +412,14 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   // two-segment DM quads: output s of both segments of DM j, packed
   // (segment 0 in the low word)
   constexpr int NSEG = Sh::NSEG;
-  unsigned long long acc2[K][ALGO == 4 ? S : 1];
+  unsigned long long acc2[K][AB == 4 ? S : 1];
 #pragma unroll
   for (int j = 0; j < K; ++j)
 #pragma unroll
-    for (int s = 0; s < (ALGO == 4 ? S : 1); ++s) acc2[j][s] = 0ull;
+    for (int s = 0; s < (AB == 4 ? S : 1); ++s) acc2[j][s] = 0ull;
   // in-lane paired DM quads: outputs s and s + S / 2 of DM j packed in
   // accp[j][s] (low word first), output 2 (S / 2) in acct[j]
-  constexpr int PH = ALGO == 5 ? S / 2 : 1;
+  constexpr int PH = AB == 5 ? S / 2 : 1;
   unsigned long long accp[K][PH];
   float acct[K];
 #pragma unroll
@@ -411,8 +431,8 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   // 8-bit mode: pk[j][m] holds outputs 2m, 2m + 1 of DM j as 16-bit lanes
   // (exact: no lane sum reaches 2^16 within kU8FoldStages stages), folded
   // into the 32-bit sums sum32 every kU8FoldStages stages
-  constexpr bool U8D = MODE == kModeU8 && ALGO == 1;  // 8-bit direct loads
-  constexpr bool U8Q = MODE == kModeU8 && ALGO == 3;  // 8-bit DM quads
+  constexpr bool U8D = MODE == kModeU8 && AB == 1;  // 8-bit direct loads
+  constexpr bool U8Q = MODE == kModeU8 && AB == 3;  // 8-bit DM quads
   constexpr int PW = U8D ? S / 2 : 1;
   constexpr int S32 = U8D ? S : 1;
   // 8-bit DM quads: qe[j][i] holds outputs 2i, 2i + 1 of DM j, qf[j][i]
@@ -468,9 +488,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
     }
   };
   using WT = typename std::conditional<MODE == kModeF32, float, unsigned>::type;
-  WT w[ALGO == 0 ? LR : 4];
+  WT w[AB == 0 ? LR : 4];
 #pragma unroll
-  for (int q = 0; q < (ALGO == 0 ? LR : 4); ++q) w[q] = 0;
+  for (int q = 0; q < (AB == 0 ? LR : 4); ++q) w[q] = 0;
   // the staged words of the lane's outputs 2m, 2m + 1 for one DM and channel,
   // given lane 0's word offset and the half-word shift of its first sample
   const int lane_bytes = lane * S * EB;
@@ -485,10 +505,61 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
     }
   };
 
+  // ALGO 6, 7: this warp issues stages warp, warp + NCONS, ..., each
+  // kLookRot stages ahead of its use (the buffer it fills was released
+  // STAGES - kLookRot stages before, which leaves the warps that much slack),
+  // and prefetches the delays of the next one into its own slot right after
+  // issuing the previous one
+  int* myslot = sdel + warp * kNC * DW;
+  int produced = -1;  // the last stage this warp issued
+  auto produce = [&](int j) -> bool {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    const int pbuf = j % STAGES;
+    if (j >= STAGES) {
+      bool got = false;
+      if (lane == 0) got = mbar_wait_bounded(&empty[pbuf], (unsigned)(((j / STAGES) - 1) & 1));
+      if (!__shfl_sync(0xffffffffu, got, 0)) return false;
+    }
+    issue_stage(j, myslot);
+    produced = j;
+    __syncwarp();  // every lane is done with the slot
+    if (j + NCONS < nstage) prefetch_to(j + NCONS, myslot);
+    return true;
+  };
+  // after a failed wait: let the copies this warp issued land, then report
+  auto bail = [&]() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (lane == 0) {
+      for (int k = produced; k >= 0 && k > produced - STAGES; k -= NCONS)
+        mbar_wait_bounded(&full[k % STAGES], (unsigned)((k / STAGES) & 1));
+      atomicExch(a.status, TP_ETIMEOUT);
+    }
+  };
+  if constexpr (ROT) {
+    if (warp < nstage) prefetch_to(warp, myslot);
+    static_assert(!ROT || kLookRot < STAGES, "lookahead within the pipeline");
+    for (int j = warp; j < kLookRot && j < nstage; j += NCONS)
+      if (!produce(j)) {
+        bail();
+        return;
+      }
+  }
+
   for (int i = 0; i < nstage; ++i) {
     const int buf = i % STAGES;
+    if constexpr (ROT) {
+      const int j = i + kLookRot;
+      if (j < nstage && j % NCONS == warp && !produce(j)) {
+        bail();
+        return;
+      }
+    }
     if (!mbar_wait_bounded(&full[buf], (unsigned)((i / STAGES) & 1))) {
-      if (lane == 0) atomicExch(a.status, TP_ETIMEOUT);
+      if constexpr (ROT)
+        bail();
+      else if (lane == 0)
+        atomicExch(a.status, TP_ETIMEOUT);
       return;
     }
     const int nc = nchan - i * kNC < kNC ? nchan - i * kNC : kNC;
@@ -520,8 +591,8 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
           }
         }
       }
-    } else if (live && ALGO == 2) {
-      if constexpr (ALGO == 2) {
+    } else if (live && AB == 2) {
+      if constexpr (AB == 2) {
         // one window per channel for the warp's two trials: S + d samples
         // at the first trial's offset, d = the second trial's extra delay
         const unsigned sbase = smem_u32(srow) + (unsigned)(lane * S * EB);
@@ -539,8 +610,8 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
                                                            sbase + (unsigned)(inf.x + (o0 & ~1) * 2), acc[0], acc[1]);
         }
       }
-    } else if (live && ALGO >= 3) {
-      if constexpr (ALGO >= 3) {
+    } else if (live && AB >= 3) {
+      if constexpr (AB >= 3) {
         // one window per channel for the warp's four trials, at the first
         // trial's offset
         // (one call site: the loop stays rolled so the jump table is emitted
@@ -549,9 +620,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 #pragma unroll 1
         for (int ci = 0; ci < nc; ++ci) {
           const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
-          if constexpr (ALGO == 5)
+          if constexpr (AB == 5)
             add_quadp<S, OMAX>(inf.y, sbase + (unsigned)inf.x, accp, acct);
-          else if constexpr (ALGO == 4)
+          else if constexpr (AB == 4)
             add_quad2<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc2);
           else if constexpr (MODE == kModeF32)
             add_quad<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc);
@@ -561,7 +632,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
             add_quad16<S, OMAX, MODE == kModeBF16 ? 1 : 0>(inf.y, sbase + (unsigned)inf.x, acc);
         }
       }
-    } else if (live && ALGO == 1) {
+    } else if (live && AB == 1) {
       // direct loads: each DM reads its own S samples at its own offset
       for (int ci = 0; ci < nc; ++ci) {
         const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
@@ -608,7 +679,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 #pragma unroll
         for (int j = 0; j < K; ++j) {
           const int o = (inf.y >> (8 * j)) & 0xff;
-          if constexpr (ALGO == 0) {
+          if constexpr (AB == 0) {
             if constexpr (MODE == kModeF32)
               add_shifted<S, LR, OMAX>(o, acc[j], w);
             else
@@ -623,6 +694,8 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       if (i % kU8FoldStages == kU8FoldStages - 1) fold();
   }
 
+  if constexpr (ROT) asm volatile("cp.async.wait_all;" ::: "memory");
+
   // epilogue: 16-bit and 8-bit modes accumulated the stored samples x~;
   // subtract the block's sum of bandpass values (exact integers for 8-bit data)
   fold();
@@ -630,10 +703,10 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
   const bool is_int = a.dtype == TP_U8;
   // output s of DM j in segment seg
   auto outv = [&](int j, int seg, int s) -> float {
-    if constexpr (ALGO == 4) {
+    if constexpr (AB == 4) {
       const unsigned long long p = acc2[j][s];
       return __uint_as_float(seg ? (unsigned)(p >> 32) : (unsigned)p);
-    } else if constexpr (ALGO == 5) {
+    } else if constexpr (AB == 5) {
       if (s == 2 * PH) return acct[j];
       const unsigned long long p = accp[j][s < PH ? s : s - PH];
       return __uint_as_float(s < PH ? (unsigned)p : (unsigned)(p >> 32));

@@ -16,7 +16,9 @@
 // ALGO 4: ALGO 3 over two output segments per lane (32 S samples apart), both
 // added by one paired FP32 add (FP32 staging only);
 // ALGO 5: ALGO 3 with the lane's outputs s and s + S / 2 added by one paired
-// FP32 add (S odd; FP32 staging only).
+// FP32 add (S odd; FP32 staging only);
+// ALGO 6, 7: ALGO 4, 5 without a producer warp: all NCONS warps consume, and
+// warp w also issues the copies of stages w, w + NCONS, ...
 // MINB: CTAs per SM the register allocation is sized for.
 #define TP_SHAPES(X)                 \
   X(0, 4, 20, 36, 8, 4, 0, 1)        \
@@ -71,7 +73,11 @@
   X(49, 4, 43, 9, 7, 4, 5, 1)        \
   X(50, 4, 27, 9, 11, 4, 5, 1)       \
   X(51, 4, 25, 9, 11, 4, 5, 1)       \
-  X(52, 4, 29, 9, 11, 4, 5, 1)
+  X(52, 4, 29, 9, 11, 4, 5, 1)       \
+  X(53, 4, 23, 9, 8, 4, 6, 1)        \
+  X(54, 4, 29, 9, 12, 4, 7, 1)       \
+  X(55, 4, 45, 9, 8, 4, 7, 1)        \
+  X(56, 4, 21, 9, 8, 4, 6, 1)
 
 namespace tp {
 constexpr int kDedispParts = 6;  // translation units the kernel instantiations are split over
