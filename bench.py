@@ -47,12 +47,14 @@ PAPER_DERIVED = 6.5e7  # DM-trial.samples/s per GPU derived from the paper's Tab
 # (sample format, kernel shape), from ncu captures of the timed launch
 # (profiles/dedisperse_kernel_dm_quads_stream1024_640dm_f32.md: shape 33,
 # dram__bytes_read.sum + dram__bytes_write.sum;
-# profiles/dedisperse_kernel_dm_quads_f32x2_stream1024_640dm_f32.md: shape 46,
+# profiles/dedisperse_kernel_dm_quads_f32x2_stream1024_640dm_f32.md: shape 46, and
+# profiles/dedisperse_kernel_dm_quads_rotating_stream1024_640dm_f32.md: shape 55,
 # dram__bytes.sum.per_second x gpu__time_duration)
-TRAFFIC_BY_SHAPE = {("f32", 33): 584.843264e6 + 331.993600e6, ("f32", 46): 175.55649461716e9 * 5.406816e-3}
+TRAFFIC_BY_SHAPE = {("f32", 33): 584.843264e6 + 331.993600e6, ("f32", 46): 175.55649461716e9 * 5.406816e-3,
+                    ("f32", 55): 192.00875257012e9 * 5.089248e-3}
 # shared-memory data-path utilisation (l1tex__data_pipe_lsu_wavefronts as a
 # fraction of peak) in the same captures
-SMEM_FRAC_BY_SHAPE = {("f32", 46): 0.6806}
+SMEM_FRAC_BY_SHAPE = {("f32", 46): 0.6806, ("f32", 55): 0.5959}
 METRIC = "DM-trial*samples/s per GB300 (real-time beams sustained, p99 block latency alongside)"
 WORKLOAD = "stream: 1 beam, 1024 ch 398-418 MHz, 51.2 us, 640 DMs 0-127.8 step 0.2, FP32, 2^17-sample blocks"
 
