@@ -141,44 +141,45 @@ constexpr int kU8FoldStages = 256 / kNC;
 
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO>
 struct Shape {
-  // ALGO 6 and 7: the consumer schemes of ALGO 4 and 5 without a producer warp
-  // (every consumer warp issues the copies of every NCONS-th stage)
+  // ALGO 6, 7 and 8: the consumer schemes of ALGO 4, 5 and 3 without a
+  // producer warp (every consumer warp issues the copies of every NCONS-th
+  // stage)
   static constexpr bool ROT = ALGO >= 6;
-  static constexpr int AB = ROT ? ALGO - 2 : ALGO;
+  static constexpr int AB = ALGO == 8 ? 3 : ROT ? ALGO - 2 : ALGO;
   static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
   static constexpr int QS = 16 / EB;                                          // samples per 16 B
   static constexpr int NSEG = AB == 4 ? 2 : 1;                              // output segments per lane
   static constexpr int TT = 32 * S * NSEG;                                    // outputs per tile
   static constexpr int L = (S + OMAX + 1 + QS - 1) / QS * QS;                 // window samples
   static constexpr int LR = L * EB / 4;                                       // window registers
-  // largest in-row offset of a warp's last trial past its first (ALGO 3, 4:
-  // three steps of at most OMAX + 1)
+  // largest in-row offset of a warp's last trial past its first (the quad
+  // schemes: three steps of at most OMAX + 1)
   static constexpr int OSPAN = AB >= 3 ? 3 * (OMAX + 1) : OMAX;
   static constexpr int ROW = (TT + kMaxOverhang + OSPAN + 2 * QS + 63) / 64 * 64;  // staged samples
   static constexpr int ROWB = ROW * EB;
   static constexpr int THREADS = (NCONS + (ROT ? 0 : 1)) * 32;               // + one producer warp
   static constexpr int DW = NCONS * K <= 32 ? 32 : 64;                        // delays staged per channel
-  static constexpr int STAGES = MODE == kModeU8 && ALGO == 1 ? kStagesU8 : ROT ? kStagesRot : kStages;
+  static constexpr int STAGES = MODE == kModeU8 && AB == 1 ? kStagesU8 : ROT ? kStagesRot : kStages;
   static constexpr size_t data_bytes = (size_t)STAGES * kNC * ROWB;
   static constexpr size_t del_bytes = sizeof(int) * (ROT ? NCONS : kDelRing) * kNC * DW;  // ring, or a slot per warp
   // 8-bit mode: per (stage, consumer warp) K int4 of word offsets (one per
   // channel of the stage) and one int4 of byte shifts; else one int4 per
   // (stage, channel, consumer warp)
-  static constexpr size_t info_bytes = MODE == kModeU8 && ALGO == 1 ? sizeof(int4) * STAGES * NCONS * (K + 1)
+  static constexpr size_t info_bytes = MODE == kModeU8 && AB == 1 ? sizeof(int4) * STAGES * NCONS * (K + 1)
                                                                      : sizeof(int4) * STAGES * kNC * NCONS;
   // 8-bit DM quads: the 32-bit sums of every consumer thread, [warp][K S][32]
-  static constexpr size_t fold_bytes = MODE == kModeU8 && ALGO == 3 ? sizeof(int) * NCONS * K * S * 32 : 0;
+  static constexpr size_t fold_bytes = MODE == kModeU8 && AB == 3 ? sizeof(int) * NCONS * K * S * 32 : 0;
   static constexpr size_t smem = data_bytes + del_bytes + info_bytes + fold_bytes + 16 * STAGES;
   static_assert(smem <= 227 * 1024, "shared memory per CTA");
-  // no bank conflicts: register windows (ALGO 0) start an odd number of 16-byte
-  // units apart, direct 32-bit loads (ALGO 1) an odd number of words apart
-  static_assert(ALGO >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
-  static_assert(ALGO != 2 || (MODE != kModeU8 && K == 2), "DM-pair windows: float data, two trials per warp");
+  // no bank conflicts: register windows (scheme 0) start an odd number of 16-byte
+  // units apart, direct 32-bit loads (scheme 1) an odd number of words apart
+  static_assert(AB >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
+  static_assert(AB != 2 || (MODE != kModeU8 && K == 2), "DM-pair windows: float data, two trials per warp");
   static_assert(AB < 3 || K == 4, "DM-quad windows: four trials per warp");
   static_assert(AB < 4 || MODE == kModeF32, "paired-add DM quads: FP32 staging");
   static_assert(AB != 5 || S % 2 == 1, "in-lane pairs: S = 2 (S / 2) + 1");
-  static_assert(ALGO == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
-  static_assert(MODE != kModeU8 || ALGO == 1 || ALGO == 3, "8-bit data: direct loads or DM quads");
+  static_assert(AB == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
+  static_assert(MODE != kModeU8 || AB == 1 || AB == 3, "8-bit data: direct loads or DM quads");
 };
 
 // Per (stage, channel, consumer warp) the producer writes an int4:
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       const int64_t base = (t0 + lo) & ~int64_t(QS - 1);
       const int aw = (int)(t0 + dw - base);
       if constexpr (AB >= 3) {
-        // four trials sharing one window (AB 4: one per output segment,
+        // four trials sharing one window (scheme 4: one per output segment,
         // 32 S samples apart): the steps e_j = o_j - o_{j-1}
         // between consecutive trials are m or m + 1 (the planner checks
         // this); block index m * 8 + bits.  Trials past the tile's last DM

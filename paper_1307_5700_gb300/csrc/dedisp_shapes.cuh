@@ -17,8 +17,8 @@
 // added by one paired FP32 add (FP32 staging only);
 // ALGO 5: ALGO 3 with the lane's outputs s and s + S / 2 added by one paired
 // FP32 add (S odd; FP32 staging only);
-// ALGO 6, 7: ALGO 4, 5 without a producer warp: all NCONS warps consume, and
-// warp w also issues the copies of stages w, w + NCONS, ...
+// ALGO 6, 7, 8: ALGO 4, 5, 3 without a producer warp: all NCONS warps consume,
+// and warp w also issues the copies of stages w, w + NCONS, ...
 // MINB: CTAs per SM the register allocation is sized for.
 #define TP_SHAPES(X)                 \
   X(0, 4, 20, 36, 8, 4, 0, 1)        \
@@ -77,7 +77,9 @@
   X(53, 4, 23, 9, 8, 4, 6, 1)        \
   X(54, 4, 29, 9, 12, 4, 7, 1)       \
   X(55, 4, 45, 9, 8, 4, 7, 1)        \
-  X(56, 4, 21, 9, 8, 4, 6, 1)
+  X(56, 4, 21, 9, 8, 4, 6, 1)        \
+  X(57, 4, 30, 16, 8, 3, 8, 1)       \
+  X(58, 4, 26, 16, 8, 3, 8, 1)
 
 namespace tp {
 constexpr int kDedispParts = 6;  // translation units the kernel instantiations are split over

@@ -324,10 +324,10 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
 // windows (the order of their launch times on a 1024-channel, 640-trial,
 // 2^17-sample block).
 constexpr int kShapePreference[kNumShapes] = {55, 53, 46, 56, 54, 52, 50, 51, 48, 49, 33, 44, 45,
-                                              47, 34, 42, 31, 30, 32, 35, 39, 43, 41, 40, 27, 25,
-                                              26, 24, 28, 29, 22, 18, 19, 12, 13, 14, 15, 16, 17,
-                                              23, 21, 20, 8, 10, 1, 2, 5, 0, 3, 6, 4, 7,
-                                              9, 11, 36, 37, 38};
+                                              57, 58, 47, 34, 42, 31, 30, 32, 35, 39, 43, 41, 40,
+                                              27, 25, 26, 24, 28, 29, 22, 18, 19, 12, 13, 14, 15,
+                                              16, 17, 23, 21, 20, 8, 10, 1, 2, 5, 0, 3, 6,
+                                              4, 7, 9, 11, 36, 37, 38};
 
 bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype, int sh,
                 std::vector<DmTile>* tiles) {

@@ -117,9 +117,9 @@ struct KernelShape {
               // 2: DM pairs sharing one window; 3: DM quads sharing one window;
               // 4: DM quads over two output segments with paired FP32 adds;
               // 5: DM quads with a lane's outputs s and s + S / 2 paired;
-              // 6, 7: 4, 5 without a producer warp (consumers issue the copies)
+              // 6, 7, 8: 4, 5, 3 without a producer warp (consumers issue the copies)
 };
-constexpr int kNumShapes = 57;
+constexpr int kNumShapes = 59;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
