@@ -483,8 +483,14 @@ def main():
     # first block of the stream fills the overlap tail; not timed
     tp.tp_push_block(e, beam, dev_blocks[0])
     tp.tp_dedisperse(e, beam)
+    tp.tp_detect(e, beam)
+    tp.tp_get_candidates(e, beam, 0)
+    # the second block has the steady-state length (the first yields
+    # block - max_delay outputs, a different number of CTA waves): autotune
+    # the dedispersion kernel shape on it
+    tp.tp_push_block(e, beam, dev_blocks[1 % NBUF])
+    tp.tp_dedisperse(e, beam)
     if args.shape is None:
-        # autotune the dedispersion kernel shape on this plan's geometry
         best, shape_ms = tp.tp_autotune(e, beam, reps=2)
         tp.tp_dedisperse(e, beam)
     else:

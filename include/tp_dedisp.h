@@ -395,7 +395,10 @@ int tp_plan_set_shape(tp_plan *p, int shape);
  * it in *best and the mean milliseconds per launch in ms[shape] (-1 for
  * infeasible shapes; n entries).  Blocks.  The beam's series is overwritten:
  * call tp_dedisperse again before tp_detect.  TP_ENOTREADY if the beam never
- * received a block. */
+ * received a block.  Time it on a block of the stream's regular length: the
+ * first block of a stream yields block_nsamp - max_delay outputs, and the
+ * number of CTA waves (tiles / SMs, rounded up) can then rank the shapes
+ * differently. */
 int tp_autotune(tp_engine *e, int beam, int reps, int *best, float *ms, int n);
 
 /* Batch form of tp_autotune for the batched launch of tp_run_ready: for every
