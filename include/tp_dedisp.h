@@ -523,9 +523,12 @@ int tp_server_destroy(tp_server *s);
  *
  * Scratch: a 32 MiB array inside the library, held by every device that loads
  * the library until the process exits; TP_EINVAL when nchan * ceil(nsamp / W)
- * * 16 bytes (+ 48 bytes per channel) does not fit.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and must
- * therefore come before any stream capture on that device.  No call allocates
+ * * 16 bytes (+ 34 bytes per channel, each of the seven per-channel arrays
+ * rounded up to 256 bytes) does not fit.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress), keeps it for the rest of
+ * the process and must therefore come before any stream capture on that
+ * device; after cudaDeviceReset the kept address is stale, so a process that
+ * resets a device must not call this entry point on it again.  No call allocates
  * or frees memory.  All calls share the array and it keeps the contents of the
  * last call: calls that can overlap on the GPU (different streams, or
  * different host threads) race on it and must be ordered by the caller.

@@ -64,7 +64,10 @@ extern "C" int tp_channel_stats_noalloc(const void* x, int dtype, int nchan, int
     return set_error(TP_EINVAL, "x must be 16-byte aligned with a row pitch of a multiple of 16 bytes");
   const int64_t nchunk = (nsamp + r.chunk_width - 1) / r.chunk_width;
   const size_t nc = (size_t)nchan;
-  const size_t need = align256(nc * (size_t)nchunk * 16) + 2 * align256(nc * 8) + 4 * align256(nc * 4);
+  // chunk sums; S, V; bint, mu_hi, mu_lo, chan_nflag; b16 (the bandpass value
+  // in the 16-bit storage format, written by the binary16/bfloat16 statistics)
+  const size_t need = align256(nc * (size_t)nchunk * 16) + 2 * align256(nc * 8) + 4 * align256(nc * 4) +
+                      align256(nc * 2);
   if (need > kNoAllocScratchBytes)
     return set_error(TP_EINVAL, "nchan x ceil(nsamp / W) too large: needs %zu bytes of scratch, the library "
                      "holds %zu", need, kNoAllocScratchBytes);
@@ -100,6 +103,7 @@ extern "C" int tp_channel_stats_noalloc(const void* x, int dtype, int nchan, int
   a.mu_hi = static_cast<float*>(take(nc * 4));
   a.mu_lo = static_cast<float*>(take(nc * 4));
   a.chan_nflag = static_cast<int*>(take(nc * 4));
+  a.b16 = static_cast<unsigned short*>(take(nc * 2));
   a.chunk_raw = chunk_raw;
   a.chunk_flag = chunk_flag;
   cudaError_t e = launch_channel_stats(a, chunk_sums, static_cast<cudaStream_t>(cuda_stream));

@@ -14,11 +14,28 @@ pytestmark = pytest.mark.gpu
 
 
 def _block(dtype, seed, nchan, nsamp):
+    if dtype == "c16":
+        # complex voltages whose power carries the same narrowband burst
+        env = np.ones((nchan, nsamp))
+        env[[3, 4, 40], 2000:6000] += 3.0
+        env[:, [9000, 15000]] += 6.0
+        return synth.complex_voltage(env, seed, sigma=30.0)
     xf = synth.noise(nchan, nsamp, seed, mean=128.0 if dtype == "u8" else 0.0, std=16.0 if dtype == "u8" else 1.0)
     scale = 16.0 if dtype == "u8" else 1.0
     synth.add_narrowband(xf, [3, 4, 40], 2000, 6000, 12.0 * scale)
     synth.add_broadband(xf, [9000, 15000], 6.0 * scale)
-    return synth.to_u8(xf) if dtype == "u8" else xf
+    return {"u8": synth.to_u8, "f32": lambda a: a, "f16": synth.to_f16, "bf16": synth.to_bf16_bits}[dtype](xf)
+
+
+def _to_device(x):
+    """The block as a device tensor of the same bytes (bfloat16 bit patterns
+    as int16, complex int16 pairs as one int32 per sample)."""
+    import torch
+    if x.dtype == synth.C16:
+        x = x.view(np.int32)
+    elif x.dtype == np.uint16:
+        x = x.view(np.int16)
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
 def _engine_stats(x, dtype, rfi):
@@ -39,7 +56,7 @@ def _engine_stats(x, dtype, rfi):
     return mu, sigma, cf, cr
 
 
-@pytest.mark.parametrize("dtype", ["f32", "u8"])
+@pytest.mark.parametrize("dtype", ["f32", "u8", "f16", "bf16", "c16"])
 def test_noalloc_stats_match_engine_twice(dtype):
     import torch
     tp.build()
@@ -55,7 +72,7 @@ def test_noalloc_stats_match_engine_twice(dtype):
         x = _block(dtype, seed, nchan, nsamp)
         want_mu, want_sigma, want_cf, want_cr = _engine_stats(x, dtype, rfi)
         assert want_cf.any()
-        xd = torch.from_numpy(x).cuda()
+        xd = _to_device(x)
         tp.tp_channel_stats_noalloc(xd, dtype, mu, sigma, cf, cr, rfi=rfi)
         torch.cuda.synchronize()
         np.testing.assert_allclose(mu.cpu().numpy(), want_mu, rtol=1e-12, atol=1e-12, err_msg=f"call {call}")
