@@ -52,6 +52,7 @@ def lib():
             "orc_channel_freqs": (None, [_i, _d, _d, _p]),
             "orc_delay_exact": (None, [_i, _d, _d, _d, _p, _i, _p]),
             "orc_delay_table": (_i64, [_i, _d, _d, _d, _p, _i, _p]),
+            "orc_delay_ties": (_i64, [_i, _d, _d, _d, _p, _i, _d, _p, _p, _p, _i64]),
             "orc_bandpass_float": (None, [_p, _i, _i, _i64, _i64, _p, _p]),
             "orc_bandpass_u8": (None, [_p, _i, _i64, _i64, _p, _p, _p, _p, _p, _p]),
             "orc_channel_mask_float": (None, [_p, _i, _i, _i64, _i64, _i, _d, _i, _p, _p, _p, _p]),
@@ -146,6 +147,25 @@ def delay_table(nchan, f_lo, bw, t_samp, dm):
     if dmax < 0:
         raise ValueError("invalid plan arguments")
     return out, int(dmax)
+
+
+def delay_ties(nchan, f_lo, bw, t_samp, dm, eps=1e-9):
+    """Tie log of Eq. 1's rounding (R3): the (d, c) pairs whose unrounded
+    delay lies within ``eps`` of a half-integer, as a list of (d, c, value),
+    so that a delay mismatch against another implementation can be traced to
+    a rounding tie."""
+    dm = _c(dm, np.float64)
+    cap = 1 << 16
+    od = np.zeros(cap, np.int32)
+    oc = np.zeros(cap, np.int32)
+    ov = np.zeros(cap, np.float64)
+    n = lib().orc_delay_ties(nchan, f_lo, bw, t_samp, _ptr(dm), len(dm), float(eps), _ptr(od), _ptr(oc),
+                             _ptr(ov), cap)
+    if n < 0:
+        raise ValueError("invalid plan arguments")
+    if n > cap:
+        raise ValueError(f"{n} ties: more than the log holds")
+    return [(int(od[i]), int(oc[i]), float(ov[i])) for i in range(n)]
 
 
 # ---- A1-A3 ---------------------------------------------------------------------

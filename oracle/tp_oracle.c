@@ -195,6 +195,33 @@ int64_t orc_delay_table(int nchan, double f_lo, double bw, double t_samp, const 
   return dmax;
 }
 
+/* Tie log of the rounding in Eq. 1 (R3): the (d, c) pairs whose unrounded
+ * delay v lies within eps of a half-integer, i.e. |v - floor(v) - 1/2| <= eps,
+ * where floor(v + 1/2) could go either way under a different rounding of v.
+ * Writes up to cap entries (d, c, v) in (d, c) order and returns how many pairs
+ * there are (all of them, also beyond cap); -1 for invalid arguments. */
+int64_t orc_delay_ties(int nchan, double f_lo, double bw, double t_samp, const double *dm, int ndm,
+                       double eps, int32_t *out_d, int32_t *out_c, double *out_v, int64_t cap) {
+  if (nchan <= 0 || ndm <= 0 || !(t_samp > 0.0) || !(eps >= 0.0)) return -1;
+  double *v = (double *)malloc(sizeof(double) * (size_t)nchan * (size_t)ndm);
+  orc_delay_exact(nchan, f_lo, bw, t_samp, dm, ndm, v);
+  int64_t n = 0;
+  for (int d = 0; d < ndm; ++d)
+    for (int c = 0; c < nchan; ++c) {
+      const double x = v[(int64_t)d * nchan + c];
+      if (fabs(x - floor(x) - 0.5) <= eps) {
+        if (n < cap) {
+          out_d[n] = d;
+          out_c[n] = c;
+          out_v[n] = x;
+        }
+        ++n;
+      }
+    }
+  free(v);
+  return n;
+}
+
 /* ---- A1: bandpass statistics (Sec. 2.2.1 "Bandpass Correction", R4) --------- */
 
 /* Float samples: mu_c = sum x / N, sigma_c = sqrt(sum (x - mu_c)^2 / N). */

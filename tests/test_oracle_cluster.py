@@ -105,3 +105,28 @@ def test_classification_of_pulse_and_rfi():
     assert len(spike) == 1 and spike[0]["broadband"] and not spike[0]["candidate"]
     burst = [r for r in cl if r["t_last"] >= 11000 and r["d_hi"] - r["d_lo"] > 40]
     assert len(burst) == 1 and burst[0]["rmse"] > 0.6 and not burst[0]["candidate"]
+
+
+def test_classification_hand_worked_fixture():
+    """Every classification product of two small clusters against the values
+    worked out by hand in tests/golden/classify_two_clusters.txt (Sec. 2.3,
+    steps 1-8, Eq. 3-4): the signature's largest SNR per trial, the 3-trial
+    average with its shortened end windows, d* by detection count (not by
+    SNR), the width at d*, the RMSE over the cluster's trial range and the
+    broadband / candidate decisions."""
+    from tests.golden_io import load
+    g = load("classify_two_clusters.txt")
+    m = g["meta"]
+    pts = g["points"]
+    d, t, snr, lab = pts[:, 0].astype(np.int64), pts[:, 1].astype(np.int64), pts[:, 2], pts[:, 3].astype(np.int64)
+    dms = np.arange(int(m["ndm"])) * float(m["dm_step"])
+    p = O.ClusterParams(smooth=int(m["smooth"]), dm_min=float(m["dm_min"]), rmse_max=float(m["rmse_max"]))
+    cl = O.classify(d, t, snr, lab, dms, float(m["t_samp"]), float(m["bw_mhz"]), float(m["f_ghz"]), p)
+    assert len(cl) == len(g["expected"])
+    for r, e in zip(cl, g["expected"]):
+        assert r["cluster"] == int(e[0]) and r["n"] == int(e[1])
+        assert (r["d_lo"], r["d_hi"], r["d_star"]) == (int(e[2]), int(e[3]), int(e[4]))
+        assert r["snr_max"] == e[5] and (r["t_first"], r["t_last"]) == (int(e[6]), int(e[7]))
+        assert abs(r["width_ms"] - e[8]) < 1e-12
+        assert abs(r["rmse"] - e[9]) < 1e-11, (r["rmse"], e[9])
+        assert r["broadband"] == bool(e[10]) and r["candidate"] == bool(e[11])

@@ -54,6 +54,34 @@ def test_delay_table_matches_exact_rational(nchan, f_lo, bw, ts, dms):
     assert near <= 2
 
 
+def test_delay_tie_log_finds_planted_and_exact_ties():
+    """The tie log (R3) lists exactly the (d, c) pairs whose unrounded delay,
+    computed as an exact rational, lies within 1e-9 of a half-integer.  Two
+    trials are planted on ties of channel 0 (their DM makes the exact delay
+    n + 1/2 up to the binary64 rounding of the DM itself)."""
+    nchan, f_lo, bw, ts = 16, 400.0, 16.0, "1e-3"
+    unit = BF.delays_exact(nchan, Fraction(f_lo), Fraction(bw), ts, [Fraction(1)])[0][0]  # delay at DM 1
+    planted = [float(Fraction(2 * n + 1, 2) / unit) for n in (3, 40)]
+    dms = np.array([0.0, 1.0, planted[0], 7.3, planted[1], 55.55], dtype=np.float64)
+    ties = O.delay_ties(nchan, f_lo, bw, float(ts), dms, eps=1e-9)
+    ex = BF.delays_exact(nchan, Fraction(f_lo), Fraction(bw), ts, [Fraction(float(d)) for d in dms])
+    want = {(d, c) for d in range(len(dms)) for c in range(nchan)
+            if abs(ex[d][c] - math.floor(ex[d][c]) - Fraction(1, 2)) <= Fraction(1, 10 ** 9)}
+    got = {(d, c) for d, c, _ in ties}
+    assert (2, 0) in want and (4, 0) in want
+    assert got == want
+    for d, c, v in ties:
+        assert abs(v - float(ex[d][c])) < 1e-9
+    # a plan of the benchmark's band: its ties (if any) are what the exact
+    # rational form finds within the same distance
+    dms = np.arange(0, 640, 7) * 0.2
+    ties = {(d, c) for d, c, _ in O.delay_ties(1024, 398.0, 20.0, 51.2e-6, dms)}
+    ex = BF.delays_exact(1024, Fraction(398), Fraction(20), "51.2e-6", [Fraction(float(d)) for d in dms])
+    want = {(d, c) for d in range(len(dms)) for c in range(1024)
+            if abs(ex[d][c] - math.floor(ex[d][c]) - Fraction(1, 2)) <= Fraction(1, 10 ** 9)}
+    assert ties == want
+
+
 def test_delay_uses_4148_808_not_rounded_constant():
     """The binding constant is 4148.808 s MHz^2; Eq. 1's printed 4.15e6 ms
     differs by 0.03 %, which moves the large delays by about one sample."""
