@@ -69,9 +69,10 @@ extern "C" {
  *                   chunk and its time-adjacent chunks (and, with
  *                   dilate_channels, the same chunk of channels c-1, c+1) are
  *                   flagged.
- *   spectrum stage: spectrum t is flagged when the sum over channels of the
- *                   bandpass-corrected samples, flagged chunks counting 0,
- *                   exceeds tau_spectrum * sqrt(sum_c sigma_c^2).
+ *   spectrum stage: spectrum t is flagged when the sum of the bandpass-
+ *                   corrected samples over the channels whose chunk at t is
+ *                   not flagged exceeds tau_spectrum * sqrt(sum of sigma_c^2
+ *                   over the same channels) (one threshold per chunk).
  *   A flagged sample is replaced by its channel's bandpass value. */
 typedef struct tp_rfi_params {
   int32_t enable_channel;  /* 1: run the channel stage                         */

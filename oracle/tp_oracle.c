@@ -32,9 +32,11 @@
  *       channels).
  *   R6  spectrum thresholding (Sec. 2.2.1) looks at the bandpass-corrected
  *       spectrum after the channel stage has substituted its chunks: the sum
- *       over channels of (x - mu_c), flagged chunks contributing 0, is compared
- *       with tau_s sqrt(sum_c sigma_c^2), i.e. the full-band mean against tau_s
- *       times the standard deviation of that mean.
+ *       over the channels unflagged at t of (x - mu_c) is compared with
+ *       tau_s sqrt(sum of sigma_c^2 over the same channels), i.e. the mean
+ *       over the unflagged band against tau_s times its standard deviation.
+ *       The unflagged set changes only at chunk boundaries, so the threshold
+ *       is one value per chunk.
  *   R7  a flagged sample is replaced by the channel's bandpass value b_c and b_c
  *       is subtracted from every sample, so a flagged sample contributes
  *       exactly 0.  b_c is mu_c expressed in the data's storage format: the
@@ -378,60 +380,77 @@ void orc_channel_mask_fit(const void *x, int dtype, int nchan, int64_t nsamp, in
 
 /* ---- A3: spectrum thresholding (Sec. 2.2.1 "Spectrum Thresholding", R6) ----- */
 
-/* Float samples: spectrum t is flagged when sum over channels whose chunk is
- * not flagged of (x - mu_c) > tau_s sqrt(sum_c sigma_c^2). */
+/* Per-chunk threshold tau_s sqrt(sum of sigma_c^2 over the channels whose
+ * chunk k is not flagged), the sum in channel order. */
+static void unflagged_thresholds(int nchan, int nchunk, double tau_s, const double *sigma,
+                                 const uint8_t *chunk_flag, double *thr) {
+  for (int k = 0; k < nchunk; ++k) {
+    double v = 0.0;
+    for (int c = 0; c < nchan; ++c)
+      if (!chunk_flag[(int64_t)c * nchunk + k]) v += sigma[c] * sigma[c];
+    thr[k] = tau_s * sqrt(v);
+  }
+}
+
+/* Float samples: spectrum t is flagged when the sum over the channels whose
+ * chunk is not flagged of (x - mu_c) > tau_s sqrt(sum of their sigma_c^2). */
 void orc_spectrum_mask_float(const void *x, int dtype, int nchan, int64_t nsamp, int64_t pitch,
                              int W, double tau_s, const double *mu, const double *sigma,
                              const uint8_t *chunk_flag, uint8_t *spec_flag) {
   const int nchunk = (int)((nsamp + W - 1) / W);
-  double v = 0.0;
-  for (int c = 0; c < nchan; ++c) v += sigma[c] * sigma[c];
-  const double thr = tau_s * sqrt(v);
+  double *thr = (double *)malloc(sizeof(double) * (size_t)nchunk);
+  unflagged_thresholds(nchan, nchunk, tau_s, sigma, chunk_flag, thr);
   /* m[t] accumulates channel c = 0, 1, ... in order for every t */
   double *m = (double *)calloc((size_t)nsamp, sizeof(double));
   for (int c = 0; c < nchan; ++c)
     for (int64_t t = 0; t < nsamp; ++t)
       if (!chunk_flag[(int64_t)c * nchunk + t / W]) m[t] += sample(x, dtype, (int64_t)c * pitch + t) - mu[c];
-  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)(m[t] > thr);
+  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)(m[t] > thr[t / W]);
   free(m);
+  free(thr);
 }
 
 /* 8-bit samples, block statistics, exact: multiplied through by N the test is
- * sum(N x - S_c) > tau_s sqrt(sum_c V_c).  sum_c V_c can exceed 2^63, so it is
- * kept exactly as a high part (V >> 20) and a low part (V & (2^20 - 1)) and
- * converted as hi * 2^20 + lo. */
+ * sum(N x - S_c) > tau_s sqrt(sum V_c), both sums over the channels unflagged
+ * at t.  The sum of V_c can exceed 2^63, so it is kept exactly as a high part
+ * (V >> 20) and a low part (V & (2^20 - 1)) and converted as hi * 2^20 + lo. */
 void orc_spectrum_mask_u8(const uint8_t *x, int nchan, int64_t nsamp, int64_t pitch, int W,
                           double tau_s, const int64_t *S, const int64_t *V,
                           const uint8_t *chunk_flag, uint8_t *spec_flag) {
   const int nchunk = (int)((nsamp + W - 1) / W);
-  uint64_t vhi = 0, vlo = 0;
-  for (int c = 0; c < nchan; ++c) {
-    vhi += (uint64_t)V[c] >> 20;
-    vlo += (uint64_t)V[c] & 0xFFFFFu;
+  double *thr = (double *)malloc(sizeof(double) * (size_t)nchunk);
+  for (int k = 0; k < nchunk; ++k) {
+    uint64_t vhi = 0, vlo = 0;
+    for (int c = 0; c < nchan; ++c)
+      if (!chunk_flag[(int64_t)c * nchunk + k]) {
+        vhi += (uint64_t)V[c] >> 20;
+        vlo += (uint64_t)V[c] & 0xFFFFFu;
+      }
+    thr[k] = tau_s * sqrt((double)vhi * 1048576.0 + (double)vlo);
   }
-  const double thr = tau_s * sqrt((double)vhi * 1048576.0 + (double)vlo);
   int64_t *m = (int64_t *)calloc((size_t)nsamp, sizeof(int64_t));
   for (int c = 0; c < nchan; ++c)
     for (int64_t t = 0; t < nsamp; ++t)
       if (!chunk_flag[(int64_t)c * nchunk + t / W]) m[t] += nsamp * sample_u8(x, (int64_t)c * pitch + t) - S[c];
-  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)((double)m[t] > thr);
+  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)((double)m[t] > thr[t / W]);
   free(m);
+  free(thr);
 }
 
-/* 8-bit samples with external bandpass b_c and spread sigma_c. */
+/* 8-bit samples with external (or fitted) bandpass b_c and spread sigma_c. */
 void orc_spectrum_mask_u8_ext(const uint8_t *x, int nchan, int64_t nsamp, int64_t pitch, int W,
                               double tau_s, const int64_t *b, const double *sigma,
                               const uint8_t *chunk_flag, uint8_t *spec_flag) {
   const int nchunk = (int)((nsamp + W - 1) / W);
-  double v = 0.0;
-  for (int c = 0; c < nchan; ++c) v += sigma[c] * sigma[c];
-  const double thr = tau_s * sqrt(v);
+  double *thr = (double *)malloc(sizeof(double) * (size_t)nchunk);
+  unflagged_thresholds(nchan, nchunk, tau_s, sigma, chunk_flag, thr);
   int64_t *m = (int64_t *)calloc((size_t)nsamp, sizeof(int64_t));
   for (int c = 0; c < nchan; ++c)
     for (int64_t t = 0; t < nsamp; ++t)
       if (!chunk_flag[(int64_t)c * nchunk + t / W]) m[t] += sample_u8(x, (int64_t)c * pitch + t) - b[c];
-  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)((double)m[t] > thr);
+  for (int64_t t = 0; t < nsamp; ++t) spec_flag[t] = (uint8_t)((double)m[t] > thr[t / W]);
   free(m);
+  free(thr);
 }
 
 /* ---- A4: substitution (R7) --------------------------------------------------- */

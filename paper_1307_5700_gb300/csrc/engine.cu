@@ -102,17 +102,6 @@ unsigned short storage_bits_host(int dtype, double mu) {
   return sign | (unsigned short)std::ldexp(a, 24);  // subnormal: a = m 2^-24
 }
 
-// Sum of sigma_c^2 in channel order, binary64, times tau_s: the spectrum
-// threshold under externally supplied statistics.
-double external_spectrum_threshold(const double* sigma, int nchan, double tau_s) {
-  volatile double v = 0.0;  // keep the sequential order and separate roundings
-  for (int c = 0; c < nchan; ++c) {
-    const volatile double sq = sigma[c] * sigma[c];
-    v = v + sq;
-  }
-  return tau_s * std::sqrt((double)v);
-}
-
 }  // namespace tp
 
 using namespace tp;
@@ -216,7 +205,6 @@ struct Beam {
   BeamState state = kEmpty;
   int ntt = 0;
   bool have_ext = false;
-  double ext_thr = 0.0;
   // last arguments uploaded to d_args
   DedispArgs h_args{};
   int h_cta[2] = {0, 0};
@@ -437,7 +425,7 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->mu_lo, nc * 4);
   add((void**)&b->spec_bits, (size_t)((nmax + 31) / 32) * 4);
   add((void**)&b->spec_nflag, 4);
-  add((void**)&b->spec_thr, 8);
+  add((void**)&b->spec_thr, (size_t)nchunk * 8);
   add((void**)&b->pivot, nc * 4);
   add((void**)&b->bfit, nc * 8);
   add((void**)&b->fit_masked, nc);
@@ -639,7 +627,7 @@ int issue_rfi(tp_engine* e, Beam* b, cudaStream_t s) {
   if (p->rfi.stats_mode == TP_STATS_EXTERNAL && !b->have_ext)
     return set_error(TP_ENOTREADY, "beam %d: external statistics not set", b->id);
   RfiArgs ra = rfi_args(p, b);
-  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->ext_thr, b->y, b->ypitch, s));
+  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->y, b->ypitch, s));
   e->launches += 4;
   return TP_OK;
 }
@@ -1218,7 +1206,6 @@ int tp_beam_set_bandpass(tp_engine* e, int beam, const double* mu, const double*
   TP_CUDA_TRY(cudaMemcpyAsync(b->bint, bi.data(), nchan * 4, cudaMemcpyHostToDevice, s));
   TP_CUDA_TRY(cudaMemcpyAsync(b->b16, bh.data(), nchan * 2, cudaMemcpyHostToDevice, s));
   TP_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
-  b->ext_thr = external_spectrum_threshold(sigma, nchan, p->rfi.tau_spectrum);
   b->have_ext = true;
   return TP_OK;
 }

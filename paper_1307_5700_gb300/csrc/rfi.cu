@@ -425,61 +425,55 @@ __global__ void __launch_bounds__(kThreads) dilate_kernel(RfiArgs a) {
   if (lane == 0) a.chan_nflag[c] = cnt;
 }
 
-// Spectrum threshold (one CTA).  Block statistics: float data sum sigma_c^2 in
-// binary64; 8-bit data sum V_c exactly as (V >> 20, V & (2^20 - 1)).  External
-// statistics: the threshold was computed on the host and is passed in.
-__global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a, double ext_thr) {
-  __shared__ double s_d[kThreads];
-  __shared__ unsigned long long s_hi[kThreads], s_lo[kThreads];
-  __shared__ double s_b[kThreads];
-  if (threadIdx.x == 0) *a.spec_nflag = 0;
-  // sum of the bandpass values (16-bit and 8-bit staging subtract it once)
-  double bs = 0.0;
-  if (a.dtype == TP_U8 || a.dtype == TP_F16 || a.dtype == TP_BF16)
-    for (int c = threadIdx.x; c < a.nchan; c += kThreads)
-      bs += a.dtype == TP_U8 ? (double)a.bint[c] : storage_value(a.dtype, a.b16[c]);
-  s_b[threadIdx.x] = bs;
-  __syncthreads();
-  for (int o = kThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) s_b[threadIdx.x] += s_b[threadIdx.x + o];
+// Spectrum thresholds, one per chunk k (reading R6): tau_s times the square
+// root of the sum of the spreads of the channels whose chunk k is not flagged
+// (binary64 sigma_c^2; 8-bit block statistics: the exact integer sum of V_c,
+// kept as (V >> 20, V & (2^20 - 1))).  One warp per chunk; lane l sums the
+// channels l, l + 32, ... and the warp folds the 32 partial sums in a fixed
+// order.  CTA 0 also sums the bandpass values (16-bit and 8-bit staging
+// subtract that sum once).
+__global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a) {
+  if (blockIdx.x == 0) {
+    __shared__ double s_b[kThreads];
+    if (threadIdx.x == 0) *a.spec_nflag = 0;
+    double bs = 0.0;
+    if (a.dtype == TP_U8 || a.dtype == TP_F16 || a.dtype == TP_BF16)
+      for (int c = threadIdx.x; c < a.nchan; c += kThreads)
+        bs += a.dtype == TP_U8 ? (double)a.bint[c] : storage_value(a.dtype, a.b16[c]);
+    s_b[threadIdx.x] = bs;
     __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) s_b[threadIdx.x] += s_b[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *a.bsum = s_b[0];
   }
-  if (threadIdx.x == 0) *a.bsum = s_b[0];
-  if (a.stats_mode == TP_STATS_EXTERNAL) {
-    if (threadIdx.x == 0) *a.spec_thr = ext_thr;
-    return;
-  }
+  const int k = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= a.nchunk) return;
+  // exact integer spreads: 8-bit data with the block's own statistics
+  const bool exact = a.dtype == TP_U8 && !a.fit && a.stats_mode != TP_STATS_EXTERNAL;
   double v = 0.0;
   unsigned long long hi = 0, lo = 0;
-  const bool fit = a.fit;
-  for (int c = threadIdx.x; c < a.nchan; c += kThreads) {
-    if (a.dtype == TP_U8 && !fit) {
+  for (int c = lane; c < a.nchan; c += 32) {
+    if (a.chan_nflag[c] != 0 && a.chunk_flag[(int64_t)c * a.nchunk + k]) continue;
+    if (exact) {
       const unsigned long long V = (unsigned long long)a.V[c];
       hi += V >> 20;
       lo += V & 0xFFFFFull;
     } else {
-      v += a.sigma[c] * a.sigma[c];
+      v = __dadd_rn(v, __dmul_rn(a.sigma[c], a.sigma[c]));
     }
   }
-  s_d[threadIdx.x] = v;
-  s_hi[threadIdx.x] = hi;
-  s_lo[threadIdx.x] = lo;
-  __syncthreads();
-  for (int o = kThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      s_d[threadIdx.x] += s_d[threadIdx.x + o];
-      s_hi[threadIdx.x] += s_hi[threadIdx.x + o];
-      s_lo[threadIdx.x] += s_lo[threadIdx.x + o];
-    }
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    hi += __shfl_xor_sync(0xffffffffu, hi, o);
+    lo += __shfl_xor_sync(0xffffffffu, lo, o);
   }
-  if (threadIdx.x == 0) {
-    double tot;
-    if (a.dtype == TP_U8 && !fit)
-      tot = __dadd_rn(__dmul_rn((double)s_hi[0], 1048576.0), (double)s_lo[0]);
-    else
-      tot = s_d[0];
-    *a.spec_thr = __dmul_rn(a.tau_s, __dsqrt_rn(tot));
+  if (lane == 0) {
+    const double tot = exact ? __dadd_rn(__dmul_rn((double)hi, 1048576.0), (double)lo) : v;
+    a.spec_thr[k] = __dmul_rn(a.tau_s, __dsqrt_rn(tot));
   }
 }
 
@@ -604,9 +598,9 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
     }
     __syncthreads();
     if (tid < 32) {
-      const double thr = *a.spec_thr;
       bool flag = false;
       if (t0 + tid < a.nsamp) {
+        const double thr = a.spec_thr[(t0 + tid) / a.W];
         if constexpr (!kU8) {
           double m = 0.0;
           for (int w = 0; w < 32; ++w) m += s_f[w][tid];
@@ -1032,8 +1026,7 @@ cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void* y, int64_t ypitch,
-                       cudaStream_t s) {
+cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypitch, cudaStream_t s) {
   if (a.dtype == TP_U8)
     chunk_stats_u8<<<a.nchan, kThreads, 0, s>>>(a, static_cast<longlong2*>(chunk_sums));
   else if (a.dtype == TP_F16)
@@ -1071,7 +1064,7 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void*
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  spectrum_threshold_kernel<<<1, kThreads, 0, s>>>(a, ext_thr);
+  spectrum_threshold_kernel<<<(unsigned)((a.nchunk + kWarps - 1) / kWarps), kThreads, 0, s>>>(a);
   const unsigned blocks = (unsigned)((a.nsamp + 31) / 32);
   if (a.dtype == TP_C16)
     spectrum_substitute_kernel<TP_C16><<<blocks, kThreads, 0, s>>>(a, y, ypitch);

@@ -48,7 +48,7 @@ struct RfiArgs {
   int* chan_nflag;        // [nchan] flagged chunks per channel
   uint32_t* spec_bits;    // [ceil(N_s/32)] spectrum flags
   int* spec_nflag;        // [1] flagged spectra
-  double* spec_thr;       // [1] spectrum threshold (per-block constant)
+  double* spec_thr;       // [nchunk] spectrum threshold of each chunk (its unflagged channels)
   int stage_f32;          // 16-bit data: stage y = x~ - b in FP32 (for the FP32 kernel shapes)
   // fitted bandpass (Sec. 2.2.1 "Bandpass Correction"): fit = 1 turns it on
   // (0, the zero-initialised value, leaves the block statistics); the chunk
@@ -201,9 +201,8 @@ constexpr int kDetectT = 4096;      // samples per detection CTA
 // ---- launchers (each returns a cudaError_t of the launch) -----------------------
 cudaError_t launch_delay_table(int nchan, double f_lo, double bw, double t_samp, const double* dm,
                                int ndm, int32_t* delay, int* err_flag, cudaStream_t s);
-cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, double ext_thr, void* y, int64_t ypitch,
+cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypitch,
                        cudaStream_t s);
-double external_spectrum_threshold(const double* sigma, int nchan, double tau_s);
 cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s);
 cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s);

@@ -92,16 +92,17 @@ def search(x, is_u8, W, tau_c, tau_s, chan_on, spec_on, delays, nsigma, dilate_c
     # spectrum thresholding
     spec = [False] * n
     if spec_on:
-        if is_u8:
-            thr = tau_s * math.sqrt(float(sum(V)))
-        else:
-            thr = tau_s * math.sqrt(math.fsum(s * s for s in sig))
         for t in range(n):
+            # only the channels whose chunk at t is not flagged take part,
+            # in the sum and in its spread
+            keep = [c for c in range(nchan) if not flags[c][t // W]]
             if is_u8:
-                m = sum(n * x[c][t] - S[c] for c in range(nchan) if not flags[c][t // W])
+                thr = tau_s * math.sqrt(float(sum(V[c] for c in keep)))
+                m = sum(n * x[c][t] - S[c] for c in keep)
                 spec[t] = float(m) > thr
             else:
-                m = math.fsum(x[c][t] - mu[c] for c in range(nchan) if not flags[c][t // W])
+                thr = tau_s * math.sqrt(math.fsum(sig[c] * sig[c] for c in keep))
+                m = math.fsum(x[c][t] - mu[c] for c in keep)
                 spec[t] = m > thr
 
     if not is_u8:

@@ -5,7 +5,7 @@ import pytest
 from oracle import oracle as O
 from tests.golden_io import load
 
-CASES = ["rfi_3x8_channel.txt", "rfi_3x8_spectrum.txt", "rfi_8x64_float.txt"]
+CASES = ["rfi_3x8_channel.txt", "rfi_3x8_spectrum.txt", "rfi_8x64_float.txt", "rfi_4x16_spectrum_unflagged.txt"]
 
 
 def _x(g, dtype):
