@@ -55,7 +55,7 @@ extern "C" {
 #define TP_F32 3  /* IEEE binary32; FP32 accumulation                          */
 #define TP_C16 4  /* complex voltage, int16 real then int16 imaginary part (4 bytes
                      a sample): detected as power |v|^2 = re^2 + im^2 on load by the
-                     statistics and staging kernels (Sec. 2, "power calculation";
+                     statistics and staging kernels (the power stage of Sec. 2;
                      Sec. 1.1: 16 bits per complex component); FP32 accumulation */
 
 /* ---- bandpass statistics modes ---------------------------------------------- */
@@ -199,6 +199,22 @@ int tp_plan_set_postprocess(tp_plan *p, int median_width, int detrend);
  * block statistics (TP_STATS_BLOCK) and at most 8192 channels (TP_EINVAL);
  * call before any beam of the plan is opened (TP_EBUSY). */
 int tp_plan_set_bandpass_fit(tp_plan *p, int order, double tau_mask);
+
+/* Running bandpass statistics across the blocks of a stream (Sec. 2.2.1
+ * averages the bandpass per processing iteration; reading R15).  Each beam of the
+ * plan folds a block's own mean mu_c and variance sigma_c^2 into an
+ * exponential average with weight alpha on the new block,
+ *   mu_run = alpha mu + (1 - alpha) mu_run_prev,
+ *   var_run = alpha sigma^2 + (1 - alpha) var_run_prev
+ * (binary64; the stream's first block starts the average), kept on the device
+ * between blocks, and thresholds, substitutes and subtracts with mu_run and
+ * sqrt(var_run) as with external statistics (8-bit data: the integer
+ * floor(mu_run + 1/2)).  alpha = 1 (the default) is per-block statistics.
+ * tp_get_bandpass then returns the running values.  Processing the same
+ * window again (tp_beam_rewind) repeats the same update.
+ * Errors: TP_EINVAL (alpha outside (0, 1], external statistics, or a fitted
+ * bandpass on the plan), TP_EBUSY (the plan has open beams). */
+int tp_plan_set_running_stats(tp_plan *p, double alpha);
 
 /* Clustering and classification of every block's detections (Sec. 2.3:
  * DBSCAN of the (time, DM, intensity) triplets, then each cluster's DM-SNR
@@ -426,6 +442,23 @@ int tp_set_profiling(tp_engine *e, int enable);
  * ms[2] A4-A5 (dedispersion), ms[3] A6-A7 (detection); *count = blocks timed.
  * Blocks until the beam's last timed stage has finished. */
 int tp_get_stage_times(tp_engine *e, int beam, double *ms, int64_t *count);
+
+/* Accumulated device time of the batched dedispersion launches (A4-A5 of
+ * every beam of a tp_run_ready batch, all kernel-shape groups) issued outside
+ * CUDA graphs since profiling was enabled, in ms, and how many batches that
+ * covers.  Blocks until the last timed batch has finished.  Batches replayed
+ * from graphs are not timed. */
+int tp_get_batch_times(tp_engine *e, double *ms, int64_t *count);
+
+/* Attempts (mbarrier try_wait calls) a dedispersion CTA makes while it waits
+ * for staged data or for a free stage buffer before it gives up, records
+ * TP_ETIMEOUT in the beam's status word (reported by tp_get_candidates) and
+ * leaves; before leaving it always lets its own copies in flight land.
+ * tries < 0 restores the default (2^24); 0 makes every such wait give up at
+ * once, which tests use to exercise the timeout path without a fault or a
+ * hang.  Applies to launches issued after the call (cached batch graphs are
+ * dropped).  Errors: TP_EINVAL for a NULL engine. */
+int tp_engine_set_wait_limit(tp_engine *e, long long tries);
 
 /* Kernels launched by the engine since it was created. */
 int tp_engine_launches(const tp_engine *e, uint64_t *n);

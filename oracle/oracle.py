@@ -207,6 +207,25 @@ def external_stats(dtype, mu, sigma):
     return st
 
 
+def running_stats(prev, x, dtype, alpha):
+    """Running bandpass statistics across the blocks of a stream (Sec. 2.2.1
+    averages the bandpass over each processing iteration; reading R15): the block's own
+    mean mu and variance sigma^2 (R4) are folded into an exponential average
+    with weight alpha on the new block,
+        mu_run = alpha * mu + (1 - alpha) * mu_run_prev,
+        var_run = alpha * sigma^2 + (1 - alpha) * var_run_prev,
+    starting from the first block's own values; alpha = 1 is per-block
+    statistics.  Returns (state, stats): the state (mu_run, var_run) for the
+    next block, and the statistics the block is thresholded and corrected
+    with, in the form of external statistics (mu_run, sqrt(var_run))."""
+    st = bandpass(x, dtype)
+    mu, var = st["mu"], st["sigma"] * st["sigma"]
+    if prev is not None:
+        mu = alpha * mu + (1.0 - alpha) * prev[0]
+        var = alpha * var + (1.0 - alpha) * prev[1]
+    return (mu, var), external_stats(dtype, mu, np.sqrt(var))
+
+
 def bandpass_fit(mu, order, tau_mask):
     """Fitted bandpass of Sec. 2.2.1 "Bandpass Correction", reading R13.
 

@@ -52,6 +52,7 @@ EXPORTS = (
     "tp_beam_rewind", "tp_autotune_batch", "tp_plan_set_postprocess", "tp_get_processed_series",
     "tp_get_detrend", "tp_plan_set_bandpass_fit", "tp_get_bandpass_fit", "tp_plan_set_clustering",
     "tp_get_clusters", "tp_get_candidate_labels", "tp_prefetch_block", "tp_push_prefetched",
+    "tp_get_batch_times", "tp_engine_set_wait_limit", "tp_plan_set_running_stats",
 )
 
 
@@ -122,6 +123,9 @@ _SIGS = {
     "tp_get_series_stats": (_i, [_vp, _i, _vp, _vp, _i]),
     "tp_set_profiling": (_i, [_vp, _i]),
     "tp_get_stage_times": (_i, [_vp, _i, _vp, _vp]),
+    "tp_get_batch_times": (_i, [_vp, _vp, _vp]),
+    "tp_engine_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
+    "tp_plan_set_running_stats": (_i, [_vp, _d]),
     "tp_engine_launches": (_i, [_vp, _vp]),
     "tp_plan_shapes": (_i, [_vp, _vp, _vp, _i]),
     "tp_plan_set_shape": (_i, [_vp, _i]),
@@ -393,6 +397,27 @@ def tp_get_stage_times(e, beam):
     return ms, n.value
 
 
+def tp_get_batch_times(e):
+    """(ms of the batched dedispersion launches timed since profiling was
+    enabled, number of batches)."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().tp_get_batch_times(e, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def tp_plan_set_running_stats(p, alpha):
+    """Exponential average of the bandpass statistics across blocks, weight
+    alpha on the new block (1 = per block)."""
+    return _check(lib().tp_plan_set_running_stats(p, float(alpha)))
+
+
+def tp_engine_set_wait_limit(e, tries=-1):
+    """Attempts of the dedispersion kernel's waits before it reports
+    TP_ETIMEOUT (-1: the default; 0: give up at once)."""
+    return _check(lib().tp_engine_set_wait_limit(e, int(tries)))
+
+
 def tp_engine_launches(e):
     n = ctypes.c_uint64()
     _check(lib().tp_engine_launches(e, ctypes.byref(n)))
@@ -414,7 +439,7 @@ def tp_plan_set_shape(p, shape):
 def tp_autotune(e, beam, reps=3):
     """(best shape, ms per launch for every shape; -1 where infeasible)."""
     best = ctypes.c_int()
-    ms = np.full(64, -1.0, np.float32)
+    ms = np.full(128, -1.0, np.float32)
     _check(lib().tp_autotune(e, beam, int(reps), ctypes.byref(best), ms.ctypes.data, len(ms)))
     return best.value, ms
 
@@ -491,7 +516,7 @@ def tp_get_candidate_labels(e, beam, cap=1 << 20):
 def tp_autotune_batch(e, reps=2):
     """(best shape, ms per batched launch for every shape; -1 where not timed)."""
     best = ctypes.c_int()
-    ms = np.full(64, -1.0, np.float32)
+    ms = np.full(128, -1.0, np.float32)
     _check(lib().tp_autotune_batch(e, int(reps), ctypes.byref(best), ms.ctypes.data, len(ms)))
     return best.value, ms
 

@@ -40,9 +40,16 @@
 // w, w + NCONS, ... kLookRot stages ahead of their use, over kStagesRot
 // buffers, so that the warp that fills a buffer rarely waits for the others to
 // release it.
+// ALGO 9 is ALGO 8 (8-bit quads, no producer warp) with the channels of a
+// stage in one call: each channel's block fetches the next channel's window
+// offset and block index, issues its window loads before its adds, spreads
+// the packed adds over two execution pipes, and ends with the next channel's
+// indexed branch (threaded dispatch, no branch back to a loop).
 // Each (d, t) adds its channels in index order (FP32, or exact integers).
-// Every mbarrier wait is bounded; a wait that gives up records TP_ETIMEOUT in
-// the beam's status word and the CTA leaves after letting its copies land.
+// Every mbarrier wait is bounded; a wait for staged data or a free stage
+// buffer gives up after DedispArgs::wait_tries attempts, records TP_ETIMEOUT
+// in the beam's status word, and the CTA leaves after letting its own copies
+// land (that drain always allows kDefaultWaitTries attempts).
 //
 // The epilogue writes D (FP32, or int32 for 8-bit data, exact) and per
 // (DM, time tile) sums of D and D^2 for the series statistics of A6.
@@ -65,7 +72,7 @@ constexpr int kStagesU8 = 8;
 constexpr int kStagesRot = 6;                       // ALGO 6, 7: pipeline depth
 constexpr int kLookRot = 2;                         // ALGO 6, 7: stages issued ahead of use
 constexpr int kDelRing = 8;                         // stages of delays prefetched ahead
-constexpr long long kSpinLimit = 1LL << 24;         // bounded mbarrier waits
+constexpr long long kSpinLimit = kDefaultWaitTries;  // drain of the CTA's own copies in flight
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -94,8 +101,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (long long spin = 0; spin < kSpinLimit; ++spin)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long tries = kSpinLimit) {
+  for (long long spin = 0; spin < tries; ++spin)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -139,13 +146,16 @@ constexpr int kModeU8 = 3;    // 8-bit x~ widened to 16 bits, summed as packed 1
 // into the 32-bit sums (256 x 255 < 2^16, so no lane can carry into the next)
 constexpr int kU8FoldStages = 256 / kNC;
 
-template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO>
+template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB = 1>
 struct Shape {
   // ALGO 6, 7 and 8: the consumer schemes of ALGO 4, 5 and 3 without a
   // producer warp (every consumer warp issues the copies of every NCONS-th
   // stage)
   static constexpr bool ROT = ALGO >= 6;
-  static constexpr int AB = ALGO == 8 ? 3 : ROT ? ALGO - 2 : ALGO;
+  static constexpr int AB = ALGO >= 8 ? 3 : ROT ? ALGO - 2 : ALGO;
+  // ALGO 9-11: the 8-bit quads of ALGO 8 with every channel of a stage added
+  // in one call (variant ALGO - 6 of add_quad8t)
+  static constexpr bool THREADED = ALGO >= 9;
   static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
   static constexpr int QS = 16 / EB;                                          // samples per 16 B
   static constexpr int NSEG = AB == 4 ? 2 : 1;                              // output segments per lane
@@ -159,7 +169,10 @@ struct Shape {
   static constexpr int ROWB = ROW * EB;
   static constexpr int THREADS = (NCONS + (ROT ? 0 : 1)) * 32;               // + one producer warp
   static constexpr int DW = NCONS * K <= 32 ? 32 : 64;                        // delays staged per channel
-  static constexpr int STAGES = MODE == kModeU8 && AB == 1 ? kStagesU8 : ROT ? kStagesRot : kStages;
+  // two CTAs per SM without a producer warp: one stage buffer fewer, so that
+  // both fit the SM's shared memory
+  static constexpr int STAGES =
+      MODE == kModeU8 && AB == 1 ? kStagesU8 : ROT ? (MINB >= 2 ? kStagesRot - 1 : kStagesRot) : kStages;
   static constexpr size_t data_bytes = (size_t)STAGES * kNC * ROWB;
   static constexpr size_t del_bytes = sizeof(int) * (ROT ? NCONS : kDelRing) * kNC * DW;  // ring, or a slot per warp
   // 8-bit mode: per (stage, consumer warp) K int4 of word offsets (one per
@@ -180,6 +193,7 @@ struct Shape {
   static_assert(AB != 5 || S % 2 == 1, "in-lane pairs: S = 2 (S / 2) + 1");
   static_assert(AB == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
   static_assert(MODE != kModeU8 || AB == 1 || AB == 3, "8-bit data: direct loads or DM quads");
+  static_assert(!THREADED || MODE == kModeU8, "threaded dispatch: 8-bit quads");
 };
 
 // Per (stage, channel, consumer warp) the producer writes an int4:
@@ -188,9 +202,9 @@ struct Shape {
 //   z = number of 16-byte units of the window the channel needs.
 
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
-__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS, MINB)
+__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::THREADS, MINB)
     dedisperse_kernel(BatchArgs ba) {
-  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO>;
+  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   constexpr bool ROT = Sh::ROT;
   constexpr int AB = Sh::AB;  // the consumer scheme
   // the CTA's beam: last b with cta_start[b] <= blockIdx.x
@@ -382,7 +396,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
       const int buf = i % STAGES;
       if (i >= STAGES) {
         bool got = false;
-        if (lane == 0) got = mbar_wait_bounded(&empty[buf], (unsigned)(((i / STAGES) - 1) & 1));
+        if (lane == 0) got = mbar_wait_bounded(&empty[buf], (unsigned)(((i / STAGES) - 1) & 1), a.wait_tries);
         if (!__shfl_sync(0xffffffffu, got, 0)) {
           ok = false;
           break;
@@ -519,7 +533,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
     const int pbuf = j % STAGES;
     if (j >= STAGES) {
       bool got = false;
-      if (lane == 0) got = mbar_wait_bounded(&empty[pbuf], (unsigned)(((j / STAGES) - 1) & 1));
+      if (lane == 0) got = mbar_wait_bounded(&empty[pbuf], (unsigned)(((j / STAGES) - 1) & 1), a.wait_tries);
       if (!__shfl_sync(0xffffffffu, got, 0)) return false;
     }
     issue_stage(j, myslot);
@@ -556,7 +570,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
         return;
       }
     }
-    if (!mbar_wait_bounded(&full[buf], (unsigned)((i / STAGES) & 1))) {
+    if (!mbar_wait_bounded(&full[buf], (unsigned)((i / STAGES) & 1), a.wait_tries)) {
       if constexpr (ROT)
         bail();
       else if (lane == 0)
@@ -618,6 +632,9 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
         // (one call site: the loop stays rolled so the jump table is emitted
         // once)
         const unsigned sbase = smem_u32(srow) + (unsigned)(lane * S * EB);
+        if constexpr (Sh::THREADED) {
+          add_quad8t<S, OMAX, NCONS, ALGO - 6>(sbase, smem_u32(&sinfo[(buf * kNC) * NCONS + warp]), nc, qe, qf);
+        } else {
 #pragma unroll 1
         for (int ci = 0; ci < nc; ++ci) {
           const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
@@ -631,6 +648,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
             add_quad8<S, OMAX>(inf.y, sbase + (unsigned)inf.x, qe, qf);
           else
             add_quad16<S, OMAX, MODE == kModeBF16 ? 1 : 0>(inf.y, sbase + (unsigned)inf.x, acc);
+        }
         }
       }
     } else if (live && AB == 1) {
@@ -790,7 +808,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO>::THREADS,
 
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
 cudaError_t launch_mode(const BatchArgs& ba, int ctas, cudaStream_t s) {
-  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO>;
+  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   if (ctas <= 0) return cudaErrorInvalidValue;
   auto k = dedisperse_kernel<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);

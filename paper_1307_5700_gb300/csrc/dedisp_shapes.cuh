@@ -18,7 +18,8 @@
 // ALGO 5: ALGO 3 with the lane's outputs s and s + S / 2 added by one paired
 // FP32 add (S odd; FP32 staging only);
 // ALGO 6, 7, 8: ALGO 4, 5, 3 without a producer warp: all NCONS warps consume,
-// and warp w also issues the copies of stages w, w + NCONS, ...
+// and warp w also issues the copies of stages w, w + NCONS, ...;
+// ALGO 9: ALGO 8 (8-bit data) with threaded dispatch over a stage's channels.
 // MINB: CTAs per SM the register allocation is sized for.
 #define TP_SHAPES(X)                 \
   X(0, 4, 20, 36, 8, 4, 0, 1)        \
@@ -79,7 +80,14 @@
   X(55, 4, 45, 9, 8, 4, 7, 1)        \
   X(56, 4, 21, 9, 8, 4, 6, 1)        \
   X(57, 4, 30, 16, 8, 3, 8, 1)       \
-  X(58, 4, 26, 16, 8, 3, 8, 1)
+  X(58, 4, 26, 16, 8, 3, 8, 1)       \
+  X(59, 4, 30, 16, 8, 3, 9, 1)       \
+  X(60, 4, 26, 16, 8, 3, 9, 1)       \
+  X(61, 4, 22, 16, 8, 3, 9, 1)       \
+  X(62, 4, 30, 16, 8, 3, 10, 1)      \
+  X(63, 4, 30, 16, 8, 3, 11, 1)      \
+  X(64, 4, 14, 16, 8, 3, 8, 2)       \
+  X(65, 4, 14, 16, 8, 3, 10, 2)
 
 namespace tp {
 constexpr int kDedispParts = 6;  // translation units the kernel instantiations are split over

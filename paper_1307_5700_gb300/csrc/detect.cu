@@ -46,6 +46,20 @@ constexpr int kPer = kDetectT / kThreads;  // 16 samples per thread
 
 __device__ __forceinline__ bool passes(double v, double mu, double thr) { return __dsub_rn(v, mu) >= thr; }
 
+// The smallest int i with passes(i) (INT_MAX when none does): the predicate
+// is monotone in i, so a bisection of the int range finds it in at most 32
+// steps whatever the statistics hold.
+__device__ __forceinline__ int smallest_passing_int(double mu, double thr) {
+  long long lo = INT_MIN, hi = INT_MAX;
+  if (!passes((double)hi, mu, thr)) return INT_MAX;
+  while (lo < hi) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (passes((double)mid, mu, thr)) hi = mid;
+    else lo = mid + 1;
+  }
+  return (int)lo;
+}
+
 // detrended residual y - (mean + beta u), binary64 in the order written
 __device__ __forceinline__ double residual(double v, double mean, double beta, double u) {
   return __dsub_rn(v, __dadd_rn(mean, __dmul_rn(beta, u)));
@@ -290,11 +304,7 @@ __global__ void __launch_bounds__(kThreads) row_stats_kernel(DetectArgs a) {
       for (int it = 0; it < 64 && !passes((double)f, m, thr); ++it) f = nextafterf(f, FLT_MAX);
     }
     a.row_thr_f[d] = f;
-    const double c = ceil(__dadd_rn(m, thr));
-    long long i = c > 2147483647.0 ? 2147483647LL : (c < -2147483648.0 ? -2147483648LL : (long long)c);
-    while (i > INT_MIN && passes((double)(i - 1), m, thr)) --i;
-    while (i < INT_MAX && !passes((double)i, m, thr)) ++i;
-    a.row_thr_i[d] = (int)i;
+    a.row_thr_i[d] = smallest_passing_int(m, thr);
     return;
   }
   if (a.is_int) {
@@ -362,12 +372,7 @@ __global__ void __launch_bounds__(kThreads) row_stats_kernel(DetectArgs a) {
     for (int it = 0; it < 64 && !passes((double)f, m, thr); ++it) f = nextafterf(f, FLT_MAX);
   }
   a.row_thr_f[d] = f;
-  // smallest int i with passes(i)
-  const double c = ceil(__dadd_rn(m, thr));
-  long long i = c > 2147483647.0 ? 2147483647LL : (c < -2147483648.0 ? -2147483648LL : (long long)c);
-  while (i > INT_MIN && passes((double)(i - 1), m, thr)) --i;
-  while (i < INT_MAX && !passes((double)i, m, thr)) ++i;
-  a.row_thr_i[d] = (int)i;
+  a.row_thr_i[d] = smallest_passing_int(m, thr);
 }
 
 // the series the detection reads: the median-filtered one, else D

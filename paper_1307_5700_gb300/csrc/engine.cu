@@ -202,6 +202,9 @@ struct Beam {
   int64_t nout = 0;
   int64_t t0_abs = 0;
   int64_t pushed = 0;
+  int64_t nblocks = 0;    // blocks pushed (running statistics alternate their state buffers)
+  double* run_mu[2] = {nullptr, nullptr};   // running statistics (R15): state after even / odd blocks
+  double* run_var[2] = {nullptr, nullptr};
   BeamState state = kEmpty;
   int ntt = 0;
   bool have_ext = false;
@@ -230,6 +233,7 @@ struct tp_plan {
   tp_rfi_params rfi{};
   double nsigma = 5.0;
   int fit_order = -1;    // fitted bandpass (Sec. 2.2.1): polynomial order, -1 = off
+  double run_alpha = 1.0;  // running statistics (R15): weight of the new block, 1 = per block
   double tau_mask = 5.0; // fitted bandpass: high-power channel masking threshold
   bool cluster = false;  // clustering of the detections (Sec. 2.3)
   tp_cluster_params cparams{};
@@ -259,6 +263,13 @@ struct tp_engine {
   size_t budget = 0, used = 0;
   cudaStream_t stream = nullptr;
   bool profiling = false;
+  // batched dedispersion timing (tp_set_profiling, batches issued outside
+  // graphs): event pairs around the grouped launches, harvested by
+  // tp_get_batch_times
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> bev_pool, bev_pending;
+  double batch_ms = 0.0;
+  int64_t batch_count = 0;
+  long long wait_tries = kDefaultWaitTries;  // see tp_engine_set_wait_limit
   uint64_t launches = 0;
   void* d_batch = nullptr;  // batch arguments for launches outside graphs
   std::vector<unsigned char> h_batch;
@@ -312,7 +323,7 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
 // windows (the order of their launch times on a 1024-channel, 640-trial,
 // 2^17-sample block).
 constexpr int kShapePreference[kNumShapes] = {55, 53, 46, 56, 54, 52, 50, 51, 48, 49, 33, 44, 45,
-                                              57, 58, 47, 34, 42, 31, 30, 32, 35, 39, 43, 41, 40,
+                                              57, 58, 59, 60, 61, 62, 63, 64, 65, 47, 34, 42, 31, 30, 32, 35, 39, 43, 41, 40,
                                               27, 25, 26, 24, 28, 29, 22, 18, 19, 12, 13, 14, 15,
                                               16, 17, 23, 21, 20, 8, 10, 1, 2, 5, 0, 3, 6,
                                               4, 7, 9, 11, 36, 37, 38};
@@ -431,6 +442,10 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   add((void**)&b->fit_masked, nc);
   add((void**)&b->fit_work, nc * 16);
   add((void**)&b->rmse, 8);
+  for (int i = 0; i < 2; ++i) {
+    add((void**)&b->run_mu[i], nc * 8);
+    add((void**)&b->run_var[i], nc * 8);
+  }
   const size_t yb = (size_t)staged_bytes_alloc(p->dtype);
   add((void**)&b->y, nc * (size_t)ypitch * yb);
   add((void**)&b->b16, nc * 2);
@@ -573,6 +588,17 @@ RfiArgs rfi_args(const tp_plan* p, Beam* b) {
   a.fit_masked = b->fit_masked;
   a.fit_work = b->fit_work;
   a.rmse = b->rmse;
+  a.run = p->run_alpha < 1.0 ? 1 : 0;
+  a.run_alpha = p->run_alpha;
+  // block n (1, 2, ...) folds the state of block n - 1 into buffer n % 2, so
+  // that processing the same window again (tp_beam_rewind) repeats the same
+  // update
+  const int cur = (int)(b->nblocks & 1);
+  a.run_first = b->nblocks <= 1 ? 1 : 0;
+  a.run_prev_mu = b->run_mu[cur ^ 1];
+  a.run_prev_var = b->run_var[cur ^ 1];
+  a.run_mu = b->run_mu[cur];
+  a.run_var = b->run_var[cur];
   return a;
 }
 
@@ -596,6 +622,7 @@ DedispArgs dedisp_args(const tp_plan* p, Beam* b) {
   da.dpitch = b->dpitch;
   da.row_part = b->row_part;
   da.status = b->status;
+  da.wait_tries = p->e->wait_tries;
   return da;
 }
 
@@ -792,6 +819,17 @@ int issue_batch(tp_engine* e, BatchPlan& bp, void* d_args, bool detect) {
   const int* dcta = reinterpret_cast<const int*>(static_cast<unsigned char*>(d_args) +
                                                  bp.args.size() * sizeof(DedispArgs));
   int coff = 0;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (e->profiling) {  // never set while a graph is captured
+    if (e->bev_pool.empty()) {
+      TP_CUDA_TRY(cudaEventCreate(&ev.first));
+      TP_CUDA_TRY(cudaEventCreate(&ev.second));
+    } else {
+      ev = e->bev_pool.back();
+      e->bev_pool.pop_back();
+    }
+    TP_CUDA_TRY(cudaEventRecord(ev.first, s));
+  }
   for (auto& g : bp.groups) {
     BatchArgs ba{dargs + g.first, dcta + coff, g.second};
     const int ctas = bp.cta[coff + g.second];
@@ -799,6 +837,10 @@ int issue_batch(tp_engine* e, BatchPlan& bp, void* d_args, bool detect) {
     TP_CUDA_TRY(launch_dedisperse(b0->plan->shape, b0->plan->dtype, ba, ctas, s));
     e->launches += 1;
     coff += g.second + 1;
+  }
+  if (ev.first) {
+    TP_CUDA_TRY(cudaEventRecord(ev.second, s));
+    e->bev_pending.push_back(ev);
   }
   for (size_t i = 0; i < bp.beams.size(); ++i) {
     bp.beams[i]->ntt = bp.args[i].ntt;
@@ -890,6 +932,11 @@ int tp_engine_destroy(tp_engine* e) {
       cudaFree(kv.second.d_args);
     }
     e->graphs.clear();
+    for (auto* v : {&e->bev_pool, &e->bev_pending})
+      for (auto& ev : *v) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+      }
     cudaFree(e->d_batch);
   }
   delete e;
@@ -1274,6 +1321,7 @@ int assemble_window(tp_engine* e, Beam* b, cudaStream_t s, const void* buf, int 
   TP_CUDA_TRY(cudaEventRecord(b->ev_pushed, s));
   prof_record(e, b, 1, s);
   b->pushed += nsamp;
+  b->nblocks += 1;
   b->state = kReady;
   return TP_OK;
 }
@@ -1566,6 +1614,16 @@ int tp_set_profiling(tp_engine* e, int enable) {
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   e->profiling = enable != 0;
+  if (e->profiling) {
+    DeviceGuard g(e->device);
+    for (auto& ev : e->bev_pending) {
+      cudaEventSynchronize(ev.second);
+      e->bev_pool.push_back(ev);
+    }
+    e->bev_pending.clear();
+    e->batch_ms = 0.0;
+    e->batch_count = 0;
+  }
   if (e->profiling)
     for (Beam* b : e->beams)
       if (b) {
@@ -1587,6 +1645,39 @@ int tp_get_stage_times(tp_engine* e, int beam, double* ms, int64_t* count) {
   if (ms)
     for (int i = 0; i < 4; ++i) ms[i] = b->stage_ms[i];
   if (count) *count = b->stage_count;
+  return TP_OK;
+}
+
+int tp_engine_set_wait_limit(tp_engine* e, long long tries) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  e->wait_tries = tries < 0 ? kDefaultWaitTries : tries;
+  // graphs captured earlier hold the old limit in their arguments
+  TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
+  for (auto& kv : e->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaFree(kv.second.d_args);
+  }
+  e->graphs.clear();
+  return TP_OK;
+}
+
+int tp_get_batch_times(tp_engine* e, double* ms, int64_t* count) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  for (auto& ev : e->bev_pending) {
+    TP_CUDA_TRY(cudaEventSynchronize(ev.second));
+    float t = 0.f;
+    TP_CUDA_TRY(cudaEventElapsedTime(&t, ev.first, ev.second));
+    e->batch_ms += t;
+    e->batch_count += 1;
+    e->bev_pool.push_back(ev);
+  }
+  e->bev_pending.clear();
+  if (ms) *ms = e->batch_ms;
+  if (count) *count = e->batch_count;
   return TP_OK;
 }
 
@@ -1666,11 +1757,25 @@ int tp_plan_set_bandpass_fit(tp_plan* p, int order, double tau_mask) {
   if (order >= 0) {
     if (!(tau_mask > 0.0) || !std::isfinite(tau_mask)) return set_error(TP_EINVAL, "tau_mask must be > 0");
     if (p->rfi.stats_mode != TP_STATS_BLOCK) return set_error(TP_EINVAL, "the fit needs block statistics");
+    if (p->run_alpha < 1.0) return set_error(TP_EINVAL, "the fit and running statistics exclude each other");
     if (p->nchan > kMaxFitChannels) return set_error(TP_EINVAL, "the fit takes at most %d channels", kMaxFitChannels);
   }
   if (p->users > 0) return set_error(TP_EBUSY, "plan is used by %d open beams", p->users);
   p->fit_order = order;
   p->tau_mask = tau_mask;
+  return TP_OK;
+}
+
+int tp_plan_set_running_stats(tp_plan* p, double alpha) {
+  if (!p) return set_error(TP_EINVAL, "plan is NULL");
+  std::lock_guard<std::recursive_mutex> lk(p->e->mu);
+  if (!(alpha > 0.0) || !(alpha <= 1.0)) return set_error(TP_EINVAL, "alpha must lie in (0, 1]");
+  if (alpha < 1.0) {
+    if (p->rfi.stats_mode != TP_STATS_BLOCK) return set_error(TP_EINVAL, "running statistics need block statistics");
+    if (p->fit_order >= 0) return set_error(TP_EINVAL, "the fit and running statistics exclude each other");
+  }
+  if (p->users > 0) return set_error(TP_EBUSY, "plan is used by %d open beams", p->users);
+  p->run_alpha = alpha;
   return TP_OK;
 }
 

@@ -306,7 +306,7 @@ def emit_quadp(S, MMAX):
 # (S, MMAX) of the 16-bit float DM-quad shapes: S = 2 mod 4.
 QUADS16 = [(26, 9), (30, 9)]
 # (S, MMAX) of the 8-bit DM-quad shapes: S = 2 mod 4.
-QUADS8 = [(26, 16), (22, 16), (18, 16), (30, 16)]
+QUADS8 = [(26, 16), (22, 16), (18, 16), (30, 16), (14, 16)]
 
 
 def _asm_fn(signature, body, outs, ins):
@@ -389,6 +389,87 @@ def emit_quad8(S, MMAX):
                    f"unsigned (&f)[4][{H + 1}])", body, outs, '"r"(addr), "r"(b)')
 
 
+# (S, MMAX, NCONS, variant) of the 8-bit DM-quad shapes whose stage loop runs
+# inside the assembly (ALGO 9-11: variants 3, 4, 5).
+QUADS8T = [(30, 16, 8, 3), (26, 16, 8, 3), (22, 16, 8, 3), (30, 16, 8, 4), (30, 16, 8, 5), (14, 16, 8, 4)]
+
+
+def emit_quad8t(S, MMAX, NCONS, V=0):
+    """emit_quad8 over every channel of a pipeline stage in one call, with
+    threaded dispatch: the channel's block starts by fetching the next
+    channel's (window offset, block index) pair from the stage's info (NCONS
+    int4 apart per channel), issues every window load, then the adds (in
+    load order, alternately as a 32-bit integer add and as a two-lane 16-bit
+    add so that they spread over two execution pipes; both sum the two
+    16-bit lanes exactly while no lane exceeds 16 bits), and ends with the
+    indexed branch of the next channel instead of a jump back to a loop.
+    Operands: e, f as in emit_quad8; then the lane's shared-memory base, the
+    address of the stage's first info entry for this warp, and the number
+    of channels in the stage (>= 1)."""
+    # variant: 0 threaded, loads first, alternating add forms; 1 threaded,
+    # loads first, 32-bit adds only; 2 threaded, loads and adds interleaved,
+    # 32-bit adds only; 3 a loop around one dispatch, loads first,
+    # alternating add forms; 4 the loop, interleaved, alternating forms; 5 the
+    # loop, interleaved, 32-bit adds only
+    threaded = V in (0, 1, 2)
+    first = V in (0, 1, 3)
+    alt = V in (0, 3, 4)
+    H = S // 2
+    nb = 2 * 8 * (MMAX + 1)
+    nwmax = (1 + 3 * (MMAX + 1) + S + 1) // 2 + 1
+    ne = 4 * H + 4 * (H + 1)
+    sb, inf, nc = ne, ne + 1, ne + 2
+    stride = 16 * NCONS
+    body = ["{", ".reg .pred p;", f".reg .b32 w<{nwmax}>, ci, ip, ix, iy, ad;",
+            "tbl: .branchtargets " + ", ".join(f"C{b}" for b in range(nb)) + ";",
+            f"mov.u32 ip, %{inf};",
+            "ld.shared.v2.u32 {ix, iy}, [ip];",
+            "mov.u32 ci, 1;",
+            f"add.u32 ad, %{sb}, ix;"]
+    if threaded:
+        body.append("brx.idx.uni iy, tbl;")
+    else:
+        body += ["LOOP:", "setp.lt.u32 p, ci, %{};".format(nc), "brx.idx.uni iy, tbl;"]
+    for b in range(nb):
+        r, mb = b // (8 * (MMAX + 1)), b % (8 * (MMAX + 1))
+        p = [r + o for o in quad_steps(mb)]
+        uses = {}
+        for j in range(4):
+            if p[j] % 2 == 0:
+                for i in range(H):
+                    uses.setdefault(p[j] // 2 + i, []).append(j * H + i)
+            else:
+                for i in range(H + 1):
+                    uses.setdefault((p[j] - 1) // 2 + i, []).append(4 * H + j * (H + 1) + i)
+        body.append(f"C{b}:")
+        if threaded:
+            body.append(f"setp.lt.u32 p, ci, %{nc};")
+        body.append(f"@p add.u32 ip, ip, {stride};")
+        body.append("ld.shared.v2.u32 {ix, iy}, [ip];")
+        nw = max(uses) + 1
+        n = 0
+        if first:
+            for k in range(nw):
+                body.append(f"ld.shared.b32 w{k}, [ad+{4 * k}];")
+        for k in range(nw):
+            if not first:
+                body.append(f"ld.shared.b32 w{k}, [ad+{4 * k}];")
+            for op_ in uses.get(k, []):
+                form = "add.u16x2" if alt and n % 2 else "add.u32"
+                body.append(f"{form} %{op_}, %{op_}, w{k};")
+                n += 1
+        body.append("@!p bra.uni CEND;")
+        body.append("add.u32 ci, ci, 1;")
+        body.append(f"add.u32 ad, %{sb}, ix;")
+        body.append("brx.idx.uni iy, tbl;" if threaded else "bra.uni LOOP;")
+    body += ["CEND:", "}"]
+    outs = ", ".join([f'"+r"(e[{j}][{i}])' for j in range(4) for i in range(H)] +
+                     [f'"+r"(f[{j}][{i}])' for j in range(4) for i in range(H + 1)])
+    return _asm_fn(f"void add_quad8t<{S}, {MMAX}, {NCONS}, {V}>(unsigned sbase, unsigned info, int nc, "
+                   f"unsigned (&e)[4][{H}], unsigned (&f)[4][{H + 1}])", body, outs,
+                   '"r"(sbase), "r"(info), "r"(nc)')
+
+
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
     out = [
@@ -435,6 +516,12 @@ def main():
         "__device__ __forceinline__ void add_quad8(int b, unsigned addr, unsigned (&e)[4][S / 2],",
         "                                          unsigned (&f)[4][S / 2 + 1]);",
         "",
+        "// every channel of a stage (emit_quad8t): threaded dispatch over the",
+        "// stage's info entries",
+        "template <int S, int MMAX, int NCONS, int V>",
+        "__device__ __forceinline__ void add_quad8t(unsigned sbase, unsigned info, int nc,",
+        "                                           unsigned (&e)[4][S / 2], unsigned (&f)[4][S / 2 + 1]);",
+        "",
         "// the same for 16-bit samples (kind 0 = binary16, 1 = bfloat16), block",
         "// index = first trial's half-word offset r * (OMAX + 1) + d",
         "template <int S, int OMAX, int KIND>",
@@ -466,6 +553,8 @@ def main():
             out.append(emit_quad16(S, MMAX, kind))
     for S, MMAX in QUADS8:
         out.append(emit_quad8(S, MMAX))
+    for S, MMAX, NCONS, V in QUADS8T:
+        out.append(emit_quad8t(S, MMAX, NCONS, V))
     out.append("}  // namespace tp")
     with open(os.path.join(here, "dispatch_gen.cuh"), "w") as f:
         f.write("\n".join(out) + "\n")

@@ -308,11 +308,13 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
     }
     s_m = m;
     s_sig = sig;
-    if (a.fit) a.pivot[c] = p;
+    if (a.fit || a.run) a.pivot[c] = p;
   }
   __syncthreads();
-  // with the fitted bandpass the chunk test waits for the fit (fit_chunk_test)
-  if (!a.enable_channel || a.fit) return;
+  // with the fitted bandpass the chunk test waits for the fit
+  // (fit_chunk_test), with running statistics for their update
+  // (running_chunk_test)
+  if (!a.enable_channel || a.fit || a.run) return;
   const double m = s_m, tsig = a.tau_c * s_sig;
   for (int k = threadIdx.x; k < a.nchunk; k += kThreads) {
     const int64_t lo = (int64_t)k * a.W;
@@ -379,7 +381,7 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_u8(RfiArgs a, longlong2*
     }
   }
   __syncthreads();
-  if (!a.enable_channel || a.fit) return;
+  if (!a.enable_channel || a.fit || a.run) return;
   const long long N = a.nsamp, S = s_S, V = s_V, b = s_b;
   const bool ext = a.stats_mode == TP_STATS_EXTERNAL;
   const double tsig = ext ? __dmul_rn(a.tau_c, a.sigma[c]) : 0.0;
@@ -426,37 +428,35 @@ __global__ void __launch_bounds__(kThreads) dilate_kernel(RfiArgs a) {
 }
 
 // Spectrum thresholds, one per chunk k (reading R6): tau_s times the square
-// root of the sum of the spreads of the channels whose chunk k is not flagged
-// (binary64 sigma_c^2; 8-bit block statistics: the exact integer sum of V_c,
-// kept as (V >> 20, V & (2^20 - 1))).  One warp per chunk; lane l sums the
-// channels l, l + 32, ... and the warp folds the 32 partial sums in a fixed
-// order.  CTA 0 also sums the bandpass values (16-bit and 8-bit staging
-// subtract that sum once).
+// root of the sum of the spreads of the channels whose chunk k is not flagged.
+// Every CTA sums the spreads of all channels (binary64 sigma_c^2 in a fixed
+// tree order; 8-bit block statistics: the exact integers V_c, kept as
+// (V >> 20, V & (2^20 - 1))), then one warp per chunk subtracts the sum over
+// the few channels flagged in it.  CTA 0 also sums the bandpass values
+// (16-bit and 8-bit staging subtract that sum once).
 __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a) {
+  __shared__ double s_d[kThreads];
+  __shared__ unsigned long long s_hi[kThreads], s_lo[kThreads];
+  // exact integer spreads: 8-bit data with the block's own statistics
+  const bool exact = a.dtype == TP_U8 && !a.fit && !a.run && a.stats_mode != TP_STATS_EXTERNAL;
   if (blockIdx.x == 0) {
-    __shared__ double s_b[kThreads];
     if (threadIdx.x == 0) *a.spec_nflag = 0;
     double bs = 0.0;
     if (a.dtype == TP_U8 || a.dtype == TP_F16 || a.dtype == TP_BF16)
       for (int c = threadIdx.x; c < a.nchan; c += kThreads)
         bs += a.dtype == TP_U8 ? (double)a.bint[c] : storage_value(a.dtype, a.b16[c]);
-    s_b[threadIdx.x] = bs;
+    s_d[threadIdx.x] = bs;
     __syncthreads();
     for (int o = kThreads / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) s_b[threadIdx.x] += s_b[threadIdx.x + o];
+      if (threadIdx.x < o) s_d[threadIdx.x] += s_d[threadIdx.x + o];
       __syncthreads();
     }
-    if (threadIdx.x == 0) *a.bsum = s_b[0];
+    if (threadIdx.x == 0) *a.bsum = s_d[0];
+    __syncthreads();
   }
-  const int k = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (k >= a.nchunk) return;
-  // exact integer spreads: 8-bit data with the block's own statistics
-  const bool exact = a.dtype == TP_U8 && !a.fit && a.stats_mode != TP_STATS_EXTERNAL;
   double v = 0.0;
   unsigned long long hi = 0, lo = 0;
-  for (int c = lane; c < a.nchan; c += 32) {
-    if (a.chan_nflag[c] != 0 && a.chunk_flag[(int64_t)c * a.nchunk + k]) continue;
+  for (int c = threadIdx.x; c < a.nchan; c += kThreads) {
     if (exact) {
       const unsigned long long V = (unsigned long long)a.V[c];
       hi += V >> 20;
@@ -465,14 +465,48 @@ __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a)
       v = __dadd_rn(v, __dmul_rn(a.sigma[c], a.sigma[c]));
     }
   }
+  s_d[threadIdx.x] = v;
+  s_hi[threadIdx.x] = hi;
+  s_lo[threadIdx.x] = lo;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_d[threadIdx.x] = __dadd_rn(s_d[threadIdx.x], s_d[threadIdx.x + o]);
+      s_hi[threadIdx.x] += s_hi[threadIdx.x + o];
+      s_lo[threadIdx.x] += s_lo[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const int k = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= a.nchunk) return;
+  double fv = 0.0;
+  unsigned long long fhi = 0, flo = 0;
+  for (int c = lane; c < a.nchan; c += 32) {
+    if (a.chan_nflag[c] == 0 || !a.chunk_flag[(int64_t)c * a.nchunk + k]) continue;
+    if (exact) {
+      const unsigned long long V = (unsigned long long)a.V[c];
+      fhi += V >> 20;
+      flo += V & 0xFFFFFull;
+    } else {
+      fv = __dadd_rn(fv, __dmul_rn(a.sigma[c], a.sigma[c]));
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
-    hi += __shfl_xor_sync(0xffffffffu, hi, o);
-    lo += __shfl_xor_sync(0xffffffffu, lo, o);
+    fv = __dadd_rn(fv, __shfl_xor_sync(0xffffffffu, fv, o));
+    fhi += __shfl_xor_sync(0xffffffffu, fhi, o);
+    flo += __shfl_xor_sync(0xffffffffu, flo, o);
   }
   if (lane == 0) {
-    const double tot = exact ? __dadd_rn(__dmul_rn((double)hi, 1048576.0), (double)lo) : v;
+    double tot;
+    if (exact) {
+      // the unflagged channels' sum, exactly: the flagged parts are sub-sums
+      tot = __dadd_rn(__dmul_rn((double)(s_hi[0] - fhi), 1048576.0), (double)(s_lo[0] - flo));
+    } else {
+      tot = __dadd_rn(s_d[0], -fv);
+      tot = tot > 0.0 ? tot : 0.0;
+    }
     a.spec_thr[k] = __dmul_rn(a.tau_s, __dsqrt_rn(tot));
   }
 }
@@ -576,7 +610,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
       for (int r = 0; r < 4; ++r) s_f[g][4 * q + r] = acc[r] + (double)part[r];
     } else {
       // external or fitted bandpass: sums of x - b_c (integer b_c)
-      const bool ext = a.stats_mode == TP_STATS_EXTERNAL || a.fit;
+      const bool ext = a.stats_mode == TP_STATS_EXTERNAL || a.fit || a.run;
       int sx[4] = {0, 0, 0, 0};
       long long sS[4] = {0, 0, 0, 0};
       for (int c = g; c < a.nchan; c += 32) {
@@ -981,6 +1015,59 @@ __global__ void __launch_bounds__(kThreads) fit_chunk_test_kernel(RfiArgs a, con
   }
 }
 
+// Running statistics (reading R15), one thread per channel: the block's own
+// mean and variance folded into the previous state with weight alpha,
+//   mu_run = alpha mu + (1 - alpha) mu_prev, var_run = alpha sigma^2 + (1 - alpha) var_prev
+// (binary64, in this order; the stream's first block starts the state), and
+// the block's statistics replaced by the running ones in every form the later
+// stages read (mu, sigma, the split FP32 mean, the integer and 16-bit
+// bandpass values).
+__global__ void __launch_bounds__(kThreads) running_update_kernel(RfiArgs a) {
+  const int c = blockIdx.x * kThreads + threadIdx.x;
+  if (c >= a.nchan) return;
+  double mu = a.mu[c];
+  double var = __dmul_rn(a.sigma[c], a.sigma[c]);
+  if (!a.run_first) {
+    const double w = __dsub_rn(1.0, a.run_alpha);
+    mu = __dadd_rn(__dmul_rn(a.run_alpha, mu), __dmul_rn(w, a.run_prev_mu[c]));
+    var = __dadd_rn(__dmul_rn(a.run_alpha, var), __dmul_rn(w, a.run_prev_var[c]));
+  }
+  a.run_mu[c] = mu;
+  a.run_var[c] = var;
+  a.mu[c] = mu;
+  a.sigma[c] = __dsqrt_rn(var);
+  const float hi = (float)mu;
+  a.mu_hi[c] = hi;
+  a.mu_lo[c] = (float)(mu - (double)hi);
+  a.bint[c] = (int)floor(__dadd_rn(mu, 0.5));
+  if (a.dtype == TP_F16 || a.dtype == TP_BF16) a.b16[c] = storage_bits(a.dtype, mu);
+}
+
+// Channel test with running statistics (R5 with the running mean and spread):
+// chunk k of channel c exceeds when sum(x - mu_run) > tau_c sigma_run
+// sqrt(n_k); float chunk sums are relative to the channel's pivot, 8-bit ones
+// exact integers (there the bandpass value floor(mu_run + 1/2) is subtracted,
+// as for external statistics).
+__global__ void __launch_bounds__(kThreads) running_chunk_test_kernel(RfiArgs a, const void* chunk_sums) {
+  const int c = blockIdx.x;
+  const double tsig = __dmul_rn(a.tau_c, a.sigma[c]);
+  const bool single = a.W <= 256;
+  for (int k = threadIdx.x; k < a.nchunk; k += kThreads) {
+    const int64_t lo = (int64_t)k * a.W;
+    const int64_t n = (lo + a.W < a.nsamp ? lo + a.W : a.nsamp) - lo;
+    const int64_t idx = (int64_t)c * a.nchunk + k;
+    double ex;
+    if (a.dtype == TP_U8) {
+      ex = (double)(static_cast<const longlong2*>(chunk_sums)[idx].x - n * (long long)a.bint[c]);
+    } else {
+      const double cs = single ? (double)static_cast<const float2*>(chunk_sums)[idx].x
+                               : static_cast<const double2*>(chunk_sums)[idx].x;
+      ex = __dsub_rn(cs, __dmul_rn((double)n, __dsub_rn(a.mu[c], (double)a.pivot[c])));
+    }
+    a.chunk_raw[idx] = (uint8_t)(ex > __dmul_rn(tsig, __dsqrt_rn((double)n)));
+  }
+}
+
 // Pitched row copy in 16-byte units: CTA (x, y) copies kThreads kCopyUnroll
 // consecutive units of rows y, y + gridDim.y, ...; all loads of a thread are
 // issued before its stores.
@@ -1051,6 +1138,16 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypit
     if (e != cudaSuccess) return e;
     if (a.enable_channel) {
       fit_chunk_test_kernel<<<a.nchan, kThreads, 0, s>>>(a, chunk_sums);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (a.run) {
+    running_update_kernel<<<(a.nchan + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.enable_channel) {
+      running_chunk_test_kernel<<<a.nchan, kThreads, 0, s>>>(a, chunk_sums);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }

@@ -61,6 +61,18 @@ struct RfiArgs {
   uint8_t* fit_masked;    // [nchan] channels masked before the fit
   double* fit_work;       // [2 nchan] local excess e_c, interpolated bandpass
   double* rmse;           // [1] RMSE of the fit
+  // running statistics across blocks (reading R15): run = 1 turns them on;
+  // the block's statistics are folded into the previous state (run_prev_*,
+  // ignored for the stream's first block) with weight run_alpha, the new
+  // state goes to run_mu / run_var, and the block is then thresholded and
+  // corrected with the running values
+  int run;
+  int run_first;
+  double run_alpha;
+  const double* run_prev_mu;  // [nchan]
+  const double* run_prev_var; // [nchan]
+  double* run_mu;             // [nchan]
+  double* run_var;            // [nchan]
 };
 
 // Largest polynomial order and channel count of the fitted bandpass.
@@ -92,7 +104,13 @@ struct DedispArgs {
   int64_t dpitch;
   void* row_part;         // [ndm][ntt] (float: double2 {sum, sumsq}; int: longlong2)
   int* status;            // device status word (TP_ETIMEOUT on a wait that gave up)
+  long long wait_tries;   // attempts of a wait for staged data or a free stage buffer
 };
+
+// Default number of attempts of the dedispersion kernel's waits for staged
+// data or a free stage buffer (each attempt is one mbarrier try_wait); the
+// wait for the CTA's own copies in flight before it leaves always uses this.
+constexpr long long kDefaultWaitTries = 1LL << 24;
 
 // One launch of the dedispersion kernel covers several beams (same kernel
 // shape and sample format): CTA i works for the beam b with
@@ -119,7 +137,7 @@ struct KernelShape {
               // 5: DM quads with a lane's outputs s and s + S / 2 paired;
               // 6, 7, 8: 4, 5, 3 without a producer warp (consumers issue the copies)
 };
-constexpr int kNumShapes = 59;
+constexpr int kNumShapes = 66;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 

@@ -158,3 +158,50 @@ def single_block_workload(arrival_fn, seed=1000, nchan=1024, nsamp=32768, t0=120
     if spikes:
         add_broadband(x, spikes, spike_level)
     return x
+
+
+# ---- device-side generation for large workloads ---------------------------------------
+# Blocks of the wide-band and batched benchmark workloads are generated on the
+# GPU with torch (noise from a seeded torch generator, pulses at caller-given
+# per-channel arrivals, narrowband bursts) so that a 4096 x 2^18 block takes
+# milliseconds instead of the host's tens of seconds.  No step of the method
+# is computed here.
+
+def torch_block(nchan, nsamp, seed, arrivals=(), rfi_channels=(), rfi_level=6.0, device="cuda",
+                fmt="f32", u8_mean=128.0, u8_std=16.0):
+    """One (nchan, nsamp) block on ``device``: N(0, 1) noise; for each
+    (arrival[c], fwhm_samples, amplitude) in ``arrivals`` a Gaussian pulse
+    centred at arrival[c] in channel c; for each channel in ``rfi_channels``
+    a burst of +rfi_level over a random span of 10-50 % of the block.  The
+    result in the storage format ``fmt``: "f32", "f16", "bf16" (int16 bit
+    patterns, round to nearest even) or "u8" (round(x * u8_std + u8_mean)
+    clipped to [0, 255])."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    x = torch.randn((nchan, nsamp), generator=g, device=device, dtype=torch.float32)
+    for arr, fwhm, amp in arrivals:
+        s = fwhm / (2.0 * np.sqrt(2.0 * np.log(2.0)))
+        half = int(np.ceil(6 * s)) + 1
+        a = torch.as_tensor(np.asarray(arr, np.float64), device=device)
+        base = torch.floor(a).to(torch.int64)
+        k = torch.arange(-half, half + 2, device=device, dtype=torch.int64)
+        t = base[:, None] + k[None, :]
+        ok = (t >= 0) & (t < nsamp)
+        prof = (amp * torch.exp(-0.5 * ((t.to(torch.float64) - a[:, None]) / s) ** 2)).to(torch.float32)
+        rows = torch.arange(nchan, device=device)[:, None].expand_as(t)
+        x.index_put_((rows[ok], t[ok]), prof[ok], accumulate=True)
+    h = rng(int(seed) + 1)
+    for c in rfi_channels:
+        d = int(h.integers(nsamp // 10, nsamp // 2 + 1))
+        t0 = int(h.integers(0, nsamp - d + 1))
+        x[int(c), t0:t0 + d] += float(rfi_level)
+    if fmt == "f32":
+        return x
+    if fmt == "f16":
+        return x.to(torch.float16)
+    if fmt == "bf16":
+        return x.to(torch.bfloat16).view(torch.int16)
+    if fmt == "u8":
+        return torch.clamp(torch.round(x * u8_std + u8_mean), 0, 255).to(torch.uint8)
+    raise ValueError(fmt)

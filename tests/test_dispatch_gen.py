@@ -220,3 +220,94 @@ def test_quad_steps_cover_every_pattern():
             assert o[0] == 0
             pats.add(tuple(o[j + 1] - o[j] for j in range(3)))
         assert pats == set(product((m, m + 1), repeat=3))
+
+
+def _loop_blocks(text):
+    """(prologue, {block index: [instruction, ...]}) of a function whose
+    stage loop runs inside the assembly."""
+    pro, out, cur = [], {}, None
+    for raw in text.splitlines():
+        m = re.match(r'\s*"(.*)\\n"\s*$', raw)
+        if not m:
+            continue
+        ins = m.group(1).strip()
+        lab = re.fullmatch(r"C(\d+):", ins)
+        if lab:
+            cur = int(lab.group(1))
+            out[cur] = []
+        elif ins == "CEND:":
+            cur = None
+        elif cur is not None:
+            out[cur].append(ins)
+        elif not ins.startswith((".reg", "tbl:", "{", "}")):
+            pro.append(ins)
+    return pro, out
+
+
+@pytest.mark.parametrize("S,MMAX,NCONS,V", G.QUADS8T)
+def test_quads_8bit_stage_loop(S, MMAX, NCONS, V):
+    """Every block of the 8-bit quads with the stage loop inside the assembly
+    adds the right words into the right accumulators (as emit_quad8's
+    blocks), in the load order and add forms of its variant, and the loop
+    visits the stage's channels in order, each once, for 1 to 4 channels."""
+    first, alt = V == 3, V in (3, 4)
+    H = S // 2
+    ne = 4 * H + 4 * (H + 1)
+    nb_m = 8 * (MMAX + 1)
+    pro, blocks = _loop_blocks(G.emit_quad8t(S, MMAX, NCONS, V))
+    assert pro == [f"mov.u32 ip, %{ne + 1};", "ld.shared.v2.u32 {ix, iy}, [ip];", "mov.u32 ci, 1;",
+                   f"add.u32 ad, %{ne}, ix;", "LOOP:", f"setp.lt.u32 p, ci, %{ne + 2};", "brx.idx.uni iy, tbl;"]
+    assert len(blocks) == 2 * nb_m
+    for b, body in blocks.items():
+        r0, mb = b // nb_m, b % nb_m
+        p = [r0 + o for o in G.quad_steps(mb)]
+        # the next channel's info first, the jump back to the loop last
+        assert body[:2] == [f"@p add.u32 ip, ip, {16 * NCONS};", "ld.shared.v2.u32 {ix, iy}, [ip];"]
+        assert body[-4:] == ["@!p bra.uni CEND;", "add.u32 ci, ci, 1;", f"add.u32 ad, %{ne}, ix;",
+                             "bra.uni LOOP;"]
+        word, acc, forms, seen_add = {}, defaultdict(list), defaultdict(int), False
+        for ins in body[2:-4]:
+            m = re.fullmatch(r"ld\.shared\.b32 (\w+), \[ad\+(\d+)\];", ins)
+            if m:
+                assert not (first and seen_add), "a load after the adds"
+                word[m.group(1)] = int(m.group(2)) // 4
+                continue
+            m = re.fullmatch(r"(add\.u32|add\.u16x2) %(\d+), %\2, (\w+);", ins)
+            assert m, ins
+            seen_add = True
+            forms[m.group(1)] += 1
+            acc[int(m.group(2))].append(word[m.group(3)])
+        if alt:
+            assert abs(forms["add.u32"] - forms["add.u16x2"]) <= 1
+        else:
+            assert forms["add.u16x2"] == 0
+        for j in range(4):
+            if p[j] % 2 == 0:
+                for i in range(H):
+                    assert acc[j * H + i] == [p[j] // 2 + i], (b, j, i)
+                assert all(not acc[4 * H + j * (H + 1) + i] for i in range(H + 1))
+            else:
+                for i in range(H + 1):
+                    assert acc[4 * H + j * (H + 1) + i] == [(p[j] - 1) // 2 + i], (b, j, i)
+                assert all(not acc[j * H + i] for i in range(H))
+    # control flow, step by step as the prologue, LOOP and the block ends say
+    g = __import__("numpy").random.default_rng(S + V)
+    for nc in range(1, 5):
+        base, sb = 4096, 100000
+        info = {base + k * 16 * NCONS: (int(g.integers(0, 1 << 16)), int(g.integers(0, 2 * nb_m)))
+                for k in range(4)}
+        ip = base
+        ix, iy = info[ip]
+        ci, ad, visits = 1, sb + ix, []
+        for _ in range(8):
+            pred = ci < nc            # LOOP: setp
+            visits.append((iy, ad))  # brx to block iy, which reads from ad
+            if pred:
+                ip += 16 * NCONS
+            ix, iy = info[ip]
+            if not pred:
+                break
+            ci += 1
+            ad = sb + ix
+        want = [(info[base + k * 16 * NCONS][1], sb + info[base + k * 16 * NCONS][0]) for k in range(nc)]
+        assert visits == want, (nc, visits, want)

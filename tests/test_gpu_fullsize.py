@@ -2,9 +2,11 @@
 1024-channel / 640-DM / 2^17-sample FP32 stream (second block, with the
 overlap tail carried on the device) under every kernel shape the plan admits,
 and the 4096-channel / 2048-DM / 2^18-sample 8-bit wide-band block.  The
-oracle computes the statistics and masks of the whole window and D at
-sampled points one by one; series statistics and candidates are checked
-through properties that hold at any size."""
+oracle computes the statistics and masks of the whole window, D at sampled
+points one by one, and complete D rows (with their detections) for 18 DM
+trials spread over the range, first and last included; series statistics
+and the full candidate list are also checked through properties that hold
+at any size."""
 import os
 
 import numpy as np
@@ -42,6 +44,53 @@ def _check_candidates(D, cands, n_total, row_mu, row_sigma, nsigma, t0):
     assert np.all(Dd[d, t] >= thr[d] - 1e-9 * np.abs(thr[d]))
 
 
+def _oracle_rows(window, dtype, st, cf, sf, W, od, sel, T):
+    """Complete oracle rows D[sel[i]][0..T) (binary64 or exact integers), the
+    magnitude sum_c |y| of every element (float data), and the oracle's
+    candidates of those rows (Sec. 2.3 on each row's own statistics)."""
+    D = O.dedisperse(window, dtype, st, cf, sf, W, od[sel], T)
+    mass = None
+    if dtype != "u8":
+        ya = np.abs(O.corrected(window, dtype, st, cf, sf, W))
+        mass = np.zeros((len(sel), T))
+        for i, d in enumerate(sel):
+            for c in range(window.shape[0]):
+                o = int(od[d, c])
+                mass[i] += ya[c, o:o + T]
+    ss = O.series_stats(D)
+    cands, _ = O.candidates(D, ss["mu"], ss["sigma"], 5.0)
+    return D, mass, ss, cands
+
+
+def _check_rows(Dg, sel, Do, mass, ss, ocands, gcands, t0, exact):
+    """The GPU's rows equal the oracle's (bit-exact for integers, within
+    TOL * sum|y| for floats) and so do its detections in those rows (floats:
+    outside the band where the oracle's statistic lies within the series and
+    statistics bounds of its threshold)."""
+    got = Dg[sel].astype(np.float64 if not exact else np.int64)
+    if exact:
+        assert np.array_equal(got, Do.astype(np.int64))
+    else:
+        err = np.abs(got - Do)
+        assert np.all(err <= TOL * mass), float((err / mass).max())
+    want = {(int(sel[c["dm_idx"]]), int(c["t_abs"])) for c in ocands}
+    rows = set(int(d) for d in sel)
+    have = {(int(c["dm_idx"]), int(c["t_abs"]) - t0) for c in gcands if int(c["dm_idx"]) in rows}
+    diff = want ^ have
+    if exact:
+        assert not diff, sorted(diff)[:5]
+        return
+    pos = {int(d): i for i, d in enumerate(sel)}
+    for d, t in diff:
+        i = pos[d]
+        thr = ss["mu"][i] + 5.0 * ss["sigma"][i]
+        band = TOL * mass[i, t] + 1e-5 * ss["sigma"][i]
+        assert abs(Do[i, t] - thr) <= band, (d, t, Do[i, t], thr, band)
+
+
+ROW_SEL_640 = np.unique(np.concatenate([np.linspace(0, 639, 16).astype(int), [1, 638]]))
+
+
 def test_stream1024_640dm_f32_fullsize_all_shapes():
     tp.build()
     O.set_threads(os.cpu_count() or 1)
@@ -66,6 +115,9 @@ def test_stream1024_640dm_f32_fullsize_all_shapes():
     assert cf.any()
     dd, tt = _sample_points(len(dms), B, 3000, 5)
     want, mass = O.dedisperse_points(window, "f32", st, cf, sf, rfi.chunk_width, od, dd, tt)
+    sel = ROW_SEL_640
+    Drow, mrow, ssrow, crow = _oracle_rows(window, "f32", st, cf, sf, rfi.chunk_width, od, sel, B)
+    assert len(crow) > 0
 
     e = tp.tp_engine_create(0)
     try:
@@ -100,6 +152,7 @@ def test_stream1024_640dm_f32_fullsize_all_shapes():
             np.testing.assert_allclose(mu, Dd.mean(axis=1), rtol=0, atol=1e-6 * np.abs(Dd).mean())
             np.testing.assert_allclose(sigma, Dd.std(axis=1), rtol=1e-5)
             _check_candidates(D, cands, n, mu, sigma, 5.0, info["t0_abs"])
+            _check_rows(D, sel, Drow, mrow, ssrow, crow, cands, info["t0_abs"], exact=False)
         tp.tp_plan_set_shape(p, int(best))
         tp.tp_beam_close(e, b)
         tp.tp_plan_destroy(p)
@@ -130,6 +183,8 @@ def test_wideband_4096ch_2048dm_u8_fullsize():
     sf = O.spectrum_mask(x, "u8", st, rfi, cf)
     dd, tt = _sample_points(len(dms), B, 3000, 6)
     want, _ = O.dedisperse_points(x, "u8", st, cf, sf, rfi.chunk_width, od, dd, tt)
+    sel = np.unique(np.concatenate([np.linspace(0, 2047, 16).astype(int), [1, 2046]]))
+    Drow, _, ssrow, crow = _oracle_rows(x, "u8", st, cf, sf, rfi.chunk_width, od, sel, B)
     e = tp.tp_engine_create(0)
     try:
         p = tp.tp_create_plan(e, nchan, f_lo, bw, ts, dms, "u8", tp.tp_rfi_defaults(), 5.0)
@@ -154,6 +209,7 @@ def test_wideband_4096ch_2048dm_u8_fullsize():
         assert np.array_equal(mu, m)                                    # exact integer sums
         assert np.array_equal(sigma, np.sqrt(np.maximum(s2 / T - m * m, 0.0)))
         _check_candidates(D, cands, n, mu, sigma, 5.0, 0)
+        _check_rows(D, sel, Drow, None, ssrow, crow, cands, 0, exact=True)
         tp.tp_beam_close(e, b)
         tp.tp_plan_destroy(p)
     finally:

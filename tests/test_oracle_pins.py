@@ -366,3 +366,44 @@ def test_storage_bandpass_matches_library_conversions():
     ref = torch.tensor(mu, dtype=torch.float64).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(bbf, ref)
     assert np.array_equal(O.storage_bandpass("f32", mu), mu)
+
+
+# ---- running bandpass statistics (reading R15) -------------------------------------
+
+def test_running_stats_alpha_one_is_per_block_and_closed_form():
+    """alpha = 1 gives each block's own statistics; otherwise the running mean
+    and variance after k blocks equal the closed form of the exponential
+    average, sum_i w_i m_i with w_1 = (1 - alpha)^(k - 1) and
+    w_i = alpha (1 - alpha)^(k - i) for i > 1 (weights summing to 1)."""
+    blocks = [synth.noise(8, 512, 40 + k, mean=1.0 + k, std=1.0 + 0.5 * k) for k in range(4)]
+    st = None
+    for x in blocks:
+        st, s = O.running_stats(st, x, "f32", 1.0)
+        b = O.bandpass(x, "f32")
+        assert np.array_equal(s["mu"], b["mu"]) and np.allclose(s["sigma"], b["sigma"], rtol=1e-15)
+        assert s["external"]
+    a = 0.3
+    st = None
+    for k, x in enumerate(blocks, 1):
+        st, s = O.running_stats(st, x, "f32", a)
+        w = [(1 - a) ** (k - 1)] + [a * (1 - a) ** (k - i) for i in range(2, k + 1)]
+        assert abs(sum(w) - 1.0) < 1e-12
+        mus = [O.bandpass(blocks[i], "f32")["mu"] for i in range(k)]
+        vs = [O.bandpass(blocks[i], "f32")["sigma"] ** 2 for i in range(k)]
+        np.testing.assert_allclose(s["mu"], sum(wi * m for wi, m in zip(w, mus)), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(s["sigma"] ** 2, sum(wi * v for wi, v in zip(w, vs)), rtol=1e-12)
+
+
+def test_running_stats_u8_hand_values():
+    """Two 8-bit blocks of constant channels 10 and 20 (variance 0, then a
+    channel alternating 18/22: variance 4): with alpha = 1/2 the running mean
+    is 15, the running variance 2, the integer bandpass floor(15 + 1/2) = 15."""
+    x1 = np.full((2, 8), 10, np.uint8)
+    x2 = np.full((2, 8), 20, np.uint8)
+    x2[1, 0::2], x2[1, 1::2] = 18, 22
+    st, s1 = O.running_stats(None, x1, "u8", 0.5)
+    assert np.array_equal(s1["mu"], [10.0, 10.0]) and np.array_equal(s1["sigma"], [0.0, 0.0])
+    st, s2 = O.running_stats(st, x2, "u8", 0.5)
+    assert np.array_equal(s2["mu"], [15.0, 15.0])
+    assert np.array_equal(st[1], [0.0, 2.0]) and np.array_equal(s2["sigma"], np.sqrt([0.0, 2.0]))
+    assert np.array_equal(s2["b"], [15, 15])
