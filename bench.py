@@ -811,7 +811,8 @@ def main():
                          "uneven beams batched; wide16: 16 wide-band 8-bit beams; serve32: the serving loop")
     ap.add_argument("--per-beam", action="store_true",
                     help="batch8: per-beam dedisperse/detect calls instead of the batched launch")
-    ap.add_argument("--speedup", type=float, default=50.0, help="serve32: arrival time compression")
+    ap.add_argument("--speedup", type=float, default=20.0,
+                    help="serve32: arrival time compression (20: about two thirds of the GPU's capacity)")
     ap.add_argument("--blocks-per-stream", type=int, default=4, help="serve32: blocks per stream")
     ap.add_argument("--hbm-gb", type=float, default=48.0, help="serve32: engine HBM budget")
     ap.add_argument("--shape", type=int, default=None,

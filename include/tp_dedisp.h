@@ -460,6 +460,15 @@ int tp_get_batch_times(tp_engine *e, double *ms, int64_t *count);
  * dropped).  Errors: TP_EINVAL for a NULL engine. */
 int tp_engine_set_wait_limit(tp_engine *e, long long tries);
 
+/* Grid of the batched dedispersion launch (tp_run_ready, tp_dedisperse with
+ * beam = -1, tp_autotune_batch).  The kernel drains its work items (every
+ * (DM tile, time tile) of every beam of a kernel-shape group) in a loop:
+ * ctas = 0 (the default) launches a persistent grid of as many CTAs as are
+ * resident on the device at once; ctas > 0 at most that many CTAs (tests use a
+ * small grid so that every CTA takes many items); ctas < 0 one CTA per item.
+ * Results do not depend on it.  Cached batch graphs are dropped. */
+int tp_engine_set_batch_grid(tp_engine *e, int ctas);
+
 /* Kernels launched by the engine since it was created. */
 int tp_engine_launches(const tp_engine *e, uint64_t *n);
 

@@ -52,7 +52,7 @@ EXPORTS = (
     "tp_beam_rewind", "tp_autotune_batch", "tp_plan_set_postprocess", "tp_get_processed_series",
     "tp_get_detrend", "tp_plan_set_bandpass_fit", "tp_get_bandpass_fit", "tp_plan_set_clustering",
     "tp_get_clusters", "tp_get_candidate_labels", "tp_prefetch_block", "tp_push_prefetched",
-    "tp_get_batch_times", "tp_engine_set_wait_limit", "tp_plan_set_running_stats",
+    "tp_get_batch_times", "tp_engine_set_wait_limit", "tp_plan_set_running_stats", "tp_engine_set_batch_grid",
 )
 
 
@@ -126,6 +126,7 @@ _SIGS = {
     "tp_get_batch_times": (_i, [_vp, _vp, _vp]),
     "tp_engine_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
     "tp_plan_set_running_stats": (_i, [_vp, _d]),
+    "tp_engine_set_batch_grid": (_i, [_vp, _i]),
     "tp_engine_launches": (_i, [_vp, _vp]),
     "tp_plan_shapes": (_i, [_vp, _vp, _vp, _i]),
     "tp_plan_set_shape": (_i, [_vp, _i]),
@@ -410,6 +411,12 @@ def tp_plan_set_running_stats(p, alpha):
     """Exponential average of the bandpass statistics across blocks, weight
     alpha on the new block (1 = per block)."""
     return _check(lib().tp_plan_set_running_stats(p, float(alpha)))
+
+
+def tp_engine_set_batch_grid(e, ctas=0):
+    """Batched dedispersion grid: 0 persistent (default), > 0 at most that
+    many CTAs, < 0 one CTA per work item."""
+    return _check(lib().tp_engine_set_batch_grid(e, int(ctas)))
 
 
 def tp_engine_set_wait_limit(e, tries=-1):

@@ -6,12 +6,18 @@
 
 namespace tp {
 
-cudaError_t launch_dedisperse_part0(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
-cudaError_t launch_dedisperse_part1(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
-cudaError_t launch_dedisperse_part2(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
-cudaError_t launch_dedisperse_part3(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
-cudaError_t launch_dedisperse_part4(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
-cudaError_t launch_dedisperse_part5(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
+cudaError_t launch_dedisperse_part0(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part1(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part2(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part3(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part4(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part5(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
 static_assert(kDedispParts == 6, "one launch_dedisperse_part per unit");
 
 #define TP_SHAPE_ENTRY(i, K, S, O, N, F, A, M) {K, S, O, N, F, A},
@@ -23,15 +29,15 @@ int shape_tile_t(int shape) {
   return (algo == 4 || algo == 6 ? 64 : 32) * kShapes[shape].S;  // two output segments per lane
 }
 
-cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s) {
+cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s, int grid_limit) {
   if (shape < 0 || shape >= kNumShapes) return cudaErrorInvalidValue;
   switch (shape % kDedispParts) {
-    case 0: return launch_dedisperse_part0(shape, dtype, ba, ctas, s);
-    case 1: return launch_dedisperse_part1(shape, dtype, ba, ctas, s);
-    case 2: return launch_dedisperse_part2(shape, dtype, ba, ctas, s);
-    case 3: return launch_dedisperse_part3(shape, dtype, ba, ctas, s);
-    case 4: return launch_dedisperse_part4(shape, dtype, ba, ctas, s);
-    default: return launch_dedisperse_part5(shape, dtype, ba, ctas, s);
+    case 0: return launch_dedisperse_part0(shape, dtype, ba, ctas, grid_limit, s);
+    case 1: return launch_dedisperse_part1(shape, dtype, ba, ctas, grid_limit, s);
+    case 2: return launch_dedisperse_part2(shape, dtype, ba, ctas, grid_limit, s);
+    case 3: return launch_dedisperse_part3(shape, dtype, ba, ctas, grid_limit, s);
+    case 4: return launch_dedisperse_part4(shape, dtype, ba, ctas, grid_limit, s);
+    default: return launch_dedisperse_part5(shape, dtype, ba, ctas, grid_limit, s);
   }
 }
 

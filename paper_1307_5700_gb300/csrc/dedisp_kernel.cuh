@@ -155,7 +155,10 @@ struct Shape {
   static constexpr int AB = ALGO >= 8 ? 3 : ROT ? ALGO - 2 : ALGO;
   // ALGO 9-11: the 8-bit quads of ALGO 8 with every channel of a stage added
   // in one call (variant ALGO - 6 of add_quad8t)
-  static constexpr bool THREADED = ALGO >= 9;
+  static constexpr bool THREADED = ALGO >= 9 && ALGO <= 11;
+  // ALGO 12: ALGO 8 with the copies issued four stages ahead of their use
+  // over eight stage buffers (the 8-bit rows are half as long as FP32 ones)
+  static constexpr int LOOK = ALGO == 12 ? 4 : kLookRot;
   static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
   static constexpr int QS = 16 / EB;                                          // samples per 16 B
   static constexpr int NSEG = AB == 4 ? 2 : 1;                              // output segments per lane
@@ -171,8 +174,10 @@ struct Shape {
   static constexpr int DW = NCONS * K <= 32 ? 32 : 64;                        // delays staged per channel
   // two CTAs per SM without a producer warp: one stage buffer fewer, so that
   // both fit the SM's shared memory
-  static constexpr int STAGES =
-      MODE == kModeU8 && AB == 1 ? kStagesU8 : ROT ? (MINB >= 2 ? kStagesRot - 1 : kStagesRot) : kStages;
+  static constexpr int STAGES = MODE == kModeU8 && AB == 1 ? kStagesU8
+                                : ALGO == 12                ? 8
+                                : ROT                       ? (MINB >= 2 ? kStagesRot - 1 : kStagesRot)
+                                                            : kStages;
   static constexpr size_t data_bytes = (size_t)STAGES * kNC * ROWB;
   static constexpr size_t del_bytes = sizeof(int) * (ROT ? NCONS : kDelRing) * kNC * DW;  // ring, or a slot per warp
   // 8-bit mode: per (stage, consumer warp) K int4 of word offsets (one per
@@ -201,25 +206,28 @@ struct Shape {
 //   y = byte j: in-window offset of DM j of the warp's group,
 //   z = number of 16-byte units of the window the channel needs.
 
+// The beam of work item `item`: the last b with cta_start[b] <= item.
+__device__ __forceinline__ int item_beam(const BatchArgs& ba, int item) {
+  int lo = 0, hi = ba.nbeams - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ba.cta_start[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One work item: a (DM tile, time tile) of one beam, by the whole CTA, with
+// its mbarriers freshly initialised.  Each warp returns false when one of its
+// waits gave up (after letting its own copies land and recording TP_ETIMEOUT).
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
-__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::THREADS, MINB)
-    dedisperse_kernel(BatchArgs ba) {
+__device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
   using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   constexpr bool ROT = Sh::ROT;
   constexpr int AB = Sh::AB;  // the consumer scheme
-  // the CTA's beam: last b with cta_start[b] <= blockIdx.x
-  int bi = 0;
-  {
-    int lo = 0, hi = ba.nbeams - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (ba.cta_start[mid] <= (int)blockIdx.x) lo = mid;
-      else hi = mid - 1;
-    }
-    bi = lo;
-  }
+  const int bi = item_beam(ba, item);
   const DedispArgs& a = ba.beams[bi];
-  const int local = (int)blockIdx.x - ba.cta_start[bi];
+  const int local = item - ba.cta_start[bi];
   constexpr int TT = Sh::TT, LR = Sh::LR, ROWB = Sh::ROWB, EB = Sh::EB, QS = Sh::QS;
   static_assert(MODE != kModeU8 || K <= 4, "8-bit shifts of a warp's DMs are packed in one int4");
   static_assert(NCONS * K <= 64, "a producer lane holds at most two DMs of the tile");
@@ -245,15 +253,6 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
   const int nstage = (nchan + kNC - 1) / kNC;
   const int last = dt.nd - 1;
   const unsigned char* ybytes = static_cast<const unsigned char*>(a.y);
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < STAGES; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], NCONS);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
 
   const int32_t* __restrict__ dT = a.delayT;
   // delays of stage st into `slot`: lane l copies delayT[c][d0 + j] for
@@ -412,7 +411,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
         if (!mbar_wait_bounded(&full[k % STAGES], (unsigned)((k / STAGES) & 1))) ok = false;
       if (!ok) atomicExch(a.status, TP_ETIMEOUT);
     }
-    return;
+    return ok;
   }
 
   // ------------------------------------------------------------------ consumers
@@ -553,21 +552,21 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
   };
   if constexpr (ROT) {
     if (warp < nstage) prefetch_to(warp, myslot);
-    static_assert(!ROT || kLookRot < STAGES, "lookahead within the pipeline");
-    for (int j = warp; j < kLookRot && j < nstage; j += NCONS)
+    static_assert(!ROT || Sh::LOOK < STAGES, "lookahead within the pipeline");
+    for (int j = warp; j < Sh::LOOK && j < nstage; j += NCONS)
       if (!produce(j)) {
         bail();
-        return;
+        return false;
       }
   }
 
   for (int i = 0; i < nstage; ++i) {
     const int buf = i % STAGES;
     if constexpr (ROT) {
-      const int j = i + kLookRot;
+      const int j = i + Sh::LOOK;
       if (j < nstage && j % NCONS == warp && !produce(j)) {
         bail();
-        return;
+        return false;
       }
     }
     if (!mbar_wait_bounded(&full[buf], (unsigned)((i / STAGES) & 1), a.wait_tries)) {
@@ -575,7 +574,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
         bail();
       else if (lane == 0)
         atomicExch(a.status, TP_ETIMEOUT);
-      return;
+      return false;
     }
     const int nc = nchan - i * kNC < kNC ? nchan - i * kNC : kNC;
     if constexpr (U8D) {
@@ -718,7 +717,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
   // epilogue: 16-bit and 8-bit modes accumulated the stored samples x~;
   // subtract the block's sum of bandpass values (exact integers for 8-bit data)
   fold();
-  if (!live) return;
+  if (!live) return true;
   const bool is_int = a.dtype == TP_U8;
   // output s of DM j in segment seg
   auto outv = [&](int j, int seg, int s) -> float {
@@ -804,28 +803,87 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
         static_cast<double2*>(a.row_part)[(int64_t)d * a.ntt + tt] = make_double2((double)s1, (double)s2);
     }
   }
+  return true;
 }
 
+// The kernel drains the work items of the batch (items = cta_start[nbeams]):
+// a grid of one CTA per item, or a persistent grid of a few CTAs per SM in
+// which CTA b starts with item b and then takes the next untaken item from a
+// device counter (the first free CTA gets the next item, so the items stay
+// in order and no SM idles while another has a queue).  Between items the CTA
+// synchronises (every copy of the item has landed: each warp waited on every
+// stage, or drained its own copies when it gave up) and initialises its
+// mbarriers afresh.  After a wait gave up the CTA keeps taking items only to
+// record TP_ETIMEOUT for their beams, then stops.
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
-cudaError_t launch_mode(const BatchArgs& ba, int ctas, cudaStream_t s) {
+__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::THREADS, MINB)
+    dedisperse_kernel(BatchArgs ba) {
+  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes +
+                                               Sh::fold_bytes);
+  uint64_t* empty = full + Sh::STAGES;
+  __shared__ int s_fail, s_next;
+  const int nitems = ba.cta_start[ba.nbeams];
+  auto take = [&](int cur) {
+    return ba.next_item ? (int)gridDim.x + atomicAdd(ba.next_item, 1) : cur + (int)gridDim.x;
+  };
+  for (int item = blockIdx.x; item < nitems;) {
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < Sh::STAGES; ++i) {
+        mbar_init(&full[i], 1);
+        mbar_init(&empty[i], NCONS);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      s_fail = 0;
+    }
+    __syncthreads();
+    if (!dedisperse_item<K, S, OMAX, NCONS, MODE, ALGO, MINB>(ba, item)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+      if (threadIdx.x == 0)
+        for (int rest = take(item); rest < nitems; rest = take(rest))
+          atomicExch(ba.beams[item_beam(ba, rest)].status, TP_ETIMEOUT);
+      return;
+    }
+    if (threadIdx.x == 0) s_next = take(item);
+    __syncthreads();
+    item = s_next;
+  }
+}
+
+// grid_limit < 0: one CTA per item; 0: a persistent grid of as many CTAs as
+// fit on the device at once; > 0: at most that many CTAs.
+template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
+cudaError_t launch_mode(const BatchArgs& ba, int ctas, int grid_limit, cudaStream_t s) {
   using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   if (ctas <= 0) return cudaErrorInvalidValue;
   auto k = dedisperse_kernel<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)ctas, Sh::THREADS, Sh::smem, s>>>(ba);
+  int grid = ctas;
+  if (grid_limit == 0) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Sh::THREADS, Sh::smem);
+    if (e != cudaSuccess) return e;
+    grid_limit = (per_sm > 0 ? per_sm : 1) * nsm;
+  }
+  if (grid_limit > 0 && grid_limit < grid) grid = grid_limit;
+  k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(ba);
   return cudaGetLastError();
 }
 
 template <int K, int S, int OMAX, int NCONS, int FMT, int ALGO, int MINB>
-cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t s) {
+cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, int grid_limit, cudaStream_t s) {
   if constexpr (FMT == 4) {
-    return launch_mode<K, S, OMAX, NCONS, kModeF32, ALGO, MINB>(ba, ctas, s);
+    return launch_mode<K, S, OMAX, NCONS, kModeF32, ALGO, MINB>(ba, ctas, grid_limit, s);
   } else if constexpr (FMT == 3) {
-    return launch_mode<K, S, OMAX, NCONS, kModeU8, ALGO, MINB>(ba, ctas, s);
+    return launch_mode<K, S, OMAX, NCONS, kModeU8, ALGO, MINB>(ba, ctas, grid_limit, s);
   } else {
-    if (dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16, ALGO, MINB>(ba, ctas, s);
-    return launch_mode<K, S, OMAX, NCONS, kModeF16, ALGO, MINB>(ba, ctas, s);
+    if (dtype == TP_BF16) return launch_mode<K, S, OMAX, NCONS, kModeBF16, ALGO, MINB>(ba, ctas, grid_limit, s);
+    return launch_mode<K, S, OMAX, NCONS, kModeF16, ALGO, MINB>(ba, ctas, grid_limit, s);
   }
 }
 
@@ -838,9 +896,9 @@ cudaError_t launch_shape(const BatchArgs& ba, int dtype, int ctas, cudaStream_t 
 namespace {
 
 template <int I, int K, int S, int OMAX, int NCONS, int FMT, int ALGO, int MINB>
-cudaError_t launch_in_part(const BatchArgs& ba, int dtype, int ctas, cudaStream_t s) {
+cudaError_t launch_in_part(const BatchArgs& ba, int dtype, int ctas, int grid_limit, cudaStream_t s) {
   if constexpr (I % kDedispParts == TP_DEDISP_PART)
-    return launch_shape<K, S, OMAX, NCONS, FMT, ALGO, MINB>(ba, dtype, ctas, s);
+    return launch_shape<K, S, OMAX, NCONS, FMT, ALGO, MINB>(ba, dtype, ctas, grid_limit, s);
   else
     return cudaErrorInvalidValue;
 }
@@ -850,13 +908,13 @@ cudaError_t launch_in_part(const BatchArgs& ba, int dtype, int ctas, cudaStream_
 }  // namespace tp
 
 #define TP_DEDISP_PART_CASE(i, K, S, O, N, F, A, M) \
-  case i: return launch_in_part<i, K, S, O, N, F, A, M>(ba, dtype, ctas, s);
+  case i: return launch_in_part<i, K, S, O, N, F, A, M>(ba, dtype, ctas, grid_limit, s);
 
 // Defines tp::launch_dedisperse_part<n>: the launches of this unit's shapes.
 #define TP_DEFINE_DEDISP_PART(n)                                                                      \
   namespace tp {                                                                                       \
   cudaError_t launch_dedisperse_part##n(int shape, int dtype, const BatchArgs& ba, int ctas,           \
-                                        cudaStream_t s) {                                              \
+                                        int grid_limit, cudaStream_t s) {                              \
     switch (shape) {                                                                                   \
       TP_SHAPES(TP_DEDISP_PART_CASE)                                                                   \
       default: return cudaErrorInvalidValue;                                                           \

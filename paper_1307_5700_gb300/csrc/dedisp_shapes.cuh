@@ -87,7 +87,9 @@
   X(62, 4, 30, 16, 8, 3, 10, 1)      \
   X(63, 4, 30, 16, 8, 3, 11, 1)      \
   X(64, 4, 14, 16, 8, 3, 8, 2)       \
-  X(65, 4, 14, 16, 8, 3, 10, 2)
+  X(65, 4, 14, 16, 8, 3, 10, 2)      \
+  X(66, 4, 26, 16, 8, 3, 12, 1)      \
+  X(67, 4, 22, 16, 8, 3, 12, 1)
 
 namespace tp {
 constexpr int kDedispParts = 6;  // translation units the kernel instantiations are split over

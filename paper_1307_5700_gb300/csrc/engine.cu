@@ -111,6 +111,7 @@ namespace {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 constexpr size_t kBatchBytes = 512 * 1024;  // batch arguments of up to ~2000 beams
+constexpr size_t kMaxBatchGroups = 64;        // kernel-shape groups (launches) of one batch
 
 enum BeamState { kEmpty = 0, kReady = 1, kDedispersed = 2, kDetected = 3 };
 
@@ -270,8 +271,10 @@ struct tp_engine {
   double batch_ms = 0.0;
   int64_t batch_count = 0;
   long long wait_tries = kDefaultWaitTries;  // see tp_engine_set_wait_limit
+  int batch_grid = 0;  // batched dedispersion grid: 0 persistent, > 0 at most that many CTAs, < 0 one per item
   uint64_t launches = 0;
   void* d_batch = nullptr;  // batch arguments for launches outside graphs
+  int* d_items = nullptr;   // work-item counters of the batched launches (one per kernel-shape group)
   std::vector<unsigned char> h_batch;
   std::map<std::string, GraphEntry> graphs;
   std::vector<tp_plan*> plans;
@@ -323,7 +326,7 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
 // windows (the order of their launch times on a 1024-channel, 640-trial,
 // 2^17-sample block).
 constexpr int kShapePreference[kNumShapes] = {55, 53, 46, 56, 54, 52, 50, 51, 48, 49, 33, 44, 45,
-                                              57, 58, 59, 60, 61, 62, 63, 64, 65, 47, 34, 42, 31, 30, 32, 35, 39, 43, 41, 40,
+                                              57, 58, 59, 60, 61, 62, 63, 64, 65, 66, 67, 47, 34, 42, 31, 30, 32, 35, 39, 43, 41, 40,
                                               27, 25, 26, 24, 28, 29, 22, 18, 19, 12, 13, 14, 15,
                                               16, 17, 23, 21, 20, 8, 10, 1, 2, 5, 0, 3, 6,
                                               4, 7, 9, 11, 36, 37, 38};
@@ -642,7 +645,8 @@ int launch_single(tp_engine* e, Beam* b, const DedispArgs& da, int shape, cudaSt
     b->h_args_valid = true;
   }
   BatchArgs ba{static_cast<const DedispArgs*>(b->d_args),
-               reinterpret_cast<const int*>(static_cast<unsigned char*>(b->d_args) + sizeof(DedispArgs)), 1};
+               reinterpret_cast<const int*>(static_cast<unsigned char*>(b->d_args) + sizeof(DedispArgs)), 1,
+               nullptr};
   TP_CUDA_TRY(launch_dedisperse(shape, da.dtype, ba, ctas, s));
   e->launches += 1;
   return TP_OK;
@@ -819,6 +823,10 @@ int issue_batch(tp_engine* e, BatchPlan& bp, void* d_args, bool detect) {
   const int* dcta = reinterpret_cast<const int*>(static_cast<unsigned char*>(d_args) +
                                                  bp.args.size() * sizeof(DedispArgs));
   int coff = 0;
+  // one work-item counter per kernel-shape group of the batch
+  if (bp.groups.size() > kMaxBatchGroups) return set_error(TP_EINVAL, "more than %d kernel-shape groups", kMaxBatchGroups);
+  TP_CUDA_TRY(cudaMemsetAsync(e->d_items, 0, sizeof(int) * bp.groups.size(), s));
+  int gi = 0;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (e->profiling) {  // never set while a graph is captured
     if (e->bev_pool.empty()) {
@@ -831,10 +839,10 @@ int issue_batch(tp_engine* e, BatchPlan& bp, void* d_args, bool detect) {
     TP_CUDA_TRY(cudaEventRecord(ev.first, s));
   }
   for (auto& g : bp.groups) {
-    BatchArgs ba{dargs + g.first, dcta + coff, g.second};
+    BatchArgs ba{dargs + g.first, dcta + coff, g.second, e->d_items + gi++};
     const int ctas = bp.cta[coff + g.second];
     const Beam* b0 = bp.beams[g.first];
-    TP_CUDA_TRY(launch_dedisperse(b0->plan->shape, b0->plan->dtype, ba, ctas, s));
+    TP_CUDA_TRY(launch_dedisperse(b0->plan->shape, b0->plan->dtype, ba, ctas, s, e->batch_grid));
     e->launches += 1;
     coff += g.second + 1;
   }
@@ -895,7 +903,9 @@ int tp_engine_create(int device, size_t hbm_budget_bytes, void* cuda_stream, tp_
   TP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   tp_engine* e = new (std::nothrow) tp_engine();
   if (!e) return set_error(TP_ENOMEM, "engine allocation");
-  if (cudaMalloc(&e->d_batch, kBatchBytes) != cudaSuccess) {
+  if (cudaMalloc(&e->d_batch, kBatchBytes) != cudaSuccess ||
+      cudaMalloc(&e->d_items, sizeof(int) * kMaxBatchGroups) != cudaSuccess) {
+    cudaFree(e->d_batch);
     delete e;
     return set_error(TP_ENOMEM, "engine batch arguments");
   }
@@ -938,6 +948,7 @@ int tp_engine_destroy(tp_engine* e) {
         cudaEventDestroy(ev.second);
       }
     cudaFree(e->d_batch);
+    cudaFree(e->d_items);
   }
   delete e;
   return TP_OK;
@@ -1663,6 +1674,20 @@ int tp_engine_set_wait_limit(tp_engine* e, long long tries) {
   return TP_OK;
 }
 
+int tp_engine_set_batch_grid(tp_engine* e, int ctas) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  e->batch_grid = ctas;
+  TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
+  for (auto& kv : e->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaFree(kv.second.d_args);
+  }
+  e->graphs.clear();
+  return TP_OK;
+}
+
 int tp_get_batch_times(tp_engine* e, double* ms, int64_t* count) {
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
@@ -1910,11 +1935,15 @@ int tp_autotune_batch(tp_engine* e, int reps, int* best, float* ms, int n) {
     BatchArgs ba{static_cast<const DedispArgs*>(e->d_batch),
                  reinterpret_cast<const int*>(static_cast<unsigned char*>(e->d_batch) +
                                               args.size() * sizeof(DedispArgs)),
-                 (int)args.size()};
+                 (int)args.size(), e->d_items};
     const int dtype = bs[0]->plan->dtype;
-    TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s));  // warm-up
+    TP_CUDA_TRY(cudaMemsetAsync(e->d_items, 0, sizeof(int), s));
+    TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s, e->batch_grid));  // warm-up
     TP_CUDA_TRY(cudaEventRecord(e0, s));
-    for (int r = 0; r < reps; ++r) TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s));
+    for (int r = 0; r < reps; ++r) {
+      TP_CUDA_TRY(cudaMemsetAsync(e->d_items, 0, sizeof(int), s));
+      TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s, e->batch_grid));
+    }
     TP_CUDA_TRY(cudaEventRecord(e1, s));
     TP_CUDA_TRY(cudaEventSynchronize(e1));
     e->launches += 1 + reps;

@@ -120,6 +120,8 @@ struct BatchArgs {
   const DedispArgs* beams;  // device, nbeams entries
   const int* cta_start;     // device, nbeams + 1 entries
   int nbeams;
+  int* next_item;           // device counter, 0 at launch: CTAs past their first item take
+                            // gridDim.x + atomicAdd(next_item, 1); NULL: item + gridDim.x
 };
 
 // Register-tile shapes of the dedispersion kernel.
@@ -137,7 +139,7 @@ struct KernelShape {
               // 5: DM quads with a lane's outputs s and s + S / 2 paired;
               // 6, 7, 8: 4, 5, 3 without a producer warp (consumers issue the copies)
 };
-constexpr int kNumShapes = 66;
+constexpr int kNumShapes = 68;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
@@ -222,7 +224,10 @@ cudaError_t launch_delay_table(int nchan, double f_lo, double bw, double t_samp,
 cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypitch,
                        cudaStream_t s);
 cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s);
-cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s);
+// ctas = work items; grid_limit < 0: one CTA per item, 0: a persistent grid
+// (as many CTAs as are resident at once), > 0: at most that many CTAs
+cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s,
+                              int grid_limit = -1);
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s);
 // Device-to-device copy of nrows rows of row_bytes bytes (pitched); a
 // 16-byte vector kernel when every address, pitch and the row length are

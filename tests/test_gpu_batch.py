@@ -1,6 +1,7 @@
 """Several beams of different plans in one batched launch (and through a
 cached CUDA graph) give exactly the results of their solo runs, block after
-block; one beam is also checked against the oracle."""
+block, whatever the grid that drains the batch's work items; one beam is
+also checked against the oracle."""
 import numpy as np
 import pytest
 
@@ -28,11 +29,14 @@ def _blocks(dtype, seed, nblk, B):
     return out
 
 
-def _run(mode, dtype, blocks_per_beam, B, stream=None):
-    """mode: 'solo' (per-beam calls), 'batch' (beam = -1), 'graph'."""
+def _run(mode, dtype, blocks_per_beam, B, stream=None, grid=None):
+    """mode: 'solo' (per-beam calls), 'batch' (beam = -1), 'graph'; grid:
+    the batched launch's CTA count (None: the default persistent grid)."""
     e = tp.tp_engine_create(0, 0, stream)
     res = []
     try:
+        if grid is not None:
+            tp.tp_engine_set_batch_grid(e, grid)
         plans = [tp.tp_create_plan(e, NCHAN, F_LO, BW, TS, dms, dtype, None, 4.0) for dms in PLANS]
         beams = [tp.tp_beam_open(e, p, B, 1 << 16) for p in plans]
         nblk = len(blocks_per_beam[0])
@@ -90,6 +94,27 @@ def test_batch_and_graph_equal_solo(dtype):
         _, mass = O.dedisperse_points(blocks[1][0], dtype, o["stats"], o["chunk_flag"], o["spec_flag"], 256,
                                       od, dd, tt)
         assert np.all(np.abs(D.astype(np.float64) - o["D"]).ravel() <= 1e-5 * mass)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+@pytest.mark.parametrize("grid", [-1, 1, 7, 300])
+def test_batched_grid_sizes_equal_solo(dtype, grid):
+    """The batched kernel drains its work items with any grid: one CTA per
+    item (-1), a single CTA taking every item (1), a few CTAs taking many
+    items each (7), and more CTAs than items of the smaller beams (300);
+    every beam's series and candidates equal its solo run exactly."""
+    import torch
+    tp.build()
+    B = 6000
+    blocks = [_blocks(dtype, 700 * (i + 1), 2, B) for i in range(len(PLANS))]
+    solo = _run("solo", dtype, blocks, B)
+    stream = torch.cuda.Stream()
+    for mode in ("batch", "graph"):
+        other = _run(mode, dtype, blocks, B, stream=stream.cuda_stream, grid=grid)
+        for k in range(2):
+            for i in range(len(PLANS)):
+                assert np.array_equal(solo[k][i][1], other[k][i][1]), (mode, grid, k, i)
+                assert np.array_equal(solo[k][i][0], other[k][i][0]), (mode, grid, k, i)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "u8"])

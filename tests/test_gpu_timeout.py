@@ -77,3 +77,60 @@ def test_zero_wait_limit_reports_timeout_and_engine_recovers(dtype, shapes):
     finally:
         tp.tp_engine_destroy(e)
         tp.tp_engine_destroy(ref)
+
+
+@pytest.mark.parametrize("grid", [0, 3])
+def test_timeout_in_a_persistent_batch_flags_every_beam(grid):
+    """A batch drained by a persistent grid (0: the default, 3: three CTAs
+    taking many items each) with the wait limit at 0: the CTAs give up on
+    their first items and record TP_ETIMEOUT for the beams of every item they
+    leave undone, so that each beam of the batch reports the timeout; the next
+    batch with the default limit equals a batch that never timed out."""
+    tp.build()
+    import torch
+    plans_dms = [DMS, np.arange(80) * 0.2, np.arange(24) * 1.0]
+    blocks = [_block("f32", 950 + k) for k in range(3)]
+    stream = torch.cuda.Stream()
+    e = tp.tp_engine_create(0, 0, stream.cuda_stream)
+    ref = tp.tp_engine_create(0, 0, stream.cuda_stream)
+    try:
+        tp.tp_engine_set_batch_grid(e, grid)
+        ps = [tp.tp_create_plan(e, NCHAN, *BAND, d, "f32", None, 5.0) for d in plans_dms]
+        pr = [tp.tp_create_plan(ref, NCHAN, *BAND, d, "f32", None, 5.0) for d in plans_dms]
+        bs = [tp.tp_beam_open(e, p, NSAMP, 1 << 16) for p in ps]
+        br = [tp.tp_beam_open(ref, p, NSAMP, 1 << 16) for p in pr]
+
+        def batch(eng, beams, k):
+            for b in beams:
+                tp.tp_push_block(eng, b, blocks[k])
+            tp.tp_run_ready(eng, use_graph=False)
+            return [tp.tp_get_candidates(eng, b, 1 << 16) for b in beams]
+
+        batch(e, bs, 0)
+        batch(ref, br, 0)
+        tp.tp_engine_set_wait_limit(e, 0)
+        for b in bs:
+            tp.tp_push_block(e, b, blocks[1])
+        tp.tp_run_ready(e, use_graph=False)
+        for b in bs:
+            with pytest.raises(tp.TpError) as err:
+                tp.tp_get_candidates(e, b, 1 << 16)
+            assert err.value.code == tp.TP_ETIMEOUT
+        tp.tp_engine_set_wait_limit(e, -1)
+        for b in bs:
+            tp.tp_beam_rewind(e, b)
+        tp.tp_run_ready(e, use_graph=False)
+        got = [tp.tp_get_candidates(e, b, 1 << 16) for b in bs]
+        for b in br:
+            tp.tp_push_block(ref, b, blocks[1])
+        tp.tp_run_ready(ref, use_graph=False)
+        want = [tp.tp_get_candidates(ref, b, 1 << 16) for b in br]
+        for (cg, ng, _), (cw, nw, _) in zip(got, want):
+            assert ng == nw and np.array_equal(cg, cw)
+        for b in bs:
+            tp.tp_beam_close(e, b)
+        for b in br:
+            tp.tp_beam_close(ref, b)
+    finally:
+        tp.tp_engine_destroy(e)
+        tp.tp_engine_destroy(ref)

@@ -101,6 +101,8 @@ def _run(nstage, nw, stages, look, rot, rng):
 
 @pytest.mark.parametrize("nw,stages,look,rot", [
     (8, 6, 2, True),    # ALGO 6, 7 as built (8 consumer warps)
+    (8, 8, 4, True),    # ALGO 12: four stages ahead over eight buffers
+    (8, 5, 2, True),    # two CTAs per SM: one buffer fewer
     (12, 6, 2, True),   # 12 consumer warps
     (8, 6, 3, True),
     (8, 4, 3, True),    # one stage of slack: correct, only slower
