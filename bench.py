@@ -408,6 +408,7 @@ def run_batch8(args, dtype="f16", steps=20, warmup=3, peaks=None):
     bms, bn = tp.tp_get_batch_times(e)
     tp.tp_set_profiling(e, False)
     ncand = [tp.tp_get_candidates(e, b, 0)[1] for b in beams]
+    shapes = {str(nd): int(tp.tp_plan_shapes(p)[0]) for nd, p in plans.items()}
     for b in beams:
         tp.tp_beam_close(e, b)
     for p in plans.values():
@@ -420,7 +421,7 @@ def run_batch8(args, dtype="f16", steps=20, warmup=3, peaks=None):
                         "2^17-sample blocks, every stage batched and replayed from a CUDA graph",
             "value": value, "unit": "DM-trial*samples/s", "dtype": dtype, "steps": steps, "warmup": warmup,
             "ms_per_step": ms / steps, "adds_per_s": adds * steps * world / (ms / 1e3),
-            "kernel_shape": int(best),
+            "kernel_shape": int(best), "kernel_shape_per_plan": shapes,
             "autotune_ms": {str(i): round(float(v), 3) for i, v in enumerate(shape_ms) if v >= 0},
             "realtime_beams": value / (len(DMS) / TSAMP),
             "roofline": dedisp_roof(adds, bms / bn, peaks) if bn else None,

@@ -418,16 +418,30 @@ int tp_plan_set_shape(tp_plan *p, int shape);
  * differently. */
 int tp_autotune(tp_engine *e, int beam, int reps, int *best, float *ms, int n);
 
-/* Batch form of tp_autotune for the batched launch of tp_run_ready: for every
- * shape feasible for all beams that have received a block, time `reps`
- * launches of the dedispersion kernel over all of those beams at once (one
- * launch, the layout tp_run_ready uses), select the fastest for every beam's
- * plan, and return it in *best and the milliseconds per launch in ms[shape]
- * (-1 where not timed; n entries).  A shape's speed on one beam does not
- * predict its speed in a batch (instruction-cache behaviour differs with the
- * number of CTAs in flight), hence a separate tuner.  The beams must share one
- * sample format.  Blocks; the series are overwritten (run the batch again
- * before detection).  TP_ENOTREADY if no beam has received a block. */
+/* Autotuner cache: with a path set, tp_autotune looks up its choice under a
+ * key of the device (name, compute capability, SM count), the plan (channels,
+ * band, sampling time, sample format, DM list) and the block's output length;
+ * a cached shape the plan admits is applied without timing runs (ms holds
+ * only that shape's time; as after timing runs, the beam is to be dedispersed
+ * again), otherwise the timing
+ * runs as usual and the choice is added to the file (a text file, one
+ * "key" shape ms entry per line, rewritten through a temporary file).  A
+ * missing or unreadable file starts an empty cache; path = NULL turns the
+ * cache off.  Errors: TP_EINVAL for a NULL engine. */
+int tp_engine_set_tuning_cache(tp_engine *e, const char *path);
+
+/* Batch form of tp_autotune for the batched launch of tp_run_ready: the beams
+ * that have received a block are grouped by plan, and for every plan and every
+ * shape it admits, `reps` launches of the dedispersion kernel over that plan's
+ * beams at once (the layout and grid tp_run_ready uses) are timed; each plan
+ * takes its own fastest shape (the batch then launches once per shape).
+ * *best = the shape of the plan with the most work (trials x channels x
+ * outputs); ms[shape] = the sum over plans of their launch times with that
+ * shape where every plan admits it, else -1 (n entries).  A shape's speed on
+ * one beam does not predict its speed in a batch (instruction-cache behaviour
+ * differs with the number of CTAs in flight), hence a separate tuner.  Blocks;
+ * the series are overwritten (run the batch again before detection).
+ * TP_ENOTREADY if no beam has received a block. */
 int tp_autotune_batch(tp_engine *e, int reps, int *best, float *ms, int n);
 
 /* ---- tracing -------------------------------------------------------------------- */
@@ -579,6 +593,23 @@ int tp_server_destroy(tp_server *s);
 int tp_channel_stats_noalloc(const void *x, int dtype, int nchan, int64_t nsamp, int64_t pitch,
                              const tp_rfi_params *rfi, double *mu, double *sigma, uint8_t *chunk_flag,
                              uint8_t *chunk_raw, void *cuda_stream);
+
+/* Stream state of a beam for checkpoint and resume: tp_beam_export writes,
+ * between blocks (after tp_detect of the last block, no prefetch pending),
+ * everything the next block depends on -- the overlap tail of the window (the
+ * last max_delay samples of every channel, in the sample format), the stream
+ * position, and the running bandpass statistics when the plan keeps them --
+ * to the host buffer `out` (cap bytes; out = NULL only sets *size to the
+ * bytes needed).  tp_beam_import loads such a state into a beam that has not
+ * received a block, opened on a plan with the same channels, DM list, sample
+ * format and running-statistics weight (checked); the next tp_push_block
+ * continues the stream, and its results equal those of the stream that was
+ * never interrupted.  External statistics (tp_beam_set_bandpass) are not part
+ * of the state.  Both block (synchronous copies).  Errors: TP_EINVAL (bad
+ * buffer, plan mismatch, malformed state), TP_ENOTREADY (no block yet),
+ * TP_EBUSY (export in the middle of a block, import into a used beam). */
+int tp_beam_export(tp_engine *e, int beam, void *out, size_t cap, size_t *size);
+int tp_beam_import(tp_engine *e, int beam, const void *in, size_t size);
 
 /* Text of the calling thread's last error. */
 const char *tp_last_error_string(void);

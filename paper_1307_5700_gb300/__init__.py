@@ -53,6 +53,7 @@ EXPORTS = (
     "tp_get_detrend", "tp_plan_set_bandpass_fit", "tp_get_bandpass_fit", "tp_plan_set_clustering",
     "tp_get_clusters", "tp_get_candidate_labels", "tp_prefetch_block", "tp_push_prefetched",
     "tp_get_batch_times", "tp_engine_set_wait_limit", "tp_plan_set_running_stats", "tp_engine_set_batch_grid",
+    "tp_beam_export", "tp_beam_import", "tp_engine_set_tuning_cache",
 )
 
 
@@ -127,6 +128,9 @@ _SIGS = {
     "tp_engine_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
     "tp_plan_set_running_stats": (_i, [_vp, _d]),
     "tp_engine_set_batch_grid": (_i, [_vp, _i]),
+    "tp_beam_export": (_i, [_vp, _i, _vp, _sz, _vp]),
+    "tp_beam_import": (_i, [_vp, _i, _vp, _sz]),
+    "tp_engine_set_tuning_cache": (_i, [_vp, ctypes.c_char_p]),
     "tp_engine_launches": (_i, [_vp, _vp]),
     "tp_plan_shapes": (_i, [_vp, _vp, _vp, _i]),
     "tp_plan_set_shape": (_i, [_vp, _i]),
@@ -411,6 +415,25 @@ def tp_plan_set_running_stats(p, alpha):
     """Exponential average of the bandpass statistics across blocks, weight
     alpha on the new block (1 = per block)."""
     return _check(lib().tp_plan_set_running_stats(p, float(alpha)))
+
+
+def tp_engine_set_tuning_cache(e, path):
+    """Autotuner cache file (None: off)."""
+    return _check(lib().tp_engine_set_tuning_cache(e, None if path is None else os.fsencode(path)))
+
+
+def tp_beam_export(e, beam):
+    """The beam's stream state (bytes) for tp_beam_import."""
+    n = ctypes.c_size_t()
+    _check(lib().tp_beam_export(e, beam, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().tp_beam_export(e, beam, buf, n.value, ctypes.byref(n)))
+    return buf.raw
+
+
+def tp_beam_import(e, beam, state):
+    """Continue a stream in a fresh beam from a state of tp_beam_export."""
+    return _check(lib().tp_beam_import(e, beam, state, len(state)))
 
 
 def tp_engine_set_batch_grid(e, ctas=0):

@@ -823,12 +823,16 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes +
                                                Sh::fold_bytes);
   uint64_t* empty = full + Sh::STAGES;
-  __shared__ int s_fail, s_next;
-  const int nitems = ba.cta_start[ba.nbeams];
+  __shared__ int s_item, s_next, s_fail;
   auto take = [&](int cur) {
     return ba.next_item ? (int)gridDim.x + atomicAdd(ba.next_item, 1) : cur + (int)gridDim.x;
   };
-  for (int item = blockIdx.x; item < nitems;) {
+  // the loop state lives in shared memory, so that no register stays live
+  // across an item (the item's own code uses nearly all of them)
+  if (threadIdx.x == 0) s_item = blockIdx.x;
+  for (;;) {
+    // the next item is taken before this one runs, so that a CTA on its last
+    // item (every CTA of a one-CTA-per-item grid) leaves without waiting
     if (threadIdx.x == 0) {
       for (int i = 0; i < Sh::STAGES; ++i) {
         mbar_init(&full[i], 1);
@@ -836,19 +840,21 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
       }
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       s_fail = 0;
+      s_next = s_item < ba.cta_start[ba.nbeams] ? take(s_item) : s_item;
     }
     __syncthreads();
-    if (!dedisperse_item<K, S, OMAX, NCONS, MODE, ALGO, MINB>(ba, item)) s_fail = 1;
+    if (s_item >= ba.cta_start[ba.nbeams]) return;
+    const bool ok = dedisperse_item<K, S, OMAX, NCONS, MODE, ALGO, MINB>(ba, s_item);
+    if (s_next >= ba.cta_start[ba.nbeams]) return;
+    if (!ok) s_fail = 1;
     __syncthreads();
     if (s_fail) {
       if (threadIdx.x == 0)
-        for (int rest = take(item); rest < nitems; rest = take(rest))
+        for (int rest = s_next; rest < ba.cta_start[ba.nbeams]; rest = take(rest))
           atomicExch(ba.beams[item_beam(ba, rest)].status, TP_ETIMEOUT);
       return;
     }
-    if (threadIdx.x == 0) s_next = take(item);
-    __syncthreads();
-    item = s_next;
+    if (threadIdx.x == 0) s_item = s_next;
   }
 }
 

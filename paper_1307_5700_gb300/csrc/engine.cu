@@ -271,6 +271,9 @@ struct tp_engine {
   double batch_ms = 0.0;
   int64_t batch_count = 0;
   long long wait_tries = kDefaultWaitTries;  // see tp_engine_set_wait_limit
+  // autotuner cache (tp_engine_set_tuning_cache): key -> (shape, ms per launch)
+  std::string tune_path;
+  std::map<std::string, std::pair<int, float>> tune_cache;
   int batch_grid = 0;  // batched dedispersion grid: 0 persistent, > 0 at most that many CTAs, < 0 one per item
   uint64_t launches = 0;
   void* d_batch = nullptr;  // batch arguments for launches outside graphs
@@ -1535,6 +1538,127 @@ int tp_get_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, int* n
   return TP_OK;
 }
 
+namespace {
+
+// Saved stream state of a beam (tp_beam_export / tp_beam_import): this
+// header, then the overlap tail [nchan][max_delay] in the sample format, then
+// (running statistics) the running means and variances, nchan doubles each.
+struct BeamStateHeader {
+  char magic[4];
+  uint32_t version;
+  int32_t nchan, ndm, dtype, max_delay;
+  uint64_t delay_sum;  // sum of the plan's delay table: a plan mismatch check
+  int64_t pushed, nblocks;
+  double run_alpha;
+  uint64_t tail_bytes, run_bytes;
+};
+
+uint64_t delay_sum(const tp_plan* p) {
+  uint64_t v = 0;
+  for (int32_t d : p->h_delay) v = v * 1000003u + (uint32_t)d;
+  return v;
+}
+
+}  // namespace
+
+int tp_beam_export(tp_engine* e, int beam, void* out, size_t cap, size_t* size) {
+  if (!e || !size) return set_error(TP_EINVAL, "engine or size is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  const tp_plan* p = b->plan;
+  const size_t es = dtype_size(p->dtype);
+  const size_t tail = (size_t)p->nchan * (size_t)p->max_delay * es;
+  const bool run = p->run_alpha < 1.0;
+  const size_t runb = run ? (size_t)p->nchan * 16 : 0;
+  *size = sizeof(BeamStateHeader) + tail + runb;
+  if (!out) return TP_OK;
+  if (cap < *size) return set_error(TP_EINVAL, "buffer of %zu bytes, %zu needed", cap, *size);
+  if (b->pushed == 0) return set_error(TP_ENOTREADY, "beam %d holds no block yet", beam);
+  if (b->state != kDetected) return set_error(TP_EBUSY, "beam %d: export between blocks (after detection)", beam);
+  if (b->pf_pending) return set_error(TP_EBUSY, "beam %d holds a prefetched block", beam);
+  DeviceGuard g(e->device);
+  TP_CUDA_TRY(cudaStreamSynchronize(beam_stream(e, b)));
+  TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
+  BeamStateHeader h{};
+  std::memcpy(h.magic, "TPBS", 4);
+  h.version = 1;
+  h.nchan = p->nchan;
+  h.ndm = p->ndm;
+  h.dtype = p->dtype;
+  h.max_delay = p->max_delay;
+  h.delay_sum = delay_sum(p);
+  h.pushed = b->pushed;
+  h.nblocks = b->nblocks;
+  h.run_alpha = p->run_alpha;
+  h.tail_bytes = tail;
+  h.run_bytes = runb;
+  unsigned char* o = static_cast<unsigned char*>(out);
+  std::memcpy(o, &h, sizeof h);
+  if (tail) {
+    const size_t rowb = (size_t)p->max_delay * es;
+    const char* src = static_cast<const char*>(b->win[b->cur]) + (size_t)(b->nsamp_win - p->max_delay) * es;
+    TP_CUDA_TRY(cudaMemcpy2D(o + sizeof h, rowb, src, (size_t)b->pitch * es, rowb, p->nchan, cudaMemcpyDeviceToHost));
+  }
+  if (run) {
+    const int cur = (int)(b->nblocks & 1);
+    TP_CUDA_TRY(cudaMemcpy(o + sizeof h + tail, b->run_mu[cur], (size_t)p->nchan * 8, cudaMemcpyDeviceToHost));
+    TP_CUDA_TRY(cudaMemcpy(o + sizeof h + tail + (size_t)p->nchan * 8, b->run_var[cur], (size_t)p->nchan * 8,
+                           cudaMemcpyDeviceToHost));
+  }
+  return TP_OK;
+}
+
+int tp_beam_import(tp_engine* e, int beam, const void* in, size_t size) {
+  if (!e || !in) return set_error(TP_EINVAL, "engine or state is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->pushed != 0) return set_error(TP_EBUSY, "beam %d has received blocks: import into a fresh beam", beam);
+  const tp_plan* p = b->plan;
+  if (size < sizeof(BeamStateHeader)) return set_error(TP_EINVAL, "state of %zu bytes is too short", size);
+  BeamStateHeader h;
+  std::memcpy(&h, in, sizeof h);
+  if (std::memcmp(h.magic, "TPBS", 4) != 0 || h.version != 1) return set_error(TP_EINVAL, "not a beam state");
+  const size_t es = dtype_size(p->dtype);
+  const size_t tail = (size_t)p->nchan * (size_t)p->max_delay * es;
+  const bool run = p->run_alpha < 1.0;
+  const size_t runb = run ? (size_t)p->nchan * 16 : 0;
+  if (h.nchan != p->nchan || h.ndm != p->ndm || h.dtype != p->dtype || h.max_delay != p->max_delay ||
+      h.delay_sum != delay_sum(p))
+    return set_error(TP_EINVAL, "the state was saved under a different plan");
+  if (h.run_alpha != p->run_alpha) return set_error(TP_EINVAL, "the state's running-statistics weight differs");
+  if (h.tail_bytes != tail || h.run_bytes != runb || size < sizeof h + tail + runb || h.pushed <= 0 ||
+      h.nblocks <= 0)
+    return set_error(TP_EINVAL, "inconsistent beam state");
+  DeviceGuard g(e->device);
+  cudaStream_t s = beam_stream(e, b);
+  const unsigned char* src = static_cast<const unsigned char*>(in);
+  if (tail) {
+    const size_t rowb = (size_t)p->max_delay * es;
+    TP_CUDA_TRY(cudaMemcpy2DAsync(b->win[0], (size_t)b->pitch * es, src + sizeof h, rowb, rowb, p->nchan,
+                                  cudaMemcpyHostToDevice, s));
+  }
+  if (run) {
+    const int cur = (int)(h.nblocks & 1);
+    TP_CUDA_TRY(cudaMemcpyAsync(b->run_mu[cur], src + sizeof h + tail, (size_t)p->nchan * 8,
+                                cudaMemcpyHostToDevice, s));
+    TP_CUDA_TRY(cudaMemcpyAsync(b->run_var[cur], src + sizeof h + tail + (size_t)p->nchan * 8,
+                                (size_t)p->nchan * 8, cudaMemcpyHostToDevice, s));
+  }
+  TP_CUDA_TRY(cudaStreamSynchronize(s));  // the caller's buffer may go once we return
+  // the window now holds only the overlap tail: the next push continues the
+  // stream from it exactly as after the exported block
+  b->cur = 0;
+  b->nsamp_win = p->max_delay;
+  b->nout = 0;
+  b->pushed = h.pushed;
+  b->nblocks = h.nblocks;
+  b->t0_abs = h.pushed - p->max_delay;
+  b->state = kEmpty;
+  return TP_OK;
+}
+
 int tp_beam_info(tp_engine* e, int beam, int64_t* nsamp_window, int64_t* nout, int64_t* t0_abs, int* nchunk) {
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
@@ -1897,6 +2021,22 @@ int tp_autotune_batch(tp_engine* e, int reps, int* best, float* ms, int n) {
   if (bs.empty()) return set_error(TP_ENOTREADY, "no beam has received a block");
   const size_t need = bs.size() * sizeof(DedispArgs) + 2 * sizeof(int) + bs.size() * sizeof(int) + 16;
   if (need > kBatchBytes) return set_error(TP_EINVAL, "batch of %zu beams too large", bs.size());
+  // the beams grouped by plan: each plan gets its own kernel shape
+  std::vector<tp_plan*> plans;
+  std::vector<std::vector<Beam*>> groups;
+  std::vector<double> work;
+  for (Beam* b : bs) {
+    tp_plan* p = const_cast<tp_plan*>(b->plan);
+    size_t k = 0;
+    while (k < plans.size() && plans[k] != p) ++k;
+    if (k == plans.size()) {
+      plans.push_back(p);
+      groups.emplace_back();
+      work.push_back(0.0);
+    }
+    groups[k].push_back(b);
+    work[k] += (double)p->ndm * (double)p->nchan * (double)b->nout;
+  }
   // every earlier block of every beam is finished before the timing runs
   for (Beam* b : bs) TP_CUDA_TRY(cudaStreamSynchronize(beam_stream(e, b)));
   TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
@@ -1905,63 +2045,147 @@ int tp_autotune_batch(tp_engine* e, int reps, int* best, float* ms, int n) {
   TP_CUDA_TRY(cudaEventCreate(&e0));
   TP_CUDA_TRY(cudaEventCreate(&e1));
   reps = reps < 1 ? 1 : reps;
-  int bestsh = -1;
-  float bestms = 0.f;
   std::vector<unsigned char> buf;
-  for (int sh = 0; sh < kNumShapes; ++sh) {
-    if (ms && sh < n) ms[sh] = -1.f;
-    bool ok = true;
-    for (Beam* b : bs) ok = ok && b->plan->feasible[sh];
-    if (!ok) continue;
-    // one launch over every beam with shape sh (bfloat16 beams take their own
-    // launch in tp_run_ready; the timing treats the whole set as one group)
-    std::vector<DedispArgs> args;
-    std::vector<int> cta{0};
-    for (Beam* b : bs) {
-      DedispArgs da = dedisp_args(b->plan, b);
-      da.shape = sh;
-      da.tiles = b->plan->d_shape_tiles[sh];
-      da.ntiles = (int)b->plan->shape_tiles[sh].size();
-      da.ntt = (int)((b->nout + shape_tile_t(sh) - 1) / shape_tile_t(sh));
-      if (da.ntt > b->ntt_max) ok = false;
-      args.push_back(da);
-      cta.push_back(cta.back() + da.ntiles * da.ntt);
-    }
-    if (!ok) continue;
-    buf.resize(args.size() * sizeof(DedispArgs) + cta.size() * sizeof(int));
-    std::memcpy(buf.data(), args.data(), args.size() * sizeof(DedispArgs));
-    std::memcpy(buf.data() + args.size() * sizeof(DedispArgs), cta.data(), cta.size() * sizeof(int));
-    TP_CUDA_TRY(cudaMemcpyAsync(e->d_batch, buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
-    BatchArgs ba{static_cast<const DedispArgs*>(e->d_batch),
-                 reinterpret_cast<const int*>(static_cast<unsigned char*>(e->d_batch) +
-                                              args.size() * sizeof(DedispArgs)),
-                 (int)args.size(), e->d_items};
-    const int dtype = bs[0]->plan->dtype;
-    TP_CUDA_TRY(cudaMemsetAsync(e->d_items, 0, sizeof(int), s));
-    TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s, e->batch_grid));  // warm-up
-    TP_CUDA_TRY(cudaEventRecord(e0, s));
-    for (int r = 0; r < reps; ++r) {
+  // ms of the batched launch of group k with shape sh (-1: not feasible)
+  std::vector<std::vector<float>> t(plans.size(), std::vector<float>(kNumShapes, -1.f));
+  for (int sh = 0; sh < kNumShapes; ++sh)
+    for (size_t k = 0; k < plans.size(); ++k) {
+      if (!plans[k]->feasible[sh]) continue;
+      std::vector<DedispArgs> args;
+      std::vector<int> cta{0};
+      bool ok = true;
+      for (Beam* b : groups[k]) {
+        DedispArgs da = dedisp_args(b->plan, b);
+        da.shape = sh;
+        da.tiles = b->plan->d_shape_tiles[sh];
+        da.ntiles = (int)b->plan->shape_tiles[sh].size();
+        da.ntt = (int)((b->nout + shape_tile_t(sh) - 1) / shape_tile_t(sh));
+        if (da.ntt > b->ntt_max) ok = false;
+        args.push_back(da);
+        cta.push_back(cta.back() + da.ntiles * da.ntt);
+      }
+      if (!ok) continue;
+      buf.resize(args.size() * sizeof(DedispArgs) + cta.size() * sizeof(int));
+      std::memcpy(buf.data(), args.data(), args.size() * sizeof(DedispArgs));
+      std::memcpy(buf.data() + args.size() * sizeof(DedispArgs), cta.data(), cta.size() * sizeof(int));
+      TP_CUDA_TRY(cudaMemcpyAsync(e->d_batch, buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
+      BatchArgs ba{static_cast<const DedispArgs*>(e->d_batch),
+                   reinterpret_cast<const int*>(static_cast<unsigned char*>(e->d_batch) +
+                                                args.size() * sizeof(DedispArgs)),
+                   (int)args.size(), e->d_items};
+      const int dtype = plans[k]->dtype;
       TP_CUDA_TRY(cudaMemsetAsync(e->d_items, 0, sizeof(int), s));
-      TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s, e->batch_grid));
+      TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s, e->batch_grid));  // warm-up
+      TP_CUDA_TRY(cudaEventRecord(e0, s));
+      for (int r = 0; r < reps; ++r) {
+        TP_CUDA_TRY(cudaMemsetAsync(e->d_items, 0, sizeof(int), s));
+        TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s, e->batch_grid));
+      }
+      TP_CUDA_TRY(cudaEventRecord(e1, s));
+      TP_CUDA_TRY(cudaEventSynchronize(e1));
+      e->launches += 1 + reps;
+      float tt = 0.f;
+      TP_CUDA_TRY(cudaEventElapsedTime(&tt, e0, e1));
+      t[k][sh] = tt / reps;
     }
-    TP_CUDA_TRY(cudaEventRecord(e1, s));
-    TP_CUDA_TRY(cudaEventSynchronize(e1));
-    e->launches += 1 + reps;
-    float t = 0.f;
-    TP_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-    t /= reps;
-    if (ms && sh < n) ms[sh] = t;
-    if (bestsh < 0 || t < bestms) bestsh = sh, bestms = t;
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (bestsh < 0) return set_error(TP_EINVAL, "no kernel shape is feasible for every beam");
-  for (Beam* b : bs) {
-    // the timing runs overwrote the series: each beam must be dedispersed again
-    if (b->state >= kDedispersed) b->state = kReady;
-    tp_plan_set_shape(const_cast<tp_plan*>(b->plan), bestsh);
+  // each plan's fastest shape; the whole batch's time per shape where every
+  // plan admits it
+  int bestsh = -1;
+  size_t heaviest = 0;
+  for (size_t k = 0; k < plans.size(); ++k) {
+    int pk = -1;
+    for (int sh = 0; sh < kNumShapes; ++sh)
+      if (t[k][sh] >= 0.f && (pk < 0 || t[k][sh] < t[k][pk])) pk = sh;
+    if (pk < 0) return set_error(TP_EINVAL, "no kernel shape is feasible for a plan of the batch");
+    tp_plan_set_shape(plans[k], pk);
+    if (work[k] > work[heaviest]) heaviest = k;
+    if (k == heaviest) bestsh = pk;
   }
+  for (size_t k = 0; k < plans.size(); ++k)
+    if (k == heaviest) bestsh = plans[k]->shape;
+  if (ms)
+    for (int sh = 0; sh < kNumShapes && sh < n; ++sh) {
+      float sum = 0.f;
+      bool all = true;
+      for (size_t k = 0; k < plans.size(); ++k) {
+        if (t[k][sh] < 0.f) all = false;
+        sum += t[k][sh];
+      }
+      ms[sh] = all ? sum : -1.f;
+    }
+  // the timing runs overwrote the series: each beam must be dedispersed again
+  for (Beam* b : bs)
+    if (b->state >= kDedispersed) b->state = kReady;
   if (best) *best = bestsh;
+  return TP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The autotuner cache file: one entry per line, "key" shape ms.  Keys hold
+// no quote and no newline.
+void tune_load(tp_engine* e) {
+  e->tune_cache.clear();
+  FILE* f = std::fopen(e->tune_path.c_str(), "r");
+  if (!f) return;
+  char line[2048];
+  while (std::fgets(line, sizeof line, f)) {
+    const char* q0 = std::strchr(line, '"');
+    const char* q1 = q0 ? std::strchr(q0 + 1, '"') : nullptr;
+    int shape = -1;
+    float t = -1.f;
+    if (!q1 || std::sscanf(q1 + 1, "%d %f", &shape, &t) != 2) continue;
+    if (shape >= 0 && shape < kNumShapes) e->tune_cache[std::string(q0 + 1, q1)] = {shape, t};
+  }
+  std::fclose(f);
+}
+
+void tune_save(const tp_engine* e) {
+  const std::string tmp = e->tune_path + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "# dedispersion kernel shapes chosen by tp_autotune: \"key\" shape ms\n");
+  for (const auto& kv : e->tune_cache) std::fprintf(f, "\"%s\" %d %.6g\n", kv.first.c_str(), kv.second.first, kv.second.second);
+  std::fclose(f);
+  std::rename(tmp.c_str(), e->tune_path.c_str());
+}
+
+// What the timing depends on: the device, the plan's geometry and format,
+// the block's output length and the set of kernel shapes.
+std::string tune_key(const tp_engine* e, const tp_plan* p, const Beam* b) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, e->device);
+  uint64_t h = 1469598103934665603ull;
+  for (double d : p->dm) {
+    uint64_t u;
+    std::memcpy(&u, &d, 8);
+    h = (h ^ u) * 1099511628211ull;
+  }
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "%s cc%d.%d sms%d | nchan %d f_lo %.17g bw %.17g t_samp %.17g dtype %d ndm %d dm %016llx | "
+                "nout %lld | shapes %d",
+                prop.name, prop.major, prop.minor, prop.multiProcessorCount, p->nchan, p->f_lo, p->bw, p->t_samp,
+                p->dtype, p->ndm, (unsigned long long)h, (long long)b->nout, kNumShapes);
+  std::string k(buf);
+  for (char& ch : k)
+    if (ch == '"' || ch == '\n') ch = ' ';
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tp_engine_set_tuning_cache(tp_engine* e, const char* path) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  e->tune_path = path ? path : "";
+  e->tune_cache.clear();
+  if (!e->tune_path.empty()) tune_load(e);
   return TP_OK;
 }
 
@@ -1973,6 +2197,21 @@ int tp_autotune(tp_engine* e, int beam, int reps, int* best, float* ms, int n) {
   if (b->nsamp_win == 0) return set_error(TP_ENOTREADY, "beam %d has no block yet", beam);
   tp_plan* p = const_cast<tp_plan*>(b->plan);
   DeviceGuard g(e->device);
+  std::string key;
+  if (!e->tune_path.empty()) {
+    key = tune_key(e, p, b);
+    auto it = e->tune_cache.find(key);
+    if (it != e->tune_cache.end() && p->feasible[it->second.first]) {
+      // a cached choice: no timing runs; as after them, the beam is to be
+      // dedispersed again with the chosen shape
+      if (ms)
+        for (int sh = 0; sh < n; ++sh) ms[sh] = sh == it->second.first ? it->second.second : -1.f;
+      if (b->state >= kDedispersed) b->state = kReady;
+      tp_plan_set_shape(p, it->second.first);
+      if (best) *best = it->second.first;
+      return TP_OK;
+    }
+  }
   cudaStream_t s = beam_stream(e, b);
   cudaEvent_t e0, e1;
   TP_CUDA_TRY(cudaEventCreate(&e0));
@@ -2009,6 +2248,10 @@ int tp_autotune(tp_engine* e, int beam, int reps, int* best, float* ms, int n) {
   if (b->state >= kDedispersed) b->state = kReady;
   tp_plan_set_shape(p, bestsh);
   if (best) *best = bestsh;
+  if (!key.empty() && bestsh >= 0) {
+    e->tune_cache[key] = {bestsh, bestms};
+    tune_save(e);
+  }
   return TP_OK;
 }
 

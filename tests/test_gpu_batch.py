@@ -119,9 +119,10 @@ def test_batched_grid_sizes_equal_solo(dtype, grid):
 
 @pytest.mark.parametrize("dtype", ["f32", "u8"])
 def test_batch_autotune_keeps_results(dtype):
-    """tp_autotune_batch picks a shape every plan admits; the batch run with
-    it gives the solo series exactly (every shape adds each output's channels
-    in index order, FP32 or exact integers) and the same candidates."""
+    """tp_autotune_batch picks for each plan a shape it admits (the heaviest
+    plan's is returned); the batch run with them gives the solo series exactly
+    (every shape adds each output's channels in index order, FP32 or exact
+    integers) and the same candidates."""
     import torch
     tp.build()
     B = 6000
@@ -136,10 +137,12 @@ def test_batch_autotune_keeps_results(dtype):
             tp.tp_push_block(e, b, bl[0])
         tp.tp_run_ready(e, use_graph=False)
         best, ms = tp.tp_autotune_batch(e, reps=1)
-        for p in plans:
+        work = [len(dms) for dms in PLANS]
+        for p, w in zip(plans, work):
             cur, feas = tp.tp_plan_shapes(p)
-            assert cur == best and feas[best]
-            assert ms[best] > 0 and all(ms[s] < 0 or ms[s] >= ms[best] for s in range(len(feas)))
+            assert feas[cur]
+            if w == max(work):
+                assert cur == best
         assert tp.tp_run_ready(e, use_graph=True) == len(beams)
         for i, (b, dms) in enumerate(zip(beams, PLANS)):
             c, n, rc = tp.tp_get_candidates(e, b, 1 << 16)
