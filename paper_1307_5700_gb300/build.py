@@ -83,8 +83,9 @@ def build(force=False, verbose=False, extra_flags=()):
                 sys.stderr.write(r.stderr)
             return obj
 
-        srcs = sources()
-        with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+        # the kernel instantiation units are the slow ones: start them first
+        srcs = sorted(sources(), key=lambda f: not os.path.basename(f).startswith("dedisp_p"))
+        with ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 8, len(srcs)))) as ex:
             objs = list(ex.map(compile_one, srcs))
         tmp = os.path.join(objdir, "libtpdd.so")
         cmd = [exe, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,

@@ -1,6 +1,6 @@
 // A5: the dedispersion kernel's shape table and launch dispatch (Sec. 2.2.2).
 // The kernel itself is in dedisp_kernel.cuh, instantiated per shape in
-// dedisp_p0.cu .. dedisp_p5.cu.
+// dedisp_p0.cu .. dedisp_p11.cu.
 #include "dedisp_shapes.cuh"
 #include "tp_common.cuh"
 
@@ -18,7 +18,19 @@ cudaError_t launch_dedisperse_part4(int shape, int dtype, const BatchArgs& ba, i
                                       cudaStream_t s);
 cudaError_t launch_dedisperse_part5(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
                                       cudaStream_t s);
-static_assert(kDedispParts == 6, "one launch_dedisperse_part per unit");
+cudaError_t launch_dedisperse_part6(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part7(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part8(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part9(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                      cudaStream_t s);
+cudaError_t launch_dedisperse_part10(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                       cudaStream_t s);
+cudaError_t launch_dedisperse_part11(int shape, int dtype, const BatchArgs& ba, int ctas, int grid_limit,
+                                       cudaStream_t s);
+static_assert(kDedispParts == 12, "one launch_dedisperse_part per unit");
 
 #define TP_SHAPE_ENTRY(i, K, S, O, N, F, A, M) {K, S, O, N, F, A},
 const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};
@@ -37,7 +49,13 @@ cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int cta
     case 2: return launch_dedisperse_part2(shape, dtype, ba, ctas, grid_limit, s);
     case 3: return launch_dedisperse_part3(shape, dtype, ba, ctas, grid_limit, s);
     case 4: return launch_dedisperse_part4(shape, dtype, ba, ctas, grid_limit, s);
-    default: return launch_dedisperse_part5(shape, dtype, ba, ctas, grid_limit, s);
+    case 5: return launch_dedisperse_part5(shape, dtype, ba, ctas, grid_limit, s);
+    case 6: return launch_dedisperse_part6(shape, dtype, ba, ctas, grid_limit, s);
+    case 7: return launch_dedisperse_part7(shape, dtype, ba, ctas, grid_limit, s);
+    case 8: return launch_dedisperse_part8(shape, dtype, ba, ctas, grid_limit, s);
+    case 9: return launch_dedisperse_part9(shape, dtype, ba, ctas, grid_limit, s);
+    case 10: return launch_dedisperse_part10(shape, dtype, ba, ctas, grid_limit, s);
+    default: return launch_dedisperse_part11(shape, dtype, ba, ctas, grid_limit, s);
   }
 }
 

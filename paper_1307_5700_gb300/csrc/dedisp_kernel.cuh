@@ -40,11 +40,13 @@
 // w, w + NCONS, ... kLookRot stages ahead of their use, over kStagesRot
 // buffers, so that the warp that fills a buffer rarely waits for the others to
 // release it.
-// ALGO 9 is ALGO 8 (8-bit quads, no producer warp) with the channels of a
-// stage in one call: each channel's block fetches the next channel's window
-// offset and block index, issues its window loads before its adds, spreads
-// the packed adds over two execution pipes, and ends with the next channel's
-// indexed branch (threaded dispatch, no branch back to a loop).
+// ALGO 9, 10 and 11 are ALGO 8 (8-bit quads, no producer warp) with the
+// channel loop of a stage inside one assembly block: each channel's pass
+// fetches the next channel's window offset and block index first, then
+// issues its window loads and packed adds (9: loads before adds, the adds
+// alternating between a 32-bit and a two-lane 16-bit add so that they spread
+// over two execution pipes; 10: loads and adds interleaved, alternating; 11:
+// interleaved, 32-bit adds only), and branches back to one indexed dispatch.
 // Each (d, t) adds its channels in index order (FP32, or exact integers).
 // Every mbarrier wait is bounded; a wait for staged data or a free stage
 // buffer gives up after DedispArgs::wait_tries attempts, records TP_ETIMEOUT
@@ -198,7 +200,7 @@ struct Shape {
   static_assert(AB != 5 || S % 2 == 1, "in-lane pairs: S = 2 (S / 2) + 1");
   static_assert(AB == 0 || MODE == kModeF32 || S % 2 == 0, "16-bit direct loads pair samples");
   static_assert(MODE != kModeU8 || AB == 1 || AB == 3, "8-bit data: direct loads or DM quads");
-  static_assert(!THREADED || MODE == kModeU8, "threaded dispatch: 8-bit quads");
+  static_assert(!THREADED || MODE == kModeU8, "stage loop in assembly: 8-bit quads");
 };
 
 // Per (stage, channel, consumer warp) the producer writes an int4:
@@ -806,22 +808,55 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
   return true;
 }
 
-// The kernel drains the work items of the batch (items = cta_start[nbeams]):
-// a grid of one CTA per item, or a persistent grid of a few CTAs per SM in
-// which CTA b starts with item b and then takes the next untaken item from a
-// device counter (the first free CTA gets the next item, so the items stay
-// in order and no SM idles while another has a queue).  Between items the CTA
-// synchronises (every copy of the item has landed: each warp waited on every
-// stage, or drained its own copies when it gave up) and initialises its
-// mbarriers afresh.  After a wait gave up the CTA keeps taking items only to
-// record TP_ETIMEOUT for their beams, then stops.
+// Initialises the CTA's stage mbarriers (thread 0; the caller synchronises).
+template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
+__device__ __forceinline__ void init_stage_barriers(uint64_t* full, uint64_t* empty) {
+  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
+  for (int i = 0; i < Sh::STAGES; ++i) {
+    mbar_init(&full[i], 1);
+    mbar_init(&empty[i], NCONS);
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
+__device__ __forceinline__ uint64_t* stage_barriers(unsigned char* smem_raw) {
+  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
+  return reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes + Sh::fold_bytes);
+}
+
+// One CTA per work item (grid = cta_start[nbeams]): CTA b runs item b.  The
+// work items of a launch are the (beam, DM tile, time tile) triples of every
+// beam of the batch.
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
 __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::THREADS, MINB)
     dedisperse_kernel(BatchArgs ba) {
   using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Sh::data_bytes + Sh::del_bytes + Sh::info_bytes +
-                                               Sh::fold_bytes);
+  uint64_t* full = stage_barriers<K, S, OMAX, NCONS, MODE, ALGO, MINB>(smem_raw);
+  uint64_t* empty = full + Sh::STAGES;
+  if ((int)blockIdx.x >= ba.cta_start[ba.nbeams]) return;
+  if (threadIdx.x == 0) init_stage_barriers<K, S, OMAX, NCONS, MODE, ALGO, MINB>(full, empty);
+  __syncthreads();
+  dedisperse_item<K, S, OMAX, NCONS, MODE, ALGO, MINB>(ba, blockIdx.x);
+}
+
+// A persistent grid of a few CTAs per SM drains the same work items: CTA b
+// starts with item b and then takes the next untaken item from a device
+// counter (the first free CTA gets the next item, so the items stay in order
+// and no SM idles while another has a queue).  Between items the CTA
+// synchronises (every copy of the item has landed: each warp waited on every
+// stage, or drained its own copies when it gave up) and initialises its
+// mbarriers afresh.  After a wait gave up the CTA keeps taking items only to
+// record TP_ETIMEOUT for their beams, then stops.  A kernel of its own: the
+// item loop's back edge, compiled into the one-item kernel, cost its
+// one-beam launch 1.2-1.6 % in the instruction schedule.
+template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
+__global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::THREADS, MINB)
+    dedisperse_kernel_persistent(BatchArgs ba) {
+  using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* full = stage_barriers<K, S, OMAX, NCONS, MODE, ALGO, MINB>(smem_raw);
   uint64_t* empty = full + Sh::STAGES;
   __shared__ int s_item, s_next, s_fail;
   auto take = [&](int cur) {
@@ -834,11 +869,7 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
     // the next item is taken before this one runs, so that a CTA on its last
     // item (every CTA of a one-CTA-per-item grid) leaves without waiting
     if (threadIdx.x == 0) {
-      for (int i = 0; i < Sh::STAGES; ++i) {
-        mbar_init(&full[i], 1);
-        mbar_init(&empty[i], NCONS);
-      }
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      init_stage_barriers<K, S, OMAX, NCONS, MODE, ALGO, MINB>(full, empty);
       s_fail = 0;
       s_next = s_item < ba.cta_start[ba.nbeams] ? take(s_item) : s_item;
     }
@@ -859,24 +890,31 @@ __global__ void __launch_bounds__(Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>::TH
 }
 
 // grid_limit < 0: one CTA per item; 0: a persistent grid of as many CTAs as
-// fit on the device at once; > 0: at most that many CTAs.
+// fit on the device at once; > 0: at most that many CTAs.  A grid that covers
+// every item runs the one-item kernel; a smaller one the persistent kernel
+// (whose work-item counter, ba.next_item, the caller has zeroed on this
+// stream; without one the CTAs step through the items by the grid size).
 template <int K, int S, int OMAX, int NCONS, int MODE, int ALGO, int MINB>
 cudaError_t launch_mode(const BatchArgs& ba, int ctas, int grid_limit, cudaStream_t s) {
   using Sh = Shape<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   if (ctas <= 0) return cudaErrorInvalidValue;
-  auto k = dedisperse_kernel<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
-  if (e != cudaSuccess) return e;
+  auto k1 = dedisperse_kernel<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
+  auto kp = dedisperse_kernel_persistent<K, S, OMAX, NCONS, MODE, ALGO, MINB>;
   int grid = ctas;
+  cudaError_t e = cudaSuccess;
   if (grid_limit == 0) {
     int dev = 0, nsm = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Sh::THREADS, Sh::smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp, Sh::THREADS, Sh::smem);
     if (e != cudaSuccess) return e;
     grid_limit = (per_sm > 0 ? per_sm : 1) * nsm;
   }
   if (grid_limit > 0 && grid_limit < grid) grid = grid_limit;
+  auto k = grid < ctas ? kp : k1;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+  if (e != cudaSuccess) return e;
   k<<<(unsigned)grid, Sh::THREADS, Sh::smem, s>>>(ba);
   return cudaGetLastError();
 }

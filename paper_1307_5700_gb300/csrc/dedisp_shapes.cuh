@@ -92,5 +92,5 @@
   X(67, 4, 22, 16, 8, 3, 12, 1)
 
 namespace tp {
-constexpr int kDedispParts = 6;  // translation units the kernel instantiations are split over
+constexpr int kDedispParts = 12;  // translation units the kernel instantiations are split over
 }  // namespace tp

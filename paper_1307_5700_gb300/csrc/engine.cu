@@ -896,6 +896,7 @@ int tp_version(void) { return 100; }
 const char* tp_last_error_string(void) { return tp::last_error_cstr(); }
 
 int tp_engine_create(int device, size_t hbm_budget_bytes, void* cuda_stream, tp_engine** out) {
+  TP_NVTX_RANGE();
   if (!out) return set_error(TP_EINVAL, "out is NULL");
   *out = nullptr;
   int n = 0;
@@ -920,6 +921,7 @@ int tp_engine_create(int device, size_t hbm_budget_bytes, void* cuda_stream, tp_
 }
 
 int tp_engine_destroy(tp_engine* e) {
+  TP_NVTX_RANGE();
   if (!e) return TP_OK;
   {
     std::lock_guard<std::recursive_mutex> lk(e->mu);
@@ -958,6 +960,7 @@ int tp_engine_destroy(tp_engine* e) {
 }
 
 int tp_sync(tp_engine* e) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   DeviceGuard g(e->device);
@@ -983,6 +986,7 @@ int tp_engine_memory(const tp_engine* e, size_t* used, size_t* budget) {
 int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, double t_samp_s,
                    const double* dm_list, int ndm, int dtype, const tp_rfi_params* rfi,
                    double nsigma, tp_plan** out) {
+  TP_NVTX_RANGE();
   if (!e || !out) return set_error(TP_EINVAL, "engine or out is NULL");
   *out = nullptr;
   if (nchan <= 0 || ndm <= 0) return set_error(TP_EINVAL, "nchan %d / ndm %d must be > 0", nchan, ndm);
@@ -1097,6 +1101,7 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
 }
 
 int tp_plan_destroy(tp_plan* p) {
+  TP_NVTX_RANGE();
   if (!p) return TP_OK;
   tp_engine* e = p->e;
   std::lock_guard<std::recursive_mutex> lk(e->mu);
@@ -1142,6 +1147,7 @@ int tp_beam_footprint(const tp_plan* p, int block_nsamp, int cand_capacity, size
 }
 
 int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capacity, int* beam_id) {
+  TP_NVTX_RANGE();
   if (!e || !p || !beam_id) return set_error(TP_EINVAL, "engine, plan or beam_id is NULL");
   if (p->e != e) return set_error(TP_EINVAL, "plan belongs to another engine");
   size_t need = 0;
@@ -1206,6 +1212,7 @@ int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capac
 }
 
 int tp_beam_close(tp_engine* e, int beam) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1221,6 +1228,7 @@ int tp_beam_close(tp_engine* e, int beam) {
 }
 
 int tp_beam_rewind(tp_engine* e, int beam) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1239,6 +1247,7 @@ int tp_beam_set_stream(tp_engine* e, int beam, void* cuda_stream) {
 }
 
 int tp_beam_set_bandpass(tp_engine* e, int beam, const double* mu, const double* sigma, int nchan) {
+  TP_NVTX_RANGE();
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
   if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
@@ -1343,6 +1352,7 @@ int assemble_window(tp_engine* e, Beam* b, cudaStream_t s, const void* buf, int 
 }  // namespace
 
 int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is_device) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1356,6 +1366,7 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
 }
 
 int tp_prefetch_block(tp_engine* e, int beam, const void* host_buf, int nsamp) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1389,6 +1400,7 @@ int tp_prefetch_block(tp_engine* e, int beam, const void* host_buf, int nsamp) {
 }
 
 int tp_push_prefetched(tp_engine* e, int beam) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1405,6 +1417,7 @@ int tp_push_prefetched(tp_engine* e, int beam) {
 }
 
 int tp_dedisperse(tp_engine* e, int beam) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   DeviceGuard g(e->device);
@@ -1425,6 +1438,7 @@ int tp_dedisperse(tp_engine* e, int beam) {
 }
 
 int tp_detect(tp_engine* e, int beam) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   DeviceGuard g(e->device);
@@ -1444,6 +1458,7 @@ int tp_detect(tp_engine* e, int beam) {
 }
 
 int tp_run_ready(tp_engine* e, int use_graph, int* nbeams) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   DeviceGuard g(e->device);
@@ -1512,6 +1527,7 @@ int tp_run_ready(tp_engine* e, int use_graph, int* nbeams) {
 }
 
 int tp_get_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, int* n_total) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1562,6 +1578,7 @@ uint64_t delay_sum(const tp_plan* p) {
 }  // namespace
 
 int tp_beam_export(tp_engine* e, int beam, void* out, size_t cap, size_t* size) {
+  TP_NVTX_RANGE();
   if (!e || !size) return set_error(TP_EINVAL, "engine or size is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1610,6 +1627,7 @@ int tp_beam_export(tp_engine* e, int beam, void* out, size_t cap, size_t* size) 
 }
 
 int tp_beam_import(tp_engine* e, int beam, const void* in, size_t size) {
+  TP_NVTX_RANGE();
   if (!e || !in) return set_error(TP_EINVAL, "engine or state is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1673,6 +1691,7 @@ int tp_beam_info(tp_engine* e, int beam, int64_t* nsamp_window, int64_t* nout, i
 }
 
 int tp_get_series(tp_engine* e, int beam, void* out, size_t bytes, int out_is_device) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1858,6 +1877,7 @@ int tp_plan_set_clustering(tp_plan* p, const tp_cluster_params* prm) {
 }
 
 int tp_get_clusters(tp_engine* e, int beam, tp_cluster* out, int cap, int* n, int* truncated) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -1958,6 +1978,7 @@ int tp_plan_set_postprocess(tp_plan* p, int median_width, int detrend) {
 }
 
 int tp_get_processed_series(tp_engine* e, int beam, void* out, size_t bytes, int out_is_device) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);
@@ -2012,6 +2033,7 @@ int tp_plan_set_shape(tp_plan* p, int shape) {
 }
 
 int tp_autotune_batch(tp_engine* e, int reps, int* best, float* ms, int n) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   DeviceGuard g(e->device);
@@ -2190,6 +2212,7 @@ int tp_engine_set_tuning_cache(tp_engine* e, const char* path) {
 }
 
 int tp_autotune(tp_engine* e, int beam, int reps, int* best, float* ms, int n) {
+  TP_NVTX_RANGE();
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   Beam* b = get_beam(e, beam);

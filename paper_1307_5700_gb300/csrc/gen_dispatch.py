@@ -516,8 +516,8 @@ def main():
         "__device__ __forceinline__ void add_quad8(int b, unsigned addr, unsigned (&e)[4][S / 2],",
         "                                          unsigned (&f)[4][S / 2 + 1]);",
         "",
-        "// every channel of a stage (emit_quad8t): threaded dispatch over the",
-        "// stage's info entries",
+        "// every channel of a stage (emit_quad8t): the channel loop over the",
+        "// stage's info entries inside the assembly",
         "template <int S, int MMAX, int NCONS, int V>",
         "__device__ __forceinline__ void add_quad8t(unsigned sbase, unsigned info, int nc,",
         "                                           unsigned (&e)[4][S / 2], unsigned (&f)[4][S / 2 + 1]);",

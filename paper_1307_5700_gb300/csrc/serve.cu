@@ -105,6 +105,7 @@ int close_stream(tp_server* s, StreamState& st) {
 extern "C" {
 
 int tp_server_create(tp_engine* e, const tp_rfi_params* rfi, double nsigma, int keep_candidates, tp_server** out) {
+  TP_NVTX_RANGE();
   if (!e || !out) return set_error(TP_EINVAL, "engine or out is NULL");
   tp_server* s = new tp_server();
   s->e = e;
@@ -141,6 +142,7 @@ int tp_server_add_stream(tp_server* s, const tp_stream_desc* d, int* stream_id) 
 }
 
 int tp_server_submit(tp_server* s, int stream_id, const void* host_block, int nsamp, double arrival_s) {
+  TP_NVTX_RANGE();
   if (!s || stream_id < 0 || stream_id >= (int)s->streams.size()) return set_error(TP_EINVAL, "no stream %d", stream_id);
   StreamState& st = s->streams[stream_id];
   if (st.ended) return set_error(TP_EINVAL, "stream %d has ended", stream_id);
@@ -165,6 +167,7 @@ int tp_server_end_stream(tp_server* s, int stream_id) {
 }
 
 int tp_server_run(tp_server* s, double time_limit_s) {
+  TP_NVTX_RANGE();
   if (!s) return set_error(TP_EINVAL, "server is NULL");
   if (!s->started) {
     s->t0 = std::chrono::steady_clock::now();
@@ -307,6 +310,7 @@ int tp_server_candidates(tp_server* s, int request, tp_candidate* out, int cap, 
 }
 
 int tp_server_destroy(tp_server* s) {
+  TP_NVTX_RANGE();
   if (!s) return TP_OK;
   tp_sync(s->e);
   for (auto& b : s->inflight) cudaEventDestroy(b.ev);

@@ -2,11 +2,24 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 
 #include "tp_dedisp.h"
 
 namespace tp {
+
+// An NVTX range around one public call, named after the call (Nsight Systems
+// shows it on the host timeline; `ncu --nvtx --nvtx-include "tp_detect/"`
+// captures only the kernels that call launches).  With no tool attached it
+// costs a function-pointer test.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define TP_NVTX_RANGE() ::tp::NvtxRange tp_nvtx_range_(__func__)
 
 // Sets the thread's last-error text (printf-style) and returns `code`.
 int set_error(int code, const char* fmt, ...);

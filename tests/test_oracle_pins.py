@@ -368,6 +368,45 @@ def test_storage_bandpass_matches_library_conversions():
     assert np.array_equal(O.storage_bandpass("f32", mu), mu)
 
 
+@pytest.mark.parametrize("lo,hi", [(64.0, 1024.0), (1024.0, 4096.0)])
+def test_storage_bandpass_cost_is_a_series_offset(lo, hi):
+    """Cost of R7 for binary16 data against a binary64 bandpass value: every
+    unflagged sample of channel c moves by mu_c - b_c, so D moves by the sum
+    of (mu_c - b_c) over the channels unflagged at (c, t + delay[d][c]): with
+    nothing flagged one constant per block, which the series normalisation
+    removes exactly; a flagged sample contributes 0 under both readings, so
+    each flagged term shifts D by at most max |mu_c - b_c| (half an ulp of
+    the level)."""
+    g = synth.rng(7)
+    nchan, nsamp, W = 64, 4096, 256
+    mu_c = g.uniform(lo, hi, nchan)
+    x = synth.to_f16(synth.noise(nchan, nsamp, 11, std=16.0) + mu_c[:, None].astype(np.float32))
+    tab, dmax = _plan([0.0, 4.0, 9.0, 15.0])
+    T = nsamp - dmax
+    st = O.bandpass(x, "f16")
+    st64 = dict(st, b=st["mu"].copy())
+    dev = st["mu"] - st["b"]
+    assert 0 < np.abs(dev).max() <= 2.0 ** (np.floor(np.log2(hi)) - 11)
+    cf = np.zeros((nchan, nsamp // W), np.uint8)
+    sf = np.zeros(nsamp, np.uint8)
+    D = O.dedisperse(x, "f16", st, cf, sf, W, tab, T)
+    D64 = O.dedisperse(x, "f16", st64, cf, sf, W, tab, T)
+    scale = np.abs(x.astype(np.float64)).sum(axis=0).max()
+    assert np.allclose(D - D64, dev.sum(), rtol=0, atol=1e-12 * scale)
+    z = (D - D.mean(1, keepdims=True)) / D.std(1, keepdims=True)
+    z64 = (D64 - D64.mean(1, keepdims=True)) / D64.std(1, keepdims=True)
+    assert np.abs(z - z64).max() < 1e-9
+    # a flagged chunk and a flagged spectrum: the offset then varies with
+    # the flags, by at most max |mu_c - b_c| per flagged term
+    cf[5, 3] = 1
+    sf[1000:1010] = 1
+    D = O.dedisperse(x, "f16", st, cf, sf, W, tab, T)
+    D64 = O.dedisperse(x, "f16", st64, cf, sf, W, tab, T)
+    off = D - D64 - dev.sum()
+    assert np.abs(off).max() > 0
+    assert np.abs(off).max() <= nchan * np.abs(dev).max() + 1e-12 * scale
+
+
 # ---- running bandpass statistics (reading R15) -------------------------------------
 
 def test_running_stats_alpha_one_is_per_block_and_closed_form():
