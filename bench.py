@@ -648,16 +648,41 @@ def run_stream(args, dtype, steps, warmup, e2e_on, peaks=None):
     beam = tp.tp_beam_open(e, plan, BLOCK, 1 << 20)
 
     host = [make_block(2000 + 17 * rank + i, delays, max_delay, dtype) for i in range(NBUF)]
-    dev_blocks = [torch.from_numpy(_raw(h)).to(dev) for h in host]
+    # device-resident inputs as a producer on the device would leave them:
+    # each block in its own buffer, after max_delay columns of headroom that
+    # the engine fills with the overlap tail (tp_push_inplace); --copy-push
+    # pushes the same blocks by copy instead
+    dev_bufs = []
+    for h in host:
+        t = torch.from_numpy(_raw(h)).to(dev)
+        es = t.element_size()
+        pitch = max_delay + BLOCK
+        pitch += (-pitch * es) % 256 // es
+        buf = torch.zeros((NCHAN, pitch), dtype=t.dtype, device=dev)
+        buf[:, max_delay:max_delay + BLOCK] = t
+        dev_bufs.append(buf)
+    dev_blocks = [b[:, max_delay:max_delay + BLOCK].contiguous() for b in dev_bufs] if args.copy_push else None
+    pushes = [0]
+
+    def push():
+        # consecutive blocks alternate the buffers (the next push copies the
+        # tail out of the previous one)
+        i = pushes[0] % NBUF
+        pushes[0] += 1
+        if args.copy_push:
+            tp.tp_push_block(e, beam, dev_blocks[i])
+        else:
+            tp.tp_push_inplace(e, beam, dev_bufs[i], BLOCK)
+
     # first block of the stream fills the overlap tail; not timed
-    tp.tp_push_block(e, beam, dev_blocks[0])
+    push()
     tp.tp_dedisperse(e, beam)
     tp.tp_detect(e, beam)
     tp.tp_get_candidates(e, beam, 0)
     # the second block has the steady-state length (the first yields
     # block - max_delay outputs, a different number of CTA waves): autotune
     # the dedispersion kernel shape on it
-    tp.tp_push_block(e, beam, dev_blocks[1 % NBUF])
+    push()
     tp.tp_dedisperse(e, beam)
     if args.shape is None:
         best, shape_ms = tp.tp_autotune(e, beam, reps=2)
@@ -669,17 +694,17 @@ def run_stream(args, dtype, steps, warmup, e2e_on, peaks=None):
     tp.tp_detect(e, beam)
     tp.tp_get_candidates(e, beam, 0)
 
-    def step(k, src, starts=None, ends=None):
+    def step(k, starts=None, ends=None):
         if starts is not None:
             starts[k].record(stream)
-        tp.tp_push_block(e, beam, src)
+        push()
         tp.tp_dedisperse(e, beam)
         tp.tp_detect(e, beam)
         if ends is not None:
             ends[k].record(stream)
 
     for k in range(warmup):
-        step(k, dev_blocks[(k + 1) % NBUF])
+        step(k)
     torch.cuda.synchronize(dev)
 
     # ---- device-resident timed region -------------------------------------------
@@ -695,7 +720,7 @@ def run_stream(args, dtype, steps, warmup, e2e_on, peaks=None):
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for k in range(steps):
-        step(k, dev_blocks[k % NBUF], starts, ends)
+        step(k, starts, ends)
     t_end.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -776,7 +801,7 @@ def run_stream(args, dtype, steps, warmup, e2e_on, peaks=None):
     tp.tp_beam_close(e, beam)
     tp.tp_plan_destroy(plan)
     tp.tp_engine_destroy(e)
-    del dev_blocks
+    del dev_bufs, dev_blocks
     torch.cuda.empty_cache()
     return {"value": value, "ms": ms, "steps": steps, "warmup": warmup, "dtype": dtype, "best": int(best),
             "tune": tune, "max_delay": int(max_delay), "delays": delays, "world": world, "rank": rank,
@@ -810,6 +835,8 @@ def main():
     ap.add_argument("--workload", default="stream", choices=["stream", "batch8", "wide16", "serve32"],
                     help="stream: the metric's 1-beam streaming workload (with the other forms); batch8: 8 "
                          "uneven beams batched; wide16: 16 wide-band 8-bit beams; serve32: the serving loop")
+    ap.add_argument("--copy-push", action="store_true",
+                    help="stream: push the device-resident blocks by copy (tp_push_block) instead of in place")
     ap.add_argument("--per-beam", action="store_true",
                     help="batch8: per-beam dedisperse/detect calls instead of the batched launch")
     ap.add_argument("--speedup", type=float, default=20.0,
@@ -878,6 +905,8 @@ def main():
         cpu = cpu_baselines(s["delays"], s["max_delay"])
     dtype = args.dtype
     cfg = stream_config(s["max_delay"], s["world"])
+    cfg["push"] = ("copy of each device-resident block (tp_push_block)" if args.copy_push else
+                   "in place: each block in its producer's buffer, the overlap tail copied in (tp_push_inplace)")
     if dtype != "f32":
         cfg["workload"] = WORKLOAD.replace("FP32", {"f16": "binary16", "bf16": "bfloat16", "u8": "8-bit",
                                                     "c16": "complex int16 voltages detected as power"}[dtype])

@@ -282,6 +282,25 @@ int tp_beam_set_bandpass(tp_engine *e, int beam, const double *mu, const double 
  * beam's previous detection (which may run on the engine stream). */
 int tp_push_block(tp_engine *e, int beam, const void *buf, int nsamp, int buf_is_device);
 
+/* Append a block that a device-side producer wrote into its own buffer, and
+ * process it where it lies (no copy of the block).  `buf` is device memory of
+ * the engine's device holding nchan rows of `pitch` elements in the plan's
+ * dtype; the block's nsamp samples of channel c sit in columns
+ * [max_delay, max_delay + nsamp) of row c (max_delay from tp_plan_info).  The
+ * engine writes the overlap tail of the previous block (Sec. 2.2.2: the last
+ * max_delay samples) into columns [0, max_delay) on the beam's stream, and
+ * the statistics and staging kernels then read the window from the buffer.
+ * The stream's first block (no overlap yet) is copied into the engine's
+ * window instead.  Ownership: the caller keeps the buffer unchanged (apart
+ * from the engine's tail) until the beam's next block has been pushed and the
+ * beam's stream has passed that push -- the next push copies this block's
+ * last max_delay samples out of it; consecutive blocks therefore alternate at
+ * least two buffers.  Results equal those of tp_push_block with the same
+ * samples.  Errors: TP_EINVAL (NULL, size, pitch < max_delay + nsamp, buf or
+ * pitch bytes not a multiple of 16, not device memory of the engine's device,
+ * buf holding the previous block), TP_EBUSY as tp_push_block. */
+int tp_push_inplace(tp_engine *e, int beam, void *buf, int64_t pitch, int nsamp);
+
 /* Double-buffered ingest (Sec. 2.1: the next GPU buffer is filled while the
  * current one is processed).  tp_prefetch_block starts the host -> device
  * copy of the next block's `nsamp` new samples per channel (`host_buf`,
@@ -482,6 +501,36 @@ int tp_engine_set_wait_limit(tp_engine *e, long long tries);
  * small grid so that every CTA takes many items); ctas < 0 one CTA per item.
  * Results do not depend on it.  Cached batch graphs are dropped. */
 int tp_engine_set_batch_grid(tp_engine *e, int ctas);
+
+/* ---- debugging aids (no compute-sanitizer: nothing here traps a GPU) ---------------
+ * Canary padding: with tp_engine_set_canaries(e, 1), every beam opened
+ * afterwards gets 256 bytes of the byte 0xA5 before each of its device buffers
+ * and after each buffer's nominal size (up to the next 256-byte boundary plus
+ * 256 bytes).  tp_engine_check_canaries synchronises the device and stores in
+ * *nbad how many of those pads (over the engine's open beams) no longer hold
+ * the pattern: a kernel wrote outside its buffer.  Padding costs 512 bytes
+ * per buffer, which the footprint (tp_beam_footprint) does not count.
+ * Errors: TP_EINVAL (NULL arguments), TP_ECUDA. */
+int tp_engine_set_canaries(tp_engine *e, int enable);
+int tp_engine_check_canaries(tp_engine *e, int *nbad);
+
+/* 1 when this is the bounds-checking build of the library
+ * (libtpdd_debug.so, compiled with TP_DEBUG_BOUNDS), else 0.  Its kernels
+ * check the accesses whose indices come from the plan's geometry, the delays
+ * or the data (the dedispersion kernel's bulk copies, delay copies, window
+ * geometry and D stores; the spectrum/substitution kernel's window loads and
+ * staged-series stores; the chunk statistics' window loads; the detection
+ * kernels' D reads and candidate writes): a failed check skips the access and
+ * records TP_EBOUNDS in the beam's status word, which the block's
+ * tp_get_candidates returns.  Nothing traps. */
+int tp_debug_bounds(void);
+
+/* Bounds-checking build only: the dedispersion kernel of `beam` treats the
+ * staged series as `bytes` long (bytes < 0: its real size), so that copies
+ * beyond it fail their check (and are skipped) while every access stays
+ * inside the real buffer.  Tests use it to see the checks fire.
+ * Errors: TP_EINVAL (no such beam; not the bounds-checking build). */
+int tp_debug_limit_staged(tp_engine *e, int beam, int64_t bytes);
 
 /* Kernels launched by the engine since it was created. */
 int tp_engine_launches(const tp_engine *e, uint64_t *n);

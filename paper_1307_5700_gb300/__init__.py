@@ -19,7 +19,9 @@ import numpy as np
 
 from . import build as _build
 
-LIB_PATH = _build.LIB
+# TP_DEBUG_BOUNDS=1 in the environment selects the bounds-checking build
+DEBUG_BOUNDS = os.environ.get("TP_DEBUG_BOUNDS", "") == "1"
+LIB_PATH = _build.LIB_DEBUG if DEBUG_BOUNDS else _build.LIB
 
 TP_OK = 0
 TP_EINVAL = -1
@@ -53,7 +55,8 @@ EXPORTS = (
     "tp_get_detrend", "tp_plan_set_bandpass_fit", "tp_get_bandpass_fit", "tp_plan_set_clustering",
     "tp_get_clusters", "tp_get_candidate_labels", "tp_prefetch_block", "tp_push_prefetched",
     "tp_get_batch_times", "tp_engine_set_wait_limit", "tp_plan_set_running_stats", "tp_engine_set_batch_grid",
-    "tp_beam_export", "tp_beam_import", "tp_engine_set_tuning_cache",
+    "tp_beam_export", "tp_beam_import", "tp_engine_set_tuning_cache", "tp_engine_set_canaries",
+    "tp_engine_check_canaries", "tp_debug_bounds", "tp_debug_limit_staged", "tp_push_inplace",
 )
 
 
@@ -114,6 +117,7 @@ _SIGS = {
     "tp_push_block": (_i, [_vp, _i, _vp, _i, _i]),
     "tp_prefetch_block": (_i, [_vp, _i, _vp, _i]),
     "tp_push_prefetched": (_i, [_vp, _i]),
+    "tp_push_inplace": (_i, [_vp, _i, _vp, ctypes.c_int64, _i]),
     "tp_dedisperse": (_i, [_vp, _i]),
     "tp_detect": (_i, [_vp, _i]),
     "tp_get_candidates": (_i, [_vp, _i, _vp, _i, _vp]),
@@ -131,6 +135,10 @@ _SIGS = {
     "tp_beam_export": (_i, [_vp, _i, _vp, _sz, _vp]),
     "tp_beam_import": (_i, [_vp, _i, _vp, _sz]),
     "tp_engine_set_tuning_cache": (_i, [_vp, ctypes.c_char_p]),
+    "tp_engine_set_canaries": (_i, [_vp, _i]),
+    "tp_engine_check_canaries": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "tp_debug_bounds": (_i, []),
+    "tp_debug_limit_staged": (_i, [_vp, _i, ctypes.c_int64]),
     "tp_engine_launches": (_i, [_vp, _vp]),
     "tp_plan_shapes": (_i, [_vp, _vp, _vp, _i]),
     "tp_plan_set_shape": (_i, [_vp, _i]),
@@ -162,9 +170,10 @@ _SIGS = {
 }
 
 
-def build(force=False):
-    """Compile the CUDA library for sm_103a (in-tree) and return its path."""
-    return _build.build(force=force)
+def build(force=False, debug=None):
+    """Compile the CUDA library for sm_103a (in-tree) and return its path
+    (debug: the bounds-checking variant; None: the one this process loads)."""
+    return _build.build(force=force, debug=DEBUG_BOUNDS if debug is None else debug)
 
 
 def lib():
@@ -315,6 +324,15 @@ def tp_push_block(e, beam, buf, nsamp=None, buf_is_device=None):
     return _check(lib().tp_push_block(e, beam, _addr(buf), int(nsamp), int(bool(buf_is_device))))
 
 
+def tp_push_inplace(e, beam, buf, nsamp, pitch=None):
+    """``buf``: a (nchan, pitch) torch CUDA tensor (or device address with
+    ``pitch`` given) whose columns [max_delay, max_delay + nsamp) hold the
+    block; the engine fills columns [0, max_delay) and reads it in place."""
+    if pitch is None:
+        pitch = buf.shape[-1]
+    return _check(lib().tp_push_inplace(e, beam, _addr(buf), int(pitch), int(nsamp)))
+
+
 def tp_prefetch_block(e, beam, host_buf, nsamp=None):
     """Start the copy of the next block from ``host_buf`` (a host numpy array
     or pinned torch tensor, (nchan, nsamp)); the caller keeps it unchanged
@@ -422,6 +440,29 @@ def tp_engine_set_tuning_cache(e, path):
     return _check(lib().tp_engine_set_tuning_cache(e, None if path is None else os.fsencode(path)))
 
 
+def tp_engine_set_canaries(e, enable):
+    """Canary padding around the buffers of beams opened from now on."""
+    return _check(lib().tp_engine_set_canaries(e, int(bool(enable))))
+
+
+def tp_engine_check_canaries(e):
+    """Number of damaged canary pads over the engine's open beams."""
+    n = ctypes.c_int()
+    _check(lib().tp_engine_check_canaries(e, ctypes.byref(n)))
+    return n.value
+
+
+def tp_debug_bounds():
+    """True when the loaded library is the bounds-checking build."""
+    return bool(lib().tp_debug_bounds())
+
+
+def tp_debug_limit_staged(e, beam, nbytes):
+    """Bounds-checking build: the staged-series extent the checks of `beam`
+    use (negative: the real one)."""
+    return _check(lib().tp_debug_limit_staged(e, beam, int(nbytes)))
+
+
 def tp_beam_export(e, beam):
     """The beam's stream state (bytes) for tp_beam_import."""
     n = ctypes.c_size_t()
@@ -457,9 +498,10 @@ def tp_engine_launches(e):
 def tp_plan_shapes(p):
     """(current shape, feasible flags per shape)."""
     sh = ctypes.c_int()
-    feas = np.zeros(64, np.int32)
-    n = _check(lib().tp_plan_shapes(p, ctypes.byref(sh), feas.ctypes.data, len(feas)))
-    return sh.value, feas[:n].astype(bool)
+    n = _check(lib().tp_plan_shapes(p, ctypes.byref(sh), None, 0))
+    feas = np.zeros(n, np.int32)
+    _check(lib().tp_plan_shapes(p, ctypes.byref(sh), feas.ctypes.data, n))
+    return sh.value, feas.astype(bool)
 
 
 def tp_plan_set_shape(p, shape):

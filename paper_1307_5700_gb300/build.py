@@ -6,6 +6,12 @@ Each ``csrc/*.cu`` translation unit is compiled in parallel with nvcc
 off in device code (``--fmad=false``) and in host code
 (``-ffp-contract=off``): the delay table, the 8-bit statistics and every
 threshold decision are specified operation by operation.
+
+``build(debug=True)`` makes the bounds-checking variant
+``paper_1307_5700_gb300/_build_debug/libtpdd_debug.so`` (``-DTP_DEBUG_BOUNDS``):
+its kernels check the accesses whose indices come from the plan's geometry,
+the delays or the data and record TP_EBOUNDS instead of making them.  The
+binding loads it when the environment variable TP_DEBUG_BOUNDS is 1.
 """
 import glob
 import os
@@ -21,6 +27,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtpdd.so")
+OUT_DIR_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DIR_DEBUG, "libtpdd_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
@@ -46,10 +54,10 @@ def _inputs():
         os.path.abspath(__file__), os.path.join(CSRC, "gen_dispatch.py")]
 
 
-def stale():
-    if not os.path.exists(LIB):
+def stale(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _inputs())
 
 
@@ -61,15 +69,18 @@ def generate():
         subprocess.run([sys.executable, gen], check=True)
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile and link the library if it is missing or older than its
-    sources; returns the library path."""
+def build(force=False, verbose=False, extra_flags=(), debug=False):
+    """Compile and link the library (``debug``: its bounds-checking variant)
+    if it is missing or older than its sources; returns the library path."""
     generate()
-    if not force and not stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    out_dir, lib = (OUT_DIR_DEBUG, LIB_DEBUG) if debug else (OUT_DIR, LIB)
+    if debug:
+        extra_flags = ("-DTP_DEBUG_BOUNDS", *extra_flags)
+    if not force and not stale(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     exe = nvcc()
-    objdir = tempfile.mkdtemp(prefix="obj_", dir=OUT_DIR)
+    objdir = tempfile.mkdtemp(prefix="obj_", dir=out_dir)
     try:
         def compile_one(src):
             obj = os.path.join(objdir, os.path.basename(src) + ".o")
@@ -87,17 +98,17 @@ def build(force=False, verbose=False, extra_flags=()):
         srcs = sorted(sources(), key=lambda f: not os.path.basename(f).startswith("dedisp_p"))
         with ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 8, len(srcs)))) as ex:
             objs = list(ex.map(compile_one, srcs))
-        tmp = os.path.join(objdir, "libtpdd.so")
+        tmp = os.path.join(objdir, os.path.basename(lib))
         cmd = [exe, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stderr)
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     finally:
         shutil.rmtree(objdir, ignore_errors=True)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -265,7 +265,8 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
       const int c = st * kNC + ci;
 #pragma unroll
       for (int h = 0; h < DW; h += 32) {
-        const bool v = st < nstage && c < nchan && lane + h < dt.nd;
+        const bool v = st < nstage && c < nchan && lane + h < dt.nd &&
+                       in_bounds((int64_t)c * a.dtpitch + dt.d0 + h + lane, 1, a.delayT_elems, a.status);
         cp_async4(slot + ci * DW + h + lane, v ? dT + (int64_t)c * a.dtpitch + dt.d0 + h + lane : dT, v);
       }
     }
@@ -374,6 +375,16 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
       const int head = (t0m + lo) & (QS - 1);  // row start = t0 + lo - head
       nb = (unsigned)(((TT + hi - lo + QS + head) * EB + 15) & ~15);
       src = ((int64_t)(i * kNC + lane) * a.ypitch + t0 + lo - head) * EB;
+      if constexpr (kDebugBounds) {
+        // the copy fits its shared-memory row and stays inside the channel's
+        // row of the staged series, and the row holds every DM of the tile
+        // (delays non-decreasing over the tile's DMs); else it is skipped
+        bool ok = in_bounds(0, nb, ROWB, a.status) &&
+                  in_bounds(src - (int64_t)(i * kNC + lane) * a.ypitch * EB, nb, a.ypitch * EB, a.status) &&
+                  in_bounds(src, nb, a.y_bytes, a.status);
+        for (int j = 0; ok && j <= last; ++j) ok = in_bounds(del[lane * DW + j] - lo, 1, hi - lo + 1, a.status);
+        if (!ok) nb = 0;
+      }
     }
     const unsigned total = __reduce_add_sync(0xffffffffu, nb);
     if (lane == 0) mbar_arrive_expect_tx(&full[buf], total);
@@ -753,7 +764,7 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         const int v = (U8D ? sum32[j][U8D ? s : 0] : U8Q ? myfold[(j * S + s) * 32] : __float2int_rn(outv(j, 0, s))) - bint;
-        if (tl + s < a.nout) {
+        if (tl + s < a.nout && in_bounds((int64_t)d * a.dpitch + tl + s, 1, a.d_elems, a.status)) {
           Drow[tl + s] = v;
           s1 += v;
           s2 += (long long)v * v;
@@ -764,7 +775,8 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, off);
         s2 += __shfl_xor_sync(0xffffffffu, s2, off);
       }
-      if (lane == 0) static_cast<longlong2*>(a.row_part)[(int64_t)d * a.ntt + tt] = make_longlong2(s1, s2);
+      if (lane == 0 && in_bounds((int64_t)d * a.ntt + tt, 1, (int64_t)a.ndm * a.ntt, a.status))
+        static_cast<longlong2*>(a.row_part)[(int64_t)d * a.ntt + tt] = make_longlong2(s1, s2);
     } else {
       float* Drow = static_cast<float*>(a.D) + (int64_t)d * a.dpitch;
       float s1 = 0.f, s2 = 0.f;
@@ -777,6 +789,9 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
           v[s] = outv(j, seg, s);
           if constexpr (MODE != kModeF32) v[s] = (v[s] - bhi) - blo;
         }
+        if (!in_bounds((int64_t)d * a.dpitch + ts, ts + S <= a.nout ? S : (ts < a.nout ? a.nout - ts : 0),
+                       a.d_elems, a.status))
+          continue;
         if (S % 4 == 0 && ts + S <= a.nout) {
 #pragma unroll
           for (int s = 0; s < (S / 4) * 4; s += 4)
@@ -801,7 +816,7 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, off);
         s2 += __shfl_xor_sync(0xffffffffu, s2, off);
       }
-      if (lane == 0)
+      if (lane == 0 && in_bounds((int64_t)d * a.ntt + tt, 1, (int64_t)a.ndm * a.ntt, a.status))
         static_cast<double2*>(a.row_part)[(int64_t)d * a.ntt + tt] = make_double2((double)s1, (double)s2);
     }
   }

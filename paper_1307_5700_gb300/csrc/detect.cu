@@ -396,6 +396,11 @@ __global__ void __launch_bounds__(kThreads) detect_count(DetectArgs a) {
   const int d = blockIdx.y;
   const int64_t t0 = (int64_t)blockIdx.x * kDetectT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the CTA reads row d of the series in [0, nout) and writes its words of
+  // row d of the hit bitmap
+  if (!in_bounds(0, a.nout, a.dpitch, a.status) || !in_bounds((int64_t)d * a.dpitch, a.nout, a.d_elems, a.status) ||
+      !in_bounds((int64_t)d * a.hit_pitch, a.hit_pitch, a.hit_elems, a.status))
+    return;
   const float tf = a.row_thr_f[d];
   const int ti = a.row_thr_i[d];
   const void* S = det_series(a);
@@ -521,6 +526,9 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
   if (cnt == 0) return;
   const uint64_t base = a.blk_off[(int64_t)d * a.nblk_t + blockIdx.x];
   if (base >= (uint64_t)a.cap) return;
+  if (!in_bounds((int64_t)d * a.dpitch, a.nout, a.d_elems, a.status) ||
+      !in_bounds((int64_t)d * a.hit_pitch, a.hit_pitch, a.hit_elems, a.status))
+    return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ uint32_t s_pre[kPer * kWarps];
   uint32_t words[kPer];
@@ -559,8 +567,8 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
     if ((w >> lane) & 1u) {
       const uint32_t rank = s_pre[j * kWarps + warp] + __popc(w & ((1u << lane) - 1u));
       const uint64_t pos = base + rank;
-      if (pos < (uint64_t)a.cap) {
-        const int64_t t = t0 + 32 * ((int64_t)j * kWarps + warp) + lane;
+      const int64_t t = t0 + 32 * ((int64_t)j * kWarps + warp) + lane;
+      if (pos < (uint64_t)a.cap && in_bounds(t, 1, a.nout, a.status)) {
         const double v = a.is_int ? (double)static_cast<const int*>(S)[(int64_t)d * a.dpitch + t]
                                   : (double)static_cast<const float*>(S)[(int64_t)d * a.dpitch + t];
         tp_candidate r;

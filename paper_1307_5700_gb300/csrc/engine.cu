@@ -197,8 +197,16 @@ struct Beam {
   unsigned long long* n_total = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
+  // canary padding (tp_engine_set_canaries): each buffer's first byte and its
+  // nominal size; kCanaryBytes of kCanaryByte sit before and after it
+  std::vector<std::pair<unsigned char*, size_t>> canaries;
+  int64_t dbg_y_bytes = -1;  // debug build: staged-series extent the checks use (tp_debug_limit_staged)
   // stream state
   int cur = 0;
+  // the current window's first sample and row pitch (elements): win[cur], or
+  // the caller's buffer after tp_push_inplace
+  const void* xwin = nullptr;
+  int64_t xpitch = 0;
   int64_t nsamp_win = 0;
   int64_t nout = 0;
   int64_t t0_abs = 0;
@@ -274,6 +282,7 @@ struct tp_engine {
   // autotuner cache (tp_engine_set_tuning_cache): key -> (shape, ms per launch)
   std::string tune_path;
   std::map<std::string, std::pair<int, float>> tune_cache;
+  bool canaries = false;  // beams opened from now on get canary padding
   int batch_grid = 0;  // batched dedispersion grid: 0 persistent, > 0 at most that many CTAs, < 0 one per item
   uint64_t launches = 0;
   void* d_batch = nullptr;  // batch arguments for launches outside graphs
@@ -397,10 +406,22 @@ Beam* get_beam(tp_engine* e, int id) {
   return e->beams[id];
 }
 
+struct SizeItem {
+  void** ptr;
+  size_t bytes;    // allocated (multiple of 256)
+  size_t nominal;  // what the buffer's layout needs
+};
+
 struct Sizes {
   size_t total = 0;
-  std::vector<std::pair<void**, size_t>> items;
+  std::vector<SizeItem> items;
 };
+
+// Canary padding around a beam's buffers (debugging aid, off by default):
+// kCanaryBytes of kCanaryByte before each buffer and after its nominal size.
+constexpr size_t kCanaryBytes = 256;
+constexpr size_t kMaxGraphs = 64;  // cached batch graphs per engine
+constexpr unsigned char kCanaryByte = 0xA5;
 
 // Every device buffer of a beam, in one place (footprint and allocation).
 void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
@@ -423,8 +444,9 @@ void beam_layout(const tp_plan* p, int B, int cap, Beam* b, Sizes* out) {
   b->ypitch = ypitch;
   const size_t nc = (size_t)p->nchan, nd = (size_t)p->ndm;
   auto add = [&](void** ptr, size_t bytes) {
+    const size_t nominal = bytes;
     bytes = round_up(std::max<size_t>(bytes, 1), 256);
-    out->items.push_back({ptr, bytes});
+    out->items.push_back({ptr, bytes, nominal});
     out->total += bytes;
   };
   add(&b->win[0], nc * (size_t)pitch * es);
@@ -507,6 +529,7 @@ void free_beam(Beam* b) {
   if (b->ev_pushed) cudaEventDestroy(b->ev_pushed);
   for (void* p : b->allocs) cudaFree(p);
   b->allocs.clear();
+  b->canaries.clear();
 }
 
 cudaStream_t beam_stream(const tp_engine* e, const Beam* b) { return b->stream ? b->stream : e->stream; }
@@ -557,8 +580,8 @@ void prof_record(tp_engine* e, Beam* b, int which, cudaStream_t s) {
 
 RfiArgs rfi_args(const tp_plan* p, Beam* b) {
   RfiArgs a{};
-  a.x = b->win[b->cur];
-  a.pitch = b->pitch;
+  a.x = b->xwin;
+  a.pitch = b->xpitch;
   a.nchan = p->nchan;
   a.nsamp = b->nsamp_win;
   a.W = p->rfi.chunk_width;
@@ -605,6 +628,9 @@ RfiArgs rfi_args(const tp_plan* p, Beam* b) {
   a.run_prev_var = b->run_var[cur ^ 1];
   a.run_mu = b->run_mu[cur];
   a.run_var = b->run_var[cur];
+  a.status = b->status;
+  a.x_elems = (int64_t)p->nchan * b->xpitch;
+  a.y_elems = (int64_t)p->nchan * b->ypitch;
   return a;
 }
 
@@ -629,6 +655,10 @@ DedispArgs dedisp_args(const tp_plan* p, Beam* b) {
   da.row_part = b->row_part;
   da.status = b->status;
   da.wait_tries = p->e->wait_tries;
+  da.y_bytes = (int64_t)p->nchan * b->ypitch * staged_bytes_alloc(p->dtype);
+  if (b->dbg_y_bytes >= 0 && b->dbg_y_bytes < da.y_bytes) da.y_bytes = b->dbg_y_bytes;
+  da.d_elems = (int64_t)p->ndm * b->dpitch;
+  da.delayT_elems = (int64_t)p->nchan * p->ndm;
   return da;
 }
 
@@ -713,6 +743,9 @@ int issue_detect(tp_engine* e, Beam* b, cudaStream_t s) {
   a.M = b->M;
   a.post_part = b->post_part;
   a.row_beta = b->row_beta;
+  a.status = b->status;
+  a.d_elems = (int64_t)p->ndm * b->dpitch;
+  a.hit_elems = (int64_t)p->ndm * b->hit_pitch;
   TP_CUDA_TRY(launch_detect(a, s));
   e->launches += (p->median_width > 1 || p->detrend) ? 5 : 4;
   if (p->cluster) {
@@ -774,7 +807,7 @@ BatchPlan plan_batch(tp_engine* e) {
     const int mx = x->plan->dtype == TP_BF16, my = y->plan->dtype == TP_BF16;
     return x->plan->shape != y->plan->shape ? x->plan->shape < y->plan->shape : mx < my;
   });
-  char tmp[96];
+  char tmp[160];
   for (size_t i = 0; i < ready.size(); ++i) {
     Beam* b = ready[i];
     const bool start = i == 0 || ready[i - 1]->plan->shape != b->plan->shape ||
@@ -789,8 +822,8 @@ BatchPlan plan_batch(tp_engine* e) {
       return bp;
     }
     bp.args.push_back(da);
-    snprintf(tmp, sizeof tmp, "%d:%d:%lld:%d:%d;", b->id, b->cur, (long long)b->nout, b->plan->shape,
-             (int)b->plan->h_tiles.size());
+    snprintf(tmp, sizeof tmp, "%d:%p:%lld:%lld:%d:%d;", b->id, b->xwin, (long long)b->xpitch,
+             (long long)b->nout, b->plan->shape, (int)b->plan->h_tiles.size());
     bp.key += tmp;
   }
   for (auto& g : bp.groups) {
@@ -1166,15 +1199,23 @@ int tp_beam_open(tp_engine* e, const tp_plan* p, int block_nsamp, int cand_capac
   beam_layout(p, block_nsamp, cand_capacity, b, &sz);
   for (auto& it : sz.items) {
     void* ptr = nullptr;
-    cudaError_t ce = cudaMalloc(&ptr, it.second);
+    const size_t pad = e->canaries ? kCanaryBytes : 0;
+    const size_t bytes = it.bytes + 2 * pad;
+    cudaError_t ce = cudaMalloc(&ptr, bytes);
+    if (ce == cudaSuccess) b->allocs.push_back(ptr);
+    if (ce == cudaSuccess && pad) {
+      unsigned char* base = static_cast<unsigned char*>(ptr);
+      ce = cudaMemset(base, kCanaryByte, pad);
+      if (ce == cudaSuccess) ce = cudaMemset(base + pad + it.nominal, kCanaryByte, bytes - pad - it.nominal);
+      b->canaries.push_back({base + pad, it.nominal});
+    }
     if (ce != cudaSuccess) {
       cudaGetLastError();
       free_beam(b);
       delete b;
-      return set_error(TP_ENOMEM, "cudaMalloc(%zu): %s", it.second, cudaGetErrorString(ce));
+      return set_error(TP_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(ce));
     }
-    b->allocs.push_back(ptr);
-    *it.first = ptr;
+    *it.ptr = static_cast<unsigned char*>(ptr) + pad;
   }
   cudaError_t ce = cudaMemset(b->y, 0, (size_t)p->nchan * b->ypitch * (size_t)staged_bytes_alloc(p->dtype));
   if (ce == cudaSuccess) ce = cudaMemset(b->status, 0, 4);
@@ -1296,13 +1337,18 @@ int check_push(const Beam* b, int nsamp, int beam) {
 
 // Assembles the next window on stream s: the overlap tail of the current
 // window, then (unless the new samples are already in place) the new block
-// from `buf`; then publishes the block (t0, events, state).
-int assemble_window(tp_engine* e, Beam* b, cudaStream_t s, const void* buf, int nsamp, int buf_is_device) {
+// from `buf` (row pitch `spitch` bytes); then publishes the block (t0, events,
+// state).  inplace_pitch > 0 (tp_push_inplace): from the stream's second
+// block on, the window is the caller's buffer itself (row pitch inplace_pitch
+// elements), which receives only the tail in its first max_delay columns.
+int assemble_window(tp_engine* e, Beam* b, cudaStream_t s, const void* buf, size_t spitch, int nsamp,
+                    int buf_is_device, int64_t inplace_pitch = 0) {
   const tp_plan* p = b->plan;
   const int64_t dmax = p->max_delay;
   const size_t es = dtype_size(p->dtype);
   const cudaMemcpyKind kind = buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t dpitch = (size_t)b->pitch * es;
+  const size_t rowb = (size_t)nsamp * es;
   // on its own stream, a push must not overwrite the window, t0 or buffers
   // while the beam's previous batch may still run on the engine stream
   if (s != e->stream && b->pushed > 0) TP_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_detect, 0));
@@ -1311,27 +1357,35 @@ int assemble_window(tp_engine* e, Beam* b, cudaStream_t s, const void* buf, int 
   if (b->pushed == 0) {
     b->cur = 0;
     if (buf && buf_is_device)
-      TP_CUDA_TRY(copy_rows(b->win[0], dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan, s, &nk));
+      TP_CUDA_TRY(copy_rows(b->win[0], dpitch, buf, spitch, rowb, p->nchan, s, &nk));
     else if (buf)
-      TP_CUDA_TRY(cudaMemcpy2DAsync(b->win[0], dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
-                                    kind, s));
+      TP_CUDA_TRY(cudaMemcpy2DAsync(b->win[0], dpitch, buf, spitch, rowb, p->nchan, kind, s));
+    b->xwin = b->win[0];
+    b->xpitch = b->pitch;
     b->nsamp_win = nsamp;
     b->nout = nsamp - dmax;
     b->t0_abs = 0;
   } else {
-    const int nxt = b->cur ^ 1;
-    char* dst = static_cast<char*>(b->win[nxt]);
-    if (dmax > 0) {
-      const char* src = static_cast<const char*>(b->win[b->cur]) + (size_t)(b->nsamp_win - dmax) * es;
-      TP_CUDA_TRY(copy_rows(dst, dpitch, src, dpitch, (size_t)dmax * es, p->nchan, s, &nk));
+    const char* tail = static_cast<const char*>(b->xwin) + (size_t)(b->nsamp_win - dmax) * es;
+    const size_t tpitch = (size_t)b->xpitch * es;
+    if (inplace_pitch > 0) {
+      char* dst = static_cast<char*>(const_cast<void*>(buf));
+      if (dmax > 0)
+        TP_CUDA_TRY(copy_rows(dst, (size_t)inplace_pitch * es, tail, tpitch, (size_t)dmax * es, p->nchan, s, &nk));
+      b->xwin = buf;
+      b->xpitch = inplace_pitch;
+    } else {
+      const int nxt = b->cur ^ 1;
+      char* dst = static_cast<char*>(b->win[nxt]);
+      if (dmax > 0) TP_CUDA_TRY(copy_rows(dst, dpitch, tail, tpitch, (size_t)dmax * es, p->nchan, s, &nk));
+      if (buf && buf_is_device)
+        TP_CUDA_TRY(copy_rows(dst + (size_t)dmax * es, dpitch, buf, spitch, rowb, p->nchan, s, &nk));
+      else if (buf)
+        TP_CUDA_TRY(cudaMemcpy2DAsync(dst + (size_t)dmax * es, dpitch, buf, spitch, rowb, p->nchan, kind, s));
+      b->cur = nxt;
+      b->xwin = b->win[nxt];
+      b->xpitch = b->pitch;
     }
-    if (buf && buf_is_device)
-      TP_CUDA_TRY(copy_rows(dst + (size_t)dmax * es, dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es, p->nchan,
-                            s, &nk));
-    else if (buf)
-      TP_CUDA_TRY(cudaMemcpy2DAsync(dst + (size_t)dmax * es, dpitch, buf, (size_t)nsamp * es, (size_t)nsamp * es,
-                                    p->nchan, kind, s));
-    b->cur = nxt;
     b->nsamp_win = dmax + nsamp;
     b->nout = nsamp;
     b->t0_abs = b->pushed - dmax;
@@ -1362,7 +1416,42 @@ int tp_push_block(tp_engine* e, int beam, const void* buf, int nsamp, int buf_is
   const int rc = check_push(b, nsamp, beam);
   if (rc != TP_OK) return rc;
   DeviceGuard g(e->device);
-  return assemble_window(e, b, beam_stream(e, b), buf, nsamp, buf_is_device);
+  return assemble_window(e, b, beam_stream(e, b), buf, (size_t)nsamp * dtype_size(b->plan->dtype), nsamp,
+                         buf_is_device);
+}
+
+int tp_push_inplace(tp_engine* e, int beam, void* buf, int64_t pitch, int nsamp) {
+  TP_NVTX_RANGE();
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (!buf) return set_error(TP_EINVAL, "buf is NULL");
+  if (b->pf_pending) return set_error(TP_EBUSY, "beam %d has a prefetched block to push first", beam);
+  const int rc = check_push(b, nsamp, beam);
+  if (rc != TP_OK) return rc;
+  const tp_plan* p = b->plan;
+  const size_t es = dtype_size(p->dtype);
+  if (pitch < p->max_delay + (int64_t)nsamp)
+    return set_error(TP_EINVAL, "pitch %lld below max_delay + nsamp = %lld", (long long)pitch,
+                     (long long)(p->max_delay + nsamp));
+  // the kernels load the window in 16-byte units
+  if ((reinterpret_cast<uintptr_t>(buf) | (uintptr_t)((size_t)pitch * es)) % 16 != 0)
+    return set_error(TP_EINVAL, "buf and the row pitch (%lld elements) must be 16-byte multiples", (long long)pitch);
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, buf) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
+      attr.device != e->device) {
+    cudaGetLastError();
+    return set_error(TP_EINVAL, "buf is not device memory of the engine's device");
+  }
+  // the previous block's samples (the tail to copy) live in its own buffer
+  if (b->pushed > 0 && buf == b->xwin)
+    return set_error(TP_EINVAL, "buf holds the previous block: alternate at least two buffers");
+  DeviceGuard g(e->device);
+  const char* block = static_cast<const char*>(buf) + (size_t)p->max_delay * es;
+  if (b->pushed == 0)  // the stream's first block: copied into the engine's window
+    return assemble_window(e, b, beam_stream(e, b), block, (size_t)pitch * es, nsamp, 1);
+  return assemble_window(e, b, beam_stream(e, b), buf, (size_t)pitch * es, nsamp, 1, pitch);
 }
 
 int tp_prefetch_block(tp_engine* e, int beam, const void* host_buf, int nsamp) {
@@ -1411,7 +1500,7 @@ int tp_push_prefetched(tp_engine* e, int beam) {
   DeviceGuard g(e->device);
   cudaStream_t s = beam_stream(e, b);
   TP_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_pf, 0));
-  const int r = assemble_window(e, b, s, nullptr, b->pf_nsamp, 0);
+  const int r = assemble_window(e, b, s, nullptr, 0, b->pf_nsamp, 0);
   if (r == TP_OK) b->pf_pending = false;
   return r;
 }
@@ -1509,6 +1598,16 @@ int tp_run_ready(tp_engine* e, int use_graph, int* nbeams) {
       cudaFree(ge.d_args);
       return cuda_error(ce, "cudaGraphInstantiate");
     }
+    if (e->graphs.size() >= kMaxGraphs) {
+      // a bounded cache: in-place windows make the key change with the
+      // caller's buffers
+      TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
+      for (auto& kv : e->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaFree(kv.second.d_args);
+      }
+      e->graphs.clear();
+    }
     it = e->graphs.emplace(bp.key, ge).first;
   }
   TP_CUDA_TRY(cudaGraphLaunch(it->second.exec, e->stream));
@@ -1540,7 +1639,9 @@ int tp_get_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, int* n
   TP_CUDA_TRY(cudaMemcpy(&status, b->status, 4, cudaMemcpyDeviceToHost));
   if (status != 0) {
     TP_CUDA_TRY(cudaMemset(b->status, 0, 4));
-    return set_error(status, "beam %d: a device-side wait gave up (status %d)", beam, status);
+    return set_error(status, status == TP_EBOUNDS ? "beam %d: a device-side bounds check failed (status %d)"
+                                                  : "beam %d: a device-side wait gave up (status %d)",
+                     beam, status);
   }
   unsigned long long tot = 0;
   TP_CUDA_TRY(cudaMemcpy(&tot, b->n_total, 8, cudaMemcpyDeviceToHost));
@@ -1614,8 +1715,8 @@ int tp_beam_export(tp_engine* e, int beam, void* out, size_t cap, size_t* size) 
   std::memcpy(o, &h, sizeof h);
   if (tail) {
     const size_t rowb = (size_t)p->max_delay * es;
-    const char* src = static_cast<const char*>(b->win[b->cur]) + (size_t)(b->nsamp_win - p->max_delay) * es;
-    TP_CUDA_TRY(cudaMemcpy2D(o + sizeof h, rowb, src, (size_t)b->pitch * es, rowb, p->nchan, cudaMemcpyDeviceToHost));
+    const char* src = static_cast<const char*>(b->xwin) + (size_t)(b->nsamp_win - p->max_delay) * es;
+    TP_CUDA_TRY(cudaMemcpy2D(o + sizeof h, rowb, src, (size_t)b->xpitch * es, rowb, p->nchan, cudaMemcpyDeviceToHost));
   }
   if (run) {
     const int cur = (int)(b->nblocks & 1);
@@ -1668,6 +1769,8 @@ int tp_beam_import(tp_engine* e, int beam, const void* in, size_t size) {
   // the window now holds only the overlap tail: the next push continues the
   // stream from it exactly as after the exported block
   b->cur = 0;
+  b->xwin = b->win[0];
+  b->xpitch = b->pitch;
   b->nsamp_win = p->max_delay;
   b->nout = 0;
   b->pushed = h.pushed;
@@ -1828,6 +1931,51 @@ int tp_engine_set_batch_grid(tp_engine* e, int ctas) {
     cudaFree(kv.second.d_args);
   }
   e->graphs.clear();
+  return TP_OK;
+}
+
+int tp_engine_set_canaries(tp_engine* e, int enable) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  e->canaries = enable != 0;
+  return TP_OK;
+}
+
+int tp_engine_check_canaries(tp_engine* e, int* nbad) {
+  TP_NVTX_RANGE();
+  if (!e || !nbad) return set_error(TP_EINVAL, "engine or nbad is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  DeviceGuard g(e->device);
+  *nbad = 0;
+  // every stream of the engine's beams may still write: wait for the device
+  TP_CUDA_TRY(cudaDeviceSynchronize());
+  std::vector<unsigned char> buf;
+  for (Beam* b : e->beams) {
+    if (!b) continue;
+    for (const auto& c : b->canaries) {
+      const size_t tail = round_up(std::max<size_t>(c.second, 1), 256) - c.second + kCanaryBytes;
+      buf.resize(kCanaryBytes + tail);
+      TP_CUDA_TRY(cudaMemcpy(buf.data(), c.first - kCanaryBytes, kCanaryBytes, cudaMemcpyDeviceToHost));
+      TP_CUDA_TRY(cudaMemcpy(buf.data() + kCanaryBytes, c.first + c.second, tail, cudaMemcpyDeviceToHost));
+      bool head_ok = true, tail_ok = true;
+      for (size_t i = 0; i < kCanaryBytes; ++i) head_ok = head_ok && buf[i] == kCanaryByte;
+      for (size_t i = 0; i < tail; ++i) tail_ok = tail_ok && buf[kCanaryBytes + i] == kCanaryByte;
+      *nbad += (head_ok ? 0 : 1) + (tail_ok ? 0 : 1);
+    }
+  }
+  return TP_OK;
+}
+
+int tp_debug_bounds(void) { return kDebugBounds ? 1 : 0; }
+
+int tp_debug_limit_staged(tp_engine* e, int beam, int64_t bytes) {
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  if (!kDebugBounds) return set_error(TP_EINVAL, "not the bounds-checking build of the library");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  b->dbg_y_bytes = bytes < 0 ? -1 : bytes;
+  b->h_args_valid = false;
   return TP_OK;
 }
 

@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
   const int c = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row = (int64_t)c * a.pitch;
+  // every load of the CTA lies in [row, row + nsamp)
+  if (!in_bounds(0, a.nsamp, a.pitch, a.status) || !in_bounds(row, a.nsamp, a.x_elems, a.status)) return;
   __shared__ float s_pivot;
   __shared__ double s_tot[2][kWarps];
 
@@ -330,6 +332,8 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_u8(RfiArgs a, longlong2*
   const int c = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row = (int64_t)c * a.pitch;
+  // every load of the CTA lies in [row, row + nsamp)
+  if (!in_bounds(0, a.nsamp, a.pitch, a.status) || !in_bounds(row, a.nsamp, a.x_elems, a.status)) return;
   __shared__ unsigned long long s_tot[2][kWarps];
   unsigned long long tot_s = 0, tot_q = 0;
   for (int k = warp; k < a.nchunk; k += kWarps) {
@@ -588,7 +592,12 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int c = c0 + 32 * u;
-          if (c < a.nchan) load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v[u]);
+          if (c < a.nchan) {
+            if (in_bounds((int64_t)c * a.pitch + tq, valid, a.x_elems, a.status))
+              load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v[u]);
+            else
+              v[u][0] = v[u][1] = v[u][2] = v[u][3] = 0.f;
+          }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -614,8 +623,9 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
       int sx[4] = {0, 0, 0, 0};
       long long sS[4] = {0, 0, 0, 0};
       for (int c = g; c < a.nchan; c += 32) {
-        float v[4];
-        load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (in_bounds((int64_t)c * a.pitch + tq, valid, a.x_elems, a.status))
+          load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
         const long long off = ext ? (long long)a.bint[c] : a.S[c];
         const bool any = a.chan_nflag[c] != 0;
         const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
@@ -678,13 +688,19 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int c = c0 + 32 * u;
-        if (c < a.nchan) raw[u] = __ldg(reinterpret_cast<const Raw*>(static_cast<const char*>(a.x) +
-                                                                    ((int64_t)c * a.pitch + tq) * sizeof(Raw) / 4));
+        if (c < a.nchan) {
+          if (in_bounds((int64_t)c * a.pitch + tq, 4, a.x_elems, a.status))
+            raw[u] = __ldg(reinterpret_cast<const Raw*>(static_cast<const char*>(a.x) +
+                                                        ((int64_t)c * a.pitch + tq) * sizeof(Raw) / 4));
+          else
+            raw[u] = Raw{};
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int c = c0 + 32 * u;
         if (c >= a.nchan) break;
+        if (!in_bounds((int64_t)c * ypitch + tq, 4, a.y_elems, a.status)) continue;
         const bool any = a.chan_nflag[c] != 0;
         const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
         bool fl[4];
@@ -735,6 +751,9 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   }
   // the window's last, partial quad
   for (int c = g; c < a.nchan; c += 32) {
+    if (!in_bounds((int64_t)c * a.pitch + tq, valid, a.x_elems, a.status) ||
+        !in_bounds((int64_t)c * ypitch + tq, valid, a.y_elems, a.status))
+      continue;
     const bool any = a.chan_nflag[c] != 0;
     const uint8_t* cf = a.chunk_flag + (int64_t)c * a.nchunk;
     bool fl[4];

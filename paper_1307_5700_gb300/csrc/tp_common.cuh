@@ -31,6 +31,33 @@ int cuda_error(cudaError_t err, const char* what);
     if (_e != cudaSuccess) return ::tp::cuda_error(_e, #expr);    \
   } while (0)
 
+// ---- debug bounds checks ----------------------------------------------------------
+
+// The debug build of the library (TP_DEBUG_BOUNDS defined, libtpdd_debug.so)
+// checks the global and shared accesses of its kernels whose indices come from
+// the plan's geometry, the delays or the data.  A failed check records
+// TP_EBOUNDS in the beam's status word (the first error is kept) and the
+// access is skipped: nothing traps, so the context stays usable and the host
+// reads the code with the block's results.  The release build compiles every
+// check to `true`.
+#ifdef TP_DEBUG_BOUNDS
+constexpr bool kDebugBounds = true;
+#else
+constexpr bool kDebugBounds = false;
+#endif
+
+// [off, off + n) inside [0, extent)?  An empty range always is.  (Debug
+// build; release: true.)
+__device__ __forceinline__ bool in_bounds(int64_t off, int64_t n, int64_t extent, int* status) {
+  if constexpr (kDebugBounds) {
+    if (n == 0 || (off >= 0 && n > 0 && off + n <= extent)) return true;
+    if (status) atomicCAS(status, 0, TP_EBOUNDS);
+    return false;
+  } else {
+    return true;
+  }
+}
+
 // ---- per-block device arguments ------------------------------------------------
 
 // What the RFI kernels need about one beam's current block.
@@ -86,6 +113,10 @@ struct RfiArgs {
   const double* run_prev_var; // [nchan]
   double* run_mu;             // [nchan]
   double* run_var;            // [nchan]
+  // extents for the debug build's bounds checks
+  int* status;                // beam status word (TP_EBOUNDS), or NULL
+  int64_t x_elems;            // elements of the window buffer x
+  int64_t y_elems;            // elements of the staged series
 };
 
 // Largest polynomial order and channel count of the fitted bandpass.
@@ -118,6 +149,10 @@ struct DedispArgs {
   void* row_part;         // [ndm][ntt] (float: double2 {sum, sumsq}; int: longlong2)
   int* status;            // device status word (TP_ETIMEOUT on a wait that gave up)
   long long wait_tries;   // attempts of a wait for staged data or a free stage buffer
+  // extents for the debug build's bounds checks
+  int64_t y_bytes;        // bytes of the staged series
+  int64_t d_elems;        // elements of D
+  int64_t delayT_elems;   // elements of delayT
 };
 
 // Default number of attempts of the dedispersion kernel's waits for staged
@@ -188,6 +223,10 @@ struct DetectArgs {
   void* M;                // [ndm][dpitch] like D
   void* post_part;        // [ndm][nblk_t] x 3: float data double {Sy, Sdy, Syy}, int data long long
   double* row_beta;       // [ndm] detrending slope per unit of u = 2t - (T - 1)
+  // extents for the debug build's bounds checks
+  int* status;            // beam status word (TP_EBOUNDS)
+  int64_t d_elems;        // elements of D (and of M)
+  int64_t hit_elems;      // words of hit_bits
 };
 
 // Clustering of a block's detections (cluster.cu).
