@@ -161,7 +161,9 @@ def test_inplace_batched_graphs():
             wants.append(out)
         finally:
             tp.tp_engine_destroy(e)
-    e = tp.tp_engine_create(0)
+    import torch
+    stream = torch.cuda.Stream()  # graphs are captured on the engine's own stream
+    e = tp.tp_engine_create(0, 0, stream.cuda_stream)
     try:
         plans = [tp.tp_create_plan(e, NCHAN, *BAND, DMS[:nd], dtype, None, 4.0) for nd in ndms]
         beams = [tp.tp_beam_open(e, p, B, 1 << 16) for p in plans]
@@ -171,13 +173,17 @@ def test_inplace_batched_graphs():
             for i, b in enumerate(beams):
                 buf = bufs[i][k % 3]
                 dmax = _dmax(plans[i])
-                import torch
                 buf[:, dmax:dmax + B] = torch.from_numpy(blocks[k]).cuda()
                 torch.cuda.synchronize()
                 tp.tp_push_inplace(e, b, buf, B)
             tp.tp_run_ready(e, use_graph=True)
             for i, b in enumerate(beams):
-                _same(_read(e, b, dtype, ndms[i]), wants[i][k], (i, k))
+                got = _read(e, b, dtype, ndms[i])
+                # the records name the beam that produced them: beam i here,
+                # beam 0 in the one-beam engines
+                assert np.all(got["c"]["beam"] == b)
+                got["c"]["beam"] = wants[i][k]["c"]["beam"]
+                _same(got, wants[i][k], (i, k))
     finally:
         tp.tp_engine_destroy(e)
 
