@@ -155,8 +155,8 @@ int tp_engine_memory(const tp_engine *e, size_t *used, size_t *budget);
  * dm_list (host, ndm doubles) is copied; it must be finite, >= 0 and
  * non-decreasing.  `rfi` may be NULL for the defaults.  `nsigma` is the
  * detection threshold of A7.  The call blocks until the table is built.
- * Errors: TP_EINVAL (nchan <= 0, ndm <= 0, t_samp <= 0, bw = 0, a channel
- * frequency <= 0, a DM negative / not finite / decreasing, bad rfi params,
+ * Errors: TP_EINVAL (nchan <= 0 or > 65535, ndm <= 0, t_samp <= 0, bw = 0, a
+ * channel frequency <= 0, a DM negative / not finite / decreasing, bad rfi params,
  * a delay above 2^31 - 1), TP_ENOMEM, TP_ECUDA. */
 int tp_create_plan(tp_engine *e, int nchan, double f_lo_mhz, double bw_mhz, double t_samp_s,
                    const double *dm_list, int ndm, int dtype, const tp_rfi_params *rfi,
@@ -619,7 +619,8 @@ int tp_server_destroy(tp_server *s);
  * tp_dedisperse runs with beam-owned scratch.
  *
  * x          device, [nchan][pitch] samples of `dtype`, 16-byte aligned, pitch
- *            * element size a multiple of 16 bytes; nsamp samples per row used
+ *            * element size a multiple of 16 bytes; nsamp samples per row used;
+ *            1 <= nchan <= 65535 (else TP_EINVAL)
  * rfi        NULL for the defaults; stats_mode must be TP_STATS_BLOCK (enable_
  *            spectrum and tau_spectrum are ignored)
  * mu, sigma  device, nchan doubles each (outputs)

@@ -499,8 +499,15 @@ __global__ void __launch_bounds__(1024) detect_scan(DetectArgs a, int nblk) {
   const int per = (nblk + 1023) / 1024;
   const int lo = threadIdx.x * per;
   const int hi = lo + per < nblk ? lo + per : nblk;
+  // the thread's counts eight at a time, their loads issued together
   unsigned long long sum = 0;
-  for (int i = lo; i < hi; ++i) sum += a.blk_count[i];
+  for (int i0 = lo; i0 < hi; i0 += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = i0 + u < hi ? a.blk_count[i0 + u] : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sum += v[u];
+  }
   s[threadIdx.x] = sum;
   __syncthreads();
   for (int o = 1; o < 1024; o <<= 1) {
@@ -510,10 +517,15 @@ __global__ void __launch_bounds__(1024) detect_scan(DetectArgs a, int nblk) {
     __syncthreads();
   }
   unsigned long long run = s[threadIdx.x] - sum;  // exclusive prefix
-  for (int i = lo; i < hi; ++i) {
-    const uint32_t c = a.blk_count[i];
-    a.blk_off[i] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
-    run += c;
+  for (int i0 = lo; i0 < hi; i0 += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = i0 + u < hi ? a.blk_count[i0 + u] : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (i0 + u < hi) a.blk_off[i0 + u] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+      run += v[u];
+    }
   }
   if (threadIdx.x == 1023) *a.n_total = s[1023];
 }

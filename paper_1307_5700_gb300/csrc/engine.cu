@@ -691,8 +691,9 @@ int issue_rfi(tp_engine* e, Beam* b, cudaStream_t s) {
   if (p->rfi.stats_mode == TP_STATS_EXTERNAL && !b->have_ext)
     return set_error(TP_ENOTREADY, "beam %d: external statistics not set", b->id);
   RfiArgs ra = rfi_args(p, b);
-  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->y, b->ypitch, s));
-  e->launches += 4;
+  int nk = 0;
+  TP_CUDA_TRY(launch_rfi(ra, b->chunk_sums, b->y, b->ypitch, s, &nk));
+  e->launches += nk;
   return TP_OK;
 }
 
@@ -1023,6 +1024,7 @@ int tp_create_plan(tp_engine* e, int nchan, double f_lo_mhz, double bw_mhz, doub
   if (!e || !out) return set_error(TP_EINVAL, "engine or out is NULL");
   *out = nullptr;
   if (nchan <= 0 || ndm <= 0) return set_error(TP_EINVAL, "nchan %d / ndm %d must be > 0", nchan, ndm);
+  if (nchan > 65535) return set_error(TP_EINVAL, "nchan %d: at most 65535 channels", nchan);
   if (!(t_samp_s > 0.0) || !std::isfinite(t_samp_s)) return set_error(TP_EINVAL, "t_samp must be > 0");
   if (!std::isfinite(f_lo_mhz) || !std::isfinite(bw_mhz) || bw_mhz == 0.0)
     return set_error(TP_EINVAL, "f_lo / bw invalid");

@@ -52,7 +52,7 @@ extern "C" int tp_channel_stats_noalloc(const void* x, int dtype, int nchan, int
                                         uint8_t* chunk_flag, uint8_t* chunk_raw, void* cuda_stream) {
   if (!x || !mu || !sigma || !chunk_flag || !chunk_raw) return set_error(TP_EINVAL, "a pointer is NULL");
   if (dtype_size(dtype) == 0) return set_error(TP_EINVAL, "unknown dtype %d", dtype);
-  if (nchan <= 0 || nsamp <= 0 || pitch < nsamp) return set_error(TP_EINVAL, "bad sizes");
+  if (nchan <= 0 || nchan > 65535 || nsamp <= 0 || pitch < nsamp) return set_error(TP_EINVAL, "bad sizes");
   tp_rfi_params r;
   if (rfi) r = *rfi;
   else tp_rfi_defaults(&r);

@@ -2,13 +2,14 @@
 // ("Bandpass Correction", "Channel Thresholding" and "Spectrum Thresholding"
 // of Sec. 2.2.1).
 //
-// Kernel chunk_stats (one CTA per channel): every W_c-sample chunk of the
-// window is summed by one warp.  Float data are summed as (x - p) with a
-// per-channel pivot p near the mean (the FP32 mean of the first 64 samples),
-// in FP32 inside sub-chunks of at most 256 samples and in FP64 above that;
-// 8-bit data are summed exactly in integers.  The per-chunk sums go to global
-// scratch; the channel totals give mu_c and sigma_c, and each chunk is then
-// tested against tau_c sigma_c sqrt(n_k).
+// Kernel chunk_sums (a CTA per 32 consecutive chunks of one channel): every
+// W_c-sample chunk of the window is summed by one warp.  Float data are summed
+// as (x - p) with a per-channel pivot p near the mean (the FP32 mean of the
+// first 64 samples), in FP32 inside sub-chunks of at most 256 samples and in
+// FP64 above that; 8-bit data are summed exactly in integers.  The per-chunk
+// sums go to global scratch.  Kernel channel_stats (a warp per channel): the
+// channel totals give mu_c and sigma_c, and each chunk is then tested against
+// tau_c sigma_c sqrt(n_k).
 // Kernel dilate: flag = own exceedance | time neighbours (| channel
 // neighbours); per-channel flagged-chunk counts.  Kernel spectrum_threshold
 // (one CTA per 256 samples): the sum over channels of the corrected samples of
@@ -117,32 +118,29 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
   return v;
 }
 
-// Chunk sums (float data).  Writes chunk_sums[c][k] = {sum(x - p), sum((x - p)^2)}
-// and the channel statistics.  When W is a multiple of 128 every lane reads
-// float-aligned quads (two per 256-sample sub-chunk, issued together).
+// Chunk sums (float data): chunk_sums[c][k] = {sum(x - p), sum((x - p)^2)}
+// with p the channel's pivot.  A CTA of chunk_sums_float covers kGroupChunks
+// consecutive chunks of one channel (blockIdx.y); when W is a multiple of
+// 128 every lane reads float-aligned quads (two per 256-sample sub-chunk).
+constexpr int kGroupChunks = kWarps * kChunkBatch;
+
+// four consecutive samples from i (those at or past `lim` read as 0, ok =
+// false), converted to FP32 from the storage format
 template <int DT>
-__device__ __forceinline__ void load4(const void* x, int64_t i, int64_t lim, float p, float (&e)[4],
-                                      bool (&ok)[4]) {
+__device__ __forceinline__ void load4_raw(const void* x, int64_t i, int64_t lim, float (&e)[4], bool (&ok)[4]) {
   if (i + 3 < lim) {
     if constexpr (DT == TP_F32) {
       const float4 v = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(x) + i));
-      e[0] = v.x - p, e[1] = v.y - p, e[2] = v.z - p, e[3] = v.w - p;
+      e[0] = v.x, e[1] = v.y, e[2] = v.z, e[3] = v.w;
     } else if constexpr (DT == TP_C16) {
       const int4 v = __ldg(reinterpret_cast<const int4*>(static_cast<const int*>(x) + i));
-      e[0] = c16_power(v.x) - p, e[1] = c16_power(v.y) - p, e[2] = c16_power(v.z) - p, e[3] = c16_power(v.w) - p;
+      e[0] = c16_power(v.x), e[1] = c16_power(v.y), e[2] = c16_power(v.z), e[3] = c16_power(v.w);
     } else {
       const uint2 v = __ldg(reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(x) + i));
       const unsigned short h[4] = {(unsigned short)(v.x & 0xffff), (unsigned short)(v.x >> 16),
                                    (unsigned short)(v.y & 0xffff), (unsigned short)(v.y >> 16)};
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        float f;
-        if constexpr (DT == TP_F16)
-          asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h[r]));
-        else
-          f = __uint_as_float((unsigned)h[r] << 16);
-        e[r] = f - p;
-      }
+      for (int r = 0; r < 4; ++r) e[r] = bits_to_float<DT>(h[r]);
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) ok[r] = true;
@@ -150,119 +148,145 @@ __device__ __forceinline__ void load4(const void* x, int64_t i, int64_t lim, flo
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       ok[r] = i + r < lim;
-      e[r] = ok[r] ? load_as_float<DT>(x, i + r) - p : 0.f;
+      e[r] = ok[r] ? load_as_float<DT>(x, i + r) : 0.f;
     }
   }
 }
 
+// The channel's pivot (one full warp): the FP32 mean of its first
+// min(64, N) samples, or the external mean's high part.  Every kernel that
+// needs it recomputes it the same way, so all see the same value.
 template <int DT>
-__global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2* chunk_sums) {
-  const int c = blockIdx.x;
+__device__ __forceinline__ float channel_pivot(const RfiArgs& a, int c, int lane) {
+  if (a.stats_mode == TP_STATS_EXTERNAL) return a.mu_hi[c];
+  const int64_t row = (int64_t)c * a.pitch;
+  const int64_t m = a.nsamp < 64 ? a.nsamp : 64;
+  float v = 0.f;
+  for (int64_t t = lane; t < m; t += 32) v += load_as_float<DT>(a.x, row + t);
+  return warp_sum_f(v) / (float)m;
+}
+
+// the FP32 sums of one <= 256-sample sub-chunk held as two quads per lane
+__device__ __forceinline__ float2 quad_sums(const float (&e0)[4], const float (&e1)[4], float p) {
+  float fs = 0.f, fq = 0.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float d = e0[r] - p;
+    fs += d;
+    fq += d * d;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float d = e1[r] - p;
+    fs += d;
+    fq += d * d;
+  }
+  return make_float2(warp_sum_f(fs), warp_sum_f(fq));
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) chunk_sums_float(RfiArgs a, double2* chunk_sums) {
+  const int c = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row = (int64_t)c * a.pitch;
   // every load of the CTA lies in [row, row + nsamp)
   if (!in_bounds(0, a.nsamp, a.pitch, a.status) || !in_bounds(row, a.nsamp, a.x_elems, a.status)) return;
+  const int k0 = blockIdx.x * kGroupChunks;
+  const int k1 = k0 + kGroupChunks < a.nchunk ? k0 + kGroupChunks : a.nchunk;
+  const bool vec = (a.W % 128) == 0;
+  // W <= 256: every chunk is one FP32 sub-chunk, its sums stored as float2;
+  // wider chunks accumulate their sub-chunks in FP64 (double2)
+  const bool single = a.W <= 256;
+  float2* sums32 = reinterpret_cast<float2*>(chunk_sums) + (int64_t)c * a.nchunk;
   __shared__ float s_pivot;
-  __shared__ double s_tot[2][kWarps];
 
-  if (warp == 0) {
-    float p;
-    if (a.stats_mode == TP_STATS_EXTERNAL) {
-      p = a.mu_hi[c];
-    } else {
-      const int64_t m = a.nsamp < 64 ? a.nsamp : 64;
-      float v = 0.f;
-      for (int64_t t = lane; t < m; t += 32) v += load_as_float<DT>(a.x, row + t);
-      p = warp_sum_f(v) / (float)m;
+  // W = 256: the warp's kChunkBatch full chunks k0 + warp + u kWarps are
+  // loaded before the pivot is known (their loads overlap its computation)
+  const int nfull = (int)(a.nsamp / 256);
+  const bool batch = vec && a.W == 256;
+  float e[kChunkBatch][2][4];
+  bool ok[kChunkBatch][2][4];
+  if (batch) {
+#pragma unroll
+    for (int u = 0; u < kChunkBatch; ++u) {
+      const int k = k0 + warp + u * kWarps;
+      if (k < nfull) {
+        const int64_t lo = (int64_t)k * 256;
+        load4_raw<DT>(a.x, row + lo + 4 * lane, row + lo + 256, e[u][0], ok[u][0]);
+        load4_raw<DT>(a.x, row + lo + 128 + 4 * lane, row + lo + 256, e[u][1], ok[u][1]);
+      }
     }
+  }
+  if (warp == 0) {
+    const float p = channel_pivot<DT>(a, c, lane);
     if (lane == 0) s_pivot = p;
   }
   __syncthreads();
   const float p = s_pivot;
-  const bool vec = (a.W % 128) == 0;
-
-  // W <= 256: every chunk is one FP32 sub-chunk and its sums are stored as
-  // float2 (no FP64 in the loops: FP64 is a small fraction of the FP32 rate
-  // on this part); wider chunks accumulate sub-chunks in FP64 (double2)
-  const bool single = a.W <= 256;
-  float2* sums32 = reinterpret_cast<float2*>(chunk_sums) + (int64_t)c * a.nchunk;
-  // W = 256 (one sub-chunk per chunk): kChunkBatch full chunks per warp and
-  // iteration, every load issued before the sums (the same FP32 summation
-  // order per chunk as the general loop below); the rest (a short last
-  // chunk) falls through to the general loop
-  int kstart = warp;
-  if (vec && a.W == 256) {
-    const int nfull = (int)(a.nsamp / 256);
-    int k = warp;
-    for (; k + (kChunkBatch - 1) * kWarps < nfull; k += kChunkBatch * kWarps) {
-      float e[kChunkBatch][2][4];
-      bool ok[kChunkBatch][2][4];
+  if (batch) {
 #pragma unroll
-      for (int u = 0; u < kChunkBatch; ++u) {
-        const int64_t lo = (int64_t)(k + u * kWarps) * 256;
-        load4<DT>(a.x, row + lo + 4 * lane, row + lo + 256, p, e[u][0], ok[u][0]);
-        load4<DT>(a.x, row + lo + 128 + 4 * lane, row + lo + 256, p, e[u][1], ok[u][1]);
-      }
-#pragma unroll
-      for (int u = 0; u < kChunkBatch; ++u) {
-        float fs = 0.f, fq = 0.f;
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            fs += e[u][h][r];
-            fq += e[u][h][r] * e[u][h][r];
-          }
-        fs = warp_sum_f(fs);
-        fq = warp_sum_f(fq);
-        if (lane == 0) sums32[k + u * kWarps] = make_float2(fs, fq);
+    for (int u = 0; u < kChunkBatch; ++u) {
+      const int k = k0 + warp + u * kWarps;
+      if (k < nfull) {
+        const float2 s = quad_sums(e[u][0], e[u][1], p);
+        if (lane == 0) sums32[k] = s;
       }
     }
-    kstart = k;
   }
-  for (int k = kstart; k < a.nchunk; k += kWarps) {
+  // the rest: every chunk of the group when W != 256, else a short last chunk
+  for (int k = k0 + warp; k < k1; k += kWarps) {
+    if (batch && k < nfull) continue;
     const int64_t lo = (int64_t)k * a.W;
     const int64_t hi = lo + a.W < a.nsamp ? lo + a.W : a.nsamp;
     double cs = 0.0, cq = 0.0;
     for (int64_t sub = lo; sub < hi; sub += 256) {
       const int64_t sh = sub + 256 < hi ? sub + 256 : hi;
-      float fs = 0.f, fq = 0.f;
+      float2 s;
       if (vec) {
         float e0[4], e1[4];
-        bool k0[4], k1[4];
-        load4<DT>(a.x, row + sub + 4 * lane, row + sh, p, e0, k0);
-        load4<DT>(a.x, row + sub + 128 + 4 * lane, row + sh, p, e1, k1);
+        bool q0[4], q1[4];
+        load4_raw<DT>(a.x, row + sub + 4 * lane, row + sh, e0, q0);
+        load4_raw<DT>(a.x, row + sub + 128 + 4 * lane, row + sh, e1, q1);
+        // samples past the end read as p, which adds 0
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          fs += e0[r];
-          fq += e0[r] * e0[r];
+          e0[r] = q0[r] ? e0[r] : p;
+          e1[r] = q1[r] ? e1[r] : p;
         }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          fs += e1[r];
-          fq += e1[r] * e1[r];
-        }
+        s = quad_sums(e0, e1, p);
       } else {
+        float fs = 0.f, fq = 0.f;
         for (int64_t t = sub + lane; t < sh; t += 32) {
-          const float e = load_as_float<DT>(a.x, row + t) - p;
-          fs += e;
-          fq += e * e;
+          const float d = load_as_float<DT>(a.x, row + t) - p;
+          fs += d;
+          fq += d * d;
         }
+        s = make_float2(warp_sum_f(fs), warp_sum_f(fq));
       }
-      fs = warp_sum_f(fs);
-      fq = warp_sum_f(fq);
       if (single) {
-        if (lane == 0) sums32[k] = make_float2(fs, fq);
+        if (lane == 0) sums32[k] = s;
       } else {
-        cs += (double)fs;
-        cq += (double)fq;
+        cs += (double)s.x;
+        cq += (double)s.y;
       }
     }
     if (!single && lane == 0) chunk_sums[(int64_t)c * a.nchunk + k] = make_double2(cs, cq);
   }
-  __syncthreads();
-  // per-warp totals over the chunks k = w, w + kWarps, ... in that order (the
-  // order the warps summed them), one thread per warp slot
+}
+
+// Channel statistics and chunk exceedances (float data), one warp per
+// channel: the binary64 totals of the chunk sums (lane l sums chunks l,
+// l + 32, ...; the lanes' totals are combined in a fixed butterfly order),
+// mu_c = p + S / N and sigma_c = sqrt(Q / N - (S / N)^2); chunk k exceeds when
+// sum(x - mu_c) > tau_c sigma_c sqrt(n_k).
+template <int DT>
+__global__ void __launch_bounds__(kThreads) channel_stats_float(RfiArgs a, const double2* chunk_sums) {
+  const int c = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= a.nchan) return;
+  const float p = channel_pivot<DT>(a, c, lane);
+  const bool single = a.W <= 256;
+  const float2* sums32 = reinterpret_cast<const float2*>(chunk_sums) + (int64_t)c * a.nchunk;
   auto chunk_sum = [&](int k) -> double2 {
     if (single) {
       const float2 f = sums32[k];
@@ -270,73 +294,94 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_float(RfiArgs a, double2
     }
     return chunk_sums[(int64_t)c * a.nchunk + k];
   };
-  if (threadIdx.x < kWarps) {
-    double tot_s = 0.0, tot_q = 0.0;
-    for (int k = threadIdx.x; k < a.nchunk; k += kWarps) {
+  double m, sig;
+  if (a.stats_mode == TP_STATS_EXTERNAL) {
+    m = (double)a.mu_lo[c];
+    sig = a.sigma[c];
+  } else {
+    double S = 0.0, Q = 0.0;
+    for (int k = lane; k < a.nchunk; k += 32) {
       const double2 v = chunk_sum(k);
-      tot_s += 0.0 + v.x;
-      tot_q += 0.0 + v.y;
+      S += v.x;
+      Q += v.y;
     }
-    s_tot[0][threadIdx.x] = tot_s;
-    s_tot[1][threadIdx.x] = tot_q;
-  }
-  __syncthreads();
-
-  // channel statistics; m = mu - p
-  __shared__ double s_m, s_sig;
-  if (threadIdx.x == 0) {
-    double m, sig;
-    if (a.stats_mode == TP_STATS_EXTERNAL) {
-      m = (double)a.mu_lo[c];
-      sig = a.sigma[c];
-    } else {
-      double S = 0.0, Q = 0.0;
-      for (int w = 0; w < kWarps; ++w) {
-        S += s_tot[0][w];
-        Q += s_tot[1][w];
-      }
-      const double N = (double)a.nsamp;
-      m = S / N;
-      double var = Q / N - m * m;
-      sig = sqrt(var > 0.0 ? var : 0.0);
-      const double mu = (double)p + m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      S += __shfl_xor_sync(0xffffffffu, S, o);
+      Q += __shfl_xor_sync(0xffffffffu, Q, o);
+    }
+    const double N = (double)a.nsamp;
+    m = S / N;
+    const double var = Q / N - m * m;
+    sig = sqrt(var > 0.0 ? var : 0.0);
+    const double mu = (double)p + m;
+    if (lane == 0) {
       a.mu[c] = mu;
       a.sigma[c] = sig;
       const float hi = (float)mu;
       a.mu_hi[c] = hi;
       a.mu_lo[c] = (float)(mu - (double)hi);
       if (DT == TP_F16 || DT == TP_BF16) a.b16[c] = storage_bits(DT, mu);
-      m = mu - (double)p;
     }
-    s_m = m;
-    s_sig = sig;
-    if (a.fit || a.run) a.pivot[c] = p;
+    m = mu - (double)p;
   }
-  __syncthreads();
+  if (lane == 0 && (a.fit || a.run)) a.pivot[c] = p;
   // with the fitted bandpass the chunk test waits for the fit
   // (fit_chunk_test), with running statistics for their update
   // (running_chunk_test)
   if (!a.enable_channel || a.fit || a.run) return;
-  const double m = s_m, tsig = a.tau_c * s_sig;
-  for (int k = threadIdx.x; k < a.nchunk; k += kThreads) {
+  const double tsig = a.tau_c * sig;
+  const double thr_w = tsig * sqrt((double)a.W);  // the threshold of a full chunk
+  for (int k = lane; k < a.nchunk; k += 32) {
     const int64_t lo = (int64_t)k * a.W;
     const int64_t n = (lo + a.W < a.nsamp ? lo + a.W : a.nsamp) - lo;
     const double2 cs = chunk_sum(k);
     const double e = cs.x - (double)n * m;
-    a.chunk_raw[(int64_t)c * a.nchunk + k] = (uint8_t)(e > tsig * sqrt((double)n));
+    a.chunk_raw[(int64_t)c * a.nchunk + k] = (uint8_t)(e > (n == a.W ? thr_w : tsig * sqrt((double)n)));
   }
 }
 
-// Chunk sums (8-bit data), exact.  chunk_sums[c][k] = {sum x, sum x^2}.
-__global__ void __launch_bounds__(kThreads) chunk_stats_u8(RfiArgs a, longlong2* chunk_sums) {
-  const int c = blockIdx.x;
+// Chunk sums (8-bit data), exact: chunk_sums[c][k] = {sum x, sum x^2}.  A CTA
+// of chunk_sums_u8 covers kGroupChunks consecutive chunks of one channel
+// (blockIdx.y).  With W = 256 and 8-byte aligned rows each lane reads 8
+// samples of a chunk with one load and sums them with byte dot products.
+__global__ void __launch_bounds__(kThreads) chunk_sums_u8(RfiArgs a, longlong2* chunk_sums) {
+  const int c = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row = (int64_t)c * a.pitch;
   // every load of the CTA lies in [row, row + nsamp)
   if (!in_bounds(0, a.nsamp, a.pitch, a.status) || !in_bounds(row, a.nsamp, a.x_elems, a.status)) return;
-  __shared__ unsigned long long s_tot[2][kWarps];
-  unsigned long long tot_s = 0, tot_q = 0;
-  for (int k = warp; k < a.nchunk; k += kWarps) {
+  const int k0 = blockIdx.x * kGroupChunks;
+  const int k1 = k0 + kGroupChunks < a.nchunk ? k0 + kGroupChunks : a.nchunk;
+  const unsigned char* xr = static_cast<const unsigned char*>(a.x) + row;
+  const int nfull = (int)(a.nsamp / 256);
+  const bool batch = a.W == 256 && ((reinterpret_cast<uintptr_t>(xr)) & 7) == 0;
+  if (batch) {
+    uint2 w[kChunkBatch];
+#pragma unroll
+    for (int u = 0; u < kChunkBatch; ++u) {
+      const int k = k0 + warp + u * kWarps;
+      w[u] = k < nfull ? __ldg(reinterpret_cast<const uint2*>(xr + (int64_t)k * 256) + lane) : make_uint2(0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kChunkBatch; ++u) {
+      const int k = k0 + warp + u * kWarps;
+      if (k >= nfull) continue;
+      // sum x <= 256 x 255 and sum x^2 <= 256 x 255^2 fit 32 bits
+      unsigned s = __dp4a(w[u].x, 0x01010101u, 0u);
+      s = __dp4a(w[u].y, 0x01010101u, s);
+      unsigned q = __dp4a(w[u].x, w[u].x, 0u);
+      q = __dp4a(w[u].y, w[u].y, q);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+      }
+      if (lane == 0) chunk_sums[(int64_t)c * a.nchunk + k] = make_longlong2((long long)s, (long long)q);
+    }
+  }
+  for (int k = k0 + warp; k < k1; k += kWarps) {
+    if (batch && k < nfull) continue;
     const int64_t lo = (int64_t)k * a.W;
     const int64_t hi = lo + a.W < a.nsamp ? lo + a.W : a.nsamp;
     unsigned long long s = 0, q = 0;
@@ -347,62 +392,97 @@ __global__ void __launch_bounds__(kThreads) chunk_stats_u8(RfiArgs a, longlong2*
     }
     s = warp_sum_u64(s);
     q = warp_sum_u64(q);
-    if (lane == 0) {
-      chunk_sums[(int64_t)c * a.nchunk + k] = make_longlong2((long long)s, (long long)q);
-      tot_s += s;
-      tot_q += q;
-    }
+    if (lane == 0) chunk_sums[(int64_t)c * a.nchunk + k] = make_longlong2((long long)s, (long long)q);
   }
-  if (lane == 0) {
-    s_tot[0][warp] = tot_s;
-    s_tot[1][warp] = tot_q;
-  }
-  __syncthreads();
-  __shared__ long long s_S, s_V;
-  __shared__ int s_b;
-  if (threadIdx.x == 0) {
-    const long long N = a.nsamp;
-    if (a.stats_mode == TP_STATS_EXTERNAL) {
-      s_b = a.bint[c];
-      s_S = 0;
-      s_V = 0;
-    } else {
-      unsigned long long S = 0, Q = 0;
-      for (int w = 0; w < kWarps; ++w) {
-        S += s_tot[0][w];
-        Q += s_tot[1][w];
-      }
-      const long long V = N * (long long)Q - (long long)S * (long long)S;
-      const int b = (int)((2 * (long long)S + N) / (2 * N));
-      a.S[c] = (long long)S;
-      a.V[c] = V;
-      a.bint[c] = b;
-      a.mu[c] = __ddiv_rn((double)(long long)S, (double)N);
-      a.sigma[c] = __ddiv_rn(__dsqrt_rn((double)V), (double)N);
-      s_S = (long long)S;
-      s_V = V;
-      s_b = b;
-    }
-  }
-  __syncthreads();
-  if (!a.enable_channel || a.fit || a.run) return;
-  const long long N = a.nsamp, S = s_S, V = s_V, b = s_b;
+}
+
+// Channel statistics and chunk exceedances (8-bit data), one warp per channel,
+// in exact integers: S = sum x, V = N sum x^2 - S^2, b_c = floor(S / N + 1/2);
+// chunk k exceeds when N s_k - n_k S > tau_c sqrt(V n_k) (block statistics;
+// s_k - n_k b_c > tau_c sigma_c sqrt(n_k) with external ones).  The binary64
+// threshold of a full chunk is computed once; an exact integer e exceeds it
+// exactly when it exceeds the threshold's floor.
+__global__ void __launch_bounds__(kThreads) channel_stats_u8(RfiArgs a, const longlong2* chunk_sums) {
+  const int c = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= a.nchan) return;
+  const long long N = a.nsamp;
+  const longlong2* cs_row = chunk_sums + (int64_t)c * a.nchunk;
   const bool ext = a.stats_mode == TP_STATS_EXTERNAL;
+  long long S = 0, V = 0, b;
+  if (ext) {
+    b = a.bint[c];
+  } else {
+    unsigned long long s = 0, q = 0;
+    for (int k = lane; k < a.nchunk; k += 32) {
+      const longlong2 v = cs_row[k];
+      s += (unsigned long long)v.x;
+      q += (unsigned long long)v.y;
+    }
+    s = warp_sum_u64(s);
+    q = warp_sum_u64(q);
+    S = (long long)s;
+    V = N * (long long)q - S * S;
+    b = (2 * S + N) / (2 * N);
+    if (lane == 0) {
+      a.S[c] = S;
+      a.V[c] = V;
+      a.bint[c] = (int)b;
+      a.mu[c] = __ddiv_rn((double)S, (double)N);
+      a.sigma[c] = __ddiv_rn(__dsqrt_rn((double)V), (double)N);
+    }
+  }
+  if (!a.enable_channel || a.fit || a.run) return;
   const double tsig = ext ? __dmul_rn(a.tau_c, a.sigma[c]) : 0.0;
-  for (int k = threadIdx.x; k < a.nchunk; k += kThreads) {
+  auto threshold = [&](long long n) -> double {
+    return ext ? __dmul_rn(tsig, __dsqrt_rn((double)n))
+               : __dmul_rn(a.tau_c, __dsqrt_rn(__dmul_rn((double)V, (double)n)));
+  };
+  const double thr_w = threshold(a.W);
+  // |e| <= 255 N W keeps (double)e exact below 2^53; the integer comparison
+  // then decides as the binary64 one does
+  const bool int_cmp = isfinite(thr_w) && fabs(thr_w) < 4.0e18 && 255.0 * (double)N * (double)a.W < 9.0e15;
+  const long long e_w = int_cmp ? (long long)floor(thr_w) : 0;
+  for (int k = lane; k < a.nchunk; k += 32) {
     const long long lo = (long long)k * a.W;
     const long long n = (lo + a.W < N ? lo + a.W : N) - lo;
-    const longlong2 cs = chunk_sums[(int64_t)c * a.nchunk + k];
+    const longlong2 cs = cs_row[k];
+    const long long e = ext ? cs.x - n * b : N * cs.x - n * S;
     bool ex;
-    if (ext) {
-      const long long e = cs.x - n * b;
-      ex = (double)e > __dmul_rn(tsig, __dsqrt_rn((double)n));
-    } else {
-      const long long e = N * cs.x - n * S;
-      ex = (double)e > __dmul_rn(a.tau_c, __dsqrt_rn(__dmul_rn((double)V, (double)n)));
-    }
+    if (n == a.W && int_cmp)
+      ex = e > e_w;
+    else
+      ex = (double)e > (n == a.W ? thr_w : threshold(n));
     a.chunk_raw[(int64_t)c * a.nchunk + k] = (uint8_t)ex;
   }
+}
+
+// Launch of the A1-A2 statistics kernels on the window described by a.
+template <int DT>
+cudaError_t launch_stats_float(const RfiArgs& a, void* chunk_sums, cudaStream_t s) {
+  const dim3 grid((unsigned)((a.nchunk + kGroupChunks - 1) / kGroupChunks), (unsigned)a.nchan);
+  chunk_sums_float<DT><<<grid, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  channel_stats_float<DT><<<(unsigned)((a.nchan + kWarps - 1) / kWarps), kThreads, 0, s>>>(
+      a, static_cast<const double2*>(chunk_sums));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s) {
+  if (a.dtype == TP_U8) {
+    const dim3 grid((unsigned)((a.nchunk + kGroupChunks - 1) / kGroupChunks), (unsigned)a.nchan);
+    chunk_sums_u8<<<grid, kThreads, 0, s>>>(a, static_cast<longlong2*>(chunk_sums));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    channel_stats_u8<<<(unsigned)((a.nchan + kWarps - 1) / kWarps), kThreads, 0, s>>>(
+        a, static_cast<const longlong2*>(chunk_sums));
+    return cudaGetLastError();
+  }
+  if (a.dtype == TP_F16) return launch_stats_float<TP_F16>(a, chunk_sums, s);
+  if (a.dtype == TP_BF16) return launch_stats_float<TP_BF16>(a, chunk_sums, s);
+  if (a.dtype == TP_C16) return launch_stats_float<TP_C16>(a, chunk_sums, s);
+  return launch_stats_float<TP_F32>(a, chunk_sums, s);
 }
 
 // Dilation of the exceedances into flags, per-channel flagged-chunk counts.
@@ -486,14 +566,26 @@ __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a)
   if (k >= a.nchunk) return;
   double fv = 0.0;
   unsigned long long fhi = 0, flo = 0;
-  for (int c = lane; c < a.nchan; c += 32) {
-    if (a.chan_nflag[c] == 0 || !a.chunk_flag[(int64_t)c * a.nchunk + k]) continue;
-    if (exact) {
-      const unsigned long long V = (unsigned long long)a.V[c];
-      fhi += V >> 20;
-      flo += V & 0xFFFFFull;
-    } else {
-      fv = __dadd_rn(fv, __dmul_rn(a.sigma[c], a.sigma[c]));
+  // the lane's channels c = lane, lane + 32, ... in order, eight at a time
+  // (their flag loads issued together)
+  for (int c0 = lane; c0 < a.nchan; c0 += 32 * 8) {
+    int nf[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) nf[u] = c0 + 32 * u < a.nchan ? a.chan_nflag[c0 + 32 * u] : 0;
+    bool fl[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) fl[u] = nf[u] != 0 && a.chunk_flag[(int64_t)(c0 + 32 * u) * a.nchunk + k];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (!fl[u]) continue;
+      const int c = c0 + 32 * u;
+      if (exact) {
+        const unsigned long long V = (unsigned long long)a.V[c];
+        fhi += V >> 20;
+        flo += V & 0xFFFFFull;
+      } else {
+        fv = __dadd_rn(fv, __dmul_rn(a.sigma[c], a.sigma[c]));
+      }
     }
   }
 #pragma unroll
@@ -524,6 +616,16 @@ __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a)
 // samples of unflagged chunks over channels (FP32 runs of 8 channels folded
 // into FP64; exact integers for 8-bit data); pass 2 re-reads the tile (an L2
 // hit) and writes y.
+// (hi, lo) += v: hi takes the FP32 sum, lo its exact rounding error (Knuth's
+// two_sum, six FP32 operations; nothing is contracted: --fmad=false)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bv = s - hi;
+  const float av = s - bv;
+  lo += (hi - av) + (v - bv);
+  hi = s;
+}
+
 template <int DT>
 __device__ __forceinline__ void load_quad(const void* x, int64_t i, int64_t valid, float (&v)[4]) {
   if (valid >= 4) {
@@ -574,19 +676,27 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   const int64_t tq = t0 + 4 * q;
   const int64_t left = a.nsamp - tq;
   const int valid = left >= 4 ? 4 : (left > 0 ? (int)left : 0);
+  // chunk index of each sample (one division when the CTA's 32 samples lie
+  // in one chunk)
   int kk[4];
+  {
+    const int k0 = (int)(t0 / a.W);
+    const bool one = (int64_t)(k0 + 1) * a.W >= t0 + 32;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) kk[r] = r < valid ? (int)((tq + r) / a.W) : 0;
-  __shared__ double s_f[32][33];
+    for (int r = 0; r < 4; ++r) kk[r] = r < valid ? (one ? k0 : (int)((tq + r) / a.W)) : 0;
+  }
+  __shared__ float s_fh[32][33], s_fl[32][33];
   __shared__ long long s_i[32][33];
   __shared__ unsigned s_word;
 
   if (a.enable_spectrum) {
     if constexpr (!kU8) {
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      // (hi, lo): an unevaluated FP32 pair, the running sum of the groups'
+      // partial sums carried without rounding error (two_sum)
+      float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
       float part[4] = {0.f, 0.f, 0.f, 0.f};
       // channels g, g + 32, ... in groups of 8: the group's loads are issued
-      // together, its FP32 partial sums flushed to FP64 after the group
+      // together, its FP32 partial sums added to (hi, lo) after the group
       for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
         float v[8][4];
 #pragma unroll
@@ -612,11 +722,18 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
         }
         if (c0 + 32 * 7 < a.nchan) {
 #pragma unroll
-          for (int r = 0; r < 4; ++r) acc[r] += (double)part[r], part[r] = 0.f;
+          for (int r = 0; r < 4; ++r) {
+            two_sum_acc(hi[r], lo[r], part[r]);
+            part[r] = 0.f;
+          }
         }
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) s_f[g][4 * q + r] = acc[r] + (double)part[r];
+      for (int r = 0; r < 4; ++r) {
+        two_sum_acc(hi[r], lo[r], part[r]);
+        s_fh[g][4 * q + r] = hi[r];
+        s_fl[g][4 * q + r] = lo[r];
+      }
     } else {
       // external or fitted bandpass: sums of x - b_c (integer b_c)
       const bool ext = a.stats_mode == TP_STATS_EXTERNAL || a.fit || a.run;
@@ -646,9 +763,12 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
       if (t0 + tid < a.nsamp) {
         const double thr = a.spec_thr[(t0 + tid) / a.W];
         if constexpr (!kU8) {
-          double m = 0.0;
-          for (int w = 0; w < 32; ++w) m += s_f[w][tid];
-          flag = m > thr;
+          float mh = 0.f, ml = 0.f;
+          for (int w = 0; w < 32; ++w) {
+            two_sum_acc(mh, ml, s_fh[w][tid]);
+            ml += s_fl[w][tid];
+          }
+          flag = (double)mh + (double)ml > thr;
         } else {
           long long m = 0;
           for (int w = 0; w < 32; ++w) m += s_i[w][tid];
@@ -1132,18 +1252,9 @@ cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypitch, cudaStream_t s) {
-  if (a.dtype == TP_U8)
-    chunk_stats_u8<<<a.nchan, kThreads, 0, s>>>(a, static_cast<longlong2*>(chunk_sums));
-  else if (a.dtype == TP_F16)
-    chunk_stats_float<TP_F16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
-  else if (a.dtype == TP_BF16)
-    chunk_stats_float<TP_BF16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
-  else if (a.dtype == TP_C16)
-    chunk_stats_float<TP_C16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
-  else
-    chunk_stats_float<TP_F32><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
-  cudaError_t e = cudaGetLastError();
+cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypitch, cudaStream_t s, int* kernels) {
+  int nk = 2;  // the statistics kernels
+  cudaError_t e = launch_stats(a, chunk_sums, s);
   if (e != cudaSuccess) return e;
   const int64_t nflag_bytes = (int64_t)a.nchan * a.nchunk;
   if (a.fit) {
@@ -1153,26 +1264,31 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypit
     e = cudaFuncSetAttribute(bandpass_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     bandpass_fit_kernel<<<1, kFitThreads, sm, s>>>(a);
+    ++nk;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.enable_channel) {
       fit_chunk_test_kernel<<<a.nchan, kThreads, 0, s>>>(a, chunk_sums);
+      ++nk;
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
   }
   if (a.run) {
     running_update_kernel<<<(a.nchan + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+    ++nk;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.enable_channel) {
       running_chunk_test_kernel<<<a.nchan, kThreads, 0, s>>>(a, chunk_sums);
+      ++nk;
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
   }
   if (a.enable_channel) {
     dilate_kernel<<<(a.nchan + kWarps - 1) / kWarps, kThreads, 0, s>>>(a);
+    ++nk;
   } else {
     e = cudaMemsetAsync(a.chunk_raw, 0, nflag_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.chunk_flag, 0, nflag_bytes, s);
@@ -1180,6 +1296,8 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypit
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  nk += 2;  // spectrum thresholds and substitution
+  if (kernels) *kernels += nk;
   spectrum_threshold_kernel<<<(unsigned)((a.nchunk + kWarps - 1) / kWarps), kThreads, 0, s>>>(a);
   const unsigned blocks = (unsigned)((a.nsamp + 31) / 32);
   if (a.dtype == TP_C16)
@@ -1199,17 +1317,7 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypit
 // with the chunk sums in caller-chosen scratch; used by the entry point that
 // allocates nothing.
 cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s) {
-  if (a.dtype == TP_U8)
-    chunk_stats_u8<<<a.nchan, kThreads, 0, s>>>(a, static_cast<longlong2*>(chunk_sums));
-  else if (a.dtype == TP_F16)
-    chunk_stats_float<TP_F16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
-  else if (a.dtype == TP_BF16)
-    chunk_stats_float<TP_BF16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
-  else if (a.dtype == TP_C16)
-    chunk_stats_float<TP_C16><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
-  else
-    chunk_stats_float<TP_F32><<<a.nchan, kThreads, 0, s>>>(a, static_cast<double2*>(chunk_sums));
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_stats(a, chunk_sums, s);
   if (e != cudaSuccess) return e;
   const int64_t nflag_bytes = (int64_t)a.nchan * a.nchunk;
   if (a.enable_channel) {

@@ -274,7 +274,7 @@ constexpr int kDetectT = 4096;      // samples per detection CTA
 cudaError_t launch_delay_table(int nchan, double f_lo, double bw, double t_samp, const double* dm,
                                int ndm, int32_t* delay, int* err_flag, cudaStream_t s);
 cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypitch,
-                       cudaStream_t s);
+                       cudaStream_t s, int* kernels = nullptr);
 cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_t s);
 // ctas = work items; grid_limit < 0: one CTA per item, 0: a persistent grid
 // (as many CTAs as are resident at once), > 0: at most that many CTAs
