@@ -112,6 +112,16 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// (hi, lo) += v: hi takes the FP32 sum, lo its exact rounding error (Knuth's
+// two_sum, six FP32 operations; nothing is contracted: --fmad=false)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bv = s - hi;
+  const float av = s - bv;
+  lo += (hi - av) + (v - bv);
+  hi = s;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -300,15 +310,37 @@ __global__ void __launch_bounds__(kThreads) channel_stats_float(RfiArgs a, const
     sig = a.sigma[c];
   } else {
     double S = 0.0, Q = 0.0;
-    for (int k = lane; k < a.nchunk; k += 32) {
-      const double2 v = chunk_sum(k);
-      S += v.x;
-      Q += v.y;
-    }
+    if (single) {
+      // FP32 chunk sums: totals carried as exact FP32 pairs (two_sum), the
+      // lanes' pairs combined in a fixed butterfly order
+      float sh = 0.f, sl = 0.f, qh = 0.f, ql = 0.f;
+      for (int k = lane; k < a.nchunk; k += 32) {
+        const float2 v = sums32[k];
+        two_sum_acc(sh, sl, v.x);
+        two_sum_acc(qh, ql, v.y);
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      S += __shfl_xor_sync(0xffffffffu, S, o);
-      Q += __shfl_xor_sync(0xffffffffu, Q, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        const float osh = __shfl_xor_sync(0xffffffffu, sh, o), osl = __shfl_xor_sync(0xffffffffu, sl, o);
+        const float oqh = __shfl_xor_sync(0xffffffffu, qh, o), oql = __shfl_xor_sync(0xffffffffu, ql, o);
+        two_sum_acc(sh, sl, osh);
+        sl += osl;
+        two_sum_acc(qh, ql, oqh);
+        ql += oql;
+      }
+      S = (double)sh + (double)sl;
+      Q = (double)qh + (double)ql;
+    } else {
+      for (int k = lane; k < a.nchunk; k += 32) {
+        const double2 v = chunk_sum(k);
+        S += v.x;
+        Q += v.y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, o);
+        Q += __shfl_xor_sync(0xffffffffu, Q, o);
+      }
     }
     const double N = (double)a.nsamp;
     m = S / N;
@@ -332,12 +364,27 @@ __global__ void __launch_bounds__(kThreads) channel_stats_float(RfiArgs a, const
   if (!a.enable_channel || a.fit || a.run) return;
   const double tsig = a.tau_c * sig;
   const double thr_w = tsig * sqrt((double)a.W);  // the threshold of a full chunk
+  // full chunks with FP32 sums are first tested in FP32: e32 - thr32 is
+  // within 2^-23 (|s_k| + |W m| + |thr|) of the binary64 e - thr, so outside
+  // a guard band eight times wider the FP32 sign is the binary64 decision;
+  // inside it (and for non-finite values) the binary64 test decides
+  const float thr32 = (float)thr_w, nm32 = (float)((double)a.W * m);
   for (int k = lane; k < a.nchunk; k += 32) {
     const int64_t lo = (int64_t)k * a.W;
     const int64_t n = (lo + a.W < a.nsamp ? lo + a.W : a.nsamp) - lo;
-    const double2 cs = chunk_sum(k);
-    const double e = cs.x - (double)n * m;
-    a.chunk_raw[(int64_t)c * a.nchunk + k] = (uint8_t)(e > (n == a.W ? thr_w : tsig * sqrt((double)n)));
+    int ex = 2;
+    if (single && n == a.W) {
+      const float cx = sums32[k].x;
+      const float d = (cx - nm32) - thr32;
+      const float guard = 9.5367431640625e-7f * (fabsf(cx) + fabsf(nm32) + fabsf(thr32));
+      ex = d > guard ? 1 : (-d > guard ? 0 : 2);
+    }
+    if (ex == 2) {
+      const double2 cs = chunk_sum(k);
+      const double e = cs.x - (double)n * m;
+      ex = e > (n == a.W ? thr_w : tsig * sqrt((double)n)) ? 1 : 0;
+    }
+    a.chunk_raw[(int64_t)c * a.nchunk + k] = (uint8_t)ex;
   }
 }
 
@@ -616,16 +663,6 @@ __global__ void __launch_bounds__(kThreads) spectrum_threshold_kernel(RfiArgs a)
 // samples of unflagged chunks over channels (FP32 runs of 8 channels folded
 // into FP64; exact integers for 8-bit data); pass 2 re-reads the tile (an L2
 // hit) and writes y.
-// (hi, lo) += v: hi takes the FP32 sum, lo its exact rounding error (Knuth's
-// two_sum, six FP32 operations; nothing is contracted: --fmad=false)
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bv = s - hi;
-  const float av = s - bv;
-  lo += (hi - av) + (v - bv);
-  hi = s;
-}
-
 template <int DT>
 __device__ __forceinline__ void load_quad(const void* x, int64_t i, int64_t valid, float (&v)[4]) {
   if (valid >= 4) {
@@ -663,6 +700,32 @@ __device__ __forceinline__ void load_quad(const void* x, int64_t i, int64_t vali
         v[r] = 0.f;
       }
     }
+  }
+}
+
+// Stores staged FP32 values o[0 .. n) of channel c, samples tq .. tq + n - 1:
+// plainly (y[c][t], a float4 for a full quad), or, with a pair distance
+// P > 0, into the row of pairs (y[u], y[u + P]): as the low word of pair t
+// and the high word of pair t - P.  The high words of the last P pairs of a
+// window feed only outputs past its end.
+__device__ __forceinline__ void store_staged_f32(const RfiArgs& a, void* yv, int64_t ypitch, int c, int64_t tq,
+                                                 const float (&o)[4], int n) {
+  if (a.pair_dist == 0) {
+    float* dst = static_cast<float*>(yv) + (int64_t)c * ypitch + tq;
+    if (n == 4) {
+      *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+      for (int r = 0; r < n; ++r) dst[r] = o[r];
+    }
+    return;
+  }
+  float* row = static_cast<float*>(yv) + 2 * (int64_t)c * ypitch;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if (r >= n) break;
+    const int64_t t = tq + r;
+    row[2 * t] = o[r];
+    if (t >= a.pair_dist) row[2 * (t - a.pair_dist) + 1] = o[r];
   }
 }
 
@@ -797,16 +860,17 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   // integers)
   if (valid == 0) return;
   if (valid == 4) {
-    // full 4-sample quads: raw loads of 4 channels (c, c + 32, c + 64,
-    // c + 96) issued together, then substitution and stores
+    // full 4-sample quads: raw loads of 8 channels (c, c + 32, ..., c + 224)
+    // issued together, then substitution and stores
     using Raw = typename std::conditional<
         DT == TP_F32, float4,
         typename std::conditional<DT == TP_C16, int4,
                                   typename std::conditional<DT == TP_U8, unsigned, uint2>::type>::type>::type;
-    for (int c0 = g; c0 < a.nchan; c0 += 32 * 4) {
-      Raw raw[4];
+    constexpr int kU = 8;
+    for (int c0 = g; c0 < a.nchan; c0 += 32 * kU) {
+      Raw raw[kU];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kU; ++u) {
         const int c = c0 + 32 * u;
         if (c < a.nchan) {
           if (in_bounds((int64_t)c * a.pitch + tq, 4, a.x_elems, a.status))
@@ -817,7 +881,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kU; ++u) {
         const int c = c0 + 32 * u;
         if (c >= a.nchan) break;
         if (!in_bounds((int64_t)c * ypitch + tq, 4, a.y_elems, a.status)) continue;
@@ -837,8 +901,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
           float o[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - mh) - ml;
-          *reinterpret_cast<float4*>(static_cast<float*>(yv) + (int64_t)c * ypitch + tq) =
-              make_float4(o[0], o[1], o[2], o[3]);
+          store_staged_f32(a, yv, ypitch, c, tq, o, 4);
         } else if constexpr (DT == TP_U8) {
           const unsigned b = (unsigned)a.bint[c];
           unsigned h[4];
@@ -857,9 +920,9 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
             // rounding of the difference of two exactly converted stored
             // values; flagged samples give exactly 0
             const float bf = bits_to_float<DT>(b);
-            *reinterpret_cast<float4*>(static_cast<float*>(yv) + (int64_t)c * ypitch + tq) =
-                make_float4(bits_to_float<DT>(h[0]) - bf, bits_to_float<DT>(h[1]) - bf,
-                            bits_to_float<DT>(h[2]) - bf, bits_to_float<DT>(h[3]) - bf);
+            const float o[4] = {bits_to_float<DT>(h[0]) - bf, bits_to_float<DT>(h[1]) - bf,
+                                bits_to_float<DT>(h[2]) - bf, bits_to_float<DT>(h[3]) - bf};
+            store_staged_f32(a, yv, ypitch, c, tq, o, 4);
           } else {
             *reinterpret_cast<uint2*>(static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq) =
                 make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16));
@@ -886,12 +949,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
       float o[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - mh) - ml;
-      float* dst = static_cast<float*>(yv) + (int64_t)c * ypitch + tq;
-      if (valid == 4) {
-        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-      } else {
-        for (int r = 0; r < valid; ++r) dst[r] = o[r];
-      }
+      store_staged_f32(a, yv, ypitch, c, tq, o, valid);
     } else if constexpr (DT == TP_U8) {
       // 8-bit data: x~ (flagged -> b) widened to 16-bit integers
       const uint8_t* src = static_cast<const uint8_t*>(a.x) + (int64_t)c * a.pitch + tq;
@@ -929,12 +987,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
         float o[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) o[r] = bits_to_float<DT>(h[r]) - bf;
-        float* dst = static_cast<float*>(yv) + (int64_t)c * ypitch + tq;
-        if (valid == 4) {
-          *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-        } else {
-          for (int r = 0; r < valid; ++r) dst[r] = o[r];
-        }
+        store_staged_f32(a, yv, ypitch, c, tq, o, valid);
         continue;
       }
       unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
