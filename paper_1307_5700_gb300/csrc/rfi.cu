@@ -1001,6 +1001,184 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   }
 }
 
+// A3 + A4 for float data when each CTA's 32 samples lie in one chunk (W a
+// multiple of 32) and the channels' parameters fit shared memory: the same
+// arithmetic as spectrum_substitute_kernel, in the same order (so the same
+// flags and the same staged values), with every channel's (mu_hi, mu_lo),
+// chunk flag for the CTA's chunk and 16-bit bandpass value read once per CTA
+// into shared memory instead of once per channel and pass by every thread.
+constexpr int kTileMaxChannels = 4096;
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, void* __restrict__ yv,
+                                                                     int64_t ypitch) {
+  static_assert(DT != TP_U8, "float data");
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  float2* s_mu = reinterpret_cast<float2*>(s_dyn);                            // [nchan] (mu_hi, mu_lo)
+  unsigned short* s_b16 = reinterpret_cast<unsigned short*>(s_mu + a.nchan);  // [nchan] (16-bit data)
+  uint8_t* s_cf = reinterpret_cast<uint8_t*>(s_b16 + a.nchan);                // [nchan] chunk flag
+  __shared__ float s_fh[32][33], s_fl[32][33];
+  __shared__ unsigned s_word;
+  const int tid = threadIdx.x;
+  const int g = tid >> 3, q = tid & 7;
+  const int64_t t0 = (int64_t)blockIdx.x * 32;
+  const int64_t tq = t0 + 4 * q;
+  const int64_t left = a.nsamp - tq;
+  const int valid = left >= 4 ? 4 : (left > 0 ? (int)left : 0);
+  const int k = (int)(t0 / a.W);
+  for (int c = tid; c < a.nchan; c += kThreads) {
+    s_mu[c] = make_float2(a.mu_hi[c], a.mu_lo[c]);
+    if constexpr (DT == TP_F16 || DT == TP_BF16) s_b16[c] = a.b16[c];
+    s_cf[c] = (uint8_t)(a.chan_nflag[c] != 0 && a.chunk_flag[(int64_t)c * a.nchunk + k]);
+  }
+  __syncthreads();
+
+  if (a.enable_spectrum) {
+    // (hi, lo): the running sum of the groups' FP32 partial sums, exact
+    // (two_sum); channels g, g + 32, ... in groups of 8, the group's loads
+    // issued together
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
+      float v[8][4];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + 32 * u;
+        if (c < a.nchan) {
+          if (in_bounds((int64_t)c * a.pitch + tq, valid, a.x_elems, a.status))
+            load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v[u]);
+          else
+            v[u][0] = v[u][1] = v[u][2] = v[u][3] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + 32 * u;
+        if (c >= a.nchan) break;
+        const float2 m = s_mu[c];
+        if (!s_cf[c]) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (r < valid) part[r] += (v[u][r] - m.x) - m.y;
+        }
+      }
+      if (c0 + 32 * 7 < a.nchan) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          two_sum_acc(hi[r], lo[r], part[r]);
+          part[r] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      two_sum_acc(hi[r], lo[r], part[r]);
+      s_fh[g][4 * q + r] = hi[r];
+      s_fl[g][4 * q + r] = lo[r];
+    }
+    __syncthreads();
+    if (tid < 32) {
+      bool flag = false;
+      if (t0 + tid < a.nsamp) {
+        float mh = 0.f, ml = 0.f;
+        for (int w = 0; w < 32; ++w) {
+          two_sum_acc(mh, ml, s_fh[w][tid]);
+          ml += s_fl[w][tid];
+        }
+        flag = (double)mh + (double)ml > a.spec_thr[k];
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, flag);
+      if (tid == 0) {
+        s_word = bits;
+        if (t0 < a.nsamp) a.spec_bits[t0 >> 5] = bits;
+        if (bits) atomicAdd(a.spec_nflag, __popc(bits));
+      }
+    }
+  } else if (tid == 0) {
+    s_word = 0u;
+    if (t0 < a.nsamp) a.spec_bits[t0 >> 5] = 0u;
+  }
+  __syncthreads();
+  const unsigned word = s_word;
+  bool sflag[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) sflag[r] = (word >> (4 * q + r)) & 1u;
+  if (valid == 0) return;
+
+  // pass 2: y = x - mu (flagged -> 0) in FP32, or the 16-bit stored samples
+  // x~ (flagged -> b16), or x~ - b16 in FP32 (stage_f32); 8 channels' loads
+  // issued together
+  using Raw = typename std::conditional<DT == TP_F32, float4,
+                                        typename std::conditional<DT == TP_C16, int4, uint2>::type>::type;
+  for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
+    Raw raw[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + 32 * u;
+      if (c < a.nchan && valid == 4 && in_bounds((int64_t)c * a.pitch + tq, 4, a.x_elems, a.status))
+        raw[u] = __ldg(reinterpret_cast<const Raw*>(static_cast<const char*>(a.x) +
+                                                    ((int64_t)c * a.pitch + tq) * sizeof(Raw) / 4));
+      else
+        raw[u] = Raw{};
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + 32 * u;
+      if (c >= a.nchan) break;
+      if (!in_bounds((int64_t)c * ypitch + tq, valid, a.y_elems, a.status)) continue;
+      const bool cfl = s_cf[c] != 0;
+      bool fl[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) fl[r] = sflag[r] || cfl;
+      if constexpr (kStagedF32<DT>) {
+        float v[4];
+        if (valid == 4) {
+          if constexpr (DT == TP_C16)
+            v[0] = c16_power(raw[u].x), v[1] = c16_power(raw[u].y), v[2] = c16_power(raw[u].z),
+            v[3] = c16_power(raw[u].w);
+          else
+            v[0] = raw[u].x, v[1] = raw[u].y, v[2] = raw[u].z, v[3] = raw[u].w;
+        } else {
+          load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
+        }
+        const float2 m = s_mu[c];
+        float o[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - m.x) - m.y;
+        store_staged_f32(a, yv, ypitch, c, tq, o, valid);
+      } else {
+        unsigned short h[4];
+        if (valid == 4) {
+          h[0] = raw[u].x & 0xffff, h[1] = raw[u].x >> 16, h[2] = raw[u].y & 0xffff, h[3] = raw[u].y >> 16;
+        } else {
+          const unsigned short* src = static_cast<const unsigned short*>(a.x) + (int64_t)c * a.pitch + tq;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) h[r] = r < valid ? __ldg(src + r) : 0;
+        }
+        const unsigned short b = s_b16[c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) h[r] = fl[r] ? b : h[r];
+        if (a.stage_f32) {
+          // y = x~ - b, one rounding of the difference of two exactly
+          // converted stored values; flagged samples give exactly 0
+          const float bf = bits_to_float<DT>(b);
+          const float o[4] = {bits_to_float<DT>(h[0]) - bf, bits_to_float<DT>(h[1]) - bf,
+                              bits_to_float<DT>(h[2]) - bf, bits_to_float<DT>(h[3]) - bf};
+          store_staged_f32(a, yv, ypitch, c, tq, o, valid);
+        } else {
+          unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
+          if (valid == 4) {
+            *reinterpret_cast<uint2*>(dst) = make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16),
+                                                        (unsigned)h[2] | ((unsigned)h[3] << 16));
+          } else {
+            for (int r = 0; r < valid; ++r) dst[r] = h[r];
+          }
+        }
+      }
+    }
+  }
+}
+
 // ---- fitted bandpass (Sec. 2.2.1 "Bandpass Correction") ---------------------------
 //
 // bandpass_fit_kernel (one CTA): local excess of each block mean over its
@@ -1305,6 +1483,17 @@ cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, 
   return cudaGetLastError();
 }
 
+template <int DT>
+cudaError_t launch_tile(const RfiArgs& a, void* y, int64_t ypitch, unsigned blocks, size_t sm, cudaStream_t s) {
+  if (sm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(spectrum_substitute_tile<DT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  spectrum_substitute_tile<DT><<<blocks, kThreads, sm, s>>>(a, y, ypitch);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypitch, cudaStream_t s, int* kernels) {
   int nk = 2;  // the statistics kernels
   cudaError_t e = launch_stats(a, chunk_sums, s);
@@ -1353,6 +1542,13 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypit
   if (kernels) *kernels += nk;
   spectrum_threshold_kernel<<<(unsigned)((a.nchunk + kWarps - 1) / kWarps), kThreads, 0, s>>>(a);
   const unsigned blocks = (unsigned)((a.nsamp + 31) / 32);
+  if (a.dtype != TP_U8 && a.W % 32 == 0 && a.nchan <= kTileMaxChannels) {
+    const size_t sm = (size_t)a.nchan * (sizeof(float2) + sizeof(unsigned short) + 1);
+    if (a.dtype == TP_C16) return launch_tile<TP_C16>(a, y, ypitch, blocks, sm, s);
+    if (a.dtype == TP_F16) return launch_tile<TP_F16>(a, y, ypitch, blocks, sm, s);
+    if (a.dtype == TP_BF16) return launch_tile<TP_BF16>(a, y, ypitch, blocks, sm, s);
+    return launch_tile<TP_F32>(a, y, ypitch, blocks, sm, s);
+  }
   if (a.dtype == TP_C16)
     spectrum_substitute_kernel<TP_C16><<<blocks, kThreads, 0, s>>>(a, y, ypitch);
   else if (a.dtype == TP_U8)

@@ -263,9 +263,11 @@ def test_paired_staging_equals_plain(dtype):
     element holds the samples of both output segments) add the same binary32
     values in the same order as the same kernel over plain staging (shape
     53, same S): the series are bit-identical, over a window with a ragged
-    last time tile and an incomplete last group of trials."""
+    last time tile and an incomplete last group of trials (DM step 0.18:
+    every step between consecutive trials, the last group's included, stays
+    within the FP32 quads' bound of 9 samples)."""
     nchan, nsamp = 256, 9001
-    dms = np.arange(62) * 0.2
+    dms = np.arange(62) * 0.18
     f_lo, bw, ts = 398.0, 20.0, 51.2e-6
     xf = synth.noise(nchan, nsamp, 7201)
     xf[40, 2000:2600] += 12.0
