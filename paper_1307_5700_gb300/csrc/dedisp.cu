@@ -38,7 +38,7 @@ const KernelShape kShapes[kNumShapes] = {TP_SHAPES(TP_SHAPE_ENTRY)};
 
 int shape_tile_t(int shape) {
   const int algo = kShapes[shape].ALGO;
-  return (algo == 4 || algo == 6 || algo == 13 ? 64 : 32) * kShapes[shape].S;  // two output segments per lane
+  return (algo == 4 || algo == 6 ? 64 : 32) * kShapes[shape].S;  // two output segments per lane
 }
 
 cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s, int grid_limit) {

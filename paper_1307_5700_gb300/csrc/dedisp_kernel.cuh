@@ -154,29 +154,23 @@ struct Shape {
   // producer warp (every consumer warp issues the copies of every NCONS-th
   // stage)
   static constexpr bool ROT = ALGO >= 6;
-  // ALGO 13: the scheme of ALGO 6 over a staged row of pairs (y[u], y[u + 32 S])
-  static constexpr bool PAIR = ALGO == 13;
-  static constexpr int AB = PAIR ? 4 : ALGO >= 8 ? 3 : ROT ? ALGO - 2 : ALGO;
+  static constexpr int AB = ALGO >= 8 ? 3 : ROT ? ALGO - 2 : ALGO;
   // ALGO 9-11: the 8-bit quads of ALGO 8 with every channel of a stage added
   // in one call (variant ALGO - 6 of add_quad8t)
   static constexpr bool THREADED = ALGO >= 9 && ALGO <= 11;
   // ALGO 12: ALGO 8 with the copies issued four stages ahead of their use
   // over eight stage buffers (the 8-bit rows are half as long as FP32 ones)
   static constexpr int LOOK = ALGO == 12 ? 4 : kLookRot;
-  static constexpr int EB = PAIR ? 8 : MODE == kModeF32 ? 4 : 2;              // bytes per staged element
+  static constexpr int EB = MODE == kModeF32 ? 4 : 2;                         // bytes per sample
   static constexpr int QS = 16 / EB;                                          // samples per 16 B
   static constexpr int NSEG = AB == 4 ? 2 : 1;                              // output segments per lane
   static constexpr int TT = 32 * S * NSEG;                                    // outputs per tile
-  // outputs a staged row spans (a pair element covers both segments)
-  static constexpr int TS = PAIR ? 32 * S : TT;
   static constexpr int L = (S + OMAX + 1 + QS - 1) / QS * QS;                 // window samples
   static constexpr int LR = L * EB / 4;                                       // window registers
   // largest in-row offset of a warp's last trial past its first (the quad
   // schemes: three steps of at most OMAX + 1)
   static constexpr int OSPAN = AB >= 3 ? 3 * (OMAX + 1) : OMAX;
-  // largest delay spread of a tile (pair rows are twice as wide per element)
-  static constexpr int OVH = PAIR ? kMaxOverhangPair : kMaxOverhang;
-  static constexpr int ROW = (TS + OVH + OSPAN + 2 * QS + 63) / 64 * 64;  // staged elements
+  static constexpr int ROW = (TT + kMaxOverhang + OSPAN + 2 * QS + 63) / 64 * 64;  // staged samples
   static constexpr int ROWB = ROW * EB;
   static constexpr int THREADS = (NCONS + (ROT ? 0 : 1)) * 32;               // + one producer warp
   static constexpr int DW = NCONS * K <= 32 ? 32 : 64;                        // delays staged per channel
@@ -184,8 +178,8 @@ struct Shape {
   // both fit the SM's shared memory
   static constexpr int STAGES = MODE == kModeU8 && AB == 1 ? kStagesU8
                                 : ALGO == 12                ? 8
-                                : ROT ? (MINB >= 2 || PAIR ? kStagesRot - 1 : kStagesRot)
-                                      : kStages;
+                                : ROT                       ? (MINB >= 2 ? kStagesRot - 1 : kStagesRot)
+                                                            : kStages;
   static constexpr size_t data_bytes = (size_t)STAGES * kNC * ROWB;
   static constexpr size_t del_bytes = sizeof(int) * (ROT ? NCONS : kDelRing) * kNC * DW;  // ring, or a slot per warp
   // 8-bit mode: per (stage, consumer warp) K int4 of word offsets (one per
@@ -199,7 +193,7 @@ struct Shape {
   static_assert(smem <= 227 * 1024, "shared memory per CTA");
   // no bank conflicts: register windows (scheme 0) start an odd number of 16-byte
   // units apart, direct 32-bit loads (scheme 1) an odd number of words apart
-  static_assert(PAIR ? S % 2 == 1 : AB >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
+  static_assert(AB >= 1 ? ((S * EB / 4) % 2 == 1) : ((S * EB / 16) % 2 == 1), "lane stride");
   static_assert(AB != 2 || (MODE != kModeU8 && K == 2), "DM-pair windows: float data, two trials per warp");
   static_assert(AB < 3 || K == 4, "DM-quad windows: four trials per warp");
   static_assert(AB < 4 || MODE == kModeF32, "paired-add DM quads: FP32 staging");
@@ -379,7 +373,7 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
     if (lane < kNC && i * kNC + lane < nchan) {
       const int lo = del[lane * DW], hi = del[lane * DW + last];
       const int head = (t0m + lo) & (QS - 1);  // row start = t0 + lo - head
-      nb = (unsigned)(((Sh::TS + hi - lo + QS + head) * EB + 15) & ~15);
+      nb = (unsigned)(((TT + hi - lo + QS + head) * EB + 15) & ~15);
       src = ((int64_t)(i * kNC + lane) * a.ypitch + t0 + lo - head) * EB;
       if constexpr (kDebugBounds) {
         // the copy fits its shared-memory row and stays inside the channel's
@@ -656,9 +650,7 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
 #pragma unroll 1
         for (int ci = 0; ci < nc; ++ci) {
           const int4 inf = sinfo[(buf * kNC + ci) * NCONS + warp];
-          if constexpr (Sh::PAIR)
-            add_quad2p<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc2);
-          else if constexpr (AB == 5)
+          if constexpr (AB == 5)
             add_quadp<S, OMAX>(inf.y, sbase + (unsigned)inf.x, accp, acct);
           else if constexpr (AB == 4)
             add_quad2<S, OMAX>(inf.y, sbase + (unsigned)inf.x, acc2);

@@ -19,10 +19,7 @@
 // FP32 add (S odd; FP32 staging only);
 // ALGO 6, 7, 8: ALGO 4, 5, 3 without a producer warp: all NCONS warps consume,
 // and warp w also issues the copies of stages w, w + NCONS, ...;
-// ALGO 9: ALGO 8 (8-bit data) with threaded dispatch over a stage's channels;
-// ALGO 13: ALGO 6 over a staged row of pairs (y[u], y[u + 32 S]), so that one
-// 64-bit shared load gives the window sample of both output segments.
-// ALGO 10-12 are variants of ALGO 9 and 8 (see the kernel).
+// ALGO 9: ALGO 8 (8-bit data) with threaded dispatch over a stage's channels.
 // MINB: CTAs per SM the register allocation is sized for.
 #define TP_SHAPES(X)                 \
   X(0, 4, 20, 36, 8, 4, 0, 1)        \
@@ -92,11 +89,7 @@
   X(64, 4, 14, 16, 8, 3, 8, 2)       \
   X(65, 4, 14, 16, 8, 3, 10, 2)      \
   X(66, 4, 26, 16, 8, 3, 12, 1)      \
-  X(67, 4, 22, 16, 8, 3, 12, 1)      \
-  X(68, 4, 23, 9, 8, 4, 13, 1)       \
-  X(69, 4, 21, 9, 8, 4, 13, 1)       \
-  X(70, 4, 19, 9, 8, 4, 13, 1)       \
-  X(71, 4, 25, 9, 8, 4, 13, 1)
+  X(67, 4, 22, 16, 8, 3, 12, 1)
 
 namespace tp {
 constexpr int kDedispParts = 12;  // translation units the kernel instantiations are split over

@@ -64,10 +64,7 @@ bool format_ok(int dtype, int fmt) {
 
 // bytes per sample the staged series buffer is allocated with (room for
 // every format the dtype can use)
-// bytes per staged element of a beam's buffer: 8-bit data stage 16-bit
-// integers; float data stage FP32, or pairs of FP32 samples for the shapes
-// over paired staging (ALGO 13)
-int staged_bytes_alloc(int dtype) { return dtype == TP_U8 ? 2 : 8; }
+int staged_bytes_alloc(int dtype) { return dtype == TP_U8 ? 2 : 4; }
 
 // Nearest value of a 16-bit storage format (ties to even), from the format's
 // definition; the same rule the statistics kernel applies on the device.
@@ -340,7 +337,7 @@ int spread(const std::vector<int32_t>& delay, int nchan, int d0, int d1) {
 // (paired-add forms first), then DM pairs, then direct loads, then register
 // windows (the order of their launch times on a 1024-channel, 640-trial,
 // 2^17-sample block).
-constexpr int kShapePreference[kNumShapes] = {68, 69, 70, 71, 55, 53, 46, 56, 54, 52, 50, 51, 48, 49, 33, 44, 45,
+constexpr int kShapePreference[kNumShapes] = {55, 53, 46, 56, 54, 52, 50, 51, 48, 49, 33, 44, 45,
                                               57, 58, 59, 60, 61, 62, 63, 64, 65, 66, 67, 47, 34, 42, 31, 30, 32, 35, 39, 43, 41, 40,
                                               27, 25, 26, 24, 28, 29, 22, 18, 19, 12, 13, 14, 15,
                                               16, 17, 23, 21, 20, 8, 10, 1, 2, 5, 0, 3, 6,
@@ -384,18 +381,17 @@ bool make_tiles(const std::vector<int32_t>& delay, int ndm, int nchan, int dtype
       const int d1 = std::min(d0 + K, ndm) - 1;
       if (spread(delay, nchan, d0, d1) + residue > kShapes[sh].OMAX) return false;
     }
-  // the staging rows hold a tile's outputs plus at most ovh samples of delay
-  // spread, which a single group must respect too
-  const int ovh = kShapes[sh].ALGO == 13 ? kMaxOverhangPair : kMaxOverhang;
+  // the staging rows hold a tile's outputs plus at most kMaxOverhang samples
+  // of delay spread, which a single group must respect too
   for (int d0 = 0; d0 < ndm; d0 += K)
-    if (spread(delay, nchan, d0, std::min(d0 + K, ndm) - 1) > ovh) return false;
+    if (spread(delay, nchan, d0, std::min(d0 + K, ndm) - 1) > kMaxOverhang) return false;
   tiles->clear();
   int d0 = 0;
   while (d0 < ndm) {
     int ng = 1;
     while (ng < kShapes[sh].NCONS && d0 + ng * K < ndm) {
       const int d1 = std::min(d0 + (ng + 1) * K, ndm) - 1;
-      if (spread(delay, nchan, d0, d1) > ovh) break;
+      if (spread(delay, nchan, d0, d1) > kMaxOverhang) break;
       ++ng;
     }
     const int nd = std::min(ng * K, ndm - d0);
@@ -613,7 +609,6 @@ RfiArgs rfi_args(const tp_plan* p, Beam* b) {
   a.spec_nflag = b->spec_nflag;
   a.spec_thr = b->spec_thr;
   a.stage_f32 = (p->dtype == TP_F16 || p->dtype == TP_BF16) && kShapes[p->shape].FMT == 4;
-  a.pair_dist = kShapes[p->shape].ALGO == 13 ? 32 * kShapes[p->shape].S : 0;
   a.fit = p->fit_order >= 0 ? 1 : 0;
   a.fit_order = p->fit_order;
   a.tau_mask = p->tau_mask;

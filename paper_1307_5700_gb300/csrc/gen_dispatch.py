@@ -258,42 +258,6 @@ def emit_quad2(S, MMAX):
                    outs, '"r"(addr), "r"(b)')
 
 
-# (S, MMAX) of the FP32 two-segment DM-quad shapes over paired staging
-# (ALGO 13): S odd.
-QUADS2P = [(23, 9), (21, 9), (19, 9), (25, 9)]
-
-
-def emit_quad2p(S, MMAX):
-    """emit_quad2 over a staged row whose element u is the pair
-    (y[u], y[u + 32 S]) (8 bytes, segment 0 in the low word): one 64-bit
-    shared load gives the window sample of both segments, which one
-    add.rn.f32x2 adds into the accumulator pair of every trial that uses it.
-    Each accumulator takes the same binary32 adds in the same order as in
-    emit_quad2."""
-    nb = 8 * (MMAX + 1)
-    nw = S + 3 * (MMAX + 1)
-    ia = 4 * S
-    body = ["{", f".reg .b64 w<{nw}>;",
-            "tbl: .branchtargets " + ", ".join(f"C{b}" for b in range(nb)) + ";",
-            f"brx.idx.uni %{4 * S + 1}, tbl;"]
-    for b in range(nb):
-        o = quad_steps(b)
-        body.append(f"C{b}:")
-        for k in range(S + o[3]):
-            body.append(f"ld.shared.b64 w{k}, [%{ia}+{8 * k}];")
-            for j in range(4):
-                s_ = k - o[j]
-                if 0 <= s_ < S:
-                    r = j * S + s_
-                    body.append(f"add.rn.f32x2 %{r}, %{r}, w{k};")
-        if b != nb - 1:
-            body.append("bra.uni CEND;")
-    body += ["CEND:", "}"]
-    outs = ", ".join(f'"+l"(a[{j}][{s_}])' for j in range(4) for s_ in range(S))
-    return _asm_fn(f"void add_quad2p<{S}, {MMAX}>(int b, unsigned addr, unsigned long long (&a)[4][{S}])", body,
-                   outs, '"r"(addr), "r"(b)')
-
-
 # (S, MMAX) of the FP32 in-lane paired DM-quad shapes (ALGO 5): S odd.
 QUADSP = [(45, 9), (43, 9), (27, 9), (25, 9), (29, 9)]
 
@@ -534,11 +498,6 @@ def main():
         "template <int S, int MMAX>",
         "__device__ __forceinline__ void add_quad2(int b, unsigned addr, unsigned long long (&a)[4][S]);",
         "",
-        "// the same over a staged row of pairs (y[u], y[u + 32 S]): one 64-bit load",
-        "// gives a window sample of both segments",
-        "template <int S, int MMAX>",
-        "__device__ __forceinline__ void add_quad2p(int b, unsigned addr, unsigned long long (&a)[4][S]);",
-        "",
         "// four trials, FP32 samples, the lane's outputs s and s + S / 2 paired in",
         "// a[j][s] (low word first), output 2 (S / 2) in t[j]",
         "template <int S, int MMAX>",
@@ -589,8 +548,6 @@ def main():
         out.append(emit_quad2(S, MMAX))
     for S, MMAX in QUADSP:
         out.append(emit_quadp(S, MMAX))
-    for S, MMAX in QUADS2P:
-        out.append(emit_quad2p(S, MMAX))
     for S, MMAX in QUADS16:
         for kind in (0, 1):
             out.append(emit_quad16(S, MMAX, kind))

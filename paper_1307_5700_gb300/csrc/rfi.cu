@@ -703,29 +703,15 @@ __device__ __forceinline__ void load_quad(const void* x, int64_t i, int64_t vali
   }
 }
 
-// Stores staged FP32 values o[0 .. n) of channel c, samples tq .. tq + n - 1:
-// plainly (y[c][t], a float4 for a full quad), or, with a pair distance
-// P > 0, into the row of pairs (y[u], y[u + P]): as the low word of pair t
-// and the high word of pair t - P.  The high words of the last P pairs of a
-// window feed only outputs past its end.
-__device__ __forceinline__ void store_staged_f32(const RfiArgs& a, void* yv, int64_t ypitch, int c, int64_t tq,
-                                                 const float (&o)[4], int n) {
-  if (a.pair_dist == 0) {
-    float* dst = static_cast<float*>(yv) + (int64_t)c * ypitch + tq;
-    if (n == 4) {
-      *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-    } else {
-      for (int r = 0; r < n; ++r) dst[r] = o[r];
-    }
-    return;
-  }
-  float* row = static_cast<float*>(yv) + 2 * (int64_t)c * ypitch;
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    if (r >= n) break;
-    const int64_t t = tq + r;
-    row[2 * t] = o[r];
-    if (t >= a.pair_dist) row[2 * (t - a.pair_dist) + 1] = o[r];
+// Stores staged FP32 values o[0 .. n) of channel c, samples tq .. tq + n - 1
+// (a float4 for a full quad).
+__device__ __forceinline__ void store_staged_f32(void* yv, int64_t ypitch, int c, int64_t tq, const float (&o)[4],
+                                                 int n) {
+  float* dst = static_cast<float*>(yv) + (int64_t)c * ypitch + tq;
+  if (n == 4) {
+    *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+    for (int r = 0; r < n; ++r) dst[r] = o[r];
   }
 }
 
@@ -901,7 +887,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
           float o[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - mh) - ml;
-          store_staged_f32(a, yv, ypitch, c, tq, o, 4);
+          store_staged_f32(yv, ypitch, c, tq, o, 4);
         } else if constexpr (DT == TP_U8) {
           const unsigned b = (unsigned)a.bint[c];
           unsigned h[4];
@@ -922,7 +908,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
             const float bf = bits_to_float<DT>(b);
             const float o[4] = {bits_to_float<DT>(h[0]) - bf, bits_to_float<DT>(h[1]) - bf,
                                 bits_to_float<DT>(h[2]) - bf, bits_to_float<DT>(h[3]) - bf};
-            store_staged_f32(a, yv, ypitch, c, tq, o, 4);
+            store_staged_f32(yv, ypitch, c, tq, o, 4);
           } else {
             *reinterpret_cast<uint2*>(static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq) =
                 make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16));
@@ -949,7 +935,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
       float o[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - mh) - ml;
-      store_staged_f32(a, yv, ypitch, c, tq, o, valid);
+      store_staged_f32(yv, ypitch, c, tq, o, valid);
     } else if constexpr (DT == TP_U8) {
       // 8-bit data: x~ (flagged -> b) widened to 16-bit integers
       const uint8_t* src = static_cast<const uint8_t*>(a.x) + (int64_t)c * a.pitch + tq;
@@ -987,7 +973,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
         float o[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) o[r] = bits_to_float<DT>(h[r]) - bf;
-        store_staged_f32(a, yv, ypitch, c, tq, o, valid);
+        store_staged_f32(yv, ypitch, c, tq, o, valid);
         continue;
       }
       unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
@@ -1145,7 +1131,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, 
         float o[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - m.x) - m.y;
-        store_staged_f32(a, yv, ypitch, c, tq, o, valid);
+        store_staged_f32(yv, ypitch, c, tq, o, valid);
       } else {
         unsigned short h[4];
         if (valid == 4) {
@@ -1164,7 +1150,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, 
           const float bf = bits_to_float<DT>(b);
           const float o[4] = {bits_to_float<DT>(h[0]) - bf, bits_to_float<DT>(h[1]) - bf,
                               bits_to_float<DT>(h[2]) - bf, bits_to_float<DT>(h[3]) - bf};
-          store_staged_f32(a, yv, ypitch, c, tq, o, valid);
+          store_staged_f32(yv, ypitch, c, tq, o, valid);
         } else {
           unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
           if (valid == 4) {

@@ -90,7 +90,6 @@ struct RfiArgs {
   int* spec_nflag;        // [1] flagged spectra
   double* spec_thr;       // [nchunk] spectrum threshold of each chunk (its unflagged channels)
   int stage_f32;          // 16-bit data: stage y = x~ - b in FP32 (for the FP32 kernel shapes)
-  int pair_dist;          // > 0: stage FP32 pairs (y[u], y[u + pair_dist]) (ALGO 13 shapes)
   // fitted bandpass (Sec. 2.2.1 "Bandpass Correction"): fit = 1 turns it on
   // (0, the zero-initialised value, leaves the block statistics); the chunk
   // test then uses the fit b_c of order fit_order and its RMSE
@@ -188,7 +187,7 @@ struct KernelShape {
               // 5: DM quads with a lane's outputs s and s + S / 2 paired;
               // 6, 7, 8: 4, 5, 3 without a producer warp (consumers issue the copies)
 };
-constexpr int kNumShapes = 72;
+constexpr int kNumShapes = 68;
 extern const KernelShape kShapes[kNumShapes];
 int shape_tile_t(int shape);
 
@@ -269,7 +268,6 @@ constexpr int kMaxMedianWidth = 9;
 constexpr int kMinTileT = 256;      // smallest output tile any shape may use (sizes buffers)
 constexpr int kMaxTileT = 1472;     // largest output tile of any shape
 constexpr int kMaxOverhang = 512;   // max delay spread inside a CTA tile
-constexpr int kMaxOverhangPair = 320;  // the same for the shapes over paired staging (ALGO 13)
 constexpr int kDetectT = 4096;      // samples per detection CTA
 
 // ---- launchers (each returns a cudaError_t of the launch) -----------------------

@@ -88,28 +88,6 @@ def test_quads_two_segments(S, MMAX):
                 assert hi[j * S + s] == [(1, s + o[j])], (b, j, s)
 
 
-@pytest.mark.parametrize("S,MMAX", G.QUADS2P)
-def test_quads_two_segments_paired_staging(S, MMAX):
-    # staged element u is the pair (y[u], y[u + 32 S]): an accumulator pair
-    # (output s of segments 0 and 1 of trial j) takes pair s + o_j only
-    for b, body in _blocks(G.emit_quad2p(S, MMAX)).items():
-        o = G.quad_steps(b)
-        reg, acc = {}, defaultdict(list)
-        for ins in body:
-            m = re.fullmatch(r"ld\.shared\.b64 (\w+), \[%\d+\+(\d+)\];", ins)
-            if m:
-                assert int(m.group(2)) % 8 == 0
-                reg[m.group(1)] = int(m.group(2)) // 8
-                continue
-            m = re.fullmatch(r"add\.rn\.f32x2 %(\d+), %\1, (\w+);", ins)
-            assert m, ins
-            acc[int(m.group(1))].append(reg[m.group(2)])
-        for j in range(4):
-            for s in range(S):
-                assert acc[j * S + s] == [s + o[j]], (b, j, s)
-        assert len(acc) == 4 * S
-
-
 @pytest.mark.parametrize("S,MMAX", G.QUADSP)
 def test_quads_in_lane_pairs(S, MMAX):
     H = S // 2

@@ -257,41 +257,6 @@ def test_every_shape_elementwise(dtype):
         g.close()
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_paired_staging_equals_plain(dtype):
-    """The two-segment DM quads over paired staging (shape 68: each staged
-    element holds the samples of both output segments) add the same binary32
-    values in the same order as the same kernel over plain staging (shape
-    53, same S): the series are bit-identical, over a window with a ragged
-    last time tile and an incomplete last group of trials (DM step 0.18:
-    every step between consecutive trials, the last group's included, stays
-    within the FP32 quads' bound of 9 samples)."""
-    nchan, nsamp = 256, 9001
-    dms = np.arange(62) * 0.18
-    f_lo, bw, ts = 398.0, 20.0, 51.2e-6
-    xf = synth.noise(nchan, nsamp, 7201)
-    xf[40, 2000:2600] += 12.0
-    x = synth.to_bf16_bits(xf) if dtype == "bf16" else xf
-    g = GpuBeam(nchan, f_lo, bw, ts, dms, dtype, rfi=O.RfiParams())
-    try:
-        g.open(nsamp)
-        g.run(x)
-        _, feasible = tp.tp_plan_shapes(g.plan)
-        assert feasible[53] and feasible[68]
-        out = {}
-        for sh in (53, 68):
-            tp.tp_plan_set_shape(g.plan, sh)
-            tp.tp_beam_rewind(g.e, g.beam)
-            tp.tp_dedisperse(g.e, g.beam)
-            tp.tp_detect(g.e, g.beam)
-            cands, n, rc = tp.tp_get_candidates(g.e, g.beam, g.cap)
-            out[sh] = (tp.tp_get_series(g.e, g.beam, ndm=len(dms)), cands.copy(), n)
-        assert np.array_equal(out[53][0].view(np.uint32), out[68][0].view(np.uint32))
-        assert out[53][2] == out[68][2] and np.array_equal(out[53][1], out[68][1])
-    finally:
-        g.close()
-
-
 def _voltage_block(nchan, nsamp, od, seed):
     env = np.ones((nchan, nsamp), np.float32)
     d = min(40, od.shape[0] - 1)
