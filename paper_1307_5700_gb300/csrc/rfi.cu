@@ -987,6 +987,78 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_kernel(RfiArgs a
   }
 }
 
+// L2 eviction-priority policies and hinted 16- / 8-byte global accesses: the
+// spectrum stage reads its tile twice (pass 1, then pass 2 right after the
+// flags are known) and writes the staged series once; the first read keeps
+// its lines (evict_last), the re-read and the staged stores mark theirs as
+// the first to go (evict_first), so that the writes do not push the tile
+// out of L2 before its re-read.
+__device__ __forceinline__ uint64_t l2_policy(bool keep) {
+  uint64_t pol;
+  if (keep)
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  else
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint4 ld_hint16(const void* p, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_hint8(const void* p, uint64_t pol) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint16(void* p, uint4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_hint8(void* p, uint2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
+}
+
+// store_staged_f32 with the stores' L2 policy pol
+__device__ __forceinline__ void store_staged_f32_hint(void* yv, int64_t ypitch, int c, int64_t tq,
+                                                      const float (&o)[4], int n, uint64_t pol) {
+  float* dst = static_cast<float*>(yv) + (int64_t)c * ypitch + tq;
+  if (n == 4) {
+    st_hint16(dst, make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]), __float_as_uint(o[3])),
+              pol);
+  } else {
+    for (int r = 0; r < n; ++r) dst[r] = o[r];
+  }
+}
+
+// The raw 4-sample quad at element i of a float-data window (16 bytes of
+// FP32 or complex int16 samples, 8 bytes of 16-bit samples), with policy pol.
+template <int DT>
+__device__ __forceinline__ uint4 ld_raw_quad(const void* x, int64_t i, uint64_t pol) {
+  if constexpr (DT == TP_F32 || DT == TP_C16) {
+    return ld_hint16(static_cast<const uint32_t*>(x) + i, pol);
+  } else {
+    const uint2 u = ld_hint8(static_cast<const unsigned short*>(x) + i, pol);
+    return make_uint4(u.x, u.y, 0u, 0u);
+  }
+}
+
+// FP32 values of a raw quad (ld_raw_quad)
+template <int DT>
+__device__ __forceinline__ void raw_quad_values(uint4 u, float (&v)[4]) {
+  if constexpr (DT == TP_F32) {
+    v[0] = __uint_as_float(u.x), v[1] = __uint_as_float(u.y), v[2] = __uint_as_float(u.z), v[3] = __uint_as_float(u.w);
+  } else if constexpr (DT == TP_C16) {
+    v[0] = c16_power((int)u.x), v[1] = c16_power((int)u.y), v[2] = c16_power((int)u.z), v[3] = c16_power((int)u.w);
+  } else {
+    v[0] = bits_to_float<DT>((unsigned short)(u.x & 0xffff)), v[1] = bits_to_float<DT>((unsigned short)(u.x >> 16));
+    v[2] = bits_to_float<DT>((unsigned short)(u.y & 0xffff)), v[3] = bits_to_float<DT>((unsigned short)(u.y >> 16));
+  }
+}
+
 // A3 + A4 for float data when each CTA's 32 samples lie in one chunk (W a
 // multiple of 32) and the channels' parameters fit shared memory: the same
 // arithmetic as spectrum_substitute_kernel, in the same order (so the same
@@ -1012,6 +1084,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, 
   const int64_t left = a.nsamp - tq;
   const int valid = left >= 4 ? 4 : (left > 0 ? (int)left : 0);
   const int k = (int)(t0 / a.W);
+  const uint64_t keep = l2_policy(true), drop = l2_policy(false);
   for (int c = tid; c < a.nchan; c += kThreads) {
     s_mu[c] = make_float2(a.mu_hi[c], a.mu_lo[c]);
     if constexpr (DT == TP_F16 || DT == TP_BF16) s_b16[c] = a.b16[c];
@@ -1031,10 +1104,12 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, 
       for (int u = 0; u < 8; ++u) {
         const int c = c0 + 32 * u;
         if (c < a.nchan) {
-          if (in_bounds((int64_t)c * a.pitch + tq, valid, a.x_elems, a.status))
-            load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v[u]);
-          else
+          if (!in_bounds((int64_t)c * a.pitch + tq, valid, a.x_elems, a.status))
             v[u][0] = v[u][1] = v[u][2] = v[u][3] = 0.f;
+          else if (valid == 4)
+            raw_quad_values<DT>(ld_raw_quad<DT>(a.x, (int64_t)c * a.pitch + tq, keep), v[u]);
+          else
+            load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v[u]);
         }
       }
 #pragma unroll
@@ -1094,18 +1169,15 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, 
   // pass 2: y = x - mu (flagged -> 0) in FP32, or the 16-bit stored samples
   // x~ (flagged -> b16), or x~ - b16 in FP32 (stage_f32); 8 channels' loads
   // issued together
-  using Raw = typename std::conditional<DT == TP_F32, float4,
-                                        typename std::conditional<DT == TP_C16, int4, uint2>::type>::type;
   for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
-    Raw raw[8];
+    uint4 raw[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int c = c0 + 32 * u;
       if (c < a.nchan && valid == 4 && in_bounds((int64_t)c * a.pitch + tq, 4, a.x_elems, a.status))
-        raw[u] = __ldg(reinterpret_cast<const Raw*>(static_cast<const char*>(a.x) +
-                                                    ((int64_t)c * a.pitch + tq) * sizeof(Raw) / 4));
+        raw[u] = ld_raw_quad<DT>(a.x, (int64_t)c * a.pitch + tq, drop);
       else
-        raw[u] = Raw{};
+        raw[u] = make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -1118,20 +1190,15 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, 
       for (int r = 0; r < 4; ++r) fl[r] = sflag[r] || cfl;
       if constexpr (kStagedF32<DT>) {
         float v[4];
-        if (valid == 4) {
-          if constexpr (DT == TP_C16)
-            v[0] = c16_power(raw[u].x), v[1] = c16_power(raw[u].y), v[2] = c16_power(raw[u].z),
-            v[3] = c16_power(raw[u].w);
-          else
-            v[0] = raw[u].x, v[1] = raw[u].y, v[2] = raw[u].z, v[3] = raw[u].w;
-        } else {
+        if (valid == 4)
+          raw_quad_values<DT>(raw[u], v);
+        else
           load_quad<DT>(a.x, (int64_t)c * a.pitch + tq, valid, v);
-        }
         const float2 m = s_mu[c];
         float o[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) o[r] = fl[r] ? 0.f : (v[r] - m.x) - m.y;
-        store_staged_f32(yv, ypitch, c, tq, o, valid);
+        store_staged_f32_hint(yv, ypitch, c, tq, o, valid, drop);
       } else {
         unsigned short h[4];
         if (valid == 4) {
@@ -1150,12 +1217,12 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, 
           const float bf = bits_to_float<DT>(b);
           const float o[4] = {bits_to_float<DT>(h[0]) - bf, bits_to_float<DT>(h[1]) - bf,
                               bits_to_float<DT>(h[2]) - bf, bits_to_float<DT>(h[3]) - bf};
-          store_staged_f32(yv, ypitch, c, tq, o, valid);
+          store_staged_f32_hint(yv, ypitch, c, tq, o, valid, drop);
         } else {
           unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
           if (valid == 4) {
-            *reinterpret_cast<uint2*>(dst) = make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16),
-                                                        (unsigned)h[2] | ((unsigned)h[3] << 16));
+            st_hint8(dst, make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16)),
+                     drop);
           } else {
             for (int r = 0; r < valid; ++r) dst[r] = h[r];
           }
