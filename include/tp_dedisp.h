@@ -357,6 +357,24 @@ int tp_run_ready(tp_engine *e, int use_graph, int *nbeams);
  * n_total > cap, TP_EOVERFLOW when n_total exceeded the beam capacity. */
 int tp_get_candidates(tp_engine *e, int beam, tp_candidate *out, int cap, int *n_total);
 
+/* The same result without a host wait (Sec. 2.3: the detections handed to the
+ * event-detection stage, Table 1's device-to-host copy reduced to the
+ * compacted list): enqueues on the beam's stream, after its detection, a
+ * kernel that writes the number found to *n_total and the first
+ * min(n_total, cand_capacity, cap) records, in the order of
+ * tp_get_candidates, to `out`, and the beam's status word (0, TP_ETIMEOUT or
+ * TP_EBOUNDS, as tp_get_candidates would report it) to *status (may be NULL),
+ * clearing it.  `out`, `n_total` and `status` must be memory the device can
+ * write -- page-locked host memory (cudaHostAlloc / cudaHostRegister) or
+ * device memory -- aligned to 8, 8 and 4 bytes; they hold the results once
+ * the stream has passed that point (an event, tp_sync), and the caller keeps
+ * them until then.  The beam can take its next block at once: the copy runs
+ * before the next block's kernels on the same stream.  Errors: TP_EINVAL
+ * (pageable or misaligned buffers, cap < 0), TP_ENOTREADY (no detection
+ * issued). */
+int tp_export_candidates(tp_engine *e, int beam, tp_candidate *out, int cap, unsigned long long *n_total,
+                         int *status);
+
 /* ---- inspection (tests, debugging) -------------------------------------------- */
 
 /* Window length, number of outputs, stream index of window sample 0 and the

@@ -57,6 +57,7 @@ EXPORTS = (
     "tp_get_batch_times", "tp_engine_set_wait_limit", "tp_plan_set_running_stats", "tp_engine_set_batch_grid",
     "tp_beam_export", "tp_beam_import", "tp_engine_set_tuning_cache", "tp_engine_set_canaries",
     "tp_engine_check_canaries", "tp_debug_bounds", "tp_debug_limit_staged", "tp_push_inplace",
+    "tp_export_candidates",
 )
 
 
@@ -121,6 +122,7 @@ _SIGS = {
     "tp_dedisperse": (_i, [_vp, _i]),
     "tp_detect": (_i, [_vp, _i]),
     "tp_get_candidates": (_i, [_vp, _i, _vp, _i, _vp]),
+    "tp_export_candidates": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "tp_beam_info": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "tp_get_series": (_i, [_vp, _i, _vp, _sz, _i]),
     "tp_get_bandpass": (_i, [_vp, _i, _vp, _vp, _i]),
@@ -364,6 +366,17 @@ def tp_get_candidates(e, beam, cap):
     if rc < 0 and rc not in (TP_ETRUNC, TP_EOVERFLOW):
         _check(rc)
     return out[:min(n.value, int(cap))], n.value, rc
+
+
+def tp_export_candidates(e, beam, out, cap, n_total, status=None):
+    """Enqueue the stream-ordered export of the beam's candidates into
+    ``out`` (cap records, CAND_DTYPE layout), the count into ``n_total`` (one
+    uint64) and the status word into ``status`` (one int32, or None): page-
+    locked host or device buffers, e.g. torch tensors made with
+    pin_memory=True; they hold the results once the stream has passed the
+    export."""
+    _check(lib().tp_export_candidates(e, beam, _addr(out) if cap else None, int(cap), _addr(n_total),
+                                      _addr(status) if status is not None else None))
 
 
 def tp_beam_info(e, beam):

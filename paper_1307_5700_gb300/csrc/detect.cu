@@ -596,6 +596,30 @@ __global__ void __launch_bounds__(kThreads) detect_write(DetectArgs a) {
   }
 }
 
+// Stream-ordered export of a beam's candidate list: the count found and the
+// first min(found, beam capacity, cap) records, copied as 8-byte words by a
+// grid-stride loop into memory the device can write (page-locked host memory
+// or device memory); the beam's status word goes along with them and is
+// cleared for the next block.
+__global__ void __launch_bounds__(kThreads) export_candidates_kernel(const tp_candidate* __restrict__ cand,
+                                                                    const unsigned long long* n_total, int beam_cap,
+                                                                    int* status, tp_candidate* out, int cap,
+                                                                    unsigned long long* out_count, int* out_status) {
+  static_assert(sizeof(tp_candidate) == 24, "three 8-byte words per record");
+  const unsigned long long tot = *n_total;
+  const unsigned long long kept = tot < (unsigned long long)beam_cap ? tot : (unsigned long long)beam_cap;
+  const int64_t n = (int64_t)(kept < (unsigned long long)cap ? kept : (unsigned long long)cap);
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(cand);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(out);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *out_count = tot;
+    const int st = atomicExch(status, 0);
+    if (out_status) *out_status = st;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s) {
@@ -615,6 +639,14 @@ cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s) {
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   detect_write<<<grid, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_candidates(const tp_candidate* cand, const unsigned long long* n_total, int beam_cap,
+                                     int* status, tp_candidate* out, int cap, unsigned long long* out_count,
+                                     int* out_status, int grid, cudaStream_t s) {
+  export_candidates_kernel<<<(unsigned)(grid > 0 ? grid : 1), kThreads, 0, s>>>(cand, n_total, beam_cap, status, out,
+                                                                               cap, out_count, out_status);
   return cudaGetLastError();
 }
 

@@ -1659,6 +1659,43 @@ int tp_get_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, int* n
 
 namespace {
 
+// Memory the device may write: page-locked (or registered) host memory,
+// device memory, managed memory.
+bool device_writable(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+int tp_export_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, unsigned long long* n_total, int* status) {
+  TP_NVTX_RANGE();
+  if (!e) return set_error(TP_EINVAL, "engine is NULL");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  Beam* b = get_beam(e, beam);
+  if (!b) return set_error(TP_EINVAL, "no beam %d", beam);
+  if (b->state != kDetected) return set_error(TP_ENOTREADY, "beam %d: detection not issued", beam);
+  if (cap < 0 || !n_total || (cap > 0 && !out)) return set_error(TP_EINVAL, "bad output buffers");
+  if ((reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(n_total)) % 8 != 0 ||
+      reinterpret_cast<uintptr_t>(status) % 4 != 0)
+    return set_error(TP_EINVAL, "output buffers must be aligned (records and count to 8 bytes, status to 4)");
+  DeviceGuard g(e->device);
+  if ((cap > 0 && !device_writable(out)) || !device_writable(n_total) || (status && !device_writable(status)))
+    return set_error(TP_EINVAL, "outputs must be page-locked host memory or device memory");
+  int dev_sms = 0;
+  TP_CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, e->device));
+  TP_CUDA_TRY(launch_export_candidates(b->cand, b->n_total, b->cap, b->status, out, cap, n_total, status, 2 * dev_sms,
+                                       beam_stream(e, b)));
+  e->launches += 1;
+  return TP_OK;
+}
+
+namespace {
+
 // Saved stream state of a beam (tp_beam_export / tp_beam_import): this
 // header, then the overlap tail [nchan][max_delay] in the sample format, then
 // (running statistics) the running means and variances, nchan doubles each.

@@ -1232,6 +1232,123 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile(RfiArgs a, 
   }
 }
 
+// A3 + A4 for 8-bit data under the same conditions (W a multiple of 32,
+// channels' parameters in shared memory): the exact integer spectrum sums of
+// spectrum_substitute_kernel (sum of x over the unflagged channels against
+// the sum of their offsets: N S_c with block statistics, b_c otherwise), then
+// x~ (flagged -> b_c) widened to 16-bit integers; eight channels' 4-byte loads
+// in flight per thread.
+__global__ void __launch_bounds__(kThreads) spectrum_substitute_tile_u8(RfiArgs a, void* __restrict__ yv,
+                                                                        int64_t ypitch) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  long long* s_off = reinterpret_cast<long long*>(s_dyn);          // [nchan] S_c or b_c
+  int* s_b = reinterpret_cast<int*>(s_off + a.nchan);              // [nchan] b_c
+  uint8_t* s_cf = reinterpret_cast<uint8_t*>(s_b + a.nchan);       // [nchan] chunk flag
+  __shared__ long long s_i[32][33];
+  __shared__ unsigned s_word;
+  const int tid = threadIdx.x;
+  const int g = tid >> 3, q = tid & 7;
+  const int64_t t0 = (int64_t)blockIdx.x * 32;
+  const int64_t tq = t0 + 4 * q;
+  const int64_t left = a.nsamp - tq;
+  const int valid = left >= 4 ? 4 : (left > 0 ? (int)left : 0);
+  const int k = (int)(t0 / a.W);
+  const bool ext = a.stats_mode == TP_STATS_EXTERNAL || a.fit || a.run;
+  for (int c = tid; c < a.nchan; c += kThreads) {
+    s_b[c] = a.bint[c];
+    s_off[c] = ext ? (long long)a.bint[c] : a.S[c];
+    s_cf[c] = (uint8_t)(a.chan_nflag[c] != 0 && a.chunk_flag[(int64_t)c * a.nchunk + k]);
+  }
+  __syncthreads();
+  const unsigned char* xb = static_cast<const unsigned char*>(a.x);
+  // the 4 samples of channel c at tq (those past the window read as 0)
+  auto load4 = [&](int c) -> unsigned {
+    if (valid == 4) return __ldg(reinterpret_cast<const unsigned*>(xb + (int64_t)c * a.pitch + tq));
+    unsigned w = 0u;
+    for (int r = 0; r < valid; ++r) w |= (unsigned)__ldg(xb + (int64_t)c * a.pitch + tq + r) << (8 * r);
+    return w;
+  };
+
+  if (a.enable_spectrum) {
+    int sx[4] = {0, 0, 0, 0};
+    long long sS[4] = {0, 0, 0, 0};
+    for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
+      unsigned w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + 32 * u;
+        w[u] = c < a.nchan && in_bounds((int64_t)c * a.pitch + tq, valid, a.x_elems, a.status) ? load4(c) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + 32 * u;
+        if (c >= a.nchan) break;
+        if (s_cf[c]) continue;
+        const long long off = s_off[c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (r < valid) {
+            sx[r] += (int)((w[u] >> (8 * r)) & 0xffu);
+            sS[r] += off;
+          }
+      }
+    }
+    const long long N = a.nsamp;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) s_i[g][4 * q + r] = ext ? (long long)sx[r] - sS[r] : N * (long long)sx[r] - sS[r];
+    __syncthreads();
+    if (tid < 32) {
+      bool flag = false;
+      if (t0 + tid < a.nsamp) {
+        long long m = 0;
+        for (int w = 0; w < 32; ++w) m += s_i[w][tid];
+        flag = (double)m > a.spec_thr[k];
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, flag);
+      if (tid == 0) {
+        s_word = bits;
+        if (t0 < a.nsamp) a.spec_bits[t0 >> 5] = bits;
+        if (bits) atomicAdd(a.spec_nflag, __popc(bits));
+      }
+    }
+  } else if (tid == 0) {
+    s_word = 0u;
+    if (t0 < a.nsamp) a.spec_bits[t0 >> 5] = 0u;
+  }
+  __syncthreads();
+  const unsigned word = s_word;
+  bool sflag[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) sflag[r] = (word >> (4 * q + r)) & 1u;
+  if (valid == 0) return;
+  const uint64_t drop = l2_policy(false);
+  for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
+    unsigned w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + 32 * u;
+      w[u] = c < a.nchan && in_bounds((int64_t)c * a.pitch + tq, valid, a.x_elems, a.status) ? load4(c) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + 32 * u;
+      if (c >= a.nchan) break;
+      if (!in_bounds((int64_t)c * ypitch + tq, valid, a.y_elems, a.status)) continue;
+      const bool cfl = s_cf[c] != 0;
+      const unsigned b = (unsigned)s_b[c];
+      unsigned h[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) h[r] = (sflag[r] || cfl) ? b : ((w[u] >> (8 * r)) & 0xffu);
+      unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
+      if (valid == 4) {
+        st_hint8(dst, make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16)), drop);
+      } else {
+        for (int r = 0; r < valid; ++r) dst[r] = (unsigned short)h[r];
+      }
+    }
+  }
+}
+
 // ---- fitted bandpass (Sec. 2.2.1 "Bandpass Correction") ---------------------------
 //
 // bandpass_fit_kernel (one CTA): local excess of each block mean over its
@@ -1595,6 +1712,16 @@ cudaError_t launch_rfi(const RfiArgs& a, void* chunk_sums, void* y, int64_t ypit
   if (kernels) *kernels += nk;
   spectrum_threshold_kernel<<<(unsigned)((a.nchunk + kWarps - 1) / kWarps), kThreads, 0, s>>>(a);
   const unsigned blocks = (unsigned)((a.nsamp + 31) / 32);
+  if (a.dtype == TP_U8 && a.W % 32 == 0 && a.nchan <= kTileMaxChannels) {
+    const size_t sm = (size_t)a.nchan * (sizeof(long long) + sizeof(int) + 1);
+    if (sm > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(spectrum_substitute_tile_u8,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    spectrum_substitute_tile_u8<<<blocks, kThreads, sm, s>>>(a, y, ypitch);
+    return cudaGetLastError();
+  }
   if (a.dtype != TP_U8 && a.W % 32 == 0 && a.nchan <= kTileMaxChannels) {
     const size_t sm = (size_t)a.nchan * (sizeof(float2) + sizeof(unsigned short) + 1);
     if (a.dtype == TP_C16) return launch_tile<TP_C16>(a, y, ypitch, blocks, sm, s);

@@ -281,6 +281,9 @@ cudaError_t launch_channel_stats(const RfiArgs& a, void* chunk_sums, cudaStream_
 cudaError_t launch_dedisperse(int shape, int dtype, const BatchArgs& ba, int ctas, cudaStream_t s,
                               int grid_limit = -1);
 cudaError_t launch_detect(const DetectArgs& a, cudaStream_t s);
+cudaError_t launch_export_candidates(const tp_candidate* cand, const unsigned long long* n_total, int beam_cap,
+                                     int* status, tp_candidate* out, int cap, unsigned long long* out_count,
+                                     int* out_status, int grid, cudaStream_t s);
 // Device-to-device copy of nrows rows of row_bytes bytes (pitched); a
 // 16-byte vector kernel when every address, pitch and the row length are
 // multiples of 16 bytes, else cudaMemcpy2DAsync.
