@@ -49,7 +49,7 @@
 // interleaved, 32-bit adds only), and branches back to one indexed dispatch.
 // Each (d, t) adds its channels in index order (FP32, or exact integers).
 // Every mbarrier wait is bounded; a wait for staged data or a free stage
-// buffer gives up after DedispArgs::wait_tries attempts, records TP_ETIMEOUT
+// buffer gives up after BatchArgs::wait_tries attempts, records TP_ETIMEOUT
 // in the beam's status word, and the CTA leaves after letting its own copies
 // land (that drain always allows kDefaultWaitTries attempts).
 //
@@ -408,7 +408,7 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
       const int buf = i % STAGES;
       if (i >= STAGES) {
         bool got = false;
-        if (lane == 0) got = mbar_wait_bounded(&empty[buf], (unsigned)(((i / STAGES) - 1) & 1), a.wait_tries);
+        if (lane == 0) got = mbar_wait_bounded(&empty[buf], (unsigned)(((i / STAGES) - 1) & 1), ba.wait_tries);
         if (!__shfl_sync(0xffffffffu, got, 0)) {
           ok = false;
           break;
@@ -545,7 +545,7 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
     const int pbuf = j % STAGES;
     if (j >= STAGES) {
       bool got = false;
-      if (lane == 0) got = mbar_wait_bounded(&empty[pbuf], (unsigned)(((j / STAGES) - 1) & 1), a.wait_tries);
+      if (lane == 0) got = mbar_wait_bounded(&empty[pbuf], (unsigned)(((j / STAGES) - 1) & 1), ba.wait_tries);
       if (!__shfl_sync(0xffffffffu, got, 0)) return false;
     }
     issue_stage(j, myslot);
@@ -582,7 +582,7 @@ __device__ __forceinline__ bool dedisperse_item(const BatchArgs& ba, int item) {
         return false;
       }
     }
-    if (!mbar_wait_bounded(&full[buf], (unsigned)((i / STAGES) & 1), a.wait_tries)) {
+    if (!mbar_wait_bounded(&full[buf], (unsigned)((i / STAGES) & 1), ba.wait_tries)) {
       if constexpr (ROT)
         bail();
       else if (lane == 0)

@@ -654,7 +654,6 @@ DedispArgs dedisp_args(const tp_plan* p, Beam* b) {
   da.dpitch = b->dpitch;
   da.row_part = b->row_part;
   da.status = b->status;
-  da.wait_tries = p->e->wait_tries;
   da.y_bytes = (int64_t)p->nchan * b->ypitch * staged_bytes_alloc(p->dtype);
   if (b->dbg_y_bytes >= 0 && b->dbg_y_bytes < da.y_bytes) da.y_bytes = b->dbg_y_bytes;
   da.d_elems = (int64_t)p->ndm * b->dpitch;
@@ -679,7 +678,7 @@ int launch_single(tp_engine* e, Beam* b, const DedispArgs& da, int shape, cudaSt
   }
   BatchArgs ba{static_cast<const DedispArgs*>(b->d_args),
                reinterpret_cast<const int*>(static_cast<unsigned char*>(b->d_args) + sizeof(DedispArgs)), 1,
-               nullptr};
+               nullptr, e->wait_tries};
   TP_CUDA_TRY(launch_dedisperse(shape, da.dtype, ba, ctas, s));
   e->launches += 1;
   return TP_OK;
@@ -876,7 +875,7 @@ int issue_batch(tp_engine* e, BatchPlan& bp, void* d_args, bool detect) {
     TP_CUDA_TRY(cudaEventRecord(ev.first, s));
   }
   for (auto& g : bp.groups) {
-    BatchArgs ba{dargs + g.first, dcta + coff, g.second, e->d_items + gi++};
+    BatchArgs ba{dargs + g.first, dcta + coff, g.second, e->d_items + gi++, e->wait_tries};
     const int ctas = bp.cta[coff + g.second];
     const Beam* b0 = bp.beams[g.first];
     TP_CUDA_TRY(launch_dedisperse(b0->plan->shape, b0->plan->dtype, ba, ctas, s, e->batch_grid));
@@ -2281,7 +2280,7 @@ int tp_autotune_batch(tp_engine* e, int reps, int* best, float* ms, int n) {
       BatchArgs ba{static_cast<const DedispArgs*>(e->d_batch),
                    reinterpret_cast<const int*>(static_cast<unsigned char*>(e->d_batch) +
                                                 args.size() * sizeof(DedispArgs)),
-                   (int)args.size(), e->d_items};
+                   (int)args.size(), e->d_items, e->wait_tries};
       const int dtype = plans[k]->dtype;
       TP_CUDA_TRY(cudaMemsetAsync(e->d_items, 0, sizeof(int), s));
       TP_CUDA_TRY(launch_dedisperse(sh, dtype, ba, cta.back(), s, e->batch_grid));  // warm-up

@@ -148,7 +148,6 @@ struct DedispArgs {
   int64_t dpitch;
   void* row_part;         // [ndm][ntt] (float: double2 {sum, sumsq}; int: longlong2)
   int* status;            // device status word (TP_ETIMEOUT on a wait that gave up)
-  long long wait_tries;   // attempts of a wait for staged data or a free stage buffer
   // extents for the debug build's bounds checks
   int64_t y_bytes;        // bytes of the staged series
   int64_t d_elems;        // elements of D
@@ -170,6 +169,8 @@ struct BatchArgs {
   int nbeams;
   int* next_item;           // device counter, 0 at launch: CTAs past their first item take
                             // gridDim.x + atomicAdd(next_item, 1); NULL: item + gridDim.x
+  long long wait_tries;     // attempts of a wait for staged data or a free stage buffer (a kernel
+                            // parameter: read from the constant bank, no load in the wait path)
 };
 
 // Register-tile shapes of the dedispersion kernel.
