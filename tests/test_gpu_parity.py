@@ -217,14 +217,18 @@ def test_ragged_shapes(dtype):
     check_block(g, o, x, dtype, od, rfi, 3.5)
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16", "u8"])
-def test_every_shape_elementwise(dtype):
+@pytest.mark.parametrize("dtype,step", [("f32", 0.2), ("f16", 0.2), ("bf16", 0.2), ("u8", 0.2),
+                                        ("f32", 0.18), ("f16", 0.18)])
+def test_every_shape_elementwise(dtype, step):
     """Every kernel shape the plan admits, element by element against the
-    oracle: 256 channels over 398-418 MHz, 62 DM trials of step 0.2 (the last
-    group of four trials is incomplete), a window that is not a multiple of
-    any tile and spans several DM tiles and time tiles."""
+    oracle: 256 channels over 398-418 MHz, 62 DM trials (the last group of
+    four trials is incomplete), a window that is not a multiple of any tile
+    and spans several DM tiles and time tiles.  At DM step 0.2 the last
+    group's single delay step (10 samples in the lowest channel) exceeds the
+    FP32 DM quads' bound of 9, so those shapes are not admitted; step 0.18
+    admits them."""
     nchan, nsamp = 256, 7777
-    dms = np.arange(62) * 0.2
+    dms = np.arange(62) * step
     f_lo, bw, ts = 398.0, 20.0, 51.2e-6
     od, dmax = O.delay_table(nchan, f_lo, bw, ts, dms)
     xf = synth.noise(nchan, nsamp, 7101, mean=128.0 if dtype == "u8" else 0.0, std=16.0 if dtype == "u8" else 1.0)
@@ -240,6 +244,8 @@ def test_every_shape_elementwise(dtype):
         _, feasible = tp.tp_plan_shapes(g.plan)
         shapes = [int(s) for s in np.nonzero(feasible)[0]]
         assert len(shapes) >= 2
+        if step == 0.18 and dtype == "f32":
+            assert {53, 55, 46, 33} <= set(shapes)  # the FP32 quad families
         for sh in shapes:
             tp.tp_plan_set_shape(g.plan, sh)
             tp.tp_beam_rewind(g.e, g.beam)
