@@ -1270,8 +1270,13 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile_u8(RfiArgs 
   };
 
   if (a.enable_spectrum) {
-    int sx[4] = {0, 0, 0, 0};
-    long long sS[4] = {0, 0, 0, 0};
+    // the thread's four samples summed as packed 16-bit lanes (samples 0, 2 in
+    // plo, 1, 3 in phi): a lane takes at most kTileMaxChannels / 32 = 128
+    // values below 256, so none carries into the next; samples past the
+    // window load as 0.  The offsets of an unflagged channel are the same for
+    // the four samples: summed once per channel.
+    unsigned plo = 0u, phi = 0u;
+    long long so = 0;
     for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
       unsigned w[8];
 #pragma unroll
@@ -1284,15 +1289,15 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile_u8(RfiArgs 
         const int c = c0 + 32 * u;
         if (c >= a.nchan) break;
         if (s_cf[c]) continue;
-        const long long off = s_off[c];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (r < valid) {
-            sx[r] += (int)((w[u] >> (8 * r)) & 0xffu);
-            sS[r] += off;
-          }
+        plo += w[u] & 0x00ff00ffu;
+        phi += (w[u] >> 8) & 0x00ff00ffu;
+        so += s_off[c];
       }
     }
+    const int sx[4] = {(int)(plo & 0xffffu), (int)(phi & 0xffffu), (int)(plo >> 16), (int)(phi >> 16)};
+    long long sS[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) sS[r] = r < valid ? so : 0;
     const long long N = a.nsamp;
 #pragma unroll
     for (int r = 0; r < 4; ++r) s_i[g][4 * q + r] = ext ? (long long)sx[r] - sS[r] : N * (long long)sx[r] - sS[r];
@@ -1320,6 +1325,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile_u8(RfiArgs 
   bool sflag[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) sflag[r] = (word >> (4 * q + r)) & 1u;
+  const bool sany = ((word >> (4 * q)) & 0xfu) != 0u;
   if (valid == 0) return;
   const uint64_t drop = l2_policy(false);
   for (int c0 = g; c0 < a.nchan; c0 += 32 * 8) {
@@ -1336,10 +1342,16 @@ __global__ void __launch_bounds__(kThreads) spectrum_substitute_tile_u8(RfiArgs 
       if (!in_bounds((int64_t)c * ypitch + tq, valid, a.y_elems, a.status)) continue;
       const bool cfl = s_cf[c] != 0;
       const unsigned b = (unsigned)s_b[c];
+      unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
+      if (valid == 4 && !cfl && !sany) {
+        // no sample of the quad is flagged: widen the four bytes to 16-bit
+        // lanes with two byte permutes
+        st_hint8(dst, make_uint2(__byte_perm(w[u], 0u, 0x4140), __byte_perm(w[u], 0u, 0x4342)), drop);
+        continue;
+      }
       unsigned h[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) h[r] = (sflag[r] || cfl) ? b : ((w[u] >> (8 * r)) & 0xffu);
-      unsigned short* dst = static_cast<unsigned short*>(yv) + (int64_t)c * ypitch + tq;
       if (valid == 4) {
         st_hint8(dst, make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16)), drop);
       } else {
