@@ -366,7 +366,7 @@ int tp_get_candidates(tp_engine *e, int beam, tp_candidate *out, int cap, int *n
  * TP_EBOUNDS, as tp_get_candidates would report it) to *status (may be NULL),
  * clearing it.  `out`, `n_total` and `status` must be memory the device can
  * write -- page-locked host memory (cudaHostAlloc / cudaHostRegister) or
- * device memory -- aligned to 8, 8 and 4 bytes; they hold the results once
+ * the engine device's memory -- aligned to 8, 8 and 4 bytes; they hold the results once
  * the stream has passed that point (an event, tp_sync), and the caller keeps
  * them until then.  The beam can take its next block at once: the copy runs
  * before the next block's kernels on the same stream.  Errors: TP_EINVAL

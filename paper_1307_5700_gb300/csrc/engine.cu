@@ -1658,15 +1658,16 @@ int tp_get_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, int* n
 
 namespace {
 
-// Memory the device may write: page-locked (or registered) host memory,
-// device memory, managed memory.
-bool device_writable(const void* p) {
+// Memory device `dev` may write: page-locked (or registered) host memory,
+// its own device memory, managed memory.
+bool device_writable(const void* p, int dev) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -1683,8 +1684,9 @@ int tp_export_candidates(tp_engine* e, int beam, tp_candidate* out, int cap, uns
       reinterpret_cast<uintptr_t>(status) % 4 != 0)
     return set_error(TP_EINVAL, "output buffers must be aligned (records and count to 8 bytes, status to 4)");
   DeviceGuard g(e->device);
-  if ((cap > 0 && !device_writable(out)) || !device_writable(n_total) || (status && !device_writable(status)))
-    return set_error(TP_EINVAL, "outputs must be page-locked host memory or device memory");
+  if ((cap > 0 && !device_writable(out, e->device)) || !device_writable(n_total, e->device) ||
+      (status && !device_writable(status, e->device)))
+    return set_error(TP_EINVAL, "outputs must be page-locked host memory or the engine device's memory");
   int dev_sms = 0;
   TP_CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, e->device));
   TP_CUDA_TRY(launch_export_candidates(b->cand, b->n_total, b->cap, b->status, out, cap, n_total, status, 2 * dev_sms,
