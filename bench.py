@@ -46,11 +46,12 @@ PAPER_DERIVED = 6.5e7  # DM-trial.samples/s per GPU derived from the paper's Tab
 # dram__bytes_write.sum) on the launch the benchmark times; shapes without
 # such a capture report null.
 TRAFFIC_BY_SHAPE = {("f32", 33): 584.843264e6 + 331.993600e6, ("f32", 46): 175.55649461716e9 * 5.406816e-3,
-                    ("f32", 55): 192.00875257012e9 * 5.089248e-3, ("f32", 53): 652.427520e6 + 315.692032e6,
-                    ("u8", 57): 291.825408e6 + 305.486592e6}
+                    ("f32", 55): 192.00875257012e9 * 5.089248e-3, ("f32", 53): 650.720768e6 + 315.274240e6,
+                    ("u8", 57): 291.825408e6 + 305.486592e6, ("u8", 43): 284.709888e6 + 299.847936e6}
 # shared-memory data-path utilisation (l1tex__data_pipe_lsu_wavefronts as a
 # fraction of peak) in the same captures
-SMEM_FRAC_BY_SHAPE = {("f32", 46): 0.6806, ("f32", 55): 0.5959, ("f32", 53): 0.7342, ("u8", 57): 0.3859}
+SMEM_FRAC_BY_SHAPE = {("f32", 46): 0.6806, ("f32", 55): 0.5959, ("f32", 53): 0.7222, ("u8", 57): 0.3859,
+                      ("u8", 43): 0.4080}
 METRIC = "DM-trial*samples/s per GB300 (real-time beams sustained, p99 block latency alongside)"
 WORKLOAD = "stream: 1 beam, 1024 ch 398-418 MHz, 51.2 us, 640 DMs 0-127.8 step 0.2, FP32, 2^17-sample blocks"
 
