@@ -507,8 +507,9 @@ int tp_get_batch_times(tp_engine *e, double *ms, int64_t *count);
  * leaves; before leaving it always lets its own copies in flight land.
  * tries < 0 restores the default (2^24); 0 makes every such wait give up at
  * once, which tests use to exercise the timeout path without a fault or a
- * hang.  Applies to launches issued after the call (cached batch graphs are
- * dropped).  Errors: TP_EINVAL for a NULL engine. */
+ * hang; values above 2^31 - 1 count as 2^31 - 1.  Applies to launches issued
+ * after the call (cached batch graphs are dropped).  Errors: TP_EINVAL for a
+ * NULL engine. */
 int tp_engine_set_wait_limit(tp_engine *e, long long tries);
 
 /* Grid of the batched dedispersion launch (tp_run_ready, tp_dedisperse with

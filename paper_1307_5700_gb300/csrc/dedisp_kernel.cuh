@@ -103,8 +103,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
+// At most `tries` (< 2^31) attempts; the first, which usually succeeds, ahead
+// of the loop.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long tries = kSpinLimit) {
-  for (long long spin = 0; spin < tries; ++spin)
+  const int n = (int)tries;
+  if (n <= 0) return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  for (int spin = 1; spin < n; ++spin)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

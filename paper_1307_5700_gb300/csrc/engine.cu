@@ -1949,7 +1949,7 @@ int tp_engine_set_wait_limit(tp_engine* e, long long tries) {
   if (!e) return set_error(TP_EINVAL, "engine is NULL");
   std::lock_guard<std::recursive_mutex> lk(e->mu);
   DeviceGuard g(e->device);
-  e->wait_tries = tries < 0 ? kDefaultWaitTries : tries;
+  e->wait_tries = tries < 0 ? kDefaultWaitTries : (tries > 0x7fffffffLL ? 0x7fffffffLL : tries);
   // graphs captured earlier hold the old limit in their arguments
   TP_CUDA_TRY(cudaStreamSynchronize(e->stream));
   for (auto& kv : e->graphs) {
