@@ -779,6 +779,18 @@ def run_stream(args, dtype, steps, warmup, e2e_on, peaks=None):
                   torch.zeros(1, dtype=torch.int64, pin_memory=True),
                   torch.zeros(1, dtype=torch.int32, pin_memory=True)) for _ in range(2)]
         done = [torch.cuda.Event() for _ in range(2)]
+        # the machine's host -> device copy rate for one block (pinned, 1D; the
+        # leg below is bound by it when it exceeds the block's device time)
+        probe = torch.empty(pinned[0].numel(), dtype=pinned[0].dtype, device=dev)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        probe.copy_(pinned[0].view(-1), non_blocking=True)
+        c0.record(stream)
+        for _ in range(3):
+            probe.copy_(pinned[0].view(-1), non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        h2d_gbps = 3 * host[0].nbytes / (c0.elapsed_time(c1) / 1e3) / 1e9
+        del probe
         barrier(world)
         torch.cuda.synchronize(dev)
         # double-buffered ingest: block k + 1's host -> device copy runs while
@@ -811,7 +823,8 @@ def run_stream(args, dtype, steps, warmup, e2e_on, peaks=None):
         e2e = {"value": len(DMS) * BLOCK * ne2e * world / w, "unit": "DM-trial*samples/s",
                "h2d_bytes_per_step": int(host[0].nbytes),
                "d2h_bytes_per_step": int(8 + 24 * float(np.mean(ncand))), "steps": ne2e,
-               "candidates_per_block": float(np.mean(ncand))}
+               "candidates_per_block": float(np.mean(ncand)), "h2d_GBps_measured": h2d_gbps,
+               "h2d_ms_per_block": host[0].nbytes / (h2d_gbps * 1e9) * 1e3}
 
     tp.tp_beam_close(e, beam)
     tp.tp_plan_destroy(plan)
