@@ -791,6 +791,7 @@ def run_stream(args, dtype, steps, warmup, e2e_on, peaks=None):
         torch.cuda.synchronize(dev)
         h2d_gbps = 3 * host[0].nbytes / (c0.elapsed_time(c1) / 1e3) / 1e9
         del probe
+        tp.tp_set_profiling(e, True)  # per-stage device times of the leg's blocks
         barrier(world)
         torch.cuda.synchronize(dev)
         # double-buffered ingest: block k + 1's host -> device copy runs while
@@ -820,11 +821,16 @@ def run_stream(args, dtype, steps, warmup, e2e_on, peaks=None):
         read(ne2e - 1)
         torch.cuda.synchronize(dev)
         w = max_over_ranks(time.perf_counter() - w0, world, dev)
+        e2e_stage_ms, e2e_nstage = tp.tp_get_stage_times(e, beam)
+        tp.tp_set_profiling(e, False)
         e2e = {"value": len(DMS) * BLOCK * ne2e * world / w, "unit": "DM-trial*samples/s",
                "h2d_bytes_per_step": int(host[0].nbytes),
                "d2h_bytes_per_step": int(8 + 24 * float(np.mean(ncand))), "steps": ne2e,
                "candidates_per_block": float(np.mean(ncand)), "h2d_GBps_measured": h2d_gbps,
-               "h2d_ms_per_block": host[0].nbytes / (h2d_gbps * 1e9) * 1e3}
+               "h2d_ms_per_block": host[0].nbytes / (h2d_gbps * 1e9) * 1e3,
+               "wall_ms_per_block": w / ne2e * 1e3,
+               "stage_ms_per_block": {n: e2e_stage_ms[i] / max(e2e_nstage, 1)
+                                      for i, n in enumerate(("push", "a1_a3", "a4_a5", "a6_a7"))}}
 
     tp.tp_beam_close(e, beam)
     tp.tp_plan_destroy(plan)

@@ -924,7 +924,7 @@ void tp_rfi_defaults(tp_rfi_params* p) {
   p->stats_mode = TP_STATS_BLOCK;
 }
 
-int tp_version(void) { return 100; }
+int tp_version(void) { return 200; }
 
 const char* tp_last_error_string(void) { return tp::last_error_cstr(); }
 
