@@ -12,8 +12,13 @@
 // tau_c sigma_c sqrt(n_k).
 // Kernel dilate: flag = own exceedance | time neighbours (| channel
 // neighbours); per-channel flagged-chunk counts.  Kernel spectrum_threshold
-// (one CTA per 256 samples): the sum over channels of the corrected samples of
-// unflagged chunks, compared with tau_s sqrt(sum_c sigma_c^2).
+// (a warp per chunk): tau_s sqrt(sum of sigma_c^2 over the channels whose
+// chunk is not flagged).  A3 + A4 (one CTA per 32 samples x all channels):
+// the sum over channels of the corrected samples of unflagged chunks,
+// compared with that threshold, then the staged series with flagged samples
+// replaced -- spectrum_substitute_tile / spectrum_substitute_tile_u8 when W_c
+// is a multiple of 32 and the channels' parameters fit shared memory,
+// spectrum_substitute_kernel otherwise.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
