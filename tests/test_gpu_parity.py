@@ -272,6 +272,29 @@ def _voltage_block(nchan, nsamp, od, seed):
     return synth.complex_voltage(env, seed, sigma=30.0)
 
 
+def test_u8_extreme_values():
+    """8-bit samples at the ends of their range over 4096 channels, the most
+    the shared-parameter staging kernel takes (its packed 16-bit lanes then sum
+    128 values of up to 255 each): mostly 255 with a tenth of the samples 0,
+    a block of zeros, channels held at 255 throughout (sigma_c = 0) and
+    whole spectra at 255 (flagged, the last one in the window's ragged last
+    32-sample tile); the exact statistics, masks, series and candidates
+    equal the oracle's."""
+    nchan, nsamp = 4096, 2600
+    dms = np.arange(6) * 1.0
+    f_lo, bw, ts = 1200.0, 300.0, 64e-6
+    g = synth.rng(7301)
+    x = np.full((nchan, nsamp), 255, np.uint8)
+    x[g.random((nchan, nsamp)) < 0.1] = 0
+    x[100:140, 1000:1300] = 0
+    x[2000:2010] = 255
+    x[:, [500, 1777, 2599]] = 255  # spectra at the top of the range: flagged
+    rfi = O.RfiParams()
+    res, o, od = run_both(x, "u8", nchan, f_lo, bw, ts, dms, rfi, nsigma=3.0)
+    assert o["spec_flag"].sum() >= 3
+    check_block(res, o, x, "u8", od, rfi, 3.0)
+
+
 def test_power_detection_c16():
     """Complex int16 voltages detected as power on the device, against the
     oracle (float bars: masks identical, D within 1e-5 of the summed
